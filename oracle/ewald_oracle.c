@@ -1,0 +1,331 @@
+/*
+ * Plain FP64 CPU Ewald summation: the oracle that the CUDA path is checked against.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or loads this
+ * file; only the tests, the smoke check and the CPU-baseline leg of the benchmark do.
+ * It shares no code, header, table or constant with the CUDA path.
+ *
+ * What it computes (paper: Sections 3.1-3.2, Eqs. 2-4, Listing 1, Algorithms 1-2):
+ *   N point charges q_j at r_j in a periodic cubic box of side L, Gaussian units
+ *   (Coulomb constant 1).  The splitting parameter is passed as beta (1/length); the
+ *   paper's Gaussian exponent is alpha = beta^2, so erfc(sqrt(alpha) r) = erfc(beta r).
+ *
+ *   E_real  = 1/2 sum_i sum_{j, n: 0 < |r_i - r_j - nL| < r_c}  q_i q_j erfc(beta d)/d
+ *             (Section 3.1.1 and Eq. 4; the 1/2 of Listing 1 counts every pair once)
+ *   F_i^real = sum_{j, n} q_i q_j (d_vec/d^2) [erfc(beta d)/d + 2 beta/sqrt(pi) exp(-beta^2 d^2)]
+ *             with d_vec = r_i - r_j - nL  (Eq. 4, second line)
+ *   S(k)    = sum_j q_j exp(i k.r_j),  k = 2 pi m / L,  m in Z^3  (Section 3.1.2; the paper's
+ *             rho_hat_k of Eq. 3 is conj(S(k)) without the Gaussian factor)
+ *   E_recip = 1/2 sum_{k != 0, |m| <= kmax} g(k) |S(k)|^2,
+ *             g(k) = 4 pi exp(-k^2 / (4 beta^2)) / (V k^2)   (C_k of Eq. 3, V = L^3)
+ *           = sum_{k in K_half} g(k) |S(k)|^2  over the half space (see kset_half)
+ *   F_i^recip = q_i sum_{k in K_half} 2 g(k) k Im(exp(i k.r_i) conj S(k))   (Algorithm 2,
+ *             the -i k C_k A q rho_hat update, with k and -k paired so the result is real)
+ *   phi_i^recip = sum_{k in K_half} 2 g(k) Re(exp(i k.r_i) conj S(k))       (Algorithm 2, u)
+ *   E_self  = -beta/sqrt(pi) sum_i q_i^2    (Section 3.2.2: computed once; formula not
+ *             printed in the paper, taken as the standard Gaussian self-interaction)
+ *
+ * The k = 0 term is dropped (neutral systems, footnote of Section 3.1.2), which is the
+ * conducting ("tin-foil") boundary condition.  The reciprocal cutoff is the sphere
+ * |m|^2 <= kmax^2 (Algorithm 1 loops over |k| < k_c; this library states the cutoff as an
+ * integer radius kmax, inclusive).
+ *
+ * Every structure factor is evaluated with direct cos/sin per (k, particle): no phase
+ * recurrence, no matrix product.  The only parallelism is OpenMP over independent outputs
+ * (one k, or one particle, per iteration); every sum over an index runs in index order, and
+ * global energies are summed serially after the parallel loop.
+ *
+ * Parity pins (all in tests/test_oracle.py): Madelung constants of rock-salt and CsCl,
+ * invariance of the total energy under beta at converged cutoffs, sum of forces = 0,
+ * central finite differences of the energy, brute-force image sums of tiny neutral cells
+ * (ewo_coulomb_cube), the exactly known S(k) of an unjittered rock-salt lattice, and
+ * lattice-point counts for the k-set.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define EWO_PI 3.14159265358979323846
+
+/* Periodic wrap into [0, L): x - L floor(x / L); a result equal to L (rounding of a tiny
+ * negative x) is mapped to 0. */
+static double wrap1(double x, double L)
+{
+    double w = x - L * floor(x / L);
+    return (w >= L) ? 0.0 : w;
+}
+
+int ewo_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void ewo_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/*
+ * Half-space k set K_half: integer m = (mx, my, mz) != 0 with mx^2 + my^2 + mz^2 <= kmax^2
+ * and (mz > 0) or (mz == 0 and my > 0) or (mz == 0 and my == 0 and mx > 0).
+ * Exactly one of every pair {m, -m} is in the set, so sums over all k != 0 of terms that
+ * are even in k equal twice the sum over K_half (the pairing behind Algorithm 1's
+ * quadrant ordering, Section 4.2).
+ * Order: mz ascending, then my ascending, then mx ascending.
+ * Writes up to `cap` triples into m_out (if non-NULL) and returns the set size.
+ */
+int64_t ewo_kset_half(int kmax, int32_t *m_out, int64_t cap)
+{
+    int64_t count = 0;
+    const int64_t k2max = (int64_t)kmax * kmax;
+    for (int mz = 0; mz <= kmax; ++mz)
+        for (int my = -kmax; my <= kmax; ++my)
+            for (int mx = -kmax; mx <= kmax; ++mx) {
+                int64_t m2 = (int64_t)mx * mx + (int64_t)my * my + (int64_t)mz * mz;
+                if (m2 == 0 || m2 > k2max) continue;
+                int in_half = (mz > 0) || (mz == 0 && my > 0) || (mz == 0 && my == 0 && mx > 0);
+                if (!in_half) continue;
+                if (m_out && count < cap) {
+                    m_out[3 * count + 0] = mx;
+                    m_out[3 * count + 1] = my;
+                    m_out[3 * count + 2] = mz;
+                }
+                ++count;
+            }
+    return count;
+}
+
+/*
+ * Real-space part (Section 3.1.1, Eq. 4, Listing 1) for the target particles `sub`
+ * (all particles when sub == NULL, nsub ignored).
+ *   phi_out[t]  = sum_{j,n} q_j erfc(beta d)/d                    (may be NULL)
+ *   F_out[t]    = q_i sum_{j,n} q_j (d_vec/d^2)[erfc(beta d)/d + 2 beta/sqrt(pi) e^{-beta^2 d^2}]
+ *   *e_real     = 1/2 sum_t q_i phi_i   (summed serially in target order; may be NULL)
+ * Pairs are counted when 0 < d < r_c (strict, as Listing 1's mask).  For r_c <= L/2 only the
+ * nearest image along every axis can lie inside the cutoff, so that image is taken directly;
+ * otherwise every shift n with |n_a| <= ceil(r_c / L) is visited (including the particle's
+ * own images, which add energy but no net force).
+ */
+void ewo_real(int64_t n, const double *pos, const double *q, double L, double beta, double rc,
+              int64_t nsub, const int64_t *sub, double *F_out, double *phi_out, double *e_real)
+{
+    const int64_t nt = sub ? nsub : n;
+    const double rc2 = rc * rc;
+    const double two_beta_rpi = 2.0 * beta / sqrt(EWO_PI);
+    const int min_image = (rc <= 0.5 * L);
+    const int ms = (int)ceil(rc / L);
+    /* phi is needed for the energy even when the caller does not want it */
+    double *phi_tmp = phi_out;
+    if (!phi_tmp && e_real) phi_tmp = (double *)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(double));
+
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        const int64_t i = sub ? sub[t] : t;
+        const double xi = wrap1(pos[3 * i + 0], L);
+        const double yi = wrap1(pos[3 * i + 1], L);
+        const double zi = wrap1(pos[3 * i + 2], L);
+        double fx = 0.0, fy = 0.0, fz = 0.0, phi = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            const double dx0 = xi - wrap1(pos[3 * j + 0], L);
+            const double dy0 = yi - wrap1(pos[3 * j + 1], L);
+            const double dz0 = zi - wrap1(pos[3 * j + 2], L);
+            if (min_image) {
+                if (j == i) continue;
+                const double dx = dx0 - L * round(dx0 / L);
+                const double dy = dy0 - L * round(dy0 / L);
+                const double dz = dz0 - L * round(dz0 / L);
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (!(d2 < rc2)) continue;
+                const double d = sqrt(d2);
+                const double e = erfc(beta * d) / d;
+                const double s = q[j] * (e + two_beta_rpi * exp(-beta * beta * d2)) / d2;
+                phi += q[j] * e;
+                fx += s * dx; fy += s * dy; fz += s * dz;
+            } else {
+                for (int sx = -ms; sx <= ms; ++sx)
+                    for (int sy = -ms; sy <= ms; ++sy)
+                        for (int sz = -ms; sz <= ms; ++sz) {
+                            if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
+                            const double dx = dx0 - L * sx;
+                            const double dy = dy0 - L * sy;
+                            const double dz = dz0 - L * sz;
+                            const double d2 = dx * dx + dy * dy + dz * dz;
+                            if (!(d2 < rc2)) continue;
+                            const double d = sqrt(d2);
+                            const double e = erfc(beta * d) / d;
+                            const double s = q[j] * (e + two_beta_rpi * exp(-beta * beta * d2)) / d2;
+                            phi += q[j] * e;
+                            fx += s * dx; fy += s * dy; fz += s * dz;
+                        }
+            }
+        }
+        if (F_out) {
+            F_out[3 * t + 0] = q[i] * fx;
+            F_out[3 * t + 1] = q[i] * fy;
+            F_out[3 * t + 2] = q[i] * fz;
+        }
+        if (phi_tmp) phi_tmp[t] = phi;
+    }
+    if (e_real) {
+        double e = 0.0;
+        for (int64_t t = 0; t < nt; ++t) e += 0.5 * q[sub ? sub[t] : t] * phi_tmp[t];
+        *e_real = e;
+    }
+    if (phi_tmp != phi_out) free(phi_tmp);
+}
+
+/*
+ * Structure factors over an explicit k list (Section 3.1.2; Algorithm 1 accumulates the
+ * conjugate): S[2 t] + i S[2 t + 1] = sum_j q_j (cos(k.r_j) + i sin(k.r_j)), k = 2 pi m_t / L.
+ * Direct cos/sin of the full phase per (k, particle).
+ */
+void ewo_structure_factor(int64_t n, const double *pos, const double *q, double L,
+                          int64_t nk, const int32_t *m, double *S)
+{
+    const double tpl = 2.0 * EWO_PI / L;
+    #pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t t = 0; t < nk; ++t) {
+        const double kx = tpl * m[3 * t + 0], ky = tpl * m[3 * t + 1], kz = tpl * m[3 * t + 2];
+        double re = 0.0, im = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            const double ph = kx * wrap1(pos[3 * j + 0], L) + ky * wrap1(pos[3 * j + 1], L)
+                            + kz * wrap1(pos[3 * j + 2], L);
+            re += q[j] * cos(ph);
+            im += q[j] * sin(ph);
+        }
+        S[2 * t + 0] = re;
+        S[2 * t + 1] = im;
+    }
+}
+
+/* g(k) = 4 pi exp(-k^2 / (4 beta^2)) / (V k^2)  (C_k of Eq. 3 with alpha = beta^2). */
+static double coef_g(const int32_t *mt, double L, double beta)
+{
+    const double tpl = 2.0 * EWO_PI / L;
+    const double kx = tpl * mt[0], ky = tpl * mt[1], kz = tpl * mt[2];
+    const double k2 = kx * kx + ky * ky + kz * kz;
+    return 4.0 * EWO_PI * exp(-k2 / (4.0 * beta * beta)) / (L * L * L * k2);
+}
+
+/* E_recip = sum_{k in K_half} g(k) |S(k)|^2 (equal to 1/2 sum over all k != 0), summed in
+ * list order.  Also returns g per k in g_out when non-NULL. */
+double ewo_recip_energy(int64_t nk, const int32_t *m, const double *S, double L, double beta,
+                        double *g_out)
+{
+    double e = 0.0;
+    for (int64_t t = 0; t < nk; ++t) {
+        const double g = coef_g(m + 3 * t, L, beta);
+        if (g_out) g_out[t] = g;
+        e += g * (S[2 * t] * S[2 * t] + S[2 * t + 1] * S[2 * t + 1]);
+    }
+    return e;
+}
+
+/*
+ * Reciprocal forces and potentials for the target particles (Algorithm 2), given S(k) over
+ * a half-space k list:
+ *   F_out[t]   = q_i sum_k 2 g(k) k Im(exp(i k.r_i) conj S(k))
+ *   phi_out[t] = sum_k 2 g(k) Re(exp(i k.r_i) conj S(k))      (either pointer may be NULL)
+ */
+void ewo_recip_forces(int64_t n, const double *pos, const double *q, double L, double beta,
+                      int64_t nk, const int32_t *m, const double *S,
+                      int64_t nsub, const int64_t *sub, double *F_out, double *phi_out)
+{
+    const int64_t nt = sub ? nsub : n;
+    const double tpl = 2.0 * EWO_PI / L;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        const int64_t i = sub ? sub[t] : t;
+        const double xi = wrap1(pos[3 * i + 0], L);
+        const double yi = wrap1(pos[3 * i + 1], L);
+        const double zi = wrap1(pos[3 * i + 2], L);
+        double fx = 0.0, fy = 0.0, fz = 0.0, phi = 0.0;
+        for (int64_t u = 0; u < nk; ++u) {
+            const double kx = tpl * m[3 * u + 0], ky = tpl * m[3 * u + 1], kz = tpl * m[3 * u + 2];
+            const double g2 = 2.0 * coef_g(m + 3 * u, L, beta);
+            const double ph = kx * xi + ky * yi + kz * zi;
+            const double c = cos(ph), s = sin(ph);
+            const double sr = S[2 * u], si = S[2 * u + 1];
+            /* exp(i ph) * conj(S) = (c + i s)(sr - i si) */
+            const double re = c * sr + s * si;
+            const double im = s * sr - c * si;
+            phi += g2 * re;
+            fx += g2 * kx * im; fy += g2 * ky * im; fz += g2 * kz * im;
+        }
+        if (F_out) {
+            F_out[3 * t + 0] = q[i] * fx;
+            F_out[3 * t + 1] = q[i] * fy;
+            F_out[3 * t + 2] = q[i] * fz;
+        }
+        if (phi_out) phi_out[t] = phi;
+    }
+}
+
+/* E_self = -beta / sqrt(pi) * sum_i q_i^2 (Section 3.2.2, amortised self-energy). */
+double ewo_self(int64_t n, const double *q, double beta)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += q[i] * q[i];
+    return -beta / sqrt(EWO_PI) * s;
+}
+
+/*
+ * Brute-force periodic Coulomb sum over whole image cells in a cube of shells
+ * (|n_a| <= shells), with the positions exactly as given (NOT wrapped: the cell dipole
+ * M = sum_i q_i r_i depends on which image of each charge forms the cell):
+ *   E = 1/2 sum_{n} sum_i sum_j' q_i q_j / |r_i - r_j - nL|   (j != i when n = 0)
+ *   F_i = q_i sum_{n} sum_j' q_j (r_i - r_j - nL) / |r_i - r_j - nL|^3
+ * This is the lattice sum of Section 2.1 taken in one particular (cubic) order; for a
+ * neutral cell its limit is the conducting-boundary Ewald energy plus the surface term
+ * 2 pi |M|^2 / (3 V) (the conditional convergence discussed in Section 2.1).
+ * Sums over the cube in shell order (n by increasing max|n_a|) so that partial results
+ * after every shell are available in E_shell[0..shells] when non-NULL.
+ */
+void ewo_coulomb_cube(int64_t n, const double *pos, const double *q, double L, int shells,
+                      double *E_shell, double *F_out)
+{
+    double e_total = 0.0;
+    if (F_out) for (int64_t t = 0; t < 3 * n; ++t) F_out[t] = 0.0;
+    for (int s = 0; s <= shells; ++s) {
+        double e_shell = 0.0;
+        for (int sx = -s; sx <= s; ++sx)
+            for (int sy = -s; sy <= s; ++sy)
+                for (int sz = -s; sz <= s; ++sz) {
+                    int ax = sx < 0 ? -sx : sx, ay = sy < 0 ? -sy : sy, az = sz < 0 ? -sz : sz;
+                    int mx = ax > ay ? ax : ay;
+                    mx = mx > az ? mx : az;
+                    if (mx != s) continue; /* only the cells of this shell */
+                    for (int64_t i = 0; i < n; ++i)
+                        for (int64_t j = 0; j < n; ++j) {
+                            if (s == 0 && i == j) continue;
+                            const double dx = pos[3 * i + 0] - pos[3 * j + 0] - L * sx;
+                            const double dy = pos[3 * i + 1] - pos[3 * j + 1] - L * sy;
+                            const double dz = pos[3 * i + 2] - pos[3 * j + 2] - L * sz;
+                            const double d2 = dx * dx + dy * dy + dz * dz;
+                            const double d = sqrt(d2);
+                            e_shell += 0.5 * q[i] * q[j] / d;
+                            if (F_out) {
+                                const double f = q[i] * q[j] / (d2 * d);
+                                F_out[3 * i + 0] += f * dx;
+                                F_out[3 * i + 1] += f * dy;
+                                F_out[3 * i + 2] += f * dz;
+                            }
+                        }
+                }
+        e_total += e_shell;
+        if (E_shell) E_shell[s] = e_total;
+    }
+}
