@@ -1,0 +1,353 @@
+"""Benchmark: Ewald force evaluations per second (particles/s) on the GPU.
+
+A step is one full evaluation of the hot path (binning, real-space pairs, S(k), energy,
+back-scatter, self term, unsort) of one synthetic system through the C ABI.  Rank 0 prints
+one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload random_32768]
+                  [--precision mixed|fp64|fp32|mixed_bf16] [--impl ours|reference]
+
+Timing: inputs resident in HBM; before every step a 512 MiB buffer is written to flush
+the L2 (129 MB); every step is bracketed by CUDA events on the launching stream and the
+per-step device times are summed.  The end-to-end figure times the host-buffer entry point
+(pinned host -> device copies of positions and charges, evaluation, device -> host copies of
+forces and energies) per step.  Multi-GPU: the method shards into independent systems, so
+N ranks evaluate N independent replicas (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1708_01135_gb300 import workloads as W  # noqa: E402
+
+TOL = 1e-6
+
+WORKLOADS = {
+    # name: (generator, fixed r_c or None)
+    "rocksalt_512": (W.rocksalt_512, 4.0),
+    "random_32768": (W.random_32768, 4.0),
+    "rocksalt_262144": (W.rocksalt_262144, None),
+    "random_2097152": (W.random_2097152, None),
+}
+
+
+def params_for(workload, n, L):
+    from paper_1708_01135_gb300 import tune
+    if workload == "rocksalt_512":
+        return 4.0, 1.0, 10          # r_c = L/2, k_max raised to 10 to reach 1e-6
+    rc_fixed = WORKLOADS[workload][1]
+    rc, beta, km = tune(n, L, TOL, r_c=rc_fixed)
+    return rc, beta, km
+
+
+# ---- roofline bookkeeping ---------------------------------------------------------------
+
+def rows_count(kmax):
+    return sum(1 for mz in range(kmax + 1) for my in range(-kmax, kmax + 1)
+               if my * my + mz * mz <= kmax * kmax and (mz > 0 or my >= 0))
+
+
+def tensor_flops(n, kmax):
+    """Issued tensor-core flops of one evaluation (both products, three split terms)."""
+    R = rows_count(kmax)
+    ncol_f = 16 * math.ceil((2 * kmax + 1) / 16)
+    ncol_b = 16 * math.ceil(3 * (2 * kmax + 1) / 16)
+    fwd = 2.0 * (2 * R) * ncol_f * n * 3
+    back = 2.0 * n * (2 * R) * ncol_b * 3
+    return fwd, back
+
+
+def simt_flops(n, kmax):
+    """Multiply-add flops of the CUDA-core products (forward and back-scatter)."""
+    R = rows_count(kmax)
+    fwd = 2.0 * 4 * R * (kmax + 1) * n
+    back = 2.0 * n * (2 * R) * 3 * (2 * kmax + 1)
+    return fwd, back
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---- clocks ------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- CPU oracle baseline ------------------------------------------------------------------
+
+def oracle_sample(pos, q, L, beta, rc, kmax, n_targets, seed=0):
+    """Time the FP64 oracle on a bounded sample of one evaluation and scale it to the whole
+    evaluation.  Sample: S(k) over all particles and all k, then real-space and reciprocal
+    forces for `n_targets` random particles; both force parts cost the same per target, so
+    the full time is t_S + (N / n_targets) * t_targets."""
+    import oracle
+    n = len(q)
+    rng = np.random.default_rng(seed)
+    sub = np.sort(rng.choice(n, size=min(n_targets, n), replace=False))
+    t0 = time.perf_counter()
+    m = oracle.kset_half(kmax)
+    S = oracle.structure_factor(pos, q, L, m)
+    t1 = time.perf_counter()
+    oracle.real(pos, q, L, beta, rc, sub=sub)
+    oracle.recip(pos, q, L, beta, kmax, sub=sub, S=S)
+    t2 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * n / len(sub)
+    return full, (t2 - t0), len(sub)
+
+
+# ---- main ---------------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    gen, _ = WORKLOADS[args.workload]
+    pos, q, L = gen()
+    n = len(q)
+    rc, beta, kmax = params_for(args.workload, n, L)
+    targets = args.cpu_targets
+    times = []
+    for s in range(args.warmup + args.steps):
+        full, wall, nt = oracle_sample(pos, q, L, beta, rc, kmax, targets, seed=s)
+        if s >= args.warmup:
+            times.append(full)
+    t = float(np.mean(times))
+    value = n / t
+    line = {
+        "impl": "reference", "metric": "ewald_particles_per_s", "value": value,
+        "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "L": L, "r_c": rc, "beta": beta,
+                   "k_max": kmax, "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"S(k) over all {n} particles and all k, forces of {targets} "
+                                   f"random particles, scaled to {n}"},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="random_32768", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32", "mixed_bf16"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-targets", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1708_01135_gb300 import Ewald
+
+    gen, _ = WORKLOADS[args.workload]
+    pos, q, L = gen()
+    n = len(q)
+    rc, beta, kmax = params_for(args.workload, n, L)
+    dev = torch.device("cuda", local)
+    tp = torch.tensor(pos, device=dev)
+    tq = torch.tensor(q, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    E = torch.empty(4, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ew = Ewald(L, beta, rc, kmax, args.precision)
+
+    for _ in range(args.warmup):
+        ew.compute_async(tp, tq, F, E)
+    torch.cuda.synchronize()
+    if ew.status() != 0:
+        raise RuntimeError("warm-up evaluation reported an error")
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = {k: [] for k in ("binning", "real", "recip_forward", "recip_coef", "recip_back",
+                             "finalize", "total", "recip_branch")}
+    ew.profile(1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        ev0[s].record(stream)
+        ew.compute_async(tp, tq, F, E)
+        ev1[s].record(stream)
+        t, nl = ew.profile(-1)          # synchronises on the last stage event
+        launches += nl
+        for k, v in t.items():
+            stage[k].append(v)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ew.profile(0)
+    if ew.status() != 0:
+        raise RuntimeError("timed evaluation reported an error")
+    ms = float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)]))
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * n / (ms * 1e-3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    hp = torch.tensor(pos).pin_memory().numpy()
+    hq = torch.tensor(q).pin_memory().numpy()
+    hf = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    for _ in range(2):
+        ew.compute_host(hp, hq, hf)
+    torch.cuda.synchronize()
+    e_times = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        _, eh = ew.compute_host(hp, hq, hf)
+        e_times.append(time.perf_counter() - t0)
+    e2e = world * n / float(np.mean(e_times))
+
+    pk, pk_kind = peaks()
+    tc = args.precision in ("mixed", "mixed_bf16")
+    back_ms = float(np.median(stage["recip_back"]))
+    fwd_ms = float(np.median(stage["recip_forward"]))
+    if tc:
+        fwd_f, back_f = tensor_flops(n, kmax)
+        achieved = back_f / (back_ms * 1e-3) / 1e12
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+        roof = {"bound": "tensor", "kernel": "back-scatter product (a8)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": f"{pk_kind} bf16 dense sustained (fp16 dense rate is equal)"}
+    else:
+        fwd_f, back_f = simt_flops(n, kmax)
+        achieved = back_f / (back_ms * 1e-3) / 1e12
+        peak = 1.25 if args.precision == "fp64" else 76.0
+        roof = {"bound": "alu", "kernel": "back-scatter product (a8)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_kind": "nominal FP64/FP32 CUDA-core rate (unit counts x clock)"}
+    stages_ms = {k: float(np.median(v)) for k, v in stage.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        full, wall, nt = oracle_sample(pos, q, L, beta, rc, kmax, args.cpu_targets)
+        cpu = {"value": n / full, "unit": "particles/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"S(k) over all {n} particles and all k, forces of "
+                                           f"{nt} random particles, scaled to {n} "
+                                           f"({wall:.1f} s of CPU work)"}
+    if rank == 0:
+        line = {
+            "metric": "ewald_particles_per_s", "value": value, "unit": "particles/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mixed": "fp32 pairs + fp16x2 tensor products (fp32 accum) + f64 reductions",
+                      "mixed_bf16": "fp32 pairs + bf16x2 tensor products (fp32 accum) + f64 reductions",
+                      "fp64": "f64", "fp32": "f32 (f64 reductions)"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "L": L, "r_c": rc, "beta": beta,
+                       "k_max": kmax, "tol": TOL, "precision": args.precision,
+                       "l2": "flushed before every step (512 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e, "unit": "particles/s", "h2d_bytes_per_step": 32 * n,
+                    "d2h_bytes_per_step": 24 * n + 32},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "stages_ms": stages_ms,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ew.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,278 @@
+/*
+ * ewald.h - C ABI of the GB300 Ewald summation library (libewald.so).
+ *
+ * The library evaluates the classical Ewald sum of the paper "Long range forces in a
+ * performance portable Molecular Dynamics framework" (arXiv 1708.01135): Coulomb energy and
+ * forces of N point charges in a periodic cubic box of side L (Section 3.1, Eq. 2), split
+ * into
+ *   - a real-space pair sum of erfc-screened charges inside a cutoff r_c
+ *     (Section 3.1.1; Eq. 4; Listing 1),
+ *   - a reciprocal-space sum over the wave vectors k = 2 pi m / L, m in Z^3, m != 0,
+ *     |m|^2 <= k_max^2 (Section 3.1.2; the two matrix-vector products of Eq. 3, built as
+ *     structure factors S(k) = sum_j q_j exp(i k.r_j) (Algorithm 1) and scattered back to
+ *     every particle as forces and potentials (Algorithm 2)),
+ *   - the self-energy term (Section 3.2.2).
+ * Units are Gaussian with the Coulomb constant 1.  The k = 0 term is dropped (neutral
+ * systems only, footnote of Section 3.1.2): the conducting ("tin-foil") boundary condition.
+ *
+ * Splitting parameter: every call takes beta (1/length), the coefficient inside erfc.  The
+ * paper writes the Gaussian exponent alpha = beta^2 (erfc(sqrt(alpha) r)).
+ *
+ * Conventions for every function:
+ *   - Positions are float64, array-of-structs [n][3] (x, y, z); charges float64 [n];
+ *     forces float64 [n][3] in the caller's particle order.  Positions may lie outside
+ *     [0, L): they are wrapped (x - L floor(x / L)).
+ *   - "dev" pointers are CUDA device pointers on the current device; "host" pointers are
+ *     host memory (pinned or pageable).  The caller owns every buffer it passes; the library
+ *     owns the plan and server objects and their device workspaces.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - No exception or longjmp crosses this ABI; every fallible call returns an
+ *     ewald_status code, and ewald_strerror() names it.
+ *   - A plan is not thread-safe: one plan, one stream at a time.  Distinct plans are
+ *     independent.
+ */
+#ifndef EWALD_H
+#define EWALD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ewald_plan *ewald_plan_t;     /* opaque, library-owned */
+typedef struct ewald_server *ewald_server_t; /* opaque, library-owned */
+
+typedef enum ewald_status {
+    EWALD_OK = 0,
+    EWALD_PENDING = 1,          /* ewald_poll: the request has not finished yet            */
+    EWALD_E_INVAL = -1,         /* bad argument (NULL pointer, L <= 0, k_max < 1, ...)     */
+    EWALD_E_NONNEUTRAL = -2,    /* |sum q| > 1e-10 sum |q|: the paper treats neutral only  */
+    EWALD_E_CUTOFF = -3,        /* r_c > L/2 (minimum image) or r_c <= 0                   */
+    EWALD_E_NOMEM = -4,         /* device or host allocation failed / over the HBM budget  */
+    EWALD_E_CUDA = -5,          /* a CUDA runtime call failed                              */
+    EWALD_E_TIMEOUT = -6,       /* a bounded wait gave up (device pipeline or server)      */
+    EWALD_E_BUSY = -7,          /* server: no free slot / queue full                       */
+    EWALD_E_NOTFOUND = -8,      /* server: unknown or already collected ticket             */
+    EWALD_E_NONFINITE = -9,     /* a position or charge is NaN or infinite                 */
+    EWALD_E_UNSUPPORTED = -10   /* parameters outside what this build implements           */
+} ewald_status;
+
+typedef enum ewald_precision {
+    /* FP64 everywhere on CUDA cores: real-space pairs, per-axis phase recurrences,
+     * structure factors and back-scatter as FP64 products.  The plain FP64 GPU Ewald. */
+    EWALD_FP64 = 0,
+    /* Real-space pairs in FP32 on cell-local coordinates; S(k) and the force back-scatter
+     * as complex matrix products on the tcgen05 tensor cores with every operand split into
+     * two FP16 terms (hi + lo, three products per term pair) and FP32 accumulation; FP64
+     * base phases, per-k energy and all global reductions. */
+    EWALD_MIXED = 1,
+    /* As EWALD_MIXED with BF16 instead of FP16 operand terms (wider range, 8 fewer
+     * mantissa bits per term). */
+    EWALD_MIXED_BF16 = 2,
+    /* FP32 on CUDA cores for pairs and for the matrix products (no tensor cores). */
+    EWALD_FP32 = 3
+} ewald_precision;
+
+/* Bit mask selecting the parts of the sum that ewald_compute_async evaluates. */
+enum {
+    EWALD_PART_REAL = 1,   /* real-space pairs                                   */
+    EWALD_PART_RECIP = 2,  /* reciprocal space (S(k), energy, back-scatter)      */
+    EWALD_PART_SELF = 4,   /* self-energy                                        */
+    EWALD_PART_ALL = 7
+};
+
+/* Index of every entry of an energy[4] array. */
+enum { EWALD_E_REAL = 0, EWALD_E_RECIP = 1, EWALD_E_SELF = 2, EWALD_E_TOTAL = 3 };
+
+/*
+ * ewald_create - make a plan for a box and a set of Ewald parameters.
+ *   L          box side (> 0)
+ *   beta       splitting parameter (> 0, 1/length); the paper's alpha is beta^2
+ *   r_c        real-space cutoff, 0 < r_c <= L/2 (pairs with distance < r_c are summed,
+ *              strict inequality as in Listing 1)
+ *   k_max      integer reciprocal cutoff: m != 0 with |m|^2 <= k_max^2 (1 <= k_max <= 127)
+ *   precision  one of ewald_precision
+ *   out        receives the plan
+ * The plan holds the cell grid (cell side >= r_c / 2 where the box allows), the half-space
+ * k set and its row tables, and device workspaces that grow on the first compute with a
+ * larger n.  Uses the device current at creation; every later call must run with that
+ * device current.  Returns EWALD_OK, EWALD_E_INVAL, EWALD_E_CUTOFF, EWALD_E_UNSUPPORTED,
+ * EWALD_E_NOMEM or EWALD_E_CUDA.
+ */
+int ewald_create(double L, double beta, double r_c, int k_max, int precision, ewald_plan_t *out);
+
+/* ewald_destroy - free a plan and its device memory (synchronises its last stream).
+ * NULL is ignored. */
+void ewald_destroy(ewald_plan_t plan);
+
+/*
+ * ewald_compute - one energy + force evaluation, device buffers, synchronous energies.
+ *   pos     dev float64 [n][3]
+ *   q       dev float64 [n]
+ *   forces  dev float64 [n][3], overwritten with F_i = -dU/dr_i (all three parts)
+ *   energy  host float64 [4]: real, reciprocal, self, total (EWALD_E_* indices)
+ *   stream  cudaStream_t (void*)
+ * Launches the whole pipeline on `stream`, then synchronises that stream to return the
+ * energies and the validation status.  n == 0 gives zero energies.  Errors:
+ * EWALD_E_INVAL, EWALD_E_NONNEUTRAL, EWALD_E_NONFINITE (checked on the device, reported
+ * here), EWALD_E_NOMEM (workspace growth), EWALD_E_TIMEOUT (a bounded device wait gave
+ * up), EWALD_E_CUDA.  On a validation error forces and energies are unspecified.
+ */
+int ewald_compute(ewald_plan_t plan, int64_t n, const double *pos, const double *q,
+                  double *forces, double energy[4], void *stream);
+
+/*
+ * ewald_compute_async - as ewald_compute, but fully asynchronous on `stream`.
+ *   energy_dev  dev float64 [4] (real, reciprocal, self, total), written on the stream
+ *   parts       EWALD_PART_* mask; forces and energies contain only the selected parts
+ *               (unselected energy entries are 0)
+ * Host-side argument errors are returned immediately.  Device-side validation (neutrality,
+ * finiteness) and bounded-wait timeouts are recorded in the plan and returned by the next
+ * ewald_status_sync() call.  Workspace growth (the first call with a larger n) allocates
+ * device memory and is therefore not capturable in a CUDA graph; later calls with n no
+ * larger than before allocate nothing.
+ */
+int ewald_compute_async(ewald_plan_t plan, int64_t n, const double *pos, const double *q,
+                        double *forces, double *energy_dev, int parts, void *stream);
+
+/* ewald_status_sync - synchronise the plan's last stream and return (and clear) the
+ * device-side status of the last evaluation: EWALD_OK, EWALD_E_NONNEUTRAL,
+ * EWALD_E_NONFINITE, EWALD_E_TIMEOUT or EWALD_E_CUDA. */
+int ewald_status_sync(ewald_plan_t plan);
+
+/*
+ * ewald_compute_host - end-to-end evaluation from host buffers: copies pos and q to the
+ * device (plan-owned staging buffers), runs the pipeline, copies forces and the four
+ * energies back, and synchronises.  pos, q, forces, energy are HOST pointers with the
+ * same layouts as ewald_compute.  Pinned host memory gives asynchronous copies.
+ */
+int ewald_compute_host(ewald_plan_t plan, int64_t n, const double *pos_host,
+                       const double *q_host, double *forces_host, double energy_host[4],
+                       void *stream);
+
+/*
+ * ewald_profile - per-stage timing of later evaluations with CUDA events recorded on the
+ * stream each stage runs on (off by default; recording adds a few event records per call).
+ *   enable    1 to record from the next evaluation on, 0 to stop, -1 to leave unchanged
+ *   times_ms  host float64 [8] or NULL: synchronises and returns the stage durations of the
+ *             last recorded evaluation: [0] binning and packing (a1-a3), [1] real-space
+ *             pairs (a4), [2] phases and structure-factor product (a5-a6), [3] S(k)
+ *             reduction, energy and coefficients (a6-a7), [4] back-scatter product and
+ *             forces (a8), [5] self term, totals and unsort (a9), [6] whole evaluation,
+ *             [7] reciprocal branch (stages 2-4 on their stream)
+ *   launches  host int or NULL: kernels launched by the last evaluation
+ */
+int ewald_profile(ewald_plan_t plan, int enable, double times_ms[8], int *launches);
+
+/* ewald_plan_info - read plan parameters chosen at creation.
+ *   info[0] = number of cells per side, info[1] = stencil half-width in cells
+ *   (0 = all pairs with the minimum image), info[2] = |K_half|, info[3] = number of
+ *   (m_y, m_z) rows, info[4] = k_max, info[5] = precision.  Any pointer may be NULL. */
+int ewald_plan_info(ewald_plan_t plan, int64_t info[6]);
+
+/*
+ * ewald_kset - the plan's half-space k set K_half, in the order used by
+ * ewald_structure_factor: m_z ascending, then m_y ascending, then m_x ascending; m != 0,
+ * |m|^2 <= k_max^2, and (m_z > 0) or (m_z = 0, m_y > 0) or (m_z = m_y = 0, m_x > 0).
+ *   m_host  host int32 [cap][3] or NULL;  *count receives |K_half|.
+ * Writes min(cap, |K_half|) triples.
+ */
+int ewald_kset(ewald_plan_t plan, int32_t *m_host, int64_t cap, int64_t *count);
+
+/* ewald_structure_factor - copy S(k) = sum_j q_j exp(i k.r_j) of the last evaluation
+ * that included EWALD_PART_RECIP, as float64 (re, im) pairs [|K_half|][2] in ewald_kset
+ * order, into the device buffer S_dev, on `stream`. */
+int ewald_structure_factor(ewald_plan_t plan, double *S_dev, void *stream);
+
+/* ewald_cell_sort - debug view of the integer binning of the last evaluation: copies, on
+ * `stream`, the cell index of every particle in caller order (int32 [n], key =
+ * (c_z n_c + c_y) n_c + c_x) and the stable cell order (int32 [n]: slot s holds particle
+ * perm[s]) into device buffers.  Either pointer may be NULL. */
+int ewald_cell_sort(ewald_plan_t plan, int32_t *key_dev, int32_t *perm_dev, void *stream);
+
+/*
+ * ewald_tune - choose (beta, r_c, k_max) for a target relative RMS force error.
+ *   n, L      particle count and box side
+ *   tol       target relative RMS force error (e.g. 1e-6), 1e-15 < tol < 1e-1
+ *   r_c       in: a fixed cutoff (> 0), or <= 0 to let the tuner choose; out: the cutoff
+ *   beta, k_max  out
+ * Both truncation errors decay as exp(-p^2) with p = beta r_c = pi k_max / (beta L)
+ * (Section 3.1.3: r_c ~ alpha^-1/2, k_c ~ alpha^1/2); p is set from tol.  With r_c free,
+ * the tuner picks r_c <= L/2 minimising a cost model of pair candidates plus k modes.
+ */
+int ewald_tune(int64_t n, double L, double tol, double *r_c, double *beta, int *k_max);
+
+/* ewald_strerror - static, NUL-terminated name of a status code. */
+const char *ewald_strerror(int status);
+
+/* ------------------------------------------------------------------------------------
+ * Serving: continuous batching of independent Ewald evaluations.
+ *
+ * A server owns a scheduler thread, a pool of CUDA streams and a pool of reusable plans
+ * ("slots").  ewald_submit() queues a request; the scheduler admits queued requests in
+ * arrival order whenever a slot is free and the request's device footprint fits in the
+ * remaining HBM budget, and launches its whole pipeline on the slot's stream, so that
+ * requests admitted while others run overlap on the device.  ewald_poll() returns the
+ * result once the request's stream has finished.
+ * ---------------------------------------------------------------------------------- */
+
+typedef struct ewald_request {
+    double L, beta, r_c;
+    int k_max;
+    int precision;       /* ewald_precision */
+    int64_t n;
+    const double *pos;   /* dev [n][3]; must stay valid until ewald_poll returns final */
+    const double *q;     /* dev [n] */
+    double *forces;      /* dev [n][3], written by the server */
+    void *stream;        /* cudaStream_t on which pos and q were produced (NULL: legacy
+                            default stream); the request starts after the work queued on
+                            it before ewald_submit */
+} ewald_request;
+
+typedef struct ewald_result {
+    int status;          /* EWALD_OK or an error code of the evaluation */
+    double energy[4];    /* real, reciprocal, self, total */
+    double t_submit;     /* seconds on the server's monotonic clock */
+    double t_admit;      /* when the scheduler launched the request */
+    double t_done;       /* when the scheduler saw the request's stream finish */
+    int64_t footprint_bytes; /* device memory charged against the budget */
+} ewald_result;
+
+/*
+ * ewald_server_create - start a server on the current device.
+ *   max_slots         concurrent requests on the device (1..64)
+ *   hbm_budget_bytes  device memory the server may hold for request workspaces
+ *                     (0 = 80 % of the free memory at creation)
+ *   out               receives the server
+ */
+int ewald_server_create(int max_slots, size_t hbm_budget_bytes, ewald_server_t *out);
+
+/* ewald_submit - queue a request (copied; the buffers it points to are not).  Returns
+ * EWALD_OK and a ticket, EWALD_E_INVAL for a request that can never run (bad
+ * parameters, footprint above the whole budget), or EWALD_E_BUSY when the queue is full. */
+int ewald_submit(ewald_server_t srv, const ewald_request *req, uint64_t *ticket);
+
+/* ewald_poll - non-blocking: EWALD_PENDING while queued or running; otherwise fills
+ * *out, forgets the ticket and returns EWALD_OK (the request's own status is in
+ * out->status).  EWALD_E_NOTFOUND for an unknown ticket. */
+int ewald_poll(ewald_server_t srv, uint64_t ticket, ewald_result *out);
+
+/* ewald_wait - blocking poll with a time limit in seconds; EWALD_E_TIMEOUT when it runs
+ * out (the request stays queued or running and can be polled again). */
+int ewald_wait(ewald_server_t srv, uint64_t ticket, double timeout_s, ewald_result *out);
+
+/* ewald_server_stats - counters since creation: stats[0] submitted, [1] completed,
+ * [2] admitted bytes now, [3] peak admitted bytes, [4] peak concurrent requests. */
+int ewald_server_stats(ewald_server_t srv, int64_t stats[5]);
+
+/* ewald_server_destroy - drain: wait for running requests, cancel queued ones (their
+ * poll results are dropped), stop the scheduler and free everything. */
+int ewald_server_destroy(ewald_server_t srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EWALD_H */

@@ -1,0 +1,691 @@
+// C ABI of libewald.so: plans, the per-call pipeline, the self/total step (a9), the tuner.
+//
+// One evaluation (ewald_compute_async) on the caller's stream:
+//   a1-a3  binning: wrap, cell keys, stable counting sort, offsets, packing   (cells.cu)
+//   fork:  the reciprocal branch runs on the plan's side stream
+//   a4     real-space pairs                                                    (realspace.cu)
+//   a5-a8  phases, S(k), energy and coefficients, back-scatter    (recip_simt.cu / recip_tc.cu)
+//   join, a9: self energy -beta/sqrt(pi) sum q^2 (Section 3.2.2), energy totals, neutrality
+//          check, and the sum of the force parts scattered back to the caller's order.
+// Every reduction is a fixed-order tree or serial sum, so repeated calls with the same input
+// give bit-identical results.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "ewald_internal.cuh"
+
+using namespace ew;
+
+
+namespace ew {
+namespace {
+
+// a9: energies (one block, fixed order) and the neutrality check.
+__global__ void k_energy(int ntile, const double *__restrict__ e_tile, int nq,
+                         const double *__restrict__ qpart, int R,
+                         const double *__restrict__ e_row, double beta, int parts,
+                         double *__restrict__ energy, int *__restrict__ status)
+{
+    __shared__ double red[4][256];
+    const int t = threadIdx.x;
+    double er = 0.0, ek = 0.0, qs = 0.0, qa = 0.0, q2 = 0.0;
+    // every thread sums a contiguous slice, then a fixed tree over threads
+    int per = (ntile + 255) / 256;
+    for (int i = t * per; i < min(ntile, (t + 1) * per); ++i) er += e_tile[i];
+    per = (R + 255) / 256;
+    for (int i = t * per; i < min(R, (t + 1) * per); ++i) ek += e_row[i];
+    red[0][t] = er;
+    red[1][t] = ek;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) { red[0][t] += red[0][t + o]; red[1][t] += red[1][t + o]; }
+        __syncthreads();
+    }
+    er = red[0][0];
+    ek = red[1][0];
+    __syncthreads();
+    per = (nq + 255) / 256;
+    for (int i = t * per; i < min(nq, (t + 1) * per); ++i) {
+        qs += qpart[3 * i]; qa += qpart[3 * i + 1]; q2 += qpart[3 * i + 2];
+    }
+    red[0][t] = qs; red[1][t] = qa; red[2][t] = q2;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) {
+            red[0][t] += red[0][t + o]; red[1][t] += red[1][t + o]; red[2][t] += red[2][t + o];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        qs = red[0][0]; qa = red[1][0]; q2 = red[2][0];
+        if (fabs(qs) > 1e-10 * qa) atomicOr(status, kStNonNeutral);
+        const double e_real = (parts & EWALD_PART_REAL) ? 0.5 * er : 0.0;
+        const double e_recip = (parts & EWALD_PART_RECIP) ? ek : 0.0;
+        const double e_self = (parts & EWALD_PART_SELF) ? -beta / sqrt(kPi) * q2 : 0.0;
+        energy[0] = e_real;
+        energy[1] = e_recip;
+        energy[2] = e_self;
+        energy[3] = (e_real + e_recip) + e_self;
+    }
+}
+
+// a9: F[perm[s]] = F_real[s] + F_recip[s] (selected parts), caller order.
+__global__ void k_unsort(int64_t n, const int *__restrict__ perm, const double *__restrict__ fr,
+                         const double *__restrict__ fk, int parts, double *__restrict__ out)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t i = perm[s];
+    const bool ur = parts & EWALD_PART_REAL, uk = parts & EWALD_PART_RECIP;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double v = 0.0;
+        if (ur) v += fr[3 * s + a];
+        if (uk) v += fk[3 * s + a];
+        out[3 * i + a] = v;
+    }
+}
+
+__global__ void k_zero_energy(double *e)
+{
+    if (threadIdx.x < 4) e[threadIdx.x] = 0.0;
+}
+
+int status_from_bits(int bits)
+{
+    if (bits & kStNonFinite) return EWALD_E_NONFINITE;
+    if (bits & kStTimeout) return EWALD_E_TIMEOUT;
+    if (bits & kStNonNeutral) return EWALD_E_NONNEUTRAL;
+    return EWALD_OK;
+}
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return EWALD_OK;
+    if (e == cudaErrorMemoryAllocation) return EWALD_E_NOMEM;
+    return EWALD_E_CUDA;
+}
+
+bool uses_tc(int precision)
+{
+    return precision == EWALD_MIXED || precision == EWALD_MIXED_BF16;
+}
+
+void free_workspace(Plan &p)
+{
+    Workspace &ws = p.ws;
+    void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
+                    ws.tiles, ws.tile_count, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
+                    ws.f_real, ws.f_recip, ws.e_tile, ws.qpart};
+    for (void *q : ptrs) pool_free(q, p.side_stream);
+    free_recip_simt(p);
+    if (uses_tc(p.precision)) free_recip_tc(p);
+    int64_t keep_host = ws.cap_host;
+    double *hp = ws.h_pos, *hq = ws.h_q, *hf = ws.h_f, *he = ws.h_e;
+    ws = Workspace();
+    ws.cap_host = keep_host;
+    ws.h_pos = hp; ws.h_q = hq; ws.h_f = hf; ws.h_e = he;
+}
+
+int binning_chunks(int64_t n)
+{
+    int64_t nb = (n + 255) / 256;
+    if (nb > 256) nb = 256;
+    return nb < 1 ? 1 : (int)nb;
+}
+
+}  // namespace
+
+// Library-owned stream-ordered memory pool of the current device.  Plans allocate their
+// workspaces from it, so a freed workspace is kept for the next plan instead of going back
+// to the driver (the serving loop creates and drops plans per request).
+cudaMemPool_t lib_pool()
+{
+    static cudaMemPool_t pools[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pl = nullptr;
+        if (cudaMemPoolCreate(&pl, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pl, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pl;
+    }
+    return pools[dev];
+}
+
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st)
+{
+    cudaMemPool_t pl = lib_pool();
+    if (!pl) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(ptr, bytes < 256 ? 256 : bytes, pl, st);
+}
+
+void pool_free(void *ptr, cudaStream_t st)
+{
+    if (ptr) cudaFreeAsync(ptr, st);
+}
+
+namespace {
+
+template <class P>
+cudaError_t dmalloc(Plan &pl, P **p, size_t bytes)
+{
+    return pool_alloc((void **)p, bytes, pl.side_stream);
+}
+
+cudaError_t grow_workspace(Plan &p, int64_t n)
+{
+    if (n <= p.ws.cap_n) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(p.last_stream ? p.last_stream : 0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(p.side_stream)) != cudaSuccess) return e;
+    free_workspace(p);
+    Workspace &ws = p.ws;
+    const int nb = binning_chunks(n);
+    const int nrows = p.nc * p.nc;
+    const int64_t tiles = real_tile_capacity(p, n);
+    const int64_t qblocks = (n + 255) / 256;
+#define EW_TRY(x) do { if ((e = (x)) != cudaSuccess) { free_workspace(p); return e; } } while (0)
+    EW_TRY(dmalloc(p, &ws.key, sizeof(int) * n));
+    EW_TRY(dmalloc(p, &ws.perm, sizeof(int) * n));
+    EW_TRY(dmalloc(p, &ws.key_sorted, sizeof(int) * n));
+    EW_TRY(dmalloc(p, &ws.hist, sizeof(int) * (size_t)nb * p.ncells));
+    EW_TRY(dmalloc(p, &ws.cell_start, sizeof(int) * (p.ncells + 1)));
+    EW_TRY(dmalloc(p, &ws.cell_total, sizeof(int) * p.ncells));
+    EW_TRY(dmalloc(p, &ws.tiles, sizeof(int2) * tiles));
+    EW_TRY(dmalloc(p, &ws.tile_count, sizeof(int) * nrows));
+    EW_TRY(dmalloc(p, &ws.tile_off, sizeof(int) * (nrows + 1)));
+    EW_TRY(dmalloc(p, &ws.pg, sizeof(double4_32a) * n));
+    if (p.precision == EWALD_FP64) EW_TRY(dmalloc(p, &ws.pl64, sizeof(double4_32a) * n));
+    else EW_TRY(dmalloc(p, &ws.pl32, sizeof(float4) * n));
+    EW_TRY(dmalloc(p, &ws.pu, sizeof(uint4) * n));
+    EW_TRY(dmalloc(p, &ws.f_real, sizeof(double) * 3 * n));
+    EW_TRY(dmalloc(p, &ws.f_recip, sizeof(double) * 3 * n));
+    EW_TRY(dmalloc(p, &ws.e_tile, sizeof(double) * tiles));
+    EW_TRY(dmalloc(p, &ws.qpart, sizeof(double) * 3 * qblocks));
+    ws.cap_n = n;
+    ws.nb = nb;
+    if (uses_tc(p.precision)) EW_TRY(alloc_recip_tc(p, n));
+    else EW_TRY(alloc_recip_simt(p, n));
+#undef EW_TRY
+    // allocations are ordered on the side stream; make them visible to every stream
+    return cudaStreamSynchronize(p.side_stream);
+}
+
+cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
+                     double *energy_dev, int parts, cudaStream_t st)
+{
+    cudaError_t e;
+    Workspace &ws = p.ws;
+    p.launches = 0;
+    prof_mark(p, kEvStart, st);
+    if ((e = cudaMemsetAsync(p.d_status, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if ((e = launch_binning(p, n, pos, q, st)) != cudaSuccess) return e;
+    prof_mark(p, kEvBinned, st);
+    const int64_t tiles = real_tile_capacity(p, n);
+    if ((e = cudaMemsetAsync(ws.e_tile, 0, sizeof(double) * tiles, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.e_recip_part, 0, sizeof(double) * p.R, st)) != cudaSuccess) return e;
+    const bool do_recip = parts & EWALD_PART_RECIP;
+    if (do_recip) {
+        if ((e = cudaEventRecord(p.ev_fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(p.side_stream, p.ev_fork, 0)) != cudaSuccess) return e;
+        e = uses_tc(p.precision) ? launch_recip_tc(p, n, p.side_stream)
+                                 : launch_recip_simt(p, n, p.side_stream);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(p.ev_join, p.side_stream)) != cudaSuccess) return e;
+    }
+    if (parts & EWALD_PART_REAL) {
+        if ((e = launch_real(p, n, st)) != cudaSuccess) return e;
+    }
+    prof_mark(p, kEvRealEnd, st);
+    if (do_recip) {
+        if ((e = cudaStreamWaitEvent(st, p.ev_join, 0)) != cudaSuccess) return e;
+    }
+    k_energy<<<1, 256, 0, st>>>((int)tiles, ws.e_tile, (int)((n + 255) / 256), ws.qpart, p.R,
+                                p.e_recip_part, p.beta, parts, energy_dev, p.d_status);
+    k_unsort<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ws.perm, ws.f_real, ws.f_recip,
+                                                          parts, forces);
+    p.launches += 2;
+    prof_mark(p, kEvFinal, st);
+    p.prof_valid = p.prof && do_recip && (parts & EWALD_PART_REAL);
+    p.last_stream = st;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t plan_footprint(const Plan &p, int64_t n)
+{
+    const int nb = binning_chunks(n);
+    const int64_t tiles = real_tile_capacity(p, n);
+    size_t b = 0;
+    b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * p.ncells;
+    b += sizeof(int) * (2 * (size_t)p.ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * (p.nc * p.nc + 1);
+    b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
+    b += sizeof(double) * 6 * (size_t)n + sizeof(double) * tiles + sizeof(double) * 3 * ((n + 255) / 256);
+    b += uses_tc(p.precision) ? recip_tc_bytes(p, n) : recip_simt_bytes(p, n);
+    b += sizeof(double) * 2 * (size_t)p.nk + sizeof(int) * 3 * (size_t)p.nk + sizeof(RowInfo) * p.R;
+    return b;
+}
+
+}  // namespace ew
+
+// ---- plan construction ------------------------------------------------------------------
+
+static void build_rows(Plan &p)
+{
+    // Rows (m_y, m_z) of the half plane; koff is each row's offset in the K_half order
+    // (m_z, then m_y, then m_x ascending).  The rows are then processed in order of
+    // decreasing m_y^2 + m_z^2: the coefficients g(k) |S(k)| grow along that order, so the
+    // back-scatter sums over rows add the small terms before the large ones.
+    const int k = p.kmax;
+    p.rows_h.clear();
+    int64_t koff = 0;
+    for (int mz = 0; mz <= k; ++mz)
+        for (int my = -k; my <= k; ++my) {
+            if (my * my + mz * mz > k * k) continue;
+            if (mz == 0 && my < 0) continue;
+            int rem = k * k - my * my - mz * mz;
+            int nx = (int)floor(sqrt((double)rem));
+            while ((nx + 1) * (nx + 1) <= rem) ++nx;
+            while (nx * nx > rem) --nx;
+            RowInfo r;
+            r.my = my; r.mz = mz; r.nxmax = nx; r.koff = (int)koff;
+            koff += (my == 0 && mz == 0) ? nx : 2 * nx + 1;
+            p.rows_h.push_back(r);
+        }
+    std::stable_sort(p.rows_h.begin(), p.rows_h.end(), [](const RowInfo &a, const RowInfo &b) {
+        return a.my * a.my + a.mz * a.mz > b.my * b.my + b.mz * b.mz;
+    });
+    p.R = (int)p.rows_h.size();
+    p.nk = koff;
+}
+
+static void choose_cells(Plan &p)
+{
+    // cells of side >= r_c / w with a (2w + 1)^3 stencil that does not wrap onto itself
+    p.w = 0;
+    p.nc = 1;
+    for (int w = 2; w >= 1; --w) {
+        int nc = (int)floor(p.L * w / p.rc * (1.0 - 1e-12));
+        if (nc > 256) nc = 256;
+        if (nc >= 2 * w + 1) {
+            p.w = w;
+            p.nc = nc;
+            break;
+        }
+    }
+    p.ncells = p.nc * p.nc * p.nc;
+    p.cell_side = p.L / p.nc;
+}
+
+namespace ew {
+
+int plan_setup_host(Plan &p, double L, double beta, double rc, int kmax, int precision)
+{
+    if (!(L > 0) || !isfinite(L) || !(beta > 0) || !isfinite(beta)) return EWALD_E_INVAL;
+    if (!(rc > 0) || !(rc <= 0.5 * L)) return EWALD_E_CUTOFF;
+    if (kmax < 1) return EWALD_E_INVAL;
+    if (kmax > 127) return EWALD_E_UNSUPPORTED;
+    if (precision < EWALD_FP64 || precision > EWALD_FP32) return EWALD_E_INVAL;
+    p.L = L; p.beta = beta; p.rc = rc; p.kmax = kmax; p.precision = precision;
+    choose_cells(p);
+    build_rows(p);
+    return EWALD_OK;
+}
+
+// Upload the row table and k list of the current parameters, (re)allocating the plan-level
+// arrays when they grow.  Runs on the side stream and waits for it.
+static cudaError_t plan_upload(Plan &p)
+{
+    cudaError_t e;
+    cudaStream_t st = p.side_stream;
+    if (p.R > p.cap_R) {
+        pool_free(p.rows_d, st); pool_free(p.e_recip_part, st);
+        p.rows_d = nullptr; p.e_recip_part = nullptr; p.cap_R = 0;
+        if ((e = pool_alloc((void **)&p.rows_d, sizeof(RowInfo) * p.R, st)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&p.e_recip_part, sizeof(double) * p.R, st)) != cudaSuccess) return e;
+        p.cap_R = p.R;
+    }
+    if (p.nk > p.cap_nk) {
+        pool_free(p.kset_d, st); pool_free(p.S_d, st);
+        p.kset_d = nullptr; p.S_d = nullptr; p.cap_nk = 0;
+        if ((e = pool_alloc((void **)&p.kset_d, sizeof(int) * 3 * p.nk, st)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&p.S_d, sizeof(double) * 2 * p.nk, st)) != cudaSuccess) return e;
+        p.cap_nk = p.nk;
+    }
+    std::vector<int> kset(3 * (size_t)p.nk);
+    for (const RowInfo &r : p.rows_h) {
+        int lo = (r.my == 0 && r.mz == 0) ? 1 : -r.nxmax;
+        int64_t t = r.koff;
+        for (int mx = lo; mx <= r.nxmax; ++mx) {
+            kset[3 * t + 0] = mx; kset[3 * t + 1] = r.my; kset[3 * t + 2] = r.mz;
+            ++t;
+        }
+    }
+    if ((e = cudaMemcpyAsync(p.rows_d, p.rows_h.data(), sizeof(RowInfo) * p.R, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(p.kset_d, kset.data(), sizeof(int) * 3 * p.nk, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.S_d, 0, sizeof(double) * 2 * p.nk, st)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+int plan_reconfigure(ewald_plan *h, double L, double beta, double rc, int kmax, int precision)
+{
+    Plan &p = h->p;
+    Plan probe;
+    int s = plan_setup_host(probe, L, beta, rc, kmax, precision);
+    if (s != EWALD_OK) return s;
+    if (p.last_stream) cudaStreamSynchronize(p.last_stream);
+    cudaStreamSynchronize(p.side_stream);
+    const bool same_shape = probe.ncells == p.ncells && probe.nc == p.nc && probe.R == p.R &&
+                            probe.kmax == p.kmax && probe.precision == p.precision;
+    if (!same_shape) free_workspace(p);
+    plan_setup_host(p, L, beta, rc, kmax, precision);
+    return cuda_status(plan_upload(p));
+}
+
+}  // namespace ew
+
+static void destroy_plan(ewald_plan *h)
+{
+    Plan &p = h->p;
+    if (p.last_stream) cudaStreamSynchronize(p.last_stream);
+    if (p.side_stream) {
+        cudaStreamSynchronize(p.side_stream);
+        free_workspace(p);
+        pool_free(p.rows_d, p.side_stream); pool_free(p.kset_d, p.side_stream);
+        pool_free(p.S_d, p.side_stream); pool_free(p.e_recip_part, p.side_stream);
+        pool_free(p.energy_d, p.side_stream); pool_free(p.d_status, p.side_stream);
+        pool_free(p.ws.h_pos, p.side_stream); pool_free(p.ws.h_q, p.side_stream);
+        pool_free(p.ws.h_f, p.side_stream);
+        cudaStreamSynchronize(p.side_stream);
+    }
+    if (p.h_status) cudaFreeHost(p.h_status);
+    if (p.side_stream) cudaStreamDestroy(p.side_stream);
+    if (p.ev_fork) cudaEventDestroy(p.ev_fork);
+    if (p.ev_join) cudaEventDestroy(p.ev_join);
+    for (cudaEvent_t ev : p.ev)
+        if (ev) cudaEventDestroy(ev);
+    delete h;
+}
+
+extern "C" int ewald_create(double L, double beta, double r_c, int k_max, int precision,
+                            ewald_plan_t *out)
+{
+    if (!out) return EWALD_E_INVAL;
+    *out = nullptr;
+    Plan probe;
+    int s = plan_setup_host(probe, L, beta, r_c, k_max, precision);
+    if (s != EWALD_OK) return s;
+    ewald_plan *h = new (std::nothrow) ewald_plan();
+    if (!h) return EWALD_E_NOMEM;
+    Plan &p = h->p;
+    plan_setup_host(p, L, beta, r_c, k_max, precision);
+    cudaGetDevice(&p.device);
+    cudaError_t e = cudaSuccess;
+#define EW_C(x) do { if ((e = (x)) != cudaSuccess) { destroy_plan(h); return cuda_status(e); } } while (0)
+    EW_C(cudaStreamCreateWithFlags(&p.side_stream, cudaStreamNonBlocking));
+    EW_C(cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming));
+    EW_C(cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming));
+    EW_C(cudaHostAlloc((void **)&p.h_status, sizeof(int), cudaHostAllocDefault));
+    EW_C(pool_alloc((void **)&p.energy_d, sizeof(double) * 4, p.side_stream));
+    EW_C(pool_alloc((void **)&p.d_status, sizeof(int), p.side_stream));
+    EW_C(cudaMemsetAsync(p.d_status, 0, sizeof(int), p.side_stream));
+    EW_C(plan_upload(p));
+#undef EW_C
+    *out = h;
+    return EWALD_OK;
+}
+
+extern "C" void ewald_destroy(ewald_plan_t plan)
+{
+    if (plan) destroy_plan(plan);
+}
+
+static int validate_call(ewald_plan_t plan, int64_t n, const void *pos, const void *q,
+                         const void *forces)
+{
+    if (!plan) return EWALD_E_INVAL;
+    if (n < 0 || n > (int64_t)INT32_MAX / 4) return EWALD_E_INVAL;
+    if (n > 0 && (!pos || !q || !forces)) return EWALD_E_INVAL;
+    return EWALD_OK;
+}
+
+extern "C" int ewald_compute_async(ewald_plan_t plan, int64_t n, const double *pos,
+                                   const double *q, double *forces, double *energy_dev,
+                                   int parts, void *stream)
+{
+    int s = validate_call(plan, n, pos, q, forces);
+    if (s != EWALD_OK) return s;
+    if (!energy_dev || (parts & ~EWALD_PART_ALL)) return EWALD_E_INVAL;
+    Plan &p = plan->p;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        k_zero_energy<<<1, 32, 0, st>>>(energy_dev);
+        p.last_stream = st;
+        return cuda_status(cudaGetLastError());
+    }
+    cudaError_t e = grow_workspace(p, n);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = pipeline(p, n, pos, q, forces, energy_dev, parts, st);
+    return cuda_status(e);
+}
+
+extern "C" int ewald_status_sync(ewald_plan_t plan)
+{
+    if (!plan) return EWALD_E_INVAL;
+    Plan &p = plan->p;
+    cudaError_t e = cudaStreamSynchronize(p.last_stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemcpy(p.h_status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_status(e);
+    int bits = *p.h_status;
+    cudaMemset(p.d_status, 0, sizeof(int));
+    return status_from_bits(bits);
+}
+
+extern "C" int ewald_compute(ewald_plan_t plan, int64_t n, const double *pos, const double *q,
+                             double *forces, double energy[4], void *stream)
+{
+    if (!energy) return EWALD_E_INVAL;
+    int s = ewald_compute_async(plan, n, pos, q, forces, plan ? plan->p.energy_d : nullptr,
+                                EWALD_PART_ALL, stream);
+    if (s != EWALD_OK) return s;
+    Plan &p = plan->p;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(energy, p.energy_d, sizeof(double) * 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemcpyAsync(p.h_status, p.d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(e);
+    return status_from_bits(n > 0 ? *p.h_status : 0);
+}
+
+extern "C" int ewald_compute_host(ewald_plan_t plan, int64_t n, const double *pos_host,
+                                  const double *q_host, double *forces_host,
+                                  double energy_host[4], void *stream)
+{
+    int s = validate_call(plan, n, pos_host, q_host, forces_host);
+    if (s != EWALD_OK || !energy_host) return s != EWALD_OK ? s : EWALD_E_INVAL;
+    Plan &p = plan->p;
+    Workspace &ws = p.ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (n > ws.cap_host) {
+        if (p.last_stream) cudaStreamSynchronize(p.last_stream);
+        cudaStreamSynchronize(p.side_stream);
+        pool_free(ws.h_pos, p.side_stream); pool_free(ws.h_q, p.side_stream);
+        pool_free(ws.h_f, p.side_stream);
+        ws.h_pos = ws.h_q = ws.h_f = nullptr;
+        ws.cap_host = 0;
+        if ((e = pool_alloc((void **)&ws.h_pos, sizeof(double) * 3 * n, p.side_stream)) != cudaSuccess) return cuda_status(e);
+        if ((e = pool_alloc((void **)&ws.h_q, sizeof(double) * n, p.side_stream)) != cudaSuccess) return cuda_status(e);
+        if ((e = pool_alloc((void **)&ws.h_f, sizeof(double) * 3 * n, p.side_stream)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaStreamSynchronize(p.side_stream)) != cudaSuccess) return cuda_status(e);
+        ws.cap_host = n;
+    }
+    if (n > 0) {
+        if ((e = cudaMemcpyAsync(ws.h_pos, pos_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_status(e);
+        if ((e = cudaMemcpyAsync(ws.h_q, q_host, sizeof(double) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    s = ewald_compute(plan, n, ws.h_pos, ws.h_q, ws.h_f, energy_host, stream);
+    if (s != EWALD_OK) return s;
+    if (n > 0) {
+        if ((e = cudaMemcpyAsync(forces_host, ws.h_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_status(e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(e);
+    }
+    return EWALD_OK;
+}
+
+extern "C" int ewald_profile(ewald_plan_t plan, int enable, double times_ms[8], int *launches)
+{
+    if (!plan) return EWALD_E_INVAL;
+    Plan &p = plan->p;
+    if (enable == 1 && !p.ev[0]) {
+        for (cudaEvent_t &ev : p.ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    }
+    if (enable >= 0) {
+        p.prof = enable == 1;
+        if (!p.prof) p.prof_valid = false;
+    }
+    if (launches) *launches = p.launches;
+    if (times_ms) {
+        for (int i = 0; i < 8; ++i) times_ms[i] = 0.0;
+        if (!p.prof_valid) return EWALD_OK;
+        cudaError_t e = cudaEventSynchronize(p.ev[kEvFinal]);
+        if (e != cudaSuccess) return cuda_status(e);
+        float ms = 0.f;
+        auto span = [&](int a, int b) {
+            return cudaEventElapsedTime(&ms, p.ev[a], p.ev[b]) == cudaSuccess ? (double)ms : -1.0;
+        };
+        times_ms[0] = span(kEvStart, kEvBinned);
+        times_ms[1] = span(kEvBinned, kEvRealEnd);
+        times_ms[2] = span(kEvRecipStart, kEvFwdEnd);
+        times_ms[3] = span(kEvFwdEnd, kEvCoefEnd);
+        times_ms[4] = span(kEvCoefEnd, kEvBackEnd);
+        times_ms[5] = span(kEvRealEnd, kEvFinal);
+        times_ms[6] = span(kEvStart, kEvFinal);
+        times_ms[7] = span(kEvRecipStart, kEvBackEnd);
+    }
+    return EWALD_OK;
+}
+
+extern "C" int ewald_plan_info(ewald_plan_t plan, int64_t info[6])
+{
+    if (!plan || !info) return EWALD_E_INVAL;
+    const Plan &p = plan->p;
+    info[0] = p.nc; info[1] = p.w; info[2] = p.nk; info[3] = p.R; info[4] = p.kmax;
+    info[5] = p.precision;
+    return EWALD_OK;
+}
+
+extern "C" int ewald_kset(ewald_plan_t plan, int32_t *m_host, int64_t cap, int64_t *count)
+{
+    if (!plan) return EWALD_E_INVAL;
+    const Plan &p = plan->p;
+    if (count) *count = p.nk;
+    if (m_host && cap > 0) {
+        int64_t m = cap < p.nk ? cap : p.nk;
+        cudaError_t e = cudaMemcpy(m_host, p.kset_d, sizeof(int) * 3 * m, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return EWALD_OK;
+}
+
+extern "C" int ewald_structure_factor(ewald_plan_t plan, double *S_dev, void *stream)
+{
+    if (!plan || !S_dev) return EWALD_E_INVAL;
+    const Plan &p = plan->p;
+    return cuda_status(cudaMemcpyAsync(S_dev, p.S_d, sizeof(double) * 2 * p.nk,
+                                       cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+}
+
+extern "C" int ewald_cell_sort(ewald_plan_t plan, int32_t *key_dev, int32_t *perm_dev, void *stream)
+{
+    if (!plan) return EWALD_E_INVAL;
+    const Plan &p = plan->p;
+    const int64_t n = p.ws.cap_n;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (key_dev && n) e = cudaMemcpyAsync(key_dev, p.ws.key, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && perm_dev && n)
+        e = cudaMemcpyAsync(perm_dev, p.ws.perm, sizeof(int) * n, cudaMemcpyDeviceToDevice, st);
+    return cuda_status(e);
+}
+
+// ---- tuner --------------------------------------------------------------------------------
+
+extern "C" int ewald_tune(int64_t n, double L, double tol, double *r_c, double *beta, int *k_max)
+{
+    if (!r_c || !beta || !k_max || n < 2 || !(L > 0) || !(tol > 1e-15) || !(tol < 0.1))
+        return EWALD_E_INVAL;
+    // Both truncation errors fall as exp(-p^2), p = beta r_c = pi k_max / (beta L); the
+    // relative RMS force error of dense ionic systems is close to exp(-p^2) itself.
+    const double p = sqrt(-log(tol));
+    double rc = *r_c;
+    if (!(rc > 0)) {
+        // cost model: pair candidates ~ N * 27 (r_c / w)^3 rho * c_pair versus
+        // modes ~ N * (2/3) pi k_max^3 * c_mode (k_max = p^2 L / (pi r_c)); pick the r_c that
+        // minimises it on a grid of r_c <= L/2.
+        const double rho = n / (L * L * L);
+        const double c_pair = 1.0, c_mode = 0.35;
+        double best = 1e300, best_rc = 0.5 * L;
+        for (int t = 1; t <= 400; ++t) {
+            double x = 0.5 * L * t / 400.0;
+            if (x < 1e-3) continue;
+            double km = p * p * L / (kPi * x);
+            double cost = 15.6 * x * x * x * rho * c_pair + (2.0 / 3.0) * kPi * km * km * km * c_mode;
+            if (cost < best) { best = cost; best_rc = x; }
+        }
+        rc = best_rc;
+    }
+    if (rc > 0.5 * L) return EWALD_E_CUTOFF;
+    const double b = p / rc;
+    int km = (int)ceil(p * b * L / kPi);
+    if (km < 1) km = 1;
+    if (km > 127) return EWALD_E_UNSUPPORTED;
+    *r_c = rc;
+    *beta = b;
+    *k_max = km;
+    return EWALD_OK;
+}
+
+extern "C" const char *ewald_strerror(int status)
+{
+    switch (status) {
+    case EWALD_OK: return "EWALD_OK";
+    case EWALD_PENDING: return "EWALD_PENDING";
+    case EWALD_E_INVAL: return "EWALD_E_INVAL: invalid argument";
+    case EWALD_E_NONNEUTRAL: return "EWALD_E_NONNEUTRAL: the system is not charge neutral";
+    case EWALD_E_CUTOFF: return "EWALD_E_CUTOFF: r_c must satisfy 0 < r_c <= L/2";
+    case EWALD_E_NOMEM: return "EWALD_E_NOMEM: out of device memory or over the budget";
+    case EWALD_E_CUDA: return "EWALD_E_CUDA: a CUDA call failed";
+    case EWALD_E_TIMEOUT: return "EWALD_E_TIMEOUT: a bounded wait gave up";
+    case EWALD_E_BUSY: return "EWALD_E_BUSY: no free slot or the queue is full";
+    case EWALD_E_NOTFOUND: return "EWALD_E_NOTFOUND: unknown ticket";
+    case EWALD_E_NONFINITE: return "EWALD_E_NONFINITE: a position or charge is not finite";
+    case EWALD_E_UNSUPPORTED: return "EWALD_E_UNSUPPORTED: parameters outside this build";
+    default: return "EWALD_E_UNKNOWN";
+    }
+}

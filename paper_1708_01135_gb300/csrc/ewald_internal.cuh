@@ -1,0 +1,174 @@
+// Internal definitions shared by the CUDA translation units of libewald.so.
+//
+// Notation follows the paper (arXiv 1708.01135, Section 3): N charges q_j at r_j in a cubic
+// box of side L; splitting parameter beta (the paper's alpha = beta^2); real-space cutoff
+// r_c; reciprocal vectors k = 2 pi m / L with m in Z^3, |m|^2 <= k_max^2.
+//
+// The reciprocal sum is organised over "rows": every (m_y, m_z) with m_y^2 + m_z^2 <=
+// k_max^2 in the half plane (m_z > 0, or m_z = 0 and m_y >= 0), ordered by m_z then m_y.
+// Along a row m_x runs over [-k_max, k_max]; the modes of K_half on row r are
+// m_x in [-nxmax_r, nxmax_r] (m_x > 0 only on the row (0, 0)), nxmax_r =
+// floor(sqrt(k_max^2 - m_y^2 - m_z^2)).  This turns S(k) = sum_j q_j exp(i k.r_j) into the
+// matrix product of Eq. 3: S[r, m_x] = sum_j (q_j e^{i(k_y y_j + k_z z_j)}) e^{i k_x x_j}.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ewald.h"
+
+struct ewald_plan;
+
+namespace ew {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Device status bits, OR-ed into plan->d_status by kernels; translated to ewald_status on
+// the host.
+enum : int {
+    kStNonFinite = 1,
+    kStTimeout = 2,
+    kStNonNeutral = 4,
+};
+
+// Row of the reciprocal grid: (m_y, m_z), nxmax, and the offset of its first mode in the
+// K_half ordering.
+struct RowInfo {
+    int my, mz, nxmax, koff;
+};
+
+struct Workspace {
+    int64_t cap_n = 0;       // particles the buffers hold
+    int nb = 0;              // binning chunks (histogram rows)
+    // binning
+    int *key = nullptr;          // [n] cell index, caller order
+    int *perm = nullptr;         // [n] sorted slot -> caller index
+    int *key_sorted = nullptr;   // [n]
+    int *hist = nullptr;         // [nb * ncells] per-chunk cell counts -> offsets
+    int *cell_start = nullptr;   // [ncells + 1]
+    int *cell_total = nullptr;   // [ncells]
+    int2 *tiles = nullptr;       // [max tiles] (row, first slot)
+    int *tile_count = nullptr;   // [nrows] tiles per row
+    int *tile_off = nullptr;     // [nrows + 1] exclusive offsets; tile_off[nrows] = tiles
+    // packed particles (sorted)
+    double4_32a *pg = nullptr;       // wrapped global position + q (FP64)
+    double4_32a *pl64 = nullptr;     // cell-local position + q (FP64)
+    float4 *pl32 = nullptr;      // cell-local position + q (FP32)
+    uint4 *pu = nullptr;         // 32-bit fixed-point fractions x/L, y/L, z/L + q (float bits)
+    // outputs (sorted)
+    double *f_real = nullptr;    // [n][3]
+    double *f_recip = nullptr;   // [n][3]
+    double *e_tile = nullptr;    // [max tiles] per-tile q_i phi_i sums
+    double *qpart = nullptr;     // [qblocks][3]: sum q, sum |q|, sum q^2 partials
+    // staging for the host-buffer entry point
+    double *h_pos = nullptr, *h_q = nullptr, *h_f = nullptr, *h_e = nullptr;
+    int64_t cap_host = 0;
+    // reciprocal (SIMT paths)
+    void *tabX = nullptr, *tabY = nullptr, *tabZ = nullptr;   // phase tables, n-major
+    void *spart = nullptr;       // forward partials
+    size_t spart_bytes = 0;
+    void *gmat = nullptr;        // back-scatter coefficient matrix
+    size_t gmat_bytes = 0;
+    int nks = 0;                 // forward K splits
+};
+
+struct Plan {
+    int device = 0;
+    double L = 0, beta = 0, rc = 0;
+    int kmax = 0;
+    int precision = 0;
+    // cells
+    int nc = 1;          // cells per side
+    int w = 0;           // stencil half-width in cells (0: all pairs, minimum image)
+    int ncells = 1;
+    double cell_side = 0;
+    // reciprocal rows
+    int R = 0;
+    int64_t nk = 0;
+    std::vector<RowInfo> rows_h;
+    RowInfo *rows_d = nullptr;
+    int *kset_d = nullptr;       // [nk][3]
+    double *S_d = nullptr;       // [nk][2] last structure factor
+    double *e_recip_part = nullptr;  // per-row partial energies [R]
+    double *energy_d = nullptr;  // [4] internal energies for the synchronous entry points
+    int cap_R = 0;               // rows the row-sized arrays hold
+    int64_t cap_nk = 0;          // modes the k-sized arrays hold
+    int *d_status = nullptr;
+    int *h_status = nullptr;     // pinned mirror
+    cudaStream_t last_stream = nullptr;
+    cudaStream_t side_stream = nullptr;  // reciprocal branch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    Workspace ws;
+    // tensor-core path state (allocated lazily)
+    void *tc = nullptr;
+    // profiling: events at stage boundaries (see ewald_profile), kernel launch counter
+    bool prof = false;
+    bool prof_valid = false;
+    cudaEvent_t ev[10] = {};
+    int launches = 0;
+};
+
+// Stage boundary events (recorded only while profiling is on).
+enum : int {
+    kEvStart = 0, kEvBinned = 1, kEvRealEnd = 2, kEvRecipStart = 3, kEvFwdEnd = 4,
+    kEvCoefEnd = 5, kEvBackEnd = 6, kEvFinal = 7,
+};
+inline void prof_mark(Plan &p, int which, cudaStream_t st)
+{
+    if (p.prof) cudaEventRecord(p.ev[which], st);
+}
+
+// ---- launchers (each returns cudaError_t of the launch) --------------------------------
+
+// a1-a3: wrap, cell keys, stable counting sort, cell offsets, packing.
+cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *q,
+                           cudaStream_t st);
+// a4: real-space pairs into ws.f_real / ws.e_tile (sorted order).
+cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st);
+int64_t real_tile_capacity(const Plan &p, int64_t n);
+// a5-a8 on CUDA cores (FP64 or FP32): S(k), energy, back-scatter into ws.f_recip.
+cudaError_t launch_recip_simt(Plan &p, int64_t n, cudaStream_t st);
+size_t recip_simt_bytes(const Plan &p, int64_t n);
+cudaError_t alloc_recip_simt(Plan &p, int64_t n);
+void free_recip_simt(Plan &p);
+// a6-a7 shared by both paths: FP64 reduction of FP32 forward partials laid out
+// [nks][R][k_max + 1][4] (T_rr, T_ri, T_ir, T_ii), S(k), per-row energies and the FP32
+// back-scatter coefficient matrix G' [2R][ncol].
+cudaError_t launch_sreduce_f32(Plan &p, int nks, const float *spart, float *gmat, int ncol,
+                               cudaStream_t st);
+// a5-a8 on the tcgen05 tensor cores (split FP16/BF16 operands).
+cudaError_t launch_recip_tc(Plan &p, int64_t n, cudaStream_t st);
+cudaError_t alloc_recip_tc(Plan &p, int64_t n);
+size_t recip_tc_bytes(const Plan &p, int64_t n);
+void free_recip_tc(Plan &p);
+// a9: self term, totals, unsort to caller order.
+cudaError_t launch_finalize(Plan &p, int64_t n, const double *q, double *forces,
+                            double *energy_dev, int parts, cudaStream_t st);
+
+// Library memory pool (stream-ordered, retains freed memory for reuse).
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st);
+void pool_free(void *ptr, cudaStream_t st);
+
+// Host-side plan set-up shared by ewald_create and the server: validates the parameters,
+// chooses the cell grid and enumerates the reciprocal rows (no device work).
+int plan_setup_host(Plan &p, double L, double beta, double rc, int kmax, int precision);
+
+// Re-parameterise an existing plan (keeps its streams and, when the grid and k-set shapes
+// are unchanged, its workspaces).
+int plan_reconfigure(struct ::ewald_plan *h, double L, double beta, double rc, int kmax,
+                     int precision);
+
+// Footprint of a plan's workspaces for n particles (serving admission).
+size_t plan_footprint(const Plan &p, int64_t n);
+
+// Bounded spin limit for mbarrier waits inside kernels (iterations of try_wait).
+constexpr long long kSpinLimit = 1ll << 26;
+
+}  // namespace ew
+
+// Opaque handle of the C ABI (ewald_plan_t points to one of these).
+struct ewald_plan {
+    ew::Plan p;
+};

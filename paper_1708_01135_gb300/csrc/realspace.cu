@@ -1,0 +1,433 @@
+// Real-space pair sum (hot-path step a4): Section 3.1.1, Eq. 4 and Listing 1.
+//
+//   phi_i = sum_{j : 0 < |r_ij| < r_c} q_j erfc(beta r_ij) / r_ij
+//   F_i   = q_i sum_j q_j (r_ij / r_ij^2) [erfc(beta r_ij) / r_ij
+//                                          + 2 beta / sqrt(pi) exp(-beta^2 r_ij^2)]
+//   E_real = 1/2 sum_i q_i phi_i            (r_ij = r_i - r_j, minimum image)
+//
+// GPU design (templated on FP64 and FP32 arithmetic):
+//   * One warp owns a tile of up to 32 consecutive sorted particles of one row of cells
+//     (fixed c_y, c_z); every lane owns one target particle i and accumulates its own force,
+//     so no two threads ever write the same particle (the paper's rule that a loop writes
+//     only its own particle, Section 3.2.3, with no atomics).
+//   * The candidate partners j of a tile are the cells of the neighbour rows (c_y + dy,
+//     c_z + dz), |dy|, |dz| <= w, in the x range of the tile widened by the reach left for
+//     that row.  A run of cells along x is a contiguous range of the sorted array, so it is
+//     copied to shared memory with one bulk TMA copy (cp.async.bulk, completion on an
+//     mbarrier), double-buffered per warp; all lanes then read each j as a broadcast.
+//   * Positions are stored relative to the corner of their own cell; the offset between a
+//     target and a partner cell is an exact small multiple of the cell side.  This keeps
+//     FP32 differences accurate to ~1e-7 of the cell size instead of ~1e-7 of L, and makes
+//     the periodic image implicit (the neighbour cell index wraps, the offset does not).
+//   * Energies: one FP64 partial per tile, summed in tile order by the finalize step.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ewald_internal.cuh"
+
+namespace ew {
+namespace {
+
+constexpr int kWarps = 4;      // warps (tiles) per block
+constexpr int kCap = 256;      // particles per staging buffer
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                             uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Whole-warp bounded wait on an mbarrier phase: true when it completed, false after ~1 s.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        uint32_t ok = mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, ok)) return true;
+        if (__any_sync(0xffffffffu, globaltimer() - t0 > 1000000000ull)) return false;
+    }
+}
+
+template <class T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+
+__device__ __forceinline__ float erfc_t(float x) { return erfcf(x); }
+__device__ __forceinline__ double erfc_t(double x) { return erfc(x); }
+__device__ __forceinline__ float exp_t(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+
+template <class T>
+struct PairAcc {
+    T fx, fy, fz, phi;
+};
+
+// One candidate pair: target at the origin shifted by (xi, yi, zi), partner p.
+template <class T, class T4>
+__device__ __forceinline__ void pair(PairAcc<T> &a, const T4 &p, T xi, T yi, T zi, T rc2,
+                                     T beta, T nb2, T two_b_rpi)
+{
+    const T dx = xi - p.x, dy = yi - p.y, dz = zi - p.z;   // r_i - r_j
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 < rc2 && r2 > T(0)) {
+        const T rinv = rsqrt_t(r2);
+        const T r = r2 * rinv;
+        const T e = erfc_t(beta * r) * rinv;                // erfc(beta r) / r
+        const T g = exp_t(nb2 * r2);                        // exp(-beta^2 r^2)
+        const T s = p.w * (e + two_b_rpi * g) * rinv * rinv;
+        a.phi += p.w * e;
+        a.fx += s * dx;
+        a.fy += s * dy;
+        a.fz += s * dz;
+    }
+}
+
+// Chunk of a contiguous run of partner cells staged in shared memory.
+struct Chunk {
+    int g0, cnt;        // sorted range [g0, g0 + cnt)
+    int rowbase;        // nrow * nc
+    int u0;             // unwrapped x index of the first cell of the run
+    int dy, dz;
+};
+
+struct ChunkIter {
+    // stencil position
+    int dz, dy, w, nc;
+    int xa, xb;          // tile x-cell range
+    int row_cy, row_cz;
+    int wx;              // x reach of the current row
+    int u, uend;         // next unwrapped cell to start a run, last cell of the row range
+    // current run
+    int g, gend, run_u0, rowbase;
+    bool in_run;
+    bool started;
+    float side, rc2;     // geometry for culling (float is enough for the reach test)
+
+    __device__ bool next_row()
+    {
+        while (true) {
+            if (!started) { started = true; dz = -w; dy = -w; }
+            else if (++dy > w) { dy = -w; if (++dz > w) return false; }
+            int ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+            float my = ay > 0 ? (ay - 1) * side : 0.f, mz = az > 0 ? (az - 1) * side : 0.f;
+            float rest = rc2 - my * my - mz * mz;
+            if (rest <= 0.f) continue;
+            int r = (int)ceilf(sqrtf(rest) / side - 1e-6f);
+            wx = r < w ? r : w;
+            if (wx < 0) wx = 0;
+            u = xa - wx;
+            uend = xb + wx;
+            int ny = ((row_cy + dy) % nc + nc) % nc, nz = ((row_cz + dz) % nc + nc) % nc;
+            rowbase = (nz * nc + ny) * nc;
+            return true;
+        }
+    }
+
+    __device__ bool next(const int *__restrict__ cell_start, Chunk &c)
+    {
+        while (true) {
+            if (in_run && g < gend) {
+                int cnt = gend - g < kCap ? gend - g : kCap;
+                c.g0 = g; c.cnt = cnt; c.rowbase = rowbase; c.u0 = run_u0; c.dy = dy; c.dz = dz;
+                g += cnt;
+                return true;
+            }
+            in_run = false;
+            if (!started || u > uend) {
+                if (!next_row()) return false;
+            }
+            int c0 = ((u % nc) + nc) % nc;
+            int u1 = u + (nc - 1 - c0);
+            if (u1 > uend) u1 = uend;
+            g = cell_start[rowbase + c0];
+            gend = cell_start[rowbase + c0 + (u1 - u) + 1];
+            run_u0 = u;
+            u = u1 + 1;
+            in_run = true;
+        }
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kWarps * 32)
+k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restrict__ key_sorted,
+             const int *__restrict__ cell_start, const int2 *__restrict__ tiles,
+             const int *__restrict__ tile_total, int nc, int w, T side, T rc2, T beta,
+             T two_b_rpi, double *__restrict__ f_out, double *__restrict__ e_tile,
+             int *__restrict__ status)
+{
+    using T4 = typename Vec4<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[kWarps][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T4 *buf[2];
+    buf[0] = reinterpret_cast<T4 *>(smem_raw) + (size_t)warp * 2 * kCap;
+    buf[1] = buf[0] + kCap;
+    uint64_t *bar = bars[warp];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int tile = blockIdx.x * kWarps + warp;
+    if (tile >= *tile_total) return;
+
+    const int2 td = tiles[tile];
+    const int row = td.x, first = td.y;
+    const int row_end = cell_start[(row + 1) * nc];
+    const int last = min(first + 32, row_end) - 1;
+    const int i = first + lane;
+    const bool valid = i <= last;
+    const T4 pi = pl[valid ? i : last];
+    const int cxi = key_sorted[valid ? i : last] % nc;
+
+    ChunkIter it;
+    it.w = w; it.nc = nc;
+    it.xa = key_sorted[first] % nc;
+    it.xb = key_sorted[last] % nc;
+    it.row_cy = row % nc; it.row_cz = row / nc;
+    it.in_run = false; it.started = false;
+    it.side = (float)side; it.rc2 = (float)rc2;
+    it.u = 0; it.uend = -1;
+
+    PairAcc<T> acc{T(0), T(0), T(0), T(0)};
+    const T nb2 = -beta * beta;
+    uint32_t phase[2] = {0u, 0u};
+    Chunk cur, nxt;
+    bool have_cur = it.next(cell_start, cur);
+    bool ok = true;
+    if (have_cur && lane == 0) {
+        mbar_expect_tx(&bar[0], cur.cnt * (uint32_t)sizeof(T4));
+        tma_bulk_g2s(buf[0], pl + cur.g0, cur.cnt * (uint32_t)sizeof(T4), &bar[0]);
+    }
+    int b = 0;
+    while (have_cur) {
+        bool have_nxt = it.next(cell_start, nxt);
+        if (have_nxt && lane == 0) {
+            // the other buffer was fully read before the last __syncwarp of the loop
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b ^ 1], nxt.cnt * (uint32_t)sizeof(T4));
+            tma_bulk_g2s(buf[b ^ 1], pl + nxt.g0, nxt.cnt * (uint32_t)sizeof(T4), &bar[b ^ 1]);
+        }
+        if (!warp_wait(&bar[b], phase[b])) { ok = false; break; }
+        phase[b] ^= 1u;
+
+        const T yi = pi.y - T(cur.dy) * side;
+        const T zi = pi.z - T(cur.dz) * side;
+        const T4 *sb = buf[b];
+        // walk the cells of the run that overlap [g0, g0 + cnt)
+        int u = cur.u0;
+        const int cend = cur.g0 + cur.cnt;
+        while (true) {
+            const int c = ((u % nc) + nc) % nc;
+            const int cb = cell_start[cur.rowbase + c];
+            const int ce = cell_start[cur.rowbase + c + 1];
+            if (ce > cur.g0) {
+                const int jb = (cb > cur.g0 ? cb : cur.g0) - cur.g0;
+                const int je = (ce < cend ? ce : cend) - cur.g0;
+                const T xi = pi.x - T(u - cxi) * side;
+                for (int j = jb; j < je; ++j) pair<T, T4>(acc, sb[j], xi, yi, zi, rc2, beta, nb2, two_b_rpi);
+            }
+            if (ce >= cend) break;
+            ++u;
+        }
+        __syncwarp();
+        cur = nxt;
+        have_cur = have_nxt;
+        b ^= 1;
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(status, kStTimeout);
+        // let a copy still in flight land before the warp leaves (bounded)
+        warp_wait(&bar[b ^ 1], phase[b ^ 1]);
+        return;
+    }
+    const double qi = (double)pi.w;
+    if (valid) {
+        f_out[3 * (int64_t)i + 0] = qi * (double)acc.fx;
+        f_out[3 * (int64_t)i + 1] = qi * (double)acc.fy;
+        f_out[3 * (int64_t)i + 2] = qi * (double)acc.fz;
+    }
+    double e = valid ? qi * (double)acc.phi : 0.0;
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if (lane == 0) e_tile[tile] = e;
+}
+
+// All pairs with the minimum image (boxes too small for a cell stencil): one tile of 32
+// targets per warp, every particle staged through the same double-buffered TMA path.
+template <class T>
+__global__ void __launch_bounds__(kWarps * 32)
+k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2, T beta,
+                T two_b_rpi, double *__restrict__ f_out, double *__restrict__ e_tile,
+                int *__restrict__ status)
+{
+    using T4 = typename Vec4<T>::type;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[kWarps][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T4 *buf[2];
+    buf[0] = reinterpret_cast<T4 *>(smem_raw) + (size_t)warp * 2 * kCap;
+    buf[1] = buf[0] + kCap;
+    uint64_t *bar = bars[warp];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int tile = blockIdx.x * kWarps + warp;
+    if (tile * 32 >= n) return;
+    const int i = tile * 32 + lane;
+    const bool valid = i < n;
+    const T4 pi = pl[valid ? i : n - 1];
+    const T invL = T(1) / L;
+    PairAcc<T> acc{T(0), T(0), T(0), T(0)};
+    const T nb2 = -beta * beta;
+    uint32_t phase[2] = {0u, 0u};
+    const int nchunks = (n + kCap - 1) / kCap;
+    if (lane == 0) {
+        int cnt = min(kCap, n);
+        mbar_expect_tx(&bar[0], cnt * (uint32_t)sizeof(T4));
+        tma_bulk_g2s(buf[0], pl, cnt * (uint32_t)sizeof(T4), &bar[0]);
+    }
+    bool ok = true;
+    int b = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        if (c + 1 < nchunks && lane == 0) {
+            int g = (c + 1) * kCap, cnt = min(kCap, n - g);
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b ^ 1], cnt * (uint32_t)sizeof(T4));
+            tma_bulk_g2s(buf[b ^ 1], pl + g, cnt * (uint32_t)sizeof(T4), &bar[b ^ 1]);
+        }
+        if (!warp_wait(&bar[b], phase[b])) { ok = false; break; }
+        phase[b] ^= 1u;
+        const int cnt = min(kCap, n - c * kCap);
+        const T4 *sb = buf[b];
+        for (int j = 0; j < cnt; ++j) {
+            T4 p = sb[j];
+            T dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
+            dx -= L * rint(dx * invL);
+            dy -= L * rint(dy * invL);
+            dz -= L * rint(dz * invL);
+            // evaluate the pair at the minimum image: shift the partner, keep the target
+            T4 pj = p;
+            pj.x = pi.x - dx; pj.y = pi.y - dy; pj.z = pi.z - dz;
+            pair<T, T4>(acc, pj, pi.x, pi.y, pi.z, rc2, beta, nb2, two_b_rpi);
+        }
+        __syncwarp();
+        b ^= 1;
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(status, kStTimeout);
+        warp_wait(&bar[b ^ 1], phase[b ^ 1]);
+        return;
+    }
+    const double qi = (double)pi.w;
+    if (valid) {
+        f_out[3 * (int64_t)i + 0] = qi * (double)acc.fx;
+        f_out[3 * (int64_t)i + 1] = qi * (double)acc.fy;
+        f_out[3 * (int64_t)i + 2] = qi * (double)acc.fz;
+    }
+    double e = valid ? qi * (double)acc.phi : 0.0;
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if (lane == 0) e_tile[tile] = e;
+}
+
+template <class T>
+cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, cudaStream_t st)
+{
+    Workspace &ws = p.ws;
+    const size_t smem = (size_t)kWarps * 2 * kCap * sizeof(typename Vec4<T>::type);
+    const T beta = (T)p.beta, rc2 = (T)(p.rc * p.rc);
+    const T tbr = (T)(2.0 * p.beta / sqrt(kPi));
+    cudaError_t e;
+    if (p.w == 0) {
+        e = cudaFuncSetAttribute(k_real_allpairs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        int tiles = (int)((n + 31) / 32);
+        k_real_allpairs<T><<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(
+            pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.e_tile, p.d_status);
+    } else {
+        e = cudaFuncSetAttribute(k_real_cells<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        int64_t tiles = real_tile_capacity(p, n);
+        k_real_cells<T><<<(unsigned)((tiles + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
+            pl, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc, p.nc, p.w,
+            (T)p.cell_side, rc2, beta, tbr, ws.f_real, ws.e_tile, p.d_status);
+    }
+    p.launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t real_tile_capacity(const Plan &p, int64_t n)
+{
+    if (p.w == 0) return (n + 31) / 32;
+    return n / 32 + (int64_t)p.nc * p.nc + 1;
+}
+
+cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st)
+{
+    if (p.precision == EWALD_FP64) return launch_real_t<double>(p, n, p.ws.pl64, st);
+    return launch_real_t<float>(p, n, p.ws.pl32, st);
+}
+
+}  // namespace ew

@@ -1,0 +1,85 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function the header
+declares, and its host-only entry points (status names, the parameter tuner, argument
+validation that fails before any CUDA call) behave as documented.  No kernel runs here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1708_01135_gb300 import ewald as E
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    src = open(os.path.join(ROOT, "include", "ewald.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ewald_[a-z_]+)\s*\(", src)))
+
+
+def _lib_or_skip():
+    try:
+        return E.lib()
+    except RuntimeError as e:  # not built in this checkout
+        pytest.skip(str(e))
+
+
+def test_every_declared_function_is_exported():
+    lib = _lib_or_skip()
+    names = _header_functions()
+    assert "ewald_create" in names and "ewald_submit" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_strerror_names_every_status():
+    _lib_or_skip()
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10):
+        assert E.strerror(code).startswith("EWALD_")
+    assert E.strerror(12345) == "EWALD_E_UNKNOWN"
+
+
+def test_tune_rule_and_cutoff_choice():
+    _lib_or_skip()
+    # fixed r_c: beta = p / r_c, k_max = ceil(p beta L / pi), p = sqrt(-ln tol)
+    rc, beta, km = E.tune(32768, 32.0, 1e-6, r_c=4.0)
+    p = math.sqrt(-math.log(1e-6))
+    assert rc == 4.0
+    assert abs(beta - p / 4.0) < 1e-12
+    assert km == math.ceil(p * beta * 32.0 / math.pi)
+    # free r_c: a cutoff inside (0, L/2]
+    rc, beta, km = E.tune(262144, 64.0, 1e-6)
+    assert 0 < rc <= 32.0 and km >= 1
+
+
+def test_tune_rejects_bad_arguments():
+    _lib_or_skip()
+    with pytest.raises(E.EwaldError):
+        E.tune(1000, 10.0, 1e-6, r_c=6.0)   # r_c > L/2
+    with pytest.raises(E.EwaldError):
+        E.tune(1000, -1.0, 1e-6)
+
+
+def test_create_rejects_bad_parameters_before_touching_the_device():
+    lib = _lib_or_skip()
+    h = ctypes.c_void_p()
+    assert lib.ewald_create(8.0, 1.0, 4.5, 8, 0, ctypes.byref(h)) == E.E_CUTOFF
+    assert lib.ewald_create(8.0, 1.0, 0.0, 8, 0, ctypes.byref(h)) == E.E_CUTOFF
+    assert lib.ewald_create(-8.0, 1.0, 2.0, 8, 0, ctypes.byref(h)) == E.E_INVAL
+    assert lib.ewald_create(8.0, 1.0, 2.0, 0, 0, ctypes.byref(h)) == E.E_INVAL
+    assert lib.ewald_create(8.0, 1.0, 2.0, 200, 0, ctypes.byref(h)) == E.E_UNSUPPORTED
+    assert lib.ewald_create(8.0, 1.0, 2.0, 8, 9, ctypes.byref(h)) == E.E_INVAL
+    assert lib.ewald_create(8.0, float("nan"), 2.0, 8, 0, ctypes.byref(h)) == E.E_INVAL
+
+
+def test_null_handles_are_rejected():
+    lib = _lib_or_skip()
+    e = (ctypes.c_double * 4)()
+    assert lib.ewald_compute(None, 4, None, None, None, e, None) == E.E_INVAL
+    assert lib.ewald_status_sync(None) == E.E_INVAL
+    assert lib.ewald_server_destroy(None) == E.E_INVAL
+    r = E._Result()
+    assert lib.ewald_poll(None, 1, ctypes.byref(r)) == E.E_INVAL

@@ -1,0 +1,45 @@
+"""Bit-exact check of the integer binning (steps a1-a2) against a CPU model of its
+definition: wrap x - L floor(x / L) (a result equal to L maps to 0), cell index
+min(floor(x nc / L), nc - 1), key (c_z nc + c_y) nc + c_x, and a stable sort by key (ties in
+input order)."""
+import numpy as np
+import pytest
+
+from gpu_common import dev, need_gpu
+
+from paper_1708_01135_gb300 import Ewald, PART_REAL
+from paper_1708_01135_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _model(pos, L, nc):
+    w = pos - L * np.floor(pos / L)
+    w[w >= L] = 0.0
+    c = np.minimum((w * (nc / L)).astype(np.int64), nc - 1)
+    key = (c[:, 2] * nc + c[:, 1]) * nc + c[:, 0]
+    perm = np.argsort(key, kind="stable")
+    return key, perm
+
+
+@pytest.mark.parametrize("n,L,rc,seed", [(5000, 17.1, 4.0, 3), (777, 9.5, 3.1, 4), (40000, 34.2, 4.0, 9)])
+def test_keys_and_stable_order_bit_exact(n, L, rc, seed):
+    need_gpu()
+    import torch
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(-L, 2 * L, size=(n, 3))          # outside the box: exercises the wrap
+    pos[:7] = np.array([0.0, L, -L])                    # exact boundaries
+    pos[7:20] = pos[20]                                 # ties: equal keys
+    q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    if n % 2:
+        q[-1] = 0.0
+    with Ewald(L, 1.0, rc, 4, "fp64") as ew:
+        nc = ew.info()["cells_per_side"]
+        F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        e = torch.empty(4, dtype=torch.float64, device="cuda")
+        ew.compute_async(dev(pos), dev(q), F, e, parts=PART_REAL)
+        ew.status()
+        key, perm = ew.cell_sort(n)
+    mkey, mperm = _model(pos, L, nc)
+    assert np.array_equal(key, mkey)
+    assert np.array_equal(perm, mperm)
