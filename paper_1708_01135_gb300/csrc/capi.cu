@@ -27,44 +27,60 @@ using namespace ew;
 namespace ew {
 namespace {
 
+// Sum of x[0..m) by one thread block of 256 threads in a fixed order: thread t sums the
+// contiguous slice t of the array (8 independent partial sums, combined in order), then a
+// fixed tree over the threads.  Every thread returns the total.
+__device__ double block_sum_fixed(const double *__restrict__ x, int m, double *red)
+{
+    const int t = threadIdx.x;
+    const int per = (m + 255) / 256;
+    const int b = t * per, e = min(m, b + per);
+    double p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int i = b;
+    for (; i + 8 <= e; i += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) p[u] += x[i + u];
+    }
+    for (int u = 0; i < e; ++i, ++u) p[u] += x[i];
+    double s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    red[t] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) red[t] += red[t + o];
+        __syncthreads();
+    }
+    s = red[0];
+    __syncthreads();
+    return s;
+}
+
 // a9: energies (one block, fixed order) and the neutrality check.
 __global__ void k_energy(int ntile, const double *__restrict__ e_tile, int nq,
                          const double *__restrict__ qpart, int R,
                          const double *__restrict__ e_row, double beta, int parts,
                          double *__restrict__ energy, int *__restrict__ status)
 {
-    __shared__ double red[4][256];
+    __shared__ double red[256];
+    __shared__ double qv[3][256];
+    const double er = block_sum_fixed(e_tile, ntile, red);
+    const double ek = block_sum_fixed(e_row, R, red);
+    // charge sums: qpart is [nq][3]
     const int t = threadIdx.x;
-    double er = 0.0, ek = 0.0, qs = 0.0, qa = 0.0, q2 = 0.0;
-    // every thread sums a contiguous slice, then a fixed tree over threads
-    int per = (ntile + 255) / 256;
-    for (int i = t * per; i < min(ntile, (t + 1) * per); ++i) er += e_tile[i];
-    per = (R + 255) / 256;
-    for (int i = t * per; i < min(R, (t + 1) * per); ++i) ek += e_row[i];
-    red[0][t] = er;
-    red[1][t] = ek;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (t < o) { red[0][t] += red[0][t + o]; red[1][t] += red[1][t + o]; }
-        __syncthreads();
-    }
-    er = red[0][0];
-    ek = red[1][0];
-    __syncthreads();
-    per = (nq + 255) / 256;
+    double qs = 0.0, qa = 0.0, q2 = 0.0;
+    const int per = (nq + 255) / 256;
     for (int i = t * per; i < min(nq, (t + 1) * per); ++i) {
         qs += qpart[3 * i]; qa += qpart[3 * i + 1]; q2 += qpart[3 * i + 2];
     }
-    red[0][t] = qs; red[1][t] = qa; red[2][t] = q2;
+    qv[0][t] = qs; qv[1][t] = qa; qv[2][t] = q2;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
         if (t < o) {
-            red[0][t] += red[0][t + o]; red[1][t] += red[1][t + o]; red[2][t] += red[2][t + o];
+            qv[0][t] += qv[0][t + o]; qv[1][t] += qv[1][t + o]; qv[2][t] += qv[2][t + o];
         }
         __syncthreads();
     }
     if (t == 0) {
-        qs = red[0][0]; qa = red[1][0]; q2 = red[2][0];
+        qs = qv[0][0]; qa = qv[1][0]; q2 = qv[2][0];
         if (fabs(qs) > 1e-10 * qa) atomicOr(status, kStNonNeutral);
         const double e_real = (parts & EWALD_PART_REAL) ? 0.5 * er : 0.0;
         const double e_recip = (parts & EWALD_PART_RECIP) ? ek : 0.0;
@@ -136,8 +152,11 @@ void free_workspace(Plan &p)
 
 int binning_chunks(int64_t n)
 {
-    int64_t nb = (n + 255) / 256;
-    if (nb > 256) nb = 256;
+    // chunks of at least 1024 particles and at most 16384 (the scatter keeps a chunk's keys
+    // in shared memory)
+    int64_t nb = (n + 1023) / 1024;
+    if (nb > 128) nb = 128;
+    if ((n + nb - 1) / nb > 16384) nb = (n + 16383) / 16384;
     return nb < 1 ? 1 : (int)nb;
 }
 
@@ -233,13 +252,16 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     cudaError_t e;
     Workspace &ws = p.ws;
     p.launches = 0;
+    // a failed call of an earlier evaluation (e.g. a rejected launch configuration) must not be
+    // reported against this one
+    (void)cudaGetLastError();
     prof_mark(p, kEvStart, st);
     if ((e = cudaMemsetAsync(p.d_status, 0, sizeof(int), st)) != cudaSuccess) return e;
     if ((e = launch_binning(p, n, pos, q, st)) != cudaSuccess) return e;
     prof_mark(p, kEvBinned, st);
     const int64_t tiles = real_tile_capacity(p, n);
     if ((e = cudaMemsetAsync(ws.e_tile, 0, sizeof(double) * tiles, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(p.e_recip_part, 0, sizeof(double) * p.R, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p.e_recip_part, 0, sizeof(double) * p.e_recip_count, st)) != cudaSuccess) return e;
     const bool do_recip = parts & EWALD_PART_RECIP;
     if (do_recip) {
         if ((e = cudaEventRecord(p.ev_fork, st)) != cudaSuccess) return e;
@@ -256,8 +278,9 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     if (do_recip) {
         if ((e = cudaStreamWaitEvent(st, p.ev_join, 0)) != cudaSuccess) return e;
     }
-    k_energy<<<1, 256, 0, st>>>((int)tiles, ws.e_tile, (int)((n + 255) / 256), ws.qpart, p.R,
-                                p.e_recip_part, p.beta, parts, energy_dev, p.d_status);
+    k_energy<<<1, 256, 0, st>>>((int)tiles, ws.e_tile, (int)((n + 255) / 256), ws.qpart,
+                                p.e_recip_count, p.e_recip_part, p.beta, parts, energy_dev,
+                                p.d_status);
     k_unsort<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ws.perm, ws.f_real, ws.f_recip,
                                                           parts, forces);
     p.launches += 2;
@@ -279,7 +302,8 @@ size_t plan_footprint(const Plan &p, int64_t n)
     b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
     b += sizeof(double) * 6 * (size_t)n + sizeof(double) * tiles + sizeof(double) * 3 * ((n + 255) / 256);
     b += uses_tc(p.precision) ? recip_tc_bytes(p, n) : recip_simt_bytes(p, n);
-    b += sizeof(double) * 2 * (size_t)p.nk + sizeof(int) * 3 * (size_t)p.nk + sizeof(RowInfo) * p.R;
+    b += sizeof(double) * 3 * (size_t)p.nk + sizeof(int) * 3 * (size_t)p.nk + sizeof(RowInfo) * p.R;
+    b += sizeof(double) * 32 * (size_t)p.R;
     return b;
 }
 
@@ -346,6 +370,7 @@ int plan_setup_host(Plan &p, double L, double beta, double rc, int kmax, int pre
     p.L = L; p.beta = beta; p.rc = rc; p.kmax = kmax; p.precision = precision;
     choose_cells(p);
     build_rows(p);
+    p.e_recip_count = uses_tc(precision) ? recip_tc_energy_parts(p) : p.R;
     return EWALD_OK;
 }
 
@@ -356,17 +381,20 @@ static cudaError_t plan_upload(Plan &p)
     cudaError_t e;
     cudaStream_t st = p.side_stream;
     if (p.R > p.cap_R) {
-        pool_free(p.rows_d, st); pool_free(p.e_recip_part, st);
-        p.rows_d = nullptr; p.e_recip_part = nullptr; p.cap_R = 0;
+        pool_free(p.rows_d, st); pool_free(p.e_recip_part, st); pool_free(p.fperm_d, st);
+        p.rows_d = nullptr; p.e_recip_part = nullptr; p.fperm_d = nullptr; p.cap_R = 0;
         if ((e = pool_alloc((void **)&p.rows_d, sizeof(RowInfo) * p.R, st)) != cudaSuccess) return e;
-        if ((e = pool_alloc((void **)&p.e_recip_part, sizeof(double) * p.R, st)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&p.fperm_d, sizeof(int) * p.R, st)) != cudaSuccess) return e;
+        // room for the partial reciprocal energies of either path (at most 32 per row)
+        if ((e = pool_alloc((void **)&p.e_recip_part, sizeof(double) * 32 * (size_t)p.R, st)) != cudaSuccess) return e;
         p.cap_R = p.R;
     }
     if (p.nk > p.cap_nk) {
-        pool_free(p.kset_d, st); pool_free(p.S_d, st);
-        p.kset_d = nullptr; p.S_d = nullptr; p.cap_nk = 0;
+        pool_free(p.kset_d, st); pool_free(p.S_d, st); pool_free(p.g_d, st);
+        p.kset_d = nullptr; p.S_d = nullptr; p.g_d = nullptr; p.cap_nk = 0;
         if ((e = pool_alloc((void **)&p.kset_d, sizeof(int) * 3 * p.nk, st)) != cudaSuccess) return e;
         if ((e = pool_alloc((void **)&p.S_d, sizeof(double) * 2 * p.nk, st)) != cudaSuccess) return e;
+        if ((e = pool_alloc((void **)&p.g_d, sizeof(double) * p.nk, st)) != cudaSuccess) return e;
         p.cap_nk = p.nk;
     }
     std::vector<int> kset(3 * (size_t)p.nk);
@@ -379,7 +407,25 @@ static cudaError_t plan_upload(Plan &p)
         }
     }
     if ((e = cudaMemcpyAsync(p.rows_d, p.rows_h.data(), sizeof(RowInfo) * p.R, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    // forward order of the rows: (m_z, m_y) ascending, so that runs of m_y are consecutive
+    std::vector<int> fperm(p.R);
+    for (int i = 0; i < p.R; ++i) fperm[i] = i;
+    std::sort(fperm.begin(), fperm.end(), [&](int a, int b) {
+        const RowInfo &x = p.rows_h[a], &y = p.rows_h[b];
+        return x.mz != y.mz ? x.mz < y.mz : x.my < y.my;
+    });
+    if ((e = cudaMemcpyAsync(p.fperm_d, fperm.data(), sizeof(int) * p.R, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(p.kset_d, kset.data(), sizeof(int) * 3 * p.nk, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    // g(k) = 4 pi exp(-k^2 / (4 beta^2)) / (V k^2) (C_k of Eq. 3), once per plan, K_half order
+    std::vector<double> g(p.nk);
+    const double tpl = 2.0 * kPi / p.L, V = p.L * p.L * p.L;
+    for (int64_t t = 0; t < p.nk; ++t) {
+        const double m2 = (double)kset[3 * t] * kset[3 * t] + (double)kset[3 * t + 1] * kset[3 * t + 1] +
+                          (double)kset[3 * t + 2] * kset[3 * t + 2];
+        const double k2 = tpl * tpl * m2;
+        g[t] = 4.0 * kPi * exp(-k2 / (4.0 * p.beta * p.beta)) / (V * k2);
+    }
+    if ((e = cudaMemcpyAsync(p.g_d, g.data(), sizeof(double) * p.nk, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.S_d, 0, sizeof(double) * 2 * p.nk, st)) != cudaSuccess) return e;
     return cudaStreamSynchronize(st);
 }
@@ -409,7 +455,9 @@ static void destroy_plan(ewald_plan *h)
         cudaStreamSynchronize(p.side_stream);
         free_workspace(p);
         pool_free(p.rows_d, p.side_stream); pool_free(p.kset_d, p.side_stream);
+        pool_free(p.fperm_d, p.side_stream);
         pool_free(p.S_d, p.side_stream); pool_free(p.e_recip_part, p.side_stream);
+        pool_free(p.g_d, p.side_stream);
         pool_free(p.energy_d, p.side_stream); pool_free(p.d_status, p.side_stream);
         pool_free(p.ws.h_pos, p.side_stream); pool_free(p.ws.h_q, p.side_stream);
         pool_free(p.ws.h_f, p.side_stream);

@@ -85,17 +85,22 @@ __global__ void k_keys(int64_t n, const double *__restrict__ pos, const double *
     }
 }
 
-// a2 (part): exclusive prefix over chunks, per cell, in place; cell totals.
+// a2 (part): exclusive prefix over chunks, per cell, in place; cell totals.  The chunk
+// counts of a cell are read 16 at a time so that the loads overlap.
 __global__ void k_colscan(int nb, int ncells, int *__restrict__ hist, int *__restrict__ total)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
     int run = 0;
-    for (int b = 0; b < nb; ++b) {
-        int64_t at = (int64_t)b * ncells + c;
-        int h = hist[at];
-        hist[at] = run;
-        run += h;
+    for (int b0 = 0; b0 < nb; b0 += 16) {
+        int h[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) h[u] = b0 + u < nb ? hist[(int64_t)(b0 + u) * ncells + c] : 0;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            if (b0 + u < nb) hist[(int64_t)(b0 + u) * ncells + c] = run;
+            run += h[u];
+        }
     }
     total[c] = run;
 }
@@ -127,34 +132,40 @@ __global__ void k_scan1(int m, const int *__restrict__ cnt, int *__restrict__ ou
     if (t == blockDim.x - 1) out[m] = part[t];
 }
 
-// a2 (part): in-order scatter of chunk b (one warp per chunk).  Running offsets per cell
-// live in shared memory when they fit, else in the chunk's histogram row.
+// a2 (part): in-order scatter of chunk b.  The whole block loads the chunk's running
+// offsets per cell and the chunk's keys into shared memory; then warp 0 walks the chunk in
+// input order, 32 particles at a time.  (When the offsets do not fit, the chunk's histogram
+// row in global memory holds them.)
 __global__ void k_scatter(int64_t n, int64_t chunk, int ncells, const int *__restrict__ key,
                           const int *__restrict__ cell_start, int *__restrict__ hist,
                           int *__restrict__ perm, int *__restrict__ key_sorted, int use_smem)
 {
-    extern __shared__ int off_s[];
+    extern __shared__ int sh[];
     const int b = blockIdx.x;
-    const int lane = threadIdx.x;
-    int *row = hist + (int64_t)b * ncells;
-    int *off = use_smem ? off_s : row;
-    for (int c = lane; c < ncells; c += 32) off[c] = row[c] + cell_start[c];
-    __syncwarp();
     const int64_t beg = (int64_t)b * chunk;
     const int64_t end = beg + chunk < n ? beg + chunk : n;
+    const int cnt = (int)(end > beg ? end - beg : 0);
+    int *keys = sh;                              // [chunk]
+    int *row = hist + (int64_t)b * ncells;
+    int *off = use_smem ? sh + chunk : row;
+    for (int c = threadIdx.x; c < ncells; c += blockDim.x) off[c] = row[c] + cell_start[c];
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) keys[i] = key[beg + i];
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t base = beg; base < end; base += 32) {
-        int64_t i = base + lane;
-        bool valid = i < end;
-        int k = valid ? key[i] : -1 - lane;   // invalid lanes match nobody
-        unsigned peers = __match_any_sync(0xffffffffu, k);
-        int rank = __popc(peers & lt);
-        int leader = __ffs(peers) - 1;
-        int start = valid ? off[k] : 0;
+    for (int base = 0; base < cnt; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < cnt;
+        const int k = valid ? keys[i] : -1 - lane;   // invalid lanes match nobody
+        const unsigned peers = __match_any_sync(0xffffffffu, k);
+        const int rank = __popc(peers & lt);
+        const int leader = __ffs(peers) - 1;
+        const int start = valid ? off[k] : 0;
         __syncwarp();
         if (valid) {
-            int slot = start + rank;
-            perm[slot] = (int)i;
+            const int slot = start + rank;
+            perm[slot] = (int)(beg + i);
             key_sorted[slot] = k;
             if (lane == leader) off[k] = start + __popc(peers);
         }
@@ -192,24 +203,24 @@ __global__ void k_pack(int64_t n, const double *__restrict__ pos, const double *
     }
 }
 
-// Tiles of up to 32 consecutive sorted particles that never leave a row of cells.
-__global__ void k_row_tiles(int nrows, int nc, const int *__restrict__ cell_start,
+// Tiles of up to `ts` consecutive sorted particles that never leave a row of cells.
+__global__ void k_row_tiles(int nrows, int nc, int ts, const int *__restrict__ cell_start,
                             int *__restrict__ tcount)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     int cnt = cell_start[(r + 1) * nc] - cell_start[r * nc];
-    tcount[r] = (cnt + 31) / 32;
+    tcount[r] = (cnt + ts - 1) / ts;
 }
 
-__global__ void k_emit_tiles(int nrows, int nc, const int *__restrict__ cell_start,
+__global__ void k_emit_tiles(int nrows, int nc, int ts, const int *__restrict__ cell_start,
                              const int *__restrict__ toff, int2 *__restrict__ tiles)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nrows) return;
     int b = cell_start[r * nc];
     int o = toff[r], e = toff[r + 1];
-    for (int t = o; t < e; ++t) tiles[t] = make_int2(r, b + 32 * (t - o));
+    for (int t = o; t < e; ++t) tiles[t] = make_int2(r, b + ts * (t - o));
 }
 
 }  // namespace
@@ -229,14 +240,15 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
                                    ws.key, ws.hist, ws.qpart, p.d_status);
     k_colscan<<<(p.ncells + 255) / 256, 256, 0, st>>>(nb, p.ncells, ws.hist, ws.cell_total);
     k_scan1<<<1, 1024, 0, st>>>(p.ncells, ws.cell_total, ws.cell_start);
-    const int use_smem = p.ncells <= 48 * 1024;
-    size_t smem = use_smem ? sizeof(int) * (size_t)p.ncells : 0;
+    const size_t key_bytes = sizeof(int) * (size_t)chunk;
+    const int use_smem = key_bytes + sizeof(int) * (size_t)p.ncells <= 200 * 1024;
+    size_t smem = key_bytes + (use_smem ? sizeof(int) * (size_t)p.ncells : 0);
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_scatter<<<nb, 32, smem, st>>>(n, chunk, p.ncells, ws.key, ws.cell_start, ws.hist, ws.perm,
-                                    ws.key_sorted, use_smem);
+    k_scatter<<<nb, 256, smem, st>>>(n, chunk, p.ncells, ws.key, ws.cell_start, ws.hist, ws.perm,
+                                     ws.key_sorted, use_smem);
     const bool need64 = p.precision == EWALD_FP64;
     const bool need32 = !need64;
     k_pack<<<(int)((n + 255) / 256), 256, 0, st>>>(n, pos, q, ws.perm, ws.key_sorted, p.L,
@@ -244,9 +256,10 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
                                                    need64 ? ws.pl64 : nullptr,
                                                    need32 ? ws.pl32 : nullptr, ws.pu);
     const int nrows = p.nc * p.nc;
-    k_row_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ws.cell_start, ws.tile_count);
+    const int ts = real_tile_size(p);
+    k_row_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ts, ws.cell_start, ws.tile_count);
     k_scan1<<<1, 1024, 0, st>>>(nrows, ws.tile_count, ws.tile_off);
-    k_emit_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ws.cell_start, ws.tile_off,
+    k_emit_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ts, ws.cell_start, ws.tile_off,
                                                       ws.tiles);
     p.launches += 8;
     return cudaGetLastError();

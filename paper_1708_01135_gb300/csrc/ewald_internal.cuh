@@ -89,9 +89,12 @@ struct Plan {
     int64_t nk = 0;
     std::vector<RowInfo> rows_h;
     RowInfo *rows_d = nullptr;
+    int *fperm_d = nullptr;      // [R] rows in (m_z, m_y) order -> row index (tensor-core forward)
     int *kset_d = nullptr;       // [nk][3]
     double *S_d = nullptr;       // [nk][2] last structure factor
-    double *e_recip_part = nullptr;  // per-row partial energies [R]
+    double *g_d = nullptr;       // [nk] g(k) = 4 pi exp(-k^2 / (4 beta^2)) / (V k^2), K_half order
+    double *e_recip_part = nullptr;  // partial reciprocal energies [e_recip_count]
+    int e_recip_count = 0;       // entries of e_recip_part summed by the finalize step
     double *energy_d = nullptr;  // [4] internal energies for the synchronous entry points
     int cap_R = 0;               // rows the row-sized arrays hold
     int64_t cap_nk = 0;          // modes the k-sized arrays hold
@@ -128,20 +131,17 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
 // a4: real-space pairs into ws.f_real / ws.e_tile (sorted order).
 cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st);
 int64_t real_tile_capacity(const Plan &p, int64_t n);
+int real_tile_size(const Plan &p);          // particles per real-space tile (cell mode: 8)
 // a5-a8 on CUDA cores (FP64 or FP32): S(k), energy, back-scatter into ws.f_recip.
 cudaError_t launch_recip_simt(Plan &p, int64_t n, cudaStream_t st);
 size_t recip_simt_bytes(const Plan &p, int64_t n);
 cudaError_t alloc_recip_simt(Plan &p, int64_t n);
 void free_recip_simt(Plan &p);
-// a6-a7 shared by both paths: FP64 reduction of FP32 forward partials laid out
-// [nks][R][k_max + 1][4] (T_rr, T_ri, T_ir, T_ii), S(k), per-row energies and the FP32
-// back-scatter coefficient matrix G' [2R][ncol].
-cudaError_t launch_sreduce_f32(Plan &p, int nks, const float *spart, float *gmat, int ncol,
-                               cudaStream_t st);
 // a5-a8 on the tcgen05 tensor cores (split FP16/BF16 operands).
 cudaError_t launch_recip_tc(Plan &p, int64_t n, cudaStream_t st);
 cudaError_t alloc_recip_tc(Plan &p, int64_t n);
 size_t recip_tc_bytes(const Plan &p, int64_t n);
+int recip_tc_energy_parts(const Plan &p);   // entries of the partial reciprocal energies
 void free_recip_tc(Plan &p);
 // a9: self term, totals, unsort to caller order.
 cudaError_t launch_finalize(Plan &p, int64_t n, const double *q, double *forces,

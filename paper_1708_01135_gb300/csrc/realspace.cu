@@ -6,10 +6,14 @@
 //   E_real = 1/2 sum_i q_i phi_i            (r_ij = r_i - r_j, minimum image)
 //
 // GPU design (templated on FP64 and FP32 arithmetic):
-//   * One warp owns a tile of up to 32 consecutive sorted particles of one row of cells
-//     (fixed c_y, c_z); every lane owns one target particle i and accumulates its own force,
-//     so no two threads ever write the same particle (the paper's rule that a loop writes
-//     only its own particle, Section 3.2.3, with no atomics).
+//   * One warp owns a tile of up to 8 consecutive sorted particles of one row of cells
+//     (fixed c_y, c_z).  Lane = (target i, partner group g): the 8 targets each have 4
+//     lanes that take every 4th partner; the 4 partial sums of a target are combined with
+//     shuffles at the end, so every target's force is written by one lane and no two threads
+//     ever write the same particle (the paper's rule that a loop writes only its own particle,
+//     Section 3.2.3, with no atomics).  Narrow tiles keep the candidate set close to the
+//     cutoff sphere and give 4 warps per 32 particles, enough to hide the latency of the
+//     pair arithmetic.
 //   * The candidate partners j of a tile are the cells of the neighbour rows (c_y + dy,
 //     c_z + dz), |dy|, |dz| <= w, in the x range of the tile widened by the reach left for
 //     that row.  A run of cells along x is a contiguous range of the sorted array, so it is
@@ -29,7 +33,9 @@ namespace ew {
 namespace {
 
 constexpr int kWarps = 4;      // warps (tiles) per block
-constexpr int kCap = 256;      // particles per staging buffer
+constexpr int kCap = 64;       // particles per staging buffer (cell mode)
+constexpr int kCapAll = 256;   // particles per staging buffer (all-pairs mode)
+constexpr int kTile = 8;       // targets per warp tile (cell mode)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -104,7 +110,6 @@ template <class T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4_32a; };
 
-__device__ __forceinline__ float erfc_t(float x) { return erfcf(x); }
 __device__ __forceinline__ double erfc_t(double x) { return erfc(x); }
 __device__ __forceinline__ float exp_t(float x) { return __expf(x); }
 __device__ __forceinline__ double exp_t(double x) { return exp(x); }
@@ -116,6 +121,26 @@ struct PairAcc {
     T fx, fy, fz, phi;
 };
 
+// erfc(x) = exp(-x^2) * t * exp(P(t)), t = 1 / (1 + x / 2), x >= 0: the Chebyshev fit
+// "erfcc" of Numerical Recipes in C (2nd ed., Sec. 6.2), fractional error below 1.2e-7 in
+// exact arithmetic (checked against the double-precision erfc in tests/test_abi_cpu.py).
+// The caller supplies g = exp(-x^2), which the force term needs as well.
+__device__ __forceinline__ float erfc_from_gauss(float x, float g)
+{
+    const float t = __fdividef(1.0f, 1.0f + 0.5f * x);
+    float p = 0.17087277f;
+    p = fmaf(p, t, -0.82215223f);
+    p = fmaf(p, t, 1.48851587f);
+    p = fmaf(p, t, -1.13520398f);
+    p = fmaf(p, t, 0.27886807f);
+    p = fmaf(p, t, -0.18628806f);
+    p = fmaf(p, t, 0.09678418f);
+    p = fmaf(p, t, 0.37409196f);
+    p = fmaf(p, t, 1.00002368f);
+    p = fmaf(p, t, -1.26551223f);
+    return t * g * __expf(p);
+}
+
 // One candidate pair: target at the origin shifted by (xi, yi, zi), partner p.
 template <class T, class T4>
 __device__ __forceinline__ void pair(PairAcc<T> &a, const T4 &p, T xi, T yi, T zi, T rc2,
@@ -126,8 +151,10 @@ __device__ __forceinline__ void pair(PairAcc<T> &a, const T4 &p, T xi, T yi, T z
     if (r2 < rc2 && r2 > T(0)) {
         const T rinv = rsqrt_t(r2);
         const T r = r2 * rinv;
-        const T e = erfc_t(beta * r) * rinv;                // erfc(beta r) / r
         const T g = exp_t(nb2 * r2);                        // exp(-beta^2 r^2)
+        T e;                                                // erfc(beta r) / r
+        if constexpr (sizeof(T) == 4) e = erfc_from_gauss(beta * r, g) * rinv;
+        else e = erfc_t(beta * r) * rinv;
         const T s = p.w * (e + two_b_rpi * g) * rinv * rinv;
         a.phi += p.w * e;
         a.fx += s * dx;
@@ -230,8 +257,9 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     const int2 td = tiles[tile];
     const int row = td.x, first = td.y;
     const int row_end = cell_start[(row + 1) * nc];
-    const int last = min(first + 32, row_end) - 1;
-    const int i = first + lane;
+    const int last = min(first + kTile, row_end) - 1;
+    const int ti = lane & (kTile - 1), g = lane >> 3;   // target slot, partner group
+    const int i = first + ti;
     const bool valid = i <= last;
     const T4 pi = pl[valid ? i : last];
     const int cxi = key_sorted[valid ? i : last] % nc;
@@ -270,21 +298,25 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         const T yi = pi.y - T(cur.dy) * side;
         const T zi = pi.z - T(cur.dz) * side;
         const T4 *sb = buf[b];
-        // walk the cells of the run that overlap [g0, g0 + cnt)
+        // walk the cells of the run that overlap [g0, g0 + cnt); inside a run the cell index
+        // advances with u without wrapping, and each cell ends where the next one starts
         int u = cur.u0;
         const int cend = cur.g0 + cur.cnt;
+        int c = u < 0 ? u + nc : (u >= nc ? u - nc : u);
+        const int *cs = cell_start + cur.rowbase;
+        int cb = cs[c];
         while (true) {
-            const int c = ((u % nc) + nc) % nc;
-            const int cb = cell_start[cur.rowbase + c];
-            const int ce = cell_start[cur.rowbase + c + 1];
+            const int ce = cs[c + 1];
             if (ce > cur.g0) {
                 const int jb = (cb > cur.g0 ? cb : cur.g0) - cur.g0;
                 const int je = (ce < cend ? ce : cend) - cur.g0;
                 const T xi = pi.x - T(u - cxi) * side;
-                for (int j = jb; j < je; ++j) pair<T, T4>(acc, sb[j], xi, yi, zi, rc2, beta, nb2, two_b_rpi);
+                for (int j = jb + g; j < je; j += 4) pair<T, T4>(acc, sb[j], xi, yi, zi, rc2, beta, nb2, two_b_rpi);
             }
             if (ce >= cend) break;
+            cb = ce;
             ++u;
+            ++c;
         }
         __syncwarp();
         cur = nxt;
@@ -297,13 +329,21 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         warp_wait(&bar[b ^ 1], phase[b ^ 1]);
         return;
     }
+    // combine the 4 partner groups of every target (lanes ti, ti + 8, ti + 16, ti + 24)
+#pragma unroll
+    for (int o = 8; o < 32; o <<= 1) {
+        acc.fx += __shfl_xor_sync(0xffffffffu, acc.fx, o);
+        acc.fy += __shfl_xor_sync(0xffffffffu, acc.fy, o);
+        acc.fz += __shfl_xor_sync(0xffffffffu, acc.fz, o);
+        acc.phi += __shfl_xor_sync(0xffffffffu, acc.phi, o);
+    }
     const double qi = (double)pi.w;
-    if (valid) {
+    if (valid && g == 0) {
         f_out[3 * (int64_t)i + 0] = qi * (double)acc.fx;
         f_out[3 * (int64_t)i + 1] = qi * (double)acc.fy;
         f_out[3 * (int64_t)i + 2] = qi * (double)acc.fz;
     }
-    double e = valid ? qi * (double)acc.phi : 0.0;
+    double e = (valid && g == 0) ? qi * (double)acc.phi : 0.0;
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
     if (lane == 0) e_tile[tile] = e;
 }
@@ -321,8 +361,8 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
     __shared__ __align__(8) uint64_t bars[kWarps][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T4 *buf[2];
-    buf[0] = reinterpret_cast<T4 *>(smem_raw) + (size_t)warp * 2 * kCap;
-    buf[1] = buf[0] + kCap;
+    buf[0] = reinterpret_cast<T4 *>(smem_raw) + (size_t)warp * 2 * kCapAll;
+    buf[1] = buf[0] + kCapAll;
     uint64_t *bar = bars[warp];
     if (lane == 0) {
         mbar_init(&bar[0], 1);
@@ -339,9 +379,9 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
     PairAcc<T> acc{T(0), T(0), T(0), T(0)};
     const T nb2 = -beta * beta;
     uint32_t phase[2] = {0u, 0u};
-    const int nchunks = (n + kCap - 1) / kCap;
+    const int nchunks = (n + kCapAll - 1) / kCapAll;
     if (lane == 0) {
-        int cnt = min(kCap, n);
+        int cnt = min(kCapAll, n);
         mbar_expect_tx(&bar[0], cnt * (uint32_t)sizeof(T4));
         tma_bulk_g2s(buf[0], pl, cnt * (uint32_t)sizeof(T4), &bar[0]);
     }
@@ -349,14 +389,14 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
     int b = 0;
     for (int c = 0; c < nchunks; ++c) {
         if (c + 1 < nchunks && lane == 0) {
-            int g = (c + 1) * kCap, cnt = min(kCap, n - g);
+            int g = (c + 1) * kCapAll, cnt = min(kCapAll, n - g);
             fence_proxy_async();
             mbar_expect_tx(&bar[b ^ 1], cnt * (uint32_t)sizeof(T4));
             tma_bulk_g2s(buf[b ^ 1], pl + g, cnt * (uint32_t)sizeof(T4), &bar[b ^ 1]);
         }
         if (!warp_wait(&bar[b], phase[b])) { ok = false; break; }
         phase[b] ^= 1u;
-        const int cnt = min(kCap, n - c * kCap);
+        const int cnt = min(kCapAll, n - c * kCapAll);
         const T4 *sb = buf[b];
         for (int j = 0; j < cnt; ++j) {
             T4 p = sb[j];
@@ -392,7 +432,7 @@ template <class T>
 cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, cudaStream_t st)
 {
     Workspace &ws = p.ws;
-    const size_t smem = (size_t)kWarps * 2 * kCap * sizeof(typename Vec4<T>::type);
+    const size_t smem = (size_t)kWarps * 2 * (p.w == 0 ? kCapAll : kCap) * sizeof(typename Vec4<T>::type);
     const T beta = (T)p.beta, rc2 = (T)(p.rc * p.rc);
     const T tbr = (T)(2.0 * p.beta / sqrt(kPi));
     cudaError_t e;
@@ -421,8 +461,10 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
 int64_t real_tile_capacity(const Plan &p, int64_t n)
 {
     if (p.w == 0) return (n + 31) / 32;
-    return n / 32 + (int64_t)p.nc * p.nc + 1;
+    return n / kTile + (int64_t)p.nc * p.nc + 1;
 }
+
+int real_tile_size(const Plan &p) { return p.w == 0 ? 32 : kTile; }
 
 cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st)
 {

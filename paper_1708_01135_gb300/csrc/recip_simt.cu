@@ -153,18 +153,11 @@ k_sfac(int64_t n, int64_t cap, int nks, int R, int kmax, const RowInfo *__restri
     }
 }
 
-__device__ __forceinline__ double coef_g(int mx, int my, int mz, double L, double beta)
-{
-    const double tpl = 2.0 * kPi / L;
-    const double k2 = tpl * tpl * (double)(mx * mx + my * my + mz * mz);
-    return 4.0 * kPi * exp(-k2 / (4.0 * beta * beta)) / (L * L * L * k2);
-}
-
 // a6 (reduction over K splits, fixed order) + a7 (per-k energy, coefficient matrix).
 // One block per row, thread m = 0..kmax.
 template <class T>
 __global__ void k_sreduce(int nks, int R, int kmax, const RowInfo *__restrict__ rows,
-                          const T *__restrict__ spart, double L, double beta,
+                          const T *__restrict__ spart, const double *__restrict__ gk,
                           double *__restrict__ S, double *__restrict__ e_row,
                           T *__restrict__ gmat, int ncol)
 {
@@ -186,14 +179,14 @@ __global__ void k_sreduce(int nks, int R, int kmax, const RowInfo *__restrict__ 
         double snr = t[0] + t[3], sni = t[2] - t[1];                      // S(-m)
         double gp = 0.0, gn = 0.0;
         if (vp) {
-            gp = coef_g(m, ri.my, ri.mz, L, beta);
             int idx = origin_row ? ri.koff + (m - 1) : ri.koff + ri.nxmax + m;
+            gp = gk[idx];
             S[2 * (int64_t)idx] = spr; S[2 * (int64_t)idx + 1] = spi;
             e += gp * (spr * spr + spi * spi);
         }
         if (vn && m > 0) {
-            gn = coef_g(-m, ri.my, ri.mz, L, beta);
             int idx = ri.koff + ri.nxmax - m;
+            gn = gk[idx];
             S[2 * (int64_t)idx] = snr; S[2 * (int64_t)idx + 1] = sni;
             e += gn * (snr * snr + sni * sni);
         }
@@ -366,8 +359,8 @@ cudaError_t launch_t(Plan &p, int64_t n, cudaStream_t st)
     prof_mark(p, kEvFwdEnd, st);
     const int nb = 2 * p.kmax + 1;
     const int ncol = 3 * nb;
-    k_sreduce<T><<<p.R, 128, 0, st>>>(nks, p.R, p.kmax, p.rows_d, (const T *)ws.spart, p.L,
-                                      p.beta, p.S_d, p.e_recip_part, (T *)ws.gmat, ncol);
+    k_sreduce<T><<<p.R, 128, 0, st>>>(nks, p.R, p.kmax, p.rows_d, (const T *)ws.spart, p.g_d,
+                                      p.S_d, p.e_recip_part, (T *)ws.gmat, ncol);
     prof_mark(p, kEvCoefEnd, st);
     const int npass = bscat_passes(p.kmax);
     dim3 gb((unsigned)((n + kBP - 1) / kBP), 3, npass);
@@ -383,14 +376,6 @@ cudaError_t launch_t(Plan &p, int64_t n, cudaStream_t st)
 }
 
 }  // namespace
-
-cudaError_t launch_sreduce_f32(Plan &p, int nks, const float *spart, float *gmat, int ncol,
-                               cudaStream_t st)
-{
-    k_sreduce<float><<<p.R, 128, 0, st>>>(nks, p.R, p.kmax, p.rows_d, spart, p.L, p.beta, p.S_d,
-                                          p.e_recip_part, gmat, ncol);
-    return cudaGetLastError();
-}
 
 size_t recip_simt_bytes(const Plan &p, int64_t n)
 {

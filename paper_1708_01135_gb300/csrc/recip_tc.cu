@@ -21,18 +21,27 @@
 // two before the FP16 split so that its largest entry sits near 2^14 (FP16 range); the
 // epilogue removes the scale.
 //
-// Kernel structure (one CTA per tile, warp-specialised, mbarrier pipeline in shared memory):
-//   warps 0-3  produce the generated operand of each stage, then run the epilogue (warp w
-//              owns TMEM lanes 32w..32w+31, i.e. rows of the accumulator)
-//   warp 4     (back-scatter) streams the pre-packed G' tiles with bulk TMA copies
-//   warp 5     (warp 4 in the forward kernel) issues tcgen05.mma from one thread and
-//              releases stages with tcgen05.commit
+// Accumulation accuracy.  The rounding error of the tensor cores' FP32 accumulation grows
+// with the number of products summed into one accumulator, so the forward product (a sum
+// over all particles) accumulates only 128 particles per TMEM accumulator: two accumulator
+// buffers alternate, and drain warps add every finished buffer into an FP32 running sum in
+// shared memory (rounded to nearest) while the tensor cores fill the other.  The back-scatter
+// (a sum over rows) processes rows in order of decreasing m_y^2 + m_z^2, so the coefficients
+// grow along the sum.
+//
+// Kernel structure (warp-specialised, mbarrier pipeline in shared memory):
+//   forward:      warps 0-7 generate A and B of each stage; warps 8-11 drain TMEM; warp 12
+//                 stages the particle data of each stage with a bulk TMA copy; warp 13
+//                 issues tcgen05.mma (one thread) and releases stages with tcgen05.commit.
+//   back-scatter: warps 0-7 generate A (one particle per thread) and then run the
+//                 epilogue; warp 8 streams the pre-packed G' tiles (with their row headers)
+//                 by bulk TMA; warp 9 issues tcgen05.mma.
 // Shared-memory operand layout (no swizzle, K-major): 8x8 core matrices of 128 contiguous
 // bytes, ordered [row / 8][k / 8][row % 8][k % 8]; descriptor LBO = 128 B (next core matrix
 // along K), SBO = (K_stage / 8) * 128 B (next 8-row group).
-// Every mbarrier wait is bounded (~1 s of globaltimer); a timeout sets a status bit and
-// lets every role leave its loop; the MMA thread's final commit is always issued and
-// waited for before TMEM is released.
+// Every mbarrier wait is bounded (~1 s of globaltimer); a timeout sets a status bit and lets
+// every role leave its loop; copies in flight and the last MMAs are waited for before the
+// CTA releases TMEM and exits.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -44,15 +53,15 @@ namespace ew {
 namespace {
 
 // ---- tiling ---------------------------------------------------------------------------
-constexpr int kFK = 64;        // forward: particles (K) per stage
-constexpr int kFStages = 2;
-constexpr int kFMT = 2;        // forward: M tiles (64 rows r = 128 matrix rows) per CTA
-constexpr int kFThreads = 160;
+constexpr int kFK = 32;        // forward: particles (K) per stage
+constexpr int kFChunk = 4;     // forward: stages per TMEM accumulator (128 particles)
+constexpr int kFThreads = 448; // forward: 14 warps
 constexpr int kBK = 32;        // back-scatter: real K per stage (16 rows r)
 constexpr int kBStages = 3;
 constexpr int kBMT = 2;        // back-scatter: M tiles of 128 particles per CTA
-constexpr int kBThreads = 192;
+constexpr int kBThreads = 320; // back-scatter: 10 warps
 constexpr int kPassMax = 256;  // N columns per back-scatter pass (one MMA)
+constexpr int kHdr = 128;      // row header of every packed G' K-block: 16 x (m_y, m_z)
 
 // ---- PTX wrappers -----------------------------------------------------------------------
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -70,12 +79,14 @@ __device__ __forceinline__ void mb_expect_tx(uint64_t *b, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware (up to ~20 us)
+// until the phase completes instead of re-issuing the poll
 __device__ __forceinline__ uint32_t mb_try(uint64_t *b, uint32_t parity)
 {
     uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+                 : "=r"(ok) : "r"(su32(b)), "r"(parity), "r"(20000u) : "memory");
     return ok;
 }
 __device__ __forceinline__ uint64_t gtime()
@@ -92,17 +103,6 @@ __device__ __forceinline__ void tma_bulk(void *dst, const void *src, uint32_t by
 }
 
 constexpr uint64_t kWaitNs = 1000000000ull;
-
-// One-thread bounded wait; false on timeout (sets *abort) or when another role aborted.
-__device__ __forceinline__ bool wait1(uint64_t *b, uint32_t parity, volatile int *abort)
-{
-    const uint64_t t0 = gtime();
-    while (!mb_try(b, parity)) {
-        if (*abort) return false;
-        if (gtime() - t0 > kWaitNs) { *abort = 1; return false; }
-    }
-    return true;
-}
 
 // Whole-warp bounded wait.
 __device__ __forceinline__ bool waitw(uint64_t *b, uint32_t parity, volatile int *abort)
@@ -212,21 +212,34 @@ __device__ __forceinline__ void st16(unsigned char *base, uint32_t off, uint32_t
 }
 
 // ---- forward: structure-factor partials ------------------------------------------------
-// grid (M groups of kFMT tiles, K splits); block kFThreads.
-// spart layout [ks][R][k_max + 1][4] = (T_rr, T_ri, T_ir, T_ii), FP32.
-template <bool BF>
+// grid (M groups of MT tiles of 64 rows r, K splits); block kFThreads.
+// Output Dpart[(ks * ntiles + tile) * NF * 128 + col * 128 + row] (FP32): row < 64 holds the
+// real part of A for row r = tile * 64 + row, row >= 64 the imaginary part.
+template <int MT, bool BF>
 __global__ void __launch_bounds__(kFThreads, 1)
-k_fwd_tc(int n, int R, int kmax, int NF, int per, const RowInfo *__restrict__ rows,
-         const uint4 *__restrict__ pu, float *__restrict__ spart, int *__restrict__ status)
+k_fwd_tc(int n, int R, int kmax, int NF, int per, int ntiles, int S, const RowInfo *__restrict__ rows,
+         const int *__restrict__ fperm, const unsigned char *__restrict__ xblob,
+         float *__restrict__ dpart, int *__restrict__ status)
 {
+    // S: pipeline stages (2 or 3, as many as fit in shared memory)
+    constexpr int BUF = 256;                     // TMEM columns per accumulator buffer
+    constexpr int KC = kFK / 8;                  // K chunks per stage
     extern __shared__ __align__(1024) unsigned char sm[];
     const int A_BYTES = 128 * kFK * 2;
     const int B_BYTES = NF * kFK * 2;
-    const int STAGE = kFMT * 2 * A_BYTES + 2 * B_BYTES;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sm + kFStages * STAGE);
-    uint64_t *empty = full + kFStages;
-    uint64_t *accf = empty + kFStages;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(accf + 1);
+    const int P_OFF = MT * 2 * A_BYTES;          // stage blob: particles, then B hi, B lo
+    const int B_OFF = P_OFF + kFK * 16;
+    const int BLOB = kFK * 16 + 2 * B_BYTES;
+    const int STAGE = P_OFF + BLOB;
+    float *acc = reinterpret_cast<float *>(sm + S * STAGE);             // [MT][NF][128]
+    int2 *rowc = reinterpret_cast<int2 *>(acc + MT * NF * 128);         // [MT * 64]
+    uint64_t *pfull = reinterpret_cast<uint64_t *>(rowc + MT * 64);
+    uint64_t *full = pfull + S;
+    uint64_t *empty = full + S;
+    uint64_t *accf = empty + S;      // [2]
+    uint64_t *acce = accf + 2;       // [2]
+    uint64_t *mmad = acce + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(mmad + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -234,188 +247,305 @@ k_fwd_tc(int n, int R, int kmax, int NF, int per, const RowInfo *__restrict__ ro
     const int p0 = ks * per;
     const int p1 = min(n, p0 + per);
     const int nst = (p1 - p0 + kFK - 1) / kFK;
-    const int kchunks = kFK / 8;
+    const int nch = (nst + kFChunk - 1) / kFChunk;
 
     if (t == 0) {
-        for (int s = 0; s < kFStages; ++s) { mb_init(&full[s], 128); mb_init(&empty[s], 1); }
-        mb_init(accf, 1);
+        for (int s = 0; s < S; ++s) { mb_init(&pfull[s], 1); mb_init(&full[s], 256); mb_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mb_init(&accf[b], 1); mb_init(&acce[b], 128); }
+        mb_init(mmad, 1);
         *abort = 0;
         mb_fence_init();
     }
-    if (warp == 0) { tm_alloc(tslot, 256); tm_relinquish(); }
-    // zero the padding columns of B once (no stage writes them)
-    for (int u = t; u < kFStages * 2 * (NF - (2 * kmax + 1)) * kchunks; u += kFThreads) {
-        int kc = u % kchunks, rest = u / kchunks;
-        int col = 2 * kmax + 1 + rest % (NF - (2 * kmax + 1));
-        int sp = rest / (NF - (2 * kmax + 1));    // stage * 2 + part
-        unsigned char *bt = sm + (sp >> 1) * STAGE + kFMT * 2 * A_BYTES + (sp & 1) * B_BYTES;
-        st16(bt, tile_off(col, kc, kchunks), 0u, 0u, 0u, 0u);
+    for (int i = t; i < MT * 64; i += kFThreads) {
+        const int gr = mgroup * MT * 64 + i;
+        int2 v = make_int2(0, 0x40000000);   // padding rows: never continue a run, zero charge
+        if (gr < R) { const RowInfo ri = rows[fperm[gr]]; v = make_int2(ri.my, ri.mz); }
+        rowc[i] = v;
     }
+    if (warp == 0) { tm_alloc(tslot, 512); tm_relinquish(); }
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tslot;
 
-    if (t < 128) {
+    if (t < 256) {
         // ---- producers ----
+        // A: thread t owns row slot rl = t % 64 and particle chunk c = (t / 64) % 4 of every
+        //    M tile (MT units, computed together for instruction-level parallelism)
+        // (the charges q_j multiply the B operand, built by k_xgen)
+        const int rl = t & 63, c = (t >> 6) & 3;
+        int2 rc[MT];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) rc[mt] = rowc[mt * 64 + rl];
         for (int it = 0; it < nst; ++it) {
-            const int s = it % kFStages, u = it / kFStages;
+            const int s = it % S, u = it / S;
             if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
+            if (!waitw(&pfull[s], u & 1, abort)) break;
             unsigned char *st = sm + s * STAGE;
-            const int j0 = p0 + it * kFK;
-            // A: (row r', particle chunk c), rows [0, 64) real parts, [64, 128) imaginary
-#pragma unroll 1
-            for (int mt = 0; mt < kFMT; ++mt) {
-                unsigned char *ahi = st + (mt * 2 + 0) * A_BYTES;
-                unsigned char *alo = st + (mt * 2 + 1) * A_BYTES;
-#pragma unroll 1
-                for (int v = 0; v < 4; ++v) {
-                    const int unit = t + 128 * v;
-                    const int rl = unit & 63, c = unit >> 6;
-                    const int gr = (mgroup * kFMT + mt) * 64 + rl;
-                    float re[8], im[8];
-                    if (gr < R) {
-                        const RowInfo ri = rows[gr];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int j = j0 + 8 * c + e;
-                            re[e] = 0.f; im[e] = 0.f;
-                            if (j < p1) {
-                                const uint4 pj = pu[j];
-                                float cs, sn;
-                                phase((uint32_t)ri.my * pj.y + (uint32_t)ri.mz * pj.z, cs, sn);
-                                const float qj = __uint_as_float(pj.w);
-                                re[e] = qj * cs; im[e] = qj * sn;
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) { re[e] = 0.f; im[e] = 0.f; }
-                    }
-                    uint32_t h[4], l[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) split2<BF>(re[2 * e], re[2 * e + 1], h[e], l[e]);
-                    st16(ahi, tile_off(rl, c, kchunks), h[0], h[1], h[2], h[3]);
-                    st16(alo, tile_off(rl, c, kchunks), l[0], l[1], l[2], l[3]);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) split2<BF>(im[2 * e], im[2 * e + 1], h[e], l[e]);
-                    st16(ahi, tile_off(64 + rl, c, kchunks), h[0], h[1], h[2], h[3]);
-                    st16(alo, tile_off(64 + rl, c, kchunks), l[0], l[1], l[2], l[3]);
-                }
-            }
-            // B: X_j[m] = e^{i k_x x_j}: column m = Re, column k_max + m = Im (m >= 1)
-            unsigned char *bhi = st + kFMT * 2 * A_BYTES;
-            unsigned char *blo = bhi + B_BYTES;
-#pragma unroll 1
-            for (int unit = t; unit < (kmax + 1) * kchunks; unit += 128) {
-                const int m = unit / kchunks, c = unit % kchunks;
-                float re[8], im[8];
+            const uint4 *P = reinterpret_cast<const uint4 *>(st + P_OFF);
+            const int jn = p1 - (p0 + it * kFK);          // valid particles in this stage
+            {
+                float re[MT][8], im[MT][8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const int j = j0 + 8 * c + e;
-                    re[e] = 0.f; im[e] = 0.f;
-                    if (j < p1) {
-                        const uint4 pj = pu[j];
-                        phase((uint32_t)m * pj.x, re[e], im[e]);
+                    const int j = 8 * c + e;
+                    const uint4 pj = P[j < jn ? j : 0];
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        float cs, sn;
+                        phase((uint32_t)rc[mt].x * pj.y + (uint32_t)rc[mt].y * pj.z, cs, sn);
+                        re[mt][e] = j < jn ? cs : 0.f; im[mt][e] = j < jn ? sn : 0.f;
                     }
                 }
-                uint32_t h[4], l[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) split2<BF>(re[2 * e], re[2 * e + 1], h[e], l[e]);
-                st16(bhi, tile_off(m, c, kchunks), h[0], h[1], h[2], h[3]);
-                st16(blo, tile_off(m, c, kchunks), l[0], l[1], l[2], l[3]);
-                if (m >= 1) {
+                for (int mt = 0; mt < MT; ++mt) {
+                    unsigned char *ahi = st + (mt * 2) * A_BYTES;
+                    uint32_t h[4], l[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) split2<BF>(im[2 * e], im[2 * e + 1], h[e], l[e]);
-                    st16(bhi, tile_off(kmax + m, c, kchunks), h[0], h[1], h[2], h[3]);
-                    st16(blo, tile_off(kmax + m, c, kchunks), l[0], l[1], l[2], l[3]);
+                    for (int e = 0; e < 4; ++e) split2<BF>(re[mt][2 * e], re[mt][2 * e + 1], h[e], l[e]);
+                    st16(ahi, tile_off(rl, c, KC), h[0], h[1], h[2], h[3]);
+                    st16(ahi + A_BYTES, tile_off(rl, c, KC), l[0], l[1], l[2], l[3]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) split2<BF>(im[mt][2 * e], im[mt][2 * e + 1], h[e], l[e]);
+                    st16(ahi, tile_off(64 + rl, c, KC), h[0], h[1], h[2], h[3]);
+                    st16(ahi + A_BYTES, tile_off(64 + rl, c, KC), l[0], l[1], l[2], l[3]);
                 }
             }
             fence_async_smem();
             mb_arrive(&full[s]);
         }
-    } else if (warp == 4) {
-        // ---- MMA issuer: the whole warp follows the loop, lane 0 issues ----
-        const uint32_t idesc = idesc_f16(128, NF, BF);
-        const uint32_t sbo = kchunks * 128;
+    } else if (t < 384) {
+        // ---- drain warps: TMEM accumulator buffer -> FP32 running sum in shared memory ----
+        const int row = t - 256;                     // TMEM lane (warp 8 + q owns lanes 32q..)
+        for (int i = 0; i < MT * NF; ++i) acc[i * 128 + row] = 0.f;
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int b = ch & 1;
+            if (!waitw(&accf[b], (ch >> 1) & 1, abort)) break;
+            tc_after();
+#pragma unroll 1
+            for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll 1
+                for (int c0 = 0; c0 < NF; c0 += 16) {
+                    float v[16];
+                    tm_ld16(tmem + lanes + b * BUF + mt * 128 + c0, v);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) acc[(mt * NF + c0 + jj) * 128 + row] += v[jj];
+                }
+            }
+            tc_before();
+            mb_arrive(&acce[b]);
+        }
+        volatile int no_abort = 0;
+        waitw(mmad, 0, &no_abort);
+        if (!*abort) {
+            for (int mt = 0; mt < MT; ++mt) {
+                const int tile = mgroup * MT + mt;
+                if (tile >= ntiles) continue;
+                float *o = dpart + ((int64_t)ks * ntiles + tile) * NF * 128;
+                for (int col = 0; col < NF; ++col) o[col * 128 + row] = acc[(mt * NF + col) * 128 + row];
+            }
+        }
+    } else if (warp == 12) {
+        // ---- TMA: particle data of every stage ----
+        int issued = 0;
         for (int it = 0; it < nst; ++it) {
-            const int s = it % kFStages, u = it / kFStages;
+            const int s = it % S, u = it / S;
+            if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
+            if (lane == 0) {
+                const int64_t gst = (int64_t)(p0 / kFK) + it;        // global stage index
+                mb_expect_tx(&pfull[s], (uint32_t)BLOB);
+                tma_bulk(sm + s * STAGE + P_OFF, xblob + gst * BLOB, (uint32_t)BLOB, &pfull[s]);
+            }
+            __syncwarp();
+            issued = it + 1;
+        }
+        for (int it = issued - S < 0 ? 0 : issued - S; it < issued; ++it) {
+            volatile int no_abort = 0;
+            waitw(&pfull[it % S], (it / S) & 1, &no_abort);
+        }
+    } else if (warp == 13) {
+        // ---- MMA issuer ----
+        const uint32_t idesc = idesc_f16(128, NF, BF);
+        const uint32_t sbo = KC * 128;
+        for (int it = 0; it < nst; ++it) {
+            const int s = it % S, u = it / S;
+            const int ch = it / kFChunk, b = ch & 1;
+            const bool first = (it % kFChunk) == 0;
+            const bool last = (it % kFChunk) == kFChunk - 1 || it == nst - 1;
+            if (first && ch >= 2 && !waitw(&acce[b], ((ch >> 1) - 1) & 1, abort)) break;
             if (!waitw(&full[s], u & 1, abort)) break;
+            if (!waitw(&pfull[s], u & 1, abort)) break;
             tc_after();
             if (lane == 0) {
                 const uint32_t st = su32(sm + s * STAGE);
-                const uint32_t bhi = st + kFMT * 2 * A_BYTES, blo = bhi + B_BYTES;
-#pragma unroll 1
-                for (int mt = 0; mt < kFMT; ++mt) {
+                const uint32_t bhi = st + B_OFF, blo = bhi + B_BYTES;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
                     const uint32_t ahi = st + (mt * 2) * A_BYTES, alo = ahi + A_BYTES;
-                    const uint32_t d = tmem + mt * 128;
+                    const uint32_t d = tmem + b * BUF + mt * 128;
 #pragma unroll
                     for (int kk = 0; kk < kFK / 16; ++kk) {
                         const uint32_t o = kk * 256;
-                        umma(d, sdesc(ahi + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, (it | kk) != 0);
+                        umma(d, sdesc(ahi + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, (first && kk == 0) ? 0u : 1u);
                         umma(d, sdesc(ahi + o, 128, sbo), sdesc(blo + o, 128, sbo), idesc, 1);
                         umma(d, sdesc(alo + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, 1);
                     }
                 }
                 umma_commit(&empty[s]);
+                if (last) umma_commit(&accf[b]);
             }
             __syncwarp();
         }
-        if (lane == 0) umma_commit(accf);
+        if (lane == 0) umma_commit(mmad);
         __syncwarp();
-    }
-
-    // ---- epilogue: TMEM -> partials ----
-    if (t < 128) {
-        const bool ok = waitw(accf, 0, abort);
-        tc_after();
-        const int row = t;
-#pragma unroll 1
-        for (int mt = 0; mt < kFMT; ++mt) {
-            const int gr = (mgroup * kFMT + mt) * 64 + (row & 63);
-            const bool im_row = row >= 64;
-#pragma unroll 1
-            for (int c0 = 0; c0 < NF; c0 += 16) {
-                float v[16];
-                tm_ld16(tmem + ((uint32_t)(warp * 32) << 16) + mt * 128 + c0, v);
-                if (!ok || gr >= R) continue;
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int col = c0 + jj;
-                    int m, comp;
-                    if (col <= kmax) { m = col; comp = im_row ? 2 : 0; }
-                    else if (col <= 2 * kmax) { m = col - kmax; comp = im_row ? 3 : 1; }
-                    else continue;
-                    spart[(((int64_t)ks * R + gr) * (kmax + 1) + m) * 4 + comp] = v[jj];
-                }
-            }
-            if (ok && gr < R) spart[(((int64_t)ks * R + gr) * (kmax + 1)) * 4 + (im_row ? 3 : 1)] = 0.f;
-        }
     }
     if (t == 0 && *abort) atomicOr(status, kStTimeout);
     tc_before();
     __syncthreads();
     tc_after();
-    if (warp == 0) tm_dealloc(tmem, 256);
+    if (warp == 0) tm_dealloc(tmem, 512);
 }
 
-// ---- coefficient max, packing of G' into FP16/BF16 split tiles --------------------------
-
-__global__ void k_gmax(int64_t count, const float *__restrict__ g, int *__restrict__ gmax)
-{
-    float m = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x)
-        m = fmaxf(m, fabsf(g[i]));
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(gmax, __float_as_int(m));   // m >= 0: int order = float order
-}
-
-// btile layout [pass][kb][part: hi, lo][NP columns x kBK] in [col/8][k/8][8][8] core matrices.
+// ---- a5: B operand of the forward product, once per evaluation --------------------------
+// blob[stage] for every 32-particle stage: [32 x uint4 particle data][hi: NF x 32][lo: NF x 32]
+// with column m = Re(q_j X_j[m]), column k_max + m = Im(q_j X_j[m]) (m >= 1), zero padding
+// columns, in the core-matrix layout; X_j[m] = e^{i 2 pi m x_j / L}.  grid: stages, block 256.
 template <bool BF>
-__global__ void k_bpack(int R2, int ncol, int NP, int nkb, const float *__restrict__ g,
-                        const int *__restrict__ gmax, float *__restrict__ gscale,
-                        uint16_t *__restrict__ btile)
+__global__ void k_xgen(int n, int kmax, int NF, const uint4 *__restrict__ pu,
+                       unsigned char *__restrict__ xblob)
+{
+    constexpr int KC = kFK / 8;
+    const int B_BYTES = NF * kFK * 2;
+    const int BLOB = kFK * 16 + 2 * B_BYTES;
+    const int stg = blockIdx.x;
+    const int j0 = stg * kFK;
+    unsigned char *out = xblob + (int64_t)stg * BLOB;
+    uint4 *P = reinterpret_cast<uint4 *>(out);
+    unsigned char *bhi = out + kFK * 16;
+    if (threadIdx.x < kFK) {
+        const int j = j0 + threadIdx.x;
+        P[threadIdx.x] = j < n ? pu[j] : make_uint4(0u, 0u, 0u, 0u);
+    }
+    for (int unit = threadIdx.x; unit < NF * KC; unit += blockDim.x) {
+        const int col = unit / KC, c = unit % KC;
+        const bool im = col > kmax;
+        const int m = im ? col - kmax : col;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int j = j0 + 8 * c + e;
+            v[e] = 0.f;
+            if (j < n && col <= 2 * kmax) {
+                const uint4 pj = pu[j];
+                float cs, sn;
+                phase((uint32_t)m * pj.x, cs, sn);
+                v[e] = __uint_as_float(pj.w) * (im ? sn : cs);
+            }
+        }
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split2<BF>(v[2 * e], v[2 * e + 1], h[e], l[e]);
+        st16(bhi, tile_off(col, c, KC), h[0], h[1], h[2], h[3]);
+        st16(bhi + B_BYTES, tile_off(col, c, KC), l[0], l[1], l[2], l[3]);
+    }
+}
+
+// ---- a6-a7: FP64 reduction of the forward partials, S(k), energy, G' ---------------------
+// grid (tiles of 64 rows in forward order, m = 0..k_max); block 64 (one row per thread).
+// Writes S in K_half order, the energy of the 64 rows and one m as a fixed-order block sum
+// e_part[m * ntiles + tile], the coefficient matrix column-major
+// gmat_t[col * 2R + (2r | 2r + 1)], and the max |G'| (as int bits).
+__global__ void __launch_bounds__(64)
+k_sreduce_tc(int nks, int ntiles, int R, int kmax, int NF, const RowInfo *__restrict__ rows,
+             const int *__restrict__ fperm, const float *__restrict__ dpart,
+             const double *__restrict__ gk, double *__restrict__ S, double *__restrict__ e_part,
+             float *__restrict__ gmat_t, int *__restrict__ gmax)
+{
+    __shared__ double ered[2];
+    const int tile = blockIdx.x, m = blockIdx.y, rl = threadIdx.x;
+    const int fr = tile * 64 + rl;                  // row in forward order
+    const int NB = 2 * kmax + 1;
+    const int64_t R2 = 2 * (int64_t)R;
+    float gm = 0.f;
+    double e = 0.0;
+    if (fr < R) {
+        const int r = fperm[fr];                    // row index of the coefficient matrix
+        const RowInfo ri = rows[r];
+        const bool origin = ri.my == 0 && ri.mz == 0;
+        const double wy = ri.my, wz = ri.mz;
+        double t[4] = {0.0, 0.0, 0.0, 0.0};         // T_rr, T_ri, T_ir, T_ii
+        const int64_t stride = (int64_t)ntiles * NF * 128;
+        const float *o = dpart + (int64_t)tile * NF * 128;
+        for (int ks = 0; ks < nks; ++ks, o += stride) {
+            t[0] += (double)o[m * 128 + rl];
+            t[2] += (double)o[m * 128 + 64 + rl];
+            if (m >= 1) {
+                t[1] += (double)o[(kmax + m) * 128 + rl];
+                t[3] += (double)o[(kmax + m) * 128 + 64 + rl];
+            }
+        }
+        const bool vp = m <= ri.nxmax && (!origin || m > 0);
+        const bool vn = m >= 1 && m <= ri.nxmax && !origin;
+        const double spr = t[0] - t[3], spi = t[2] + t[1];
+        const double snr = t[0] + t[3], sni = t[2] - t[1];
+        double gp = 0.0, gn = 0.0;
+        if (vp) {
+            const int idx = origin ? ri.koff + (m - 1) : ri.koff + ri.nxmax + m;
+            gp = gk[idx];
+            S[2 * (int64_t)idx] = spr; S[2 * (int64_t)idx + 1] = spi;
+            e += gp * (spr * spr + spi * spi);
+        }
+        if (vn) {
+            const int idx = ri.koff + ri.nxmax - m;
+            gn = gk[idx];
+            S[2 * (int64_t)idx] = snr; S[2 * (int64_t)idx + 1] = sni;
+            e += gn * (snr * snr + sni * sni);
+        }
+        const double Gpr = vp ? 2.0 * gp * spr : 0.0, Gpi = vp ? -2.0 * gp * spi : 0.0;
+        const double Gnr = vn ? 2.0 * gn * snr : 0.0, Gni = vn ? -2.0 * gn * sni : 0.0;
+        float v[3][2][2];   // [block][column 1|2][re|im]
+        int cols[2];
+        if (m == 0) {
+            cols[0] = 0; cols[1] = -1;
+            v[0][0][0] = (float)Gpr;          v[0][0][1] = (float)(-Gpi);
+            v[1][0][0] = (float)(wy * Gpi);   v[1][0][1] = (float)(wy * Gpr);
+            v[2][0][0] = (float)(wz * Gpi);   v[2][0][1] = (float)(wz * Gpr);
+        } else {
+            cols[0] = 2 * m - 1; cols[1] = 2 * m;
+            v[0][0][0] = (float)(Gpi - Gni);        v[0][0][1] = (float)(Gpr - Gnr);
+            v[0][1][0] = (float)(Gpr + Gnr);        v[0][1][1] = (float)(-(Gpi + Gni));
+            v[1][0][0] = (float)(wy * (Gpi + Gni)); v[1][0][1] = (float)(wy * (Gpr + Gnr));
+            v[1][1][0] = (float)(wy * (Gpr - Gnr)); v[1][1][1] = (float)(-wy * (Gpi - Gni));
+            v[2][0][0] = (float)(wz * (Gpi + Gni)); v[2][0][1] = (float)(wz * (Gpr + Gnr));
+            v[2][1][0] = (float)(wz * (Gpr - Gnr)); v[2][1][1] = (float)(-wz * (Gpi - Gni));
+        }
+#pragma unroll
+        for (int blk = 0; blk < 3; ++blk)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                if (cols[cc] < 0) continue;
+                const int64_t col = blk * NB + cols[cc];
+                *reinterpret_cast<float2 *>(gmat_t + col * R2 + 2 * r) = make_float2(v[blk][cc][0], v[blk][cc][1]);
+                gm = fmaxf(gm, fmaxf(fabsf(v[blk][cc][0]), fabsf(v[blk][cc][1])));
+            }
+    }
+    // fixed-order energy sum of the block (shuffle tree per warp, then warp 0 + warp 1)
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if ((rl & 31) == 0) ered[rl >> 5] = e;
+    for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_down_sync(0xffffffffu, gm, o));
+    if ((rl & 31) == 0) atomicMax(gmax, __float_as_int(gm));   // gm >= 0: int order = float order
+    __syncthreads();
+    if (rl == 0) e_part[(int64_t)m * ntiles + tile] = ered[0] + ered[1];
+}
+
+// Pack G' (column-major FP32) into split half-precision tiles with a row header:
+// blob[pass][kb] = [16 x (m_y, m_z) int2][hi: NP x kBK][lo: NP x kBK], core-matrix layout.
+// One thread packs 8 consecutive K of one column: one 16-byte store per part.
+template <bool BF>
+__global__ void k_bpack(int R, int ncol, int NP, int nkb, const RowInfo *__restrict__ rows,
+                        const float *__restrict__ gmat_t, const int *__restrict__ gmax,
+                        float *__restrict__ gscale, unsigned char *__restrict__ blob)
 {
     const int kb = blockIdx.x, pass = blockIdx.y;
     float scale = 1.f;
@@ -424,50 +554,65 @@ __global__ void k_bpack(int R2, int ncol, int NP, int nkb, const float *__restri
         if (mx > 0.f) scale = exp2f((float)(14 - ilogbf(mx)));
     }
     if (kb == 0 && pass == 0 && threadIdx.x == 0) gscale[0] = 1.f / scale;
-    uint16_t *out = btile + ((int64_t)pass * nkb + kb) * 2 * NP * kBK;
-    for (int e = threadIdx.x; e < NP * kBK; e += blockDim.x) {
-        const int col = e / kBK, k = e % kBK;
-        const int gk = kb * kBK + k, gc = pass * NP + col;
-        float v = 0.f;
-        if (gk < R2 && gc < ncol) v = g[(int64_t)gk * ncol + gc] * scale;
-        uint32_t h, l;
-        split2<BF>(v, 0.f, h, l);
-        const int off = ((col >> 3) * (kBK / 8) + (k >> 3)) * 64 + (col & 7) * 8 + (k & 7);
-        out[off] = (uint16_t)(h & 0xffffu);
-        out[NP * kBK + off] = (uint16_t)(l & 0xffffu);
+    const int64_t bsz = kHdr + 2 * (int64_t)NP * kBK * 2;
+    unsigned char *out = blob + ((int64_t)pass * nkb + kb) * bsz;
+    if (threadIdx.x < kBK / 2) {
+        const int r = kb * (kBK / 2) + threadIdx.x;
+        int2 h = make_int2(0, 0);
+        if (r < R) { const RowInfo ri = rows[r]; h = make_int2(ri.my, ri.mz); }
+        reinterpret_cast<int2 *>(out)[threadIdx.x] = h;
+    }
+    unsigned char *hi = out + kHdr;
+    unsigned char *lo = hi + NP * kBK * 2;
+    const int64_t R2 = 2 * (int64_t)R;
+    for (int u = threadIdx.x; u < NP * (kBK / 8); u += blockDim.x) {
+        const int col = u / (kBK / 8), kc = u % (kBK / 8);
+        const int gc = pass * NP + col;
+        const int64_t gk0 = (int64_t)kb * kBK + 8 * kc;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            v[e] = (gk0 + e < R2 && gc < ncol) ? gmat_t[(int64_t)gc * R2 + gk0 + e] * scale : 0.f;
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split2<BF>(v[2 * e], v[2 * e + 1], h[e], l[e]);
+        const uint32_t off = tile_off(col, kc, kBK / 8);
+        st16(hi, off, h[0], h[1], h[2], h[3]);
+        st16(lo, off, l[0], l[1], l[2], l[3]);
     }
 }
 
 // ---- back-scatter -----------------------------------------------------------------------
 // grid (particle tiles of kBMT * 128, passes); block kBThreads.
-// bpart layout [pass][n][4] = partial (F_x, F_y, F_z, phi) before q_i, 2 pi / L and scale.
+// bpart layout [pass][n] float4 = partial (F_x, F_y, F_z, phi) before q_i, 2 pi / L and scale.
 template <bool BF>
 __global__ void __launch_bounds__(kBThreads, 1)
-k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const RowInfo *__restrict__ rows,
-        const uint4 *__restrict__ pu, const uint16_t *__restrict__ btile,
-        float *__restrict__ bpart, int *__restrict__ status)
+k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const uint4 *__restrict__ pu,
+        const unsigned char *__restrict__ blob, float *__restrict__ bpart, int *__restrict__ status)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
+    constexpr int KC = kBK / 8;
     const int A_BYTES = 128 * kBK * 2;          // 8 KB
     const int B_BYTES = NP * kBK * 2;
-    const int STAGE = kBMT * 2 * A_BYTES + 2 * B_BYTES;
+    const int BLOB = kHdr + 2 * B_BYTES;
+    const int B_OFF = kBMT * 2 * A_BYTES;
+    const int STAGE = B_OFF + BLOB;
     uint64_t *full_a = reinterpret_cast<uint64_t *>(sm + kBStages * STAGE);
     uint64_t *full_b = full_a + kBStages;
     uint64_t *empty = full_b + kBStages;
     uint64_t *accf = empty + kBStages;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(accf + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
-    int *coldesc = const_cast<int *>(reinterpret_cast<volatile int *>(tslot + 2));
+    int *coldesc = reinterpret_cast<int *>(tslot + 2);
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int pass = blockIdx.y;
     const int base = blockIdx.x * (kBMT * 128);
-    const int kchunks = kBK / 8;
     const int NB = 2 * kmax + 1;
 
     if (t == 0) {
         for (int s = 0; s < kBStages; ++s) {
-            mb_init(&full_a[s], 128); mb_init(&full_b[s], 1); mb_init(&empty[s], 1);
+            mb_init(&full_a[s], 256); mb_init(&full_b[s], 1); mb_init(&empty[s], 1);
         }
         mb_init(accf, 1);
         *abort = 0;
@@ -492,77 +637,61 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const RowInfo *__rest
     tc_after();
     const uint32_t tmem = *tslot;
 
-    if (t < 128) {
-        // ---- producers: P_i[r] = e^{i (k_y y_i + k_z z_i)} for two particles per thread ----
-        uint32_t uy[kBMT], uz[kBMT];
-        bool valid[kBMT];
-#pragma unroll
-        for (int mt = 0; mt < kBMT; ++mt) {
-            const int i = base + mt * 128 + t;
-            valid[mt] = i < n;
-            const uint4 pi = pu[valid[mt] ? i : 0];
-            uy[mt] = pi.y; uz[mt] = pi.z;
-        }
+    if (t < 256) {
+        // ---- producers: P_i[r] = e^{i (k_y y_i + k_z z_i)}, one particle per thread ----
+        const int mt = t >> 7, row = t & 127;
+        const int i = base + t;
+        const bool valid = i < n;
+        const uint4 pi = pu[valid ? i : 0];
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % kBStages, u = kb / kBStages;
             if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
+            if (!waitw(&full_b[s], u & 1, abort)) break;      // row header of this K block
             unsigned char *st = sm + s * STAGE;
+            const int2 *hdr = reinterpret_cast<const int2 *>(st + B_OFF);
             const int r0 = kb * (kBK / 2);
-#pragma unroll 1
-            for (int c = 0; c < kchunks; ++c) {
-                int my[4], mz[4];
+            unsigned char *ahi = st + (mt * 2) * A_BYTES;
+#pragma unroll
+            for (int c = 0; c < KC; ++c) {
+                float v[8];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int r = r0 + 4 * c + e;
-                    if (r < R) { const RowInfo ri = rows[r]; my[e] = ri.my; mz[e] = ri.mz; }
-                    else { my[e] = 0; mz[e] = 0; }
+                    const int2 h = hdr[4 * c + e];
+                    float cs = 0.f, sn = 0.f;
+                    if (valid && r0 + 4 * c + e < R)
+                        phase((uint32_t)h.x * pi.y + (uint32_t)h.y * pi.z, cs, sn);
+                    v[2 * e] = cs; v[2 * e + 1] = sn;
                 }
+                uint32_t hh[4], ll[4];
 #pragma unroll
-                for (int mt = 0; mt < kBMT; ++mt) {
-                    float v[8];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int r = r0 + 4 * c + e;
-                        float cs = 0.f, sn = 0.f;
-                        if (r < R && valid[mt])
-                            phase((uint32_t)my[e] * uy[mt] + (uint32_t)mz[e] * uz[mt], cs, sn);
-                        v[2 * e] = cs; v[2 * e + 1] = sn;
-                    }
-                    uint32_t h[4], l[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) split2<BF>(v[2 * e], v[2 * e + 1], h[e], l[e]);
-                    unsigned char *ahi = st + (mt * 2) * A_BYTES;
-                    st16(ahi, tile_off(t, c, kchunks), h[0], h[1], h[2], h[3]);
-                    st16(ahi + A_BYTES, tile_off(t, c, kchunks), l[0], l[1], l[2], l[3]);
-                }
+                for (int e = 0; e < 4; ++e) split2<BF>(v[2 * e], v[2 * e + 1], hh[e], ll[e]);
+                st16(ahi, tile_off(row, c, KC), hh[0], hh[1], hh[2], hh[3]);
+                st16(ahi + A_BYTES, tile_off(row, c, KC), ll[0], ll[1], ll[2], ll[3]);
             }
             fence_async_smem();
             mb_arrive(&full_a[s]);
         }
-    } else if (warp == 4) {
-        // ---- TMA producer for the G' tiles: the whole warp follows the loop, lane 0 issues ----
-        const uint32_t bytes = 2u * (uint32_t)B_BYTES;
+    } else if (warp == 8) {
+        // ---- TMA producer for the packed G' blobs ----
         int issued = 0;
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % kBStages, u = kb / kBStages;
             if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
             if (lane == 0) {
-                unsigned char *dst = sm + s * STAGE + kBMT * 2 * A_BYTES;
-                mb_expect_tx(&full_b[s], bytes);
-                tma_bulk(dst, btile + ((int64_t)pass * nkb + kb) * 2 * NP * kBK, bytes, &full_b[s]);
+                mb_expect_tx(&full_b[s], (uint32_t)BLOB);
+                tma_bulk(sm + s * STAGE + B_OFF, blob + ((int64_t)pass * nkb + kb) * BLOB, (uint32_t)BLOB, &full_b[s]);
             }
             __syncwarp();
             issued = kb + 1;
         }
-        // every copy issued must have landed before the CTA can leave (bounded)
         for (int kb = issued - kBStages < 0 ? 0 : issued - kBStages; kb < issued; ++kb) {
             volatile int no_abort = 0;
             waitw(&full_b[kb % kBStages], (kb / kBStages) & 1, &no_abort);
         }
-    } else if (warp == 5) {
-        // ---- MMA issuer: the whole warp follows the loop, lane 0 issues ----
+    } else if (warp == 9) {
+        // ---- MMA issuer ----
         const uint32_t idesc = idesc_f16(128, NP, BF);
-        const uint32_t sbo = kchunks * 128;
+        const uint32_t sbo = KC * 128;
         for (int kb = 0; kb < nkb; ++kb) {
             const int s = kb % kBStages, u = kb / kBStages;
             if (!waitw(&full_a[s], u & 1, abort)) break;
@@ -570,7 +699,7 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const RowInfo *__rest
             tc_after();
             if (lane == 0) {
                 const uint32_t st = su32(sm + s * STAGE);
-                const uint32_t bhi = st + kBMT * 2 * A_BYTES, blo = bhi + B_BYTES;
+                const uint32_t bhi = st + B_OFF + kHdr, blo = bhi + B_BYTES;
 #pragma unroll
                 for (int mt = 0; mt < kBMT; ++mt) {
                     const uint32_t ahi = st + (mt * 2) * A_BYTES, alo = ahi + A_BYTES;
@@ -592,47 +721,49 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const RowInfo *__rest
     }
 
     // ---- epilogue: per particle, combine the accumulator row with X_i[m] ----
-    if (t < 128) {
+    if (t < 256) {
         const bool ok = waitw(accf, 0, abort);
         tc_after();
-        // X table in the (now idle) stage buffers: xt[m * 128 + t]
+        const int mt = t >> 7;
+        const int i = base + t;
+        // X_i[m] table in the (now idle) stage buffers, xt[m * 256 + t], when it fits;
+        // otherwise every column recomputes its phase
         float2 *xt = reinterpret_cast<float2 *>(sm);
-#pragma unroll 1
-        for (int mt = 0; mt < kBMT; ++mt) {
-            const int i = base + mt * 128 + t;
-            const uint32_t ux = pu[i < n ? i : 0].x;
+        const bool table = (kmax + 1) * 256 * (int)sizeof(float2) <= kBStages * STAGE;
+        const uint32_t ux = pu[i < n ? i : 0].x;
+        if (table)
             for (int m = 0; m <= kmax; ++m) {
                 float cs, sn;
                 phase((uint32_t)m * ux, cs, sn);
-                xt[m * 128 + t] = make_float2(cs, sn);
+                xt[m * 256 + t] = make_float2(cs, sn);
             }
-            float fx = 0.f, fy = 0.f, fz = 0.f, ph = 0.f;
+        float fx = 0.f, fy = 0.f, fz = 0.f, ph = 0.f;
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
 #pragma unroll 1
-            for (int c0 = 0; c0 < NP; c0 += 16) {
-                float v[16];
-                tm_ld16(tmem + ((uint32_t)(warp * 32) << 16) + mt * 256 + c0, v);
+        for (int c0 = 0; c0 < NP; c0 += 16) {
+            float v[16];
+            tm_ld16(tmem + lanes + mt * 256 + c0, v);
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int d = coldesc[c0 + jj];
-                    if (d & (1 << 12)) continue;
-                    const int m = d & 0xff, kind = (d >> 8) & 3, blk = (d >> 10) & 3;
-                    const float2 x = xt[m * 128 + t];
-                    const float val = v[jj];
-                    if (blk == 0) {
-                        if (kind == 0) ph += val;
-                        else if (kind == 1) { fx += (float)m * x.x * val; ph -= x.y * val; }
-                        else { fx += (float)m * x.y * val; ph += x.x * val; }
-                    } else {
-                        const float w = kind == 0 ? val : (kind == 1 ? x.x * val : x.y * val);
-                        if (blk == 1) fy += w; else fz += w;
-                    }
+            for (int jj = 0; jj < 16; ++jj) {
+                const int d = coldesc[c0 + jj];
+                if (d & (1 << 12)) continue;
+                const int m = d & 0xff, kind = (d >> 8) & 3, blk = (d >> 10) & 3;
+                float2 x;
+                if (table) x = xt[m * 256 + t];
+                else phase((uint32_t)m * ux, x.x, x.y);
+                const float val = v[jj];
+                if (blk == 0) {
+                    if (kind == 0) ph += val;
+                    else if (kind == 1) { fx += (float)m * x.x * val; ph -= x.y * val; }
+                    else { fx += (float)m * x.y * val; ph += x.x * val; }
+                } else {
+                    const float w = kind == 0 ? val : (kind == 1 ? x.x * val : x.y * val);
+                    if (blk == 1) fy += w; else fz += w;
                 }
             }
-            if (ok && i < n) {
-                float4 *o = reinterpret_cast<float4 *>(bpart) + ((int64_t)pass * n + i);
-                *o = make_float4(fx, fy, fz, ph);
-            }
         }
+        if (ok && i < n)
+            reinterpret_cast<float4 *>(bpart)[(int64_t)pass * n + i] = make_float4(fx, fy, fz, ph);
     }
     if (t == 0 && *abort) atomicOr(status, kStTimeout);
     tc_before();
@@ -663,42 +794,70 @@ __global__ void k_bs_reduce(int64_t n, int npass, const float *__restrict__ bpar
 
 struct TcState {
     int nf = 0;           // forward N (2 k_max + 1 rounded up to 16)
+    int fmt = 2;          // forward M tiles per CTA (2 while N <= 128, else 1)
+    int ntiles = 0;       // forward tiles of 64 rows
     int mgroups = 0;      // forward M groups
     int ks = 0;           // forward K splits
     int per = 0;          // forward particles per split
     int ncol = 0;         // back-scatter columns 3 (2 k_max + 1)
     int npass = 0, np = 0, nkb = 0;
-    float *spart = nullptr;     // [ks][R][k+1][4]
-    float *gmat = nullptr;      // [2R][ncol]
+    float *dpart = nullptr;        // [ks][ntiles][nf][128]
+    unsigned char *xblob = nullptr; // [stages][particles + hi + lo] forward B operand
+    int nstg = 0;                  // 32-particle stages
+    float *gmat = nullptr;         // [ncol][2R]
     int *gmax = nullptr;
     float *gscale = nullptr;
-    uint16_t *btile = nullptr;  // [npass][nkb][2][np * kBK]
-    float *bpart = nullptr;     // [npass][n][4]
+    unsigned char *blob = nullptr; // [npass][nkb][hdr + 2 * np * kBK * 2]
+    float *bpart = nullptr;        // [npass][n][4]
 };
 
 void tc_shape(const Plan &p, int64_t n, TcState &s)
 {
     s.nf = 16 * ((2 * p.kmax + 1 + 15) / 16);
-    const int tiles = (p.R + 63) / 64;
-    s.mgroups = (tiles + kFMT - 1) / kFMT;
+    s.fmt = s.nf <= 128 ? 2 : 1;
+    s.ntiles = (p.R + 63) / 64;
+    s.mgroups = (s.ntiles + s.fmt - 1) / s.fmt;
     const int nblk = (int)((n + kFK - 1) / kFK);
-    int want = (2 * 152 + s.mgroups - 1) / s.mgroups;
+    int want = (152 + s.mgroups - 1) / s.mgroups;
     if (want > nblk) want = nblk;
     if (want < 1) want = 1;
     const int blk_per = (nblk + want - 1) / want;
     s.per = blk_per * kFK;
     s.ks = (nblk + blk_per - 1) / blk_per;
+    s.nstg = nblk;
     s.ncol = 3 * (2 * p.kmax + 1);
     s.npass = (s.ncol + kPassMax - 1) / kPassMax;
     s.np = 16 * (((s.ncol + s.npass - 1) / s.npass + 15) / 16);
     s.nkb = (2 * p.R + kBK - 1) / kBK;
 }
 
-size_t fwd_smem(int nf) { return (size_t)kFStages * (kFMT * 2 * 128 * kFK * 2 + 2 * nf * kFK * 2) + 256; }
+constexpr size_t kSmemMax = 232448;   // opt-in shared memory per block (227 KB)
+
+size_t fwd_blob(int nf) { return (size_t)kFK * 16 + 2 * (size_t)nf * kFK * 2; }
+size_t fwd_smem_s(int nf, int mt, int S)
+{
+    const size_t stage = (size_t)mt * 2 * 128 * kFK * 2 + fwd_blob(nf);
+    return S * stage + (size_t)mt * nf * 128 * 4 + (size_t)mt * 64 * 8 + 256;
+}
+int fwd_stages(int nf, int mt) { return fwd_smem_s(nf, mt, 3) <= kSmemMax ? 3 : 2; }
+size_t fwd_smem(int nf, int mt) { return fwd_smem_s(nf, mt, fwd_stages(nf, mt)); }
+size_t bs_blob(int np) { return kHdr + 2 * (size_t)np * kBK * 2; }
 size_t bs_smem(int np)
 {
-    size_t stage = (size_t)kBMT * 2 * 128 * kBK * 2 + 2 * (size_t)np * kBK * 2;
-    return kBStages * stage + 256 + 4 * (size_t)np;
+    const size_t stage = (size_t)kBMT * 2 * 128 * kBK * 2 + bs_blob(np);
+    return kBStages * stage + 128 + 4 * (size_t)np;
+}
+
+template <int MT, bool BF>
+cudaError_t launch_fwd(Plan &p, int64_t n, TcState &s, cudaStream_t st)
+{
+    const size_t fs = fwd_smem(s.nf, MT);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<MT, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs);
+    if (e != cudaSuccess) return e;
+    k_fwd_tc<MT, BF><<<dim3(s.mgroups, s.ks), kFThreads, fs, st>>>(
+        (int)n, p.R, p.kmax, s.nf, s.per, s.ntiles, fwd_stages(s.nf, MT), p.rows_d, p.fperm_d,
+        s.xblob, s.dpart, p.d_status);
+    return cudaGetLastError();
 }
 
 template <bool BF>
@@ -708,24 +867,23 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
     Workspace &ws = p.ws;
     cudaError_t e;
     prof_mark(p, kEvRecipStart, st);
-    const size_t fs = fwd_smem(s.nf);
-    if ((e = cudaFuncSetAttribute(k_fwd_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs)) != cudaSuccess)
-        return e;
-    k_fwd_tc<BF><<<dim3(s.mgroups, s.ks), kFThreads, fs, st>>>((int)n, p.R, p.kmax, s.nf, s.per,
-                                                               p.rows_d, ws.pu, s.spart, p.d_status);
+    k_xgen<BF><<<s.nstg, 256, 0, st>>>((int)n, p.kmax, s.nf, ws.pu, s.xblob);
+    e = s.fmt == 2 ? launch_fwd<2, BF>(p, n, s, st) : launch_fwd<1, BF>(p, n, s, st);
+    if (e != cudaSuccess) return e;
     prof_mark(p, kEvFwdEnd, st);
-    if ((e = launch_sreduce_f32(p, s.ks, s.spart, s.gmat, s.ncol, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(s.gmax, 0, sizeof(int), st)) != cudaSuccess) return e;
-    k_gmax<<<152, 256, 0, st>>>((int64_t)2 * p.R * s.ncol, s.gmat, s.gmax);
-    k_bpack<BF><<<dim3(s.nkb, s.npass), 256, 0, st>>>(2 * p.R, s.ncol, s.np, s.nkb, s.gmat, s.gmax,
-                                                      s.gscale, s.btile);
+    k_sreduce_tc<<<dim3(s.ntiles, p.kmax + 1), 64, 0, st>>>(s.ks, s.ntiles, p.R, p.kmax, s.nf, p.rows_d,
+                                                       p.fperm_d, s.dpart, p.g_d, p.S_d,
+                                                       p.e_recip_part, s.gmat, s.gmax);
+    k_bpack<BF><<<dim3(s.nkb, s.npass), 256, 0, st>>>(p.R, s.ncol, s.np, s.nkb, p.rows_d, s.gmat,
+                                                      s.gmax, s.gscale, s.blob);
     prof_mark(p, kEvCoefEnd, st);
     const size_t bs = bs_smem(s.np);
     if ((e = cudaFuncSetAttribute(k_bs_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs)) != cudaSuccess)
         return e;
     const int ptiles = (int)((n + kBMT * 128 - 1) / (kBMT * 128));
-    k_bs_tc<BF><<<dim3(ptiles, s.npass), kBThreads, bs, st>>>((int)n, p.R, p.kmax, s.ncol, s.np, s.nkb,
-                                                              p.rows_d, ws.pu, s.btile, s.bpart,
+    k_bs_tc<BF><<<dim3(ptiles, s.npass), kBThreads, bs, st>>>((int)n, p.R, p.kmax, s.ncol, s.np,
+                                                              s.nkb, ws.pu, s.blob, s.bpart,
                                                               p.d_status);
     k_bs_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s.npass, s.bpart, ws.pg, s.gscale,
                                                             p.L, ws.f_recip);
@@ -736,16 +894,19 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
 
 }  // namespace
 
+int recip_tc_energy_parts(const Plan &p) { return ((p.R + 63) / 64) * (p.kmax + 1); }
+
 size_t recip_tc_bytes(const Plan &p, int64_t n)
 {
     TcState s;
     tc_shape(p, n, s);
     size_t b = 0;
-    b += (size_t)s.ks * p.R * (p.kmax + 1) * 4 * sizeof(float);
+    b += (size_t)s.ks * s.ntiles * s.nf * 128 * sizeof(float);
+    b += (size_t)s.nstg * fwd_blob(s.nf);
     b += (size_t)2 * p.R * s.ncol * sizeof(float);
-    b += (size_t)s.npass * s.nkb * 2 * s.np * kBK * sizeof(uint16_t);
+    b += (size_t)s.npass * s.nkb * bs_blob(s.np);
     b += (size_t)s.npass * n * 4 * sizeof(float);
-    return b + 64;
+    return b + 1024;
 }
 
 cudaError_t alloc_recip_tc(Plan &p, int64_t n)
@@ -756,11 +917,12 @@ cudaError_t alloc_recip_tc(Plan &p, int64_t n)
     p.tc = s;
     cudaStream_t st = p.side_stream;
     cudaError_t e;
-    if ((e = pool_alloc((void **)&s->spart, (size_t)s->ks * p.R * (p.kmax + 1) * 4 * sizeof(float), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->dpart, (size_t)s->ks * s->ntiles * s->nf * 128 * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->gmat, (size_t)2 * p.R * s->ncol * sizeof(float), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->xblob, (size_t)s->nstg * fwd_blob(s->nf), st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->gmax, 64, st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->gscale, 64, st)) != cudaSuccess) return e;
-    if ((e = pool_alloc((void **)&s->btile, (size_t)s->npass * s->nkb * 2 * s->np * kBK * sizeof(uint16_t), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->blob, (size_t)s->npass * s->nkb * bs_blob(s->np), st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->bpart, (size_t)s->npass * n * 4 * sizeof(float), st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -770,8 +932,9 @@ void free_recip_tc(Plan &p)
     TcState *s = static_cast<TcState *>(p.tc);
     if (!s) return;
     cudaStream_t st = p.side_stream;
-    pool_free(s->spart, st); pool_free(s->gmat, st); pool_free(s->gmax, st);
-    pool_free(s->gscale, st); pool_free(s->btile, st); pool_free(s->bpart, st);
+    pool_free(s->dpart, st); pool_free(s->gmat, st); pool_free(s->gmax, st);
+    pool_free(s->xblob, st);
+    pool_free(s->gscale, st); pool_free(s->blob, st); pool_free(s->bpart, st);
     delete s;
     p.tc = nullptr;
 }
