@@ -434,6 +434,7 @@ int plan_reconfigure(ewald_plan *h, double L, double beta, double rc, int kmax, 
 {
     Plan &p = h->p;
     Plan probe;
+    probe.num_sms = p.num_sms;
     int s = plan_setup_host(probe, L, beta, rc, kmax, precision);
     if (s != EWALD_OK) return s;
     if (p.last_stream) cudaStreamSynchronize(p.last_stream);
@@ -485,6 +486,8 @@ extern "C" int ewald_create(double L, double beta, double r_c, int k_max, int pr
     Plan &p = h->p;
     plan_setup_host(p, L, beta, r_c, k_max, precision);
     cudaGetDevice(&p.device);
+    cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
+    if (p.num_sms < 1) p.num_sms = 1;
     cudaError_t e = cudaSuccess;
 #define EW_C(x) do { if ((e = (x)) != cudaSuccess) { destroy_plan(h); return cuda_status(e); } } while (0)
     EW_C(cudaStreamCreateWithFlags(&p.side_stream, cudaStreamNonBlocking));

@@ -76,6 +76,7 @@ struct Workspace {
 
 struct Plan {
     int device = 0;
+    int num_sms = 148;           // streaming multiprocessors of the plan's device
     double L = 0, beta = 0, rc = 0;
     int kmax = 0;
     int precision = 0;

@@ -817,8 +817,10 @@ void tc_shape(const Plan &p, int64_t n, TcState &s)
     s.fmt = s.nf <= 128 ? 2 : 1;
     s.ntiles = (p.R + 63) / 64;
     s.mgroups = (s.ntiles + s.fmt - 1) / s.fmt;
+    // one wave: as many K splits as fit next to the M groups on the GPU's SMs (a second,
+    // partial wave would double the kernel time)
     const int nblk = (int)((n + kFK - 1) / kFK);
-    int want = (152 + s.mgroups - 1) / s.mgroups;
+    int want = p.num_sms / s.mgroups;
     if (want > nblk) want = nblk;
     if (want < 1) want = 1;
     const int blk_per = (nblk + want - 1) / want;

@@ -91,6 +91,9 @@ namespace {
 size_t request_footprint(const ewald_request &r)
 {
     Plan probe;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&probe.num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (plan_setup_host(probe, r.L, r.beta, r.r_c, r.k_max, r.precision) != EWALD_OK) return 0;
     return plan_footprint(probe, r.n);
 }
