@@ -204,6 +204,40 @@ int ewald_cell_sort(ewald_plan_t plan, int32_t *key_dev, int32_t *perm_dev, void
  */
 int ewald_tune(int64_t n, double L, double tol, double *r_c, double *beta, int *k_max);
 
+/*
+ * ewald_real_noalloc - the real-space part alone, without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers of this library that
+ * cannot allocate device memory -- code running while a stream is being captured into a
+ * CUDA graph (allocation is not allowed there), programs whose device memory is owned by
+ * another allocator or capped by a quota, and latency-critical loops that must never enter
+ * the allocator.  The plan-based calls above allocate workspaces on first use; this one
+ * does not call cudaMalloc, cudaFree or any routine that allocates.
+ *
+ *   L, beta, r_c   as in ewald_create (0 < r_c <= L/2)
+ *   n              0 <= n <= EWALD_NOALLOC_MAX_N particles; larger n returns
+ *                  EWALD_E_UNSUPPORTED without doing anything
+ *   pos, q         dev float64 [n][3], [n]
+ *   forces         dev float64 [n][3], overwritten with the real-space forces (caller order)
+ *   energy_dev     dev float64 [4]: E_real, 0, 0, E_real (the reciprocal and self parts are
+ *                  not evaluated)
+ *   stream         cudaStream_t; the call is asynchronous on it
+ * Results equal ewald_compute_async(..., EWALD_PART_REAL) of an EWALD_FP64 plan up to
+ * floating-point summation order (every pair is visited with the minimum image).  There is
+ * no device-side validation: non-neutral input is not reported and non-finite input gives
+ * non-finite output.
+ *
+ * Scratch: a fixed device array inside the library (packed particles and per-tile energy
+ * partials for EWALD_NOALLOC_MAX_N particles, about 516 KB), present on every GPU that loads
+ * the library until the process exits.  Every call shares it: calls whose GPU work overlaps
+ * (different streams, or unordered calls from several host threads) race and give undefined
+ * results.  The first call on a device looks up the array's device address (and may load the
+ * library's device code into the context), so make it before any stream capture.
+ */
+#define EWALD_NOALLOC_MAX_N 16384
+int ewald_real_noalloc(double L, double beta, double r_c, int64_t n, const double *pos,
+                       const double *q, double *forces, double *energy_dev, void *stream);
+
 /* ewald_strerror - static, NUL-terminated name of a status code. */
 const char *ewald_strerror(int status);
 

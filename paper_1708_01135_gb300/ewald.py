@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
                 "ewald_wait": (_i, [_p, ctypes.c_uint64, _d, ctypes.POINTER(_Result)]),
                 "ewald_server_stats": (_i, [_p, _p]),
                 "ewald_server_destroy": (_i, [_p]),
+                "ewald_real_noalloc": (_i, [_d, _d, _d, _i64, _p, _p, _p, _p, _p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -122,6 +123,20 @@ def tune(n: int, L: float, tol: float = 1e-6, r_c: float | None = None):
     _check(lib().ewald_tune(int(n), float(L), float(tol), ctypes.byref(rc), ctypes.byref(beta),
                             ctypes.byref(km)), "ewald_tune")
     return rc.value, beta.value, km.value
+
+
+NOALLOC_MAX_N = 16384
+
+
+def real_noalloc(L, beta, r_c, pos, q, forces, energy, stream=None):
+    """Real-space part without any device allocation (ewald_real_noalloc): for callers that
+    cannot allocate (stream capture, foreign allocators, allocation-free loops).  pos [n,3],
+    q [n], forces [n,3], energy [4] are CUDA float64 tensors; n <= NOALLOC_MAX_N."""
+    n = int(q.shape[0])
+    _check(lib().ewald_real_noalloc(float(L), float(beta), float(r_c), n, _dev_f64(pos, (n, 3), "pos"),
+                                    _dev_f64(q, (n,), "q"), _dev_f64(forces, (n, 3), "forces"),
+                                    _dev_f64(energy, (4,), "energy"), _stream_handle(stream)),
+           "ewald_real_noalloc")
 
 
 class Ewald:
