@@ -101,7 +101,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -163,6 +163,85 @@ def oracle_sample(pos, q, L, beta, rc, kmax, n_targets, seed=0):
 
 # ---- main ---------------------------------------------------------------------------------
 
+def _gen_request(item):
+    """One system of the serving stream (runs in a worker process)."""
+    import numpy as np_
+    from paper_1708_01135_gb300 import workloads as W_
+    r, kind, n, rho, m, seed = item
+    L = (n / rho) ** (1.0 / 3.0)
+    if kind == "rocksalt":
+        pos, q, L = W_.rocksalt(m, a=L / m, jitter=0.05 * L / m, seed=seed * 1000 + r)
+    else:
+        pos, q, L = W_.random_neutral(n, L=L, hard_core=0.8 * (1.0 / rho) ** (1.0 / 3.0),
+                                      seed=seed * 1000 + r)
+    return np_.ascontiguousarray(pos), np_.ascontiguousarray(q), float(L)
+
+
+def run_serving(args, rank, world, local):
+    """Serving stream: independent systems of uneven N (log-uniform in [256, 65536], half
+    jittered rock-salt, half random neutral, density U[0.8, 1.2], each with its own box and
+    tuned parameters), submitted to the continuous-batching server.  First a closed-loop run
+    measures the saturation rate; then Poisson arrivals at several fractions of it give p50/p99
+    latency (submit -> result) and the aggregate particles/s."""
+    import multiprocessing as mp
+    seed = 1238
+    count = args.requests
+    items = [(r, kind, n, rho, m, seed) for r, (kind, n, rho, m) in
+             enumerate(W.request_sizes(count, 256, 65536, seed))]
+    ctx = mp.get_context("spawn")          # before the first CUDA call of this process
+    with ctx.Pool(min(16, os.cpu_count() or 4)) as pool:
+        systems = pool.map(_gen_request, items)
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1708_01135_gb300 import Server, tune
+    dev = torch.device("cuda", local)
+    reqs = []
+    for pos, q, L in systems:
+        rc, beta, km = tune(len(q), L, 1e-5, r_c=min(0.5 * L, 4.0 * (len(q) / L ** 3) ** (-1.0 / 3.0)))
+        reqs.append(dict(pos=torch.tensor(pos, device=dev), q=torch.tensor(q, device=dev),
+                         F=torch.empty((len(q), 3), dtype=torch.float64, device=dev),
+                         L=L, beta=beta, rc=rc, km=km, n=len(q)))
+    total_n = sum(r["n"] for r in reqs)
+    srv = Server(max_slots=args.slots)
+
+    def run(times):
+        t0 = time.perf_counter()
+        tickets = []
+        for r, ta in zip(reqs, times):
+            while time.perf_counter() - t0 < ta:
+                time.sleep(0.0002)
+            tickets.append(srv.submit(r["pos"], r["q"], r["F"], r["L"], r["beta"], r["rc"], r["km"],
+                                      args.precision))
+        res = [srv.wait(t, 600.0) for t in tickets]
+        if any(x["status"] != 0 for x in res):
+            raise RuntimeError("a serving request failed")
+        lat = np.array([x["t_done"] - x["t_submit"] for x in res]) * 1e3
+        span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
+        return lat, span
+
+    run([0.0] * min(16, count))            # warm-up: plans, pools, module load
+    lat, span = run([0.0] * count)         # closed loop: everything at once
+    sat_rate = count / span
+    out = {"saturation": {"requests_per_s": sat_rate, "particles_per_s": total_n / span,
+                          "p50_ms": float(np.percentile(lat, 50)),
+                          "p99_ms": float(np.percentile(lat, 99))}}
+    rng = np.random.default_rng(seed + 7)
+    for frac in (0.25, 0.5, 0.75, 0.9, 1.1):
+        rate = frac * sat_rate
+        times = np.cumsum(rng.exponential(1.0 / rate, size=count))
+        lat, span = run(list(times - times[0]))
+        out[f"load_{frac}"] = {"arrival_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                               "p99_ms": float(np.percentile(lat, 99)),
+                               "particles_per_s": total_n / span}
+    stats = srv.stats()
+    srv.close()
+    if rank == 0:
+        print(json.dumps({"metric": "ewald_serving", "unit": "ms / particles/s", "n_gpus": world,
+                          "requests": count, "total_particles": total_n, "slots": args.slots,
+                          "precision": args.precision, "tol": 1e-5, "data": "synthetic",
+                          "results": out, "server": stats}), flush=True)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -206,19 +285,23 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="random_32768", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="random_32768", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32", "mixed_bf16"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-targets", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--slots", type=int, default=8)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -240,8 +323,17 @@ def main():
     stream = torch.cuda.current_stream()
     ew = Ewald(L, beta, rc, kmax, args.precision)
 
-    for _ in range(args.warmup):
+    # the clock sampler runs through the warm-up (at least ~0.5 s of back-to-back steps) and
+    # the timed steps, so that its samples see the GPU under this workload's load
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_warm = time.perf_counter()
+    w = 0
+    while w < args.warmup or time.perf_counter() - t_warm < 0.5:
         ew.compute_async(tp, tq, F, E)
+        w += 1
+        if w % 8 == 0:
+            torch.cuda.synchronize()
     torch.cuda.synchronize()
     if ew.status() != 0:
         raise RuntimeError("warm-up evaluation reported an error")
@@ -251,8 +343,6 @@ def main():
     stage = {k: [] for k in ("binning", "real", "recip_forward", "recip_coef", "recip_back",
                              "finalize", "total", "recip_branch")}
     ew.profile(1)
-    clocks = ClockSampler(local)
-    clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()

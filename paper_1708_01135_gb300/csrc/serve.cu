@@ -55,6 +55,8 @@ struct Slot {
     int launch_status = EWALD_OK;
 };
 
+constexpr int kMaxBypass = 64;   // requests admitted past a waiting head before it blocks them
+
 double now_s(std::chrono::steady_clock::time_point t0)
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -83,6 +85,7 @@ struct ewald_server {
     uint64_t next_ticket = 1;
     int64_t submitted = 0, completed = 0;
     int64_t held_total = 0, peak_held = 0, peak_running = 0;
+    int head_bypass = 0;             // admissions that passed over the head of the queue
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 };
 
@@ -173,15 +176,39 @@ void scheduler(ewald_server *s)
             progress = true;
         }
         if (s->stop && running == 0) break;
-        // admit: first fit over the queue, in arrival order
+        // admit: first fit over the queue, in arrival order.  A request that does not fit
+        // first reclaims the workspaces of idle slots; once the head of the queue has been
+        // passed over kMaxBypass times, nothing behind it is admitted before it.
         if (!s->stop) {
             for (auto it = s->queue.begin(); it != s->queue.end();) {
                 Slot *free_slot = nullptr;
                 for (Slot &sl : s->slots)
                     if (!sl.busy && (!free_slot || sl.held > free_slot->held)) free_slot = &sl;
                 if (!free_slot) break;
-                const int64_t after = s->held_total - (int64_t)free_slot->held + (int64_t)it->footprint;
-                if (after > (int64_t)s->budget) { ++it; continue; }
+                const bool is_head = it == s->queue.begin();
+                int64_t after = s->held_total - (int64_t)free_slot->held + (int64_t)it->footprint;
+                if (after > (int64_t)s->budget) {
+                    for (Slot &sl : s->slots) {
+                        if (after <= (int64_t)s->budget) break;
+                        if (sl.busy || &sl == free_slot || sl.held == 0) continue;
+                        lk.unlock();
+                        if (sl.plan) { ewald_destroy(sl.plan); sl.plan = nullptr; }
+                        lk.lock();
+                        s->held_total -= (int64_t)sl.held;
+                        after -= (int64_t)sl.held;
+                        sl.held = 0;
+                    }
+                }
+                if (after > (int64_t)s->budget) {   // does not fit now: try the next one
+                    ++it;
+                    continue;
+                }
+                if (is_head) {
+                    s->head_bypass = 0;
+                } else {
+                    if (s->head_bypass >= kMaxBypass) break;   // the head has waited long enough
+                    ++s->head_bypass;
+                }
                 Pending pd = *it;
                 it = s->queue.erase(it);
                 Slot &sl = *free_slot;
