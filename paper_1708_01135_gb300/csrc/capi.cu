@@ -696,17 +696,19 @@ extern "C" int ewald_tune(int64_t n, double L, double tol, double *r_c, double *
     const double p = sqrt(-log(tol));
     double rc = *r_c;
     if (!(rc > 0)) {
-        // cost model: pair candidates ~ N * 27 (r_c / w)^3 rho * c_pair versus
-        // modes ~ N * (2/3) pi k_max^3 * c_mode (k_max = p^2 L / (pi r_c)); pick the r_c that
-        // minimises it on a grid of r_c <= L/2.
+        // Cost per particle, calibrated on GB300 with the EWALD_MIXED path: the real-space
+        // kernel visits ~18.75 r_c^3 rho candidates per target at ~4.2 ps each; the two
+        // reciprocal products cost ~0.06 ps per (particle, grid cell) over a cylinder of
+        // ~pi k_max^3 cells, k_max = p^2 L / (pi r_c).  Pick the r_c <= L/2 that minimises
+        // the sum on a grid.
         const double rho = n / (L * L * L);
-        const double c_pair = 1.0, c_mode = 0.35;
+        const double c_pair = 4.2e-12 * 18.75, c_mode = 6.0e-14 * kPi;
         double best = 1e300, best_rc = 0.5 * L;
         for (int t = 1; t <= 400; ++t) {
             double x = 0.5 * L * t / 400.0;
             if (x < 1e-3) continue;
             double km = p * p * L / (kPi * x);
-            double cost = 15.6 * x * x * x * rho * c_pair + (2.0 / 3.0) * kPi * km * km * km * c_mode;
+            double cost = c_pair * x * x * x * rho + c_mode * km * km * km;
             if (cost < best) { best = cost; best_rc = x; }
         }
         rc = best_rc;

@@ -113,7 +113,7 @@ def random_neutral(n: int, L: float | None = None, density: float = 1.0, hard_co
     reach = int(math.ceil(hard_core / h))
     if 2 * reach + 1 > g:
         raise ValueError("box too small for the hard-core grid")
-    grid = np.full(g * g * g, -1, dtype=np.int64)
+    grid = np.full(g * g * g, -1, dtype=np.int64 if n >= 2 ** 31 else np.int32)
     pts = np.empty((n, 3), dtype=np.float64)
     count = 0
     offs = np.arange(-reach, reach + 1)
@@ -140,21 +140,30 @@ def random_neutral(n: int, L: float | None = None, density: float = 1.0, hard_co
             bad = (d * d).sum(axis=1) < hc2
             ok[rows[bad]] = False
         # conflicts inside the batch: a candidate is dropped when it lies closer than the
-        # hard core to any earlier candidate of the same batch (earlier in proposal order)
+        # hard core to any earlier candidate of the same batch (earlier in proposal order).
+        # The batch's own cells are looked up by binary search in its sorted cell keys.
         idx = np.nonzero(ok)[0]
         if idx.size > 1:
             key = (cell[idx, 0] * g + cell[idx, 1]) * g + cell[idx, 2]
-            tmp = np.full(g * g * g, np.iinfo(np.int64).max, dtype=np.int64)
-            np.minimum.at(tmp, key, idx)
+            order = np.lexsort((idx, key))                 # by cell, then proposal order
+            skey, sidx = key[order], idx[order]
+            first = np.ones(skey.size, dtype=bool)
+            first[1:] = skey[1:] != skey[:-1]
             # two candidates in one grid cell are always too close: keep the first one
-            first = tmp[key] == idx
-            idx = idx[first]
-            occ = tmp[(nx[idx] * g + ny[idx]) * g + nz[idx]]
-            has = (occ < idx[:, None])
+            ukey, uidx = skey[first], sidx[first]
+            alive = np.zeros(want, dtype=bool)
+            alive[uidx] = True
+            idx = np.nonzero(alive)[0]
+            nkey = (nx[idx] * g + ny[idx]) * g + nz[idx]    # [m, (2 reach + 1)^3]
+            pos_ = np.searchsorted(ukey, nkey)
+            pos_ = np.minimum(pos_, ukey.size - 1)
+            hit = ukey[pos_] == nkey
+            other = np.where(hit, uidx[pos_], np.iinfo(np.int64).max)
+            has = other < idx[:, None]
             keep = np.ones(idx.size, dtype=bool)
             if has.any():
                 rows, cols = np.nonzero(has)
-                d = cand[idx[rows]] - cand[occ[rows, cols]]
+                d = cand[idx[rows]] - cand[other[rows, cols]]
                 d -= L * np.round(d / L)
                 bad = (d * d).sum(axis=1) < hc2
                 keep[rows[bad]] = False
