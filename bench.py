@@ -6,6 +6,7 @@ one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload random_32768]
                   [--precision mixed|fp64|fp32|mixed_bf16] [--impl ours|reference]
+                  [--md STEPS [--dt DT]]
 
 Timing: inputs resident in HBM; before every step a 512 MiB buffer is written to flush
 the L2 (129 MB); every step is bracketed by CUDA events on the launching stream and the
@@ -162,24 +163,40 @@ class ClockSampler:
 
 # ---- CPU oracle baseline ------------------------------------------------------------------
 
-def oracle_sample(pos, q, L, beta, rc, kmax, n_targets, seed=0):
+def oracle_sample(pos, q, L, beta, rc, kmax, n_targets, seed=0, S_given=None,
+                  max_sk_terms=8e9):
     """Time the FP64 oracle on a bounded sample of one evaluation and scale it to the whole
-    evaluation.  Sample: S(k) over all particles and all k, then real-space and reciprocal
-    forces for `n_targets` random particles; both force parts cost the same per target, so
-    the full time is t_S + (N / n_targets) * t_targets."""
+    evaluation.  Sample: S(k) over all particles (over a random subset of the modes when
+    |K_half| N exceeds max_sk_terms, scaled by the mode count), then real-space and
+    reciprocal forces for `n_targets` random particles; both force parts cost the same per
+    target, so the full time is t_S + (N / n_targets) t_targets.  When S(k) is sampled the
+    reciprocal forces use S_given (the structure factor of the path under test), so the
+    returned forces compare that path's back-scatter and real-space sums with the oracle's.
+    Returns (full time, CPU seconds spent, targets, target indices, oracle forces, note)."""
     import oracle
     n = len(q)
     rng = np.random.default_rng(seed)
     sub = np.sort(rng.choice(n, size=min(n_targets, n), replace=False))
-    t0 = time.perf_counter()
     m = oracle.kset_half(kmax)
-    S = oracle.structure_factor(pos, q, L, m)
+    nk = len(m)
+    t0 = time.perf_counter()
+    if nk * n <= max_sk_terms or S_given is None:
+        S = oracle.structure_factor(pos, q, L, m)
+        t_s = time.perf_counter() - t0
+        note = f"S(k) over all {n} particles and all {nk} modes"
+    else:
+        ms = np.sort(rng.choice(nk, size=max(1, int(max_sk_terms // n)), replace=False))
+        oracle.structure_factor(pos, q, L, m[ms])
+        t_s = (time.perf_counter() - t0) * nk / len(ms)
+        S = S_given
+        note = (f"S(k) over all {n} particles for {len(ms)} random modes, scaled to {nk} modes "
+                f"(reciprocal forces from the GPU's S(k))")
     t1 = time.perf_counter()
-    oracle.real(pos, q, L, beta, rc, sub=sub)
-    oracle.recip(pos, q, L, beta, kmax, sub=sub, S=S)
+    _, Fr, _ = oracle.real(pos, q, L, beta, rc, sub=sub)
+    _, Fk, _, _, _ = oracle.recip(pos, q, L, beta, kmax, sub=sub, S=S)
     t2 = time.perf_counter()
-    full = (t1 - t0) + (t2 - t1) * n / len(sub)
-    return full, (t2 - t0), len(sub)
+    full = t_s + (t2 - t1) * n / len(sub)
+    return full, (t2 - t0), len(sub), sub, Fr + Fk, note
 
 
 # ---- main ---------------------------------------------------------------------------------
@@ -263,6 +280,89 @@ def run_serving(args, rank, world, local):
                           "results": out, "server": stats}), flush=True)
 
 
+def run_md(args, rank, world, local):
+    """Molecular dynamics: `--md K` velocity-Verlet steps (unit masses, dt = 1e-3, the system
+    starting at rest) in one ewald_md call per replica; every step is one full evaluation plus
+    the kick/drift kernels.  Reports particle-steps/s over the K steps (the call also evaluates
+    the initial forces, which is counted inside the timed region) and the energy drift
+    max_s |E_tot(s) - E_tot(0)| relative to |E_pot(0)|."""
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1708_01135_gb300 import MD_RECORD, Ewald
+    gen, _ = WORKLOADS[args.workload]
+    pos, q, L = gen()
+    n = len(q)
+    rc, beta, kmax = params_for(args.workload, n, L)
+    dev = torch.device("cuda", local)
+    tq = torch.tensor(q, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    steps, dt = args.md, args.dt
+    log = torch.empty((steps + 1, MD_RECORD), dtype=torch.float64, device=dev)
+    ew = Ewald(L, beta, rc, kmax, args.precision)
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_warm = time.perf_counter()
+    w = 0
+    while w < args.warmup or time.perf_counter() - t_warm < 0.5:
+        tp = torch.tensor(pos, device=dev)
+        tv = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+        ew.md(tp, tv, tq, F, dt, 1)
+        w += 1
+        torch.cuda.synchronize()
+    if ew.status() != 0:
+        raise RuntimeError("warm-up MD step reported an error")
+    ew.profile(1)
+    ew.compute_async(tp, tq, F, torch.empty(4, dtype=torch.float64, device=dev))
+    _, per_eval = ew.profile(-1)
+    ew.profile(0)
+    tp = torch.tensor(pos, device=dev)
+    tv = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ew.md(tp, tv, tq, F, dt, steps, log=log)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    if ew.status() != 0:
+        raise RuntimeError("MD run reported an error")
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    lg = log.cpu().numpy()
+    e_tot = lg[:, 5]
+    drift = float(np.abs(e_tot - e_tot[0]).max() / abs(lg[0, 3]))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "ewald_md_particle_steps_per_s", "value": world * n * steps / (ms * 1e-3),
+            "unit": "particle-steps/s", "n_gpus": world, "steps": steps, "warmup": w,
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "L": L, "r_c": rc, "beta": beta,
+                       "k_max": kmax, "dt": dt, "mass": 1.0, "v0": 0.0,
+                       "precision": args.precision,
+                       "l2": "not flushed: the MD state stays resident from step to step",
+                       "parallelism": f"replicas x{world}"},
+            "energy": {"E_pot0": float(lg[0, 3]), "E_tot0": float(e_tot[0]),
+                       "E_kin_end": float(lg[-1, 4]), "drift_rel_max": drift,
+                       "drift_rel_end": float(abs(e_tot[-1] - e_tot[0]) / abs(lg[0, 3]))},
+            "gpu_launches": (steps + 1) * (per_eval + 2) + steps,
+            "clocks": clk}), flush=True)
+    ew.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -281,7 +381,9 @@ def run_reference(args, rank, world):
     targets = args.cpu_targets
     times = []
     for s in range(args.warmup + args.steps):
-        full, wall, nt = oracle_sample(pos, q, L, beta, rc, kmax, targets, seed=s)
+        full, wall, nt, _, _, note = oracle_sample(pos, q, L, beta, rc, kmax, targets, seed=s,
+                                                   S_given=np.zeros(len(oracle.kset_half(kmax)),
+                                                                    dtype=complex))
         if s >= args.warmup:
             times.append(full)
     t = float(np.mean(times))
@@ -295,8 +397,8 @@ def run_reference(args, rank, world):
                    "k_max": kmax, "tol": TOL},
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": f"S(k) over all {n} particles and all k, forces of {targets} "
-                                   f"random particles, scaled to {n}"},
+                         "sample": f"{note}; forces of {targets} random particles, scaled "
+                                   f"to {n}"},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -315,6 +417,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--fp64-max-n", type=int, default=300000,
+                    help="time the FP64 GPU path beside the line up to this N")
+    ap.add_argument("--md", type=int, default=0, help="velocity-Verlet MD steps (0: single evaluations)")
+    ap.add_argument("--dt", type=float, default=1e-3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -323,6 +429,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
+    if args.md:
+        return run_md(args, rank, world, local)
 
     import torch
     torch.cuda.set_device(local)
@@ -427,14 +535,45 @@ def main():
                 "peak_kind": "nominal FP64/FP32 CUDA-core rate (unit counts x clock)"}
     stages_ms = {k: float(np.median(v)) for k, v in stage.items()}
 
+    # the plain FP64 GPU path on the same system and parameters
+    fp64 = None
+    if args.precision != "fp64" and n <= args.fp64_max_n:
+        with Ewald(L, beta, rc, kmax, "fp64") as ew64:
+            for _ in range(2):
+                ew64.compute_async(tp, tq, F, E)
+            torch.cuda.synchronize()
+            t64 = []
+            for s in range(3):
+                flush.fill_(float(s))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ew64.compute_async(tp, tq, F, E)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t64.append(a.elapsed_time(b))
+            if ew64.status() != 0:
+                raise RuntimeError("FP64 evaluation reported an error")
+        ms64 = float(np.mean(t64))
+        fp64 = {"value": world * n / (ms64 * 1e-3), "unit": "particles/s", "ms_per_step": ms64,
+                "steps": 3, "speedup_of_this_line": ms64 / ms}
+
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        full, wall, nt = oracle_sample(pos, q, L, beta, rc, kmax, args.cpu_targets)
+        Sg = ew.structure_factor()
+        full, wall, nt, sub, Fo, note = oracle_sample(pos, q, L, beta, rc, kmax, args.cpu_targets,
+                                                      S_given=Sg)
         cpu = {"value": n / full, "unit": "particles/s", "cores": oracle.num_threads(),
-               "kind": "oracle", "sample": f"S(k) over all {n} particles and all k, forces of "
-                                           f"{nt} random particles, scaled to {n} "
-                                           f"({wall:.1f} s of CPU work)"}
+               "kind": "oracle", "sample": f"{note}; forces of {nt} random particles, scaled "
+                                           f"to {n} ({wall:.1f} s of CPU work)"}
+        Fg = hf[sub]        # forces of the last end-to-end evaluation (same input)
+        accuracy = {"rel_force_rms_vs_oracle": float(np.sqrt(((Fg - Fo) ** 2).sum() / (Fo ** 2).sum())),
+                    "particles": int(nt),
+                    "reference": "FP64 oracle at the same (beta, r_c, k_max): arithmetic error "
+                                 "of this path; the truncation error of the parameters is "
+                                 "stated separately",
+                    "oracle_sample": note}
     if rank == 0:
         line = {
             "metric": "ewald_particles_per_s", "value": value, "unit": "particles/s",
@@ -455,6 +594,8 @@ def main():
             "stages_ms": stages_ms,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
+            "fp64_gpu": fp64,
         }
         print(json.dumps(line), flush=True)
     ew.close()

@@ -192,6 +192,40 @@ int ewald_structure_factor(ewald_plan_t plan, double *S_dev, void *stream);
  * perm[s]) into device buffers.  Either pointer may be NULL. */
 int ewald_cell_sort(ewald_plan_t plan, int32_t *key_dev, int32_t *perm_dev, void *stream);
 
+/* Index of every entry of one ewald_md energy record (EWALD_MD_RECORD doubles). */
+enum { EWALD_MD_REAL = 0, EWALD_MD_RECIP = 1, EWALD_MD_SELF = 2, EWALD_MD_POT = 3,
+       EWALD_MD_KIN = 4, EWALD_MD_TOTAL = 5, EWALD_MD_RECORD = 6 };
+
+/*
+ * ewald_md - molecular dynamics with the Ewald forces: `steps` velocity-Verlet time steps
+ * of N charges in the plan's periodic box, every step ending with a full evaluation (the
+ * per-timestep force computation of Section 2.1; the paper benchmarks such time steps of
+ * an NaCl system in Section 4).  Per step, with a = F / m:
+ *     v <- v + (dt/2) a(x);   x <- x + dt v;   F <- forces at x (ewald_compute_async);
+ *     v <- v + (dt/2) a(x)
+ * The forces at the initial positions are evaluated first, so a call costs steps + 1
+ * evaluations.
+ *   pos         dev float64 [n][3], advanced in place (not wrapped: trajectories stay
+ *               continuous; every evaluation wraps internally)
+ *   vel         dev float64 [n][3], advanced in place
+ *   q           dev float64 [n]
+ *   mass        dev float64 [n] (every entry > 0), or NULL for unit masses
+ *   dt          time step (> 0, finite); steps >= 0
+ *   forces      dev float64 [n][3]: on return the forces at the final positions
+ *   energy_log  dev float64 [steps + 1][EWALD_MD_RECORD] or NULL: record s holds, after s
+ *               steps, E_real, E_recip, E_self, E_pot = their sum, the kinetic energy
+ *               1/2 sum m v^2 and E_pot + E_kin (record 0: the initial state)
+ *   stream      cudaStream_t; the call is asynchronous on it (it never synchronises except
+ *               for the first call with a larger n, which grows the plan's workspaces)
+ * Host-side argument errors are returned immediately (EWALD_E_INVAL).  Device-side
+ * validation of every evaluation of the run (neutrality, finiteness, bounded waits) is
+ * accumulated and returned by the next ewald_status_sync().  Every reduction has a fixed
+ * order: repeated runs from the same state give bit-identical trajectories.
+ */
+int ewald_md(ewald_plan_t plan, int64_t n, double *pos, double *vel, const double *q,
+             const double *mass, double dt, int steps, double *forces, double *energy_log,
+             void *stream);
+
 /*
  * ewald_tune - choose (beta, r_c, k_max) for a target relative RMS force error.
  *   n, L      particle count and box side

@@ -52,6 +52,8 @@ def lib():
             L.ewo_kset_half.argtypes = [ctypes.c_int, _p, _i64]
             L.ewo_real.restype = None
             L.ewo_real.argtypes = [_i64, _p, _p, _d, _d, _d, _i64, _p, _p, _p, _p]
+            L.ewo_real_cells.restype = ctypes.c_int
+            L.ewo_real_cells.argtypes = [_i64, _p, _p, _d, _d, _d, _i64, _p, _p, _p, _p]
             L.ewo_structure_factor.restype = None
             L.ewo_structure_factor.argtypes = [_i64, _p, _p, _d, _i64, _p, _p]
             L.ewo_recip_energy.restype = _d
@@ -107,6 +109,22 @@ def real(pos, q, L, beta, rc, sub=None):
     lib().ewo_real(len(q), _ptr(pos), _ptr(q), float(L), float(beta), float(rc),
                    0 if sub is None else len(sub), _ptr(sub), _ptr(F), _ptr(phi),
                    ctypes.byref(e) if sub is None else None)
+    return (e.value if sub is None else None), F, phi
+
+
+def real_cells(pos, q, L, beta, rc, sub=None):
+    """Real-space part through a cell list (needs r_c <= L/2 and floor(L / r_c) >= 3):
+    (E_real or None when sub is given, F [nt, 3], phi [nt]); the same sums as real()."""
+    pos, q, sub = _f64(pos), _f64(q), _sub(sub)
+    nt = len(q) if sub is None else len(sub)
+    F = np.zeros((nt, 3))
+    phi = np.zeros(nt)
+    e = _d(0.0)
+    rc_ = lib().ewo_real_cells(len(q), _ptr(pos), _ptr(q), float(L), float(beta), float(rc),
+                               0 if sub is None else len(sub), _ptr(sub), _ptr(F), _ptr(phi),
+                               ctypes.byref(e) if sub is None else None)
+    if rc_ != 0:
+        raise ValueError("real_cells needs r_c <= L/2 and at least 3 cells per side")
     return (e.value if sub is None else None), F, phi
 
 

@@ -38,8 +38,9 @@
  * Parity pins (all in tests/test_oracle.py): Madelung constants of rock-salt and CsCl,
  * invariance of the total energy under beta at converged cutoffs, sum of forces = 0,
  * central finite differences of the energy, brute-force image sums of tiny neutral cells
- * (ewo_coulomb_cube), the exactly known S(k) of an unjittered rock-salt lattice, and
- * lattice-point counts for the k-set.
+ * (ewo_coulomb_cube), the exactly known S(k) of an unjittered rock-salt lattice,
+ * lattice-point counts for the k-set, and equality of the cell-list real-space sum
+ * (ewo_real_cells) with the all-pairs one (ewo_real).
  */
 #include <math.h>
 #include <stddef.h>
@@ -185,6 +186,103 @@ void ewo_real(int64_t n, const double *pos, const double *q, double L, double be
         *e_real = e;
     }
     if (phi_tmp != phi_out) free(phi_tmp);
+}
+
+/*
+ * The same real-space sum through a cell list (the binned pair loop of Section 3.1.1), for
+ * systems too large for the all-pairs loop above.  Requires r_c <= L/2 (minimum image) and
+ * at least 3 cells per side: the box is cut into nc = floor(L / r_c) cells per side, so that
+ * every partner within r_c of a target lies in the target's cell or one of its 26
+ * neighbours, and those 27 cells are distinct.  Particles are bucketed by a serial counting
+ * pass in index order; a target visits its 27 cells in a fixed order and every particle of a
+ * cell in index order.  Outputs as ewo_real.  Returns 0, or -1 when the conditions above do
+ * not hold (nothing written).
+ */
+int ewo_real_cells(int64_t n, const double *pos, const double *q, double L, double beta,
+                   double rc, int64_t nsub, const int64_t *sub, double *F_out, double *phi_out,
+                   double *e_real)
+{
+    if (!(rc <= 0.5 * L)) return -1;
+    const int64_t nc = (int64_t)floor(L / rc);
+    if (nc < 3) return -1;
+    const int64_t ncell = nc * nc * nc;
+    const int64_t nt = sub ? nsub : n;
+    const double rc2 = rc * rc;
+    const double two_beta_rpi = 2.0 * beta / sqrt(EWO_PI);
+    double *w = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
+    int64_t *cell = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *start = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+    int64_t *member = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *fill = (int64_t *)malloc((size_t)ncell * sizeof(int64_t));
+    double *phi_tmp = phi_out;
+    if (!phi_tmp && e_real) phi_tmp = (double *)malloc((size_t)(nt > 0 ? nt : 1) * sizeof(double));
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t c[3];
+        for (int a = 0; a < 3; ++a) {
+            w[3 * j + a] = wrap1(pos[3 * j + a], L);
+            int64_t ca = (int64_t)floor(w[3 * j + a] * (double)nc / L);
+            if (ca >= nc) ca = nc - 1;
+            c[a] = ca;
+        }
+        cell[j] = (c[2] * nc + c[1]) * nc + c[0];
+        start[cell[j] + 1] += 1;
+    }
+    for (int64_t c = 0; c < ncell; ++c) start[c + 1] += start[c];
+    for (int64_t c = 0; c < ncell; ++c) fill[c] = start[c];
+    for (int64_t j = 0; j < n; ++j) member[fill[cell[j]]++] = j;
+    /* positions and charges copied into cell order, so that a cell's members are contiguous */
+    double *ws = (double *)malloc((size_t)(n > 0 ? n : 1) * 4 * sizeof(double));
+    for (int64_t s = 0; s < n; ++s) {
+        const int64_t j = member[s];
+        ws[4 * s + 0] = w[3 * j + 0];
+        ws[4 * s + 1] = w[3 * j + 1];
+        ws[4 * s + 2] = w[3 * j + 2];
+        ws[4 * s + 3] = q[j];
+    }
+
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        const int64_t i = sub ? sub[t] : t;
+        const double xi = w[3 * i], yi = w[3 * i + 1], zi = w[3 * i + 2];
+        const int64_t ci = cell[i];
+        const int64_t cx = ci % nc, cy = (ci / nc) % nc, cz = ci / (nc * nc);
+        double fx = 0.0, fy = 0.0, fz = 0.0, phi = 0.0;
+        for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    const int64_t c = (((cz + oz + nc) % nc) * nc + (cy + oy + nc) % nc) * nc
+                                      + (cx + ox + nc) % nc;
+                    for (int64_t s = start[c]; s < start[c + 1]; ++s) {
+                        if (member[s] == i) continue;
+                        const double *pj = ws + 4 * s;
+                        double dx = xi - pj[0], dy = yi - pj[1], dz = zi - pj[2];
+                        dx -= L * round(dx / L);
+                        dy -= L * round(dy / L);
+                        dz -= L * round(dz / L);
+                        const double d2 = dx * dx + dy * dy + dz * dz;
+                        if (!(d2 < rc2)) continue;
+                        const double d = sqrt(d2);
+                        const double e = erfc(beta * d) / d;
+                        const double sc = pj[3] * (e + two_beta_rpi * exp(-beta * beta * d2)) / d2;
+                        phi += pj[3] * e;
+                        fx += sc * dx; fy += sc * dy; fz += sc * dz;
+                    }
+                }
+        if (F_out) {
+            F_out[3 * t + 0] = q[i] * fx;
+            F_out[3 * t + 1] = q[i] * fy;
+            F_out[3 * t + 2] = q[i] * fz;
+        }
+        if (phi_tmp) phi_tmp[t] = phi;
+    }
+    if (e_real) {
+        double e = 0.0;
+        for (int64_t t = 0; t < nt; ++t) e += 0.5 * q[sub ? sub[t] : t] * phi_tmp[t];
+        *e_real = e;
+    }
+    if (phi_tmp != phi_out) free(phi_tmp);
+    free(w); free(ws); free(cell); free(start); free(member); free(fill);
+    return 0;
 }
 
 /*

@@ -247,7 +247,7 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
 }
 
 cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
-                     double *energy_dev, int parts, cudaStream_t st)
+                     double *energy_dev, int parts, cudaStream_t st, bool clear_status = true)
 {
     cudaError_t e;
     Workspace &ws = p.ws;
@@ -256,7 +256,8 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     // reported against this one
     (void)cudaGetLastError();
     prof_mark(p, kEvStart, st);
-    if ((e = cudaMemsetAsync(p.d_status, 0, sizeof(int), st)) != cudaSuccess) return e;
+    if (clear_status && (e = cudaMemsetAsync(p.d_status, 0, sizeof(int), st)) != cudaSuccess)
+        return e;
     if ((e = launch_binning(p, n, pos, q, st)) != cudaSuccess) return e;
     prof_mark(p, kEvBinned, st);
     const int64_t tiles = real_tile_capacity(p, n);
@@ -291,6 +292,14 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
 }
 
 }  // namespace
+
+cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
+                     double *energy_dev, int parts, cudaStream_t st, bool clear_status)
+{
+    cudaError_t e = grow_workspace(p, n);
+    if (e != cudaSuccess) return e;
+    return pipeline(p, n, pos, q, forces, energy_dev, parts, st, clear_status);
+}
 
 size_t plan_footprint(const Plan &p, int64_t n)
 {

@@ -144,9 +144,11 @@ cudaError_t alloc_recip_tc(Plan &p, int64_t n);
 size_t recip_tc_bytes(const Plan &p, int64_t n);
 int recip_tc_energy_parts(const Plan &p);   // entries of the partial reciprocal energies
 void free_recip_tc(Plan &p);
-// a9: self term, totals, unsort to caller order.
-cudaError_t launch_finalize(Plan &p, int64_t n, const double *q, double *forces,
-                            double *energy_dev, int parts, cudaStream_t st);
+// One whole evaluation on `st` (grows the workspaces for n first; n > 0).  With
+// clear_status false the plan's device status keeps the bits of earlier evaluations, so that
+// a sequence of evaluations reports every failure at the next ewald_status_sync.
+cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
+                     double *energy_dev, int parts, cudaStream_t st, bool clear_status);
 
 // Library memory pool (stream-ordered, retains freed memory for reuse).
 cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st);

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libewald.so")
 FP64, MIXED, MIXED_BF16, FP32 = 0, 1, 2, 3
 PRECISIONS = {"fp64": FP64, "mixed": MIXED, "mixed_bf16": MIXED_BF16, "fp32": FP32}
 PART_REAL, PART_RECIP, PART_SELF, PART_ALL = 1, 2, 4, 7
+MD_RECORD = 6      # E_real, E_recip, E_self, E_pot, E_kin, E_total per ewald_md record
 
 OK, PENDING = 0, 1
 E_INVAL, E_NONNEUTRAL, E_CUTOFF, E_NOMEM, E_CUDA = -1, -2, -3, -4, -5
@@ -80,6 +81,7 @@ def lib() -> ctypes.CDLL:
                 "ewald_server_stats": (_i, [_p, _p]),
                 "ewald_server_destroy": (_i, [_p]),
                 "ewald_real_noalloc": (_i, [_d, _d, _d, _i64, _p, _p, _p, _p, _p]),
+                "ewald_md": (_i, [_p, _i64, _p, _p, _p, _p, _d, _i, _p, _p, _p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -190,6 +192,20 @@ class Ewald:
                                          _dev_f64(q, (n,), "q"), _dev_f64(forces, (n, 3), "forces"),
                                          _dev_f64(energy, (4,), "energy"), int(parts),
                                          _stream_handle(stream)), "ewald_compute_async")
+
+    def md(self, pos, vel, q, forces, dt: float, steps: int, mass=None, log=None, stream=None):
+        """Velocity-Verlet MD (ewald_md), asynchronous on the stream: pos and vel [n,3] are
+        advanced in place, forces [n,3] ends with the forces at the final positions, and log
+        (None or [steps + 1, 6]: E_real, E_recip, E_self, E_pot, E_kin, E_total per step,
+        record 0 the initial state) is filled on the device.  mass: None (unit masses) or [n].
+        Call status() for the device-side validation of the run."""
+        n = int(q.shape[0])
+        _check(lib().ewald_md(self._h, n, _dev_f64(pos, (n, 3), "pos"), _dev_f64(vel, (n, 3), "vel"),
+                              _dev_f64(q, (n,), "q"),
+                              None if mass is None else _dev_f64(mass, (n,), "mass"),
+                              float(dt), int(steps), _dev_f64(forces, (n, 3), "forces"),
+                              None if log is None else _dev_f64(log, (int(steps) + 1, MD_RECORD), "log"),
+                              _stream_handle(stream)), "ewald_md")
 
     def status(self) -> int:
         """Synchronise and return the device-side status of the last evaluation."""

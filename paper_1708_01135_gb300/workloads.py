@@ -16,7 +16,9 @@ of shape [n]; every system is exactly neutral.
 """
 from __future__ import annotations
 
+import hashlib
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -116,21 +118,22 @@ def random_neutral(n: int, L: float | None = None, density: float = 1.0, hard_co
     grid = np.full(g * g * g, -1, dtype=np.int64 if n >= 2 ** 31 else np.int32)
     pts = np.empty((n, 3), dtype=np.float64)
     count = 0
-    offs = np.arange(-reach, reach + 1)
-    ox, oy, oz = np.meshgrid(offs, offs, offs, indexing="ij")
-    ox, oy, oz = ox.ravel(), oy.ravel(), oz.ravel()
+    kt = np.int32 if g ** 3 < 2 ** 31 else np.int64
+    offs = np.arange(-reach, reach + 1, dtype=kt)
     hc2 = hard_core * hard_core
     batch = batch or max(64, min(n, 1 << 16))
     stall = 0
     while count < n:
         want = min(batch, max(64, 2 * (n - count)))
         cand = rng.uniform(0.0, L, size=(want, 3))
-        cell = np.minimum((cand / h).astype(np.int64), g - 1)
-        # neighbour cells of every candidate: [want, (2 reach + 1)^3]
-        nx = (cell[:, 0:1] + ox) % g
-        ny = (cell[:, 1:2] + oy) % g
-        nz = (cell[:, 2:3] + oz) % g
-        occ = grid[(nx * g + ny) * g + nz]
+        cell = np.minimum((cand / h).astype(np.int64), g - 1).astype(kt)
+        # neighbour cells of every candidate: [want, (2 reach + 1)^3], built per axis
+        cx = (cell[:, 0:1] + offs) % g
+        cy = (cell[:, 1:2] + offs) % g
+        cz = (cell[:, 2:3] + offs) % g
+        nkey_all = (((cx * g)[:, :, None] + cy[:, None, :]) * g)[:, :, :, None] + cz[:, None, None, :]
+        nkey_all = nkey_all.reshape(want, -1)
+        occ = grid[nkey_all]
         ok = np.ones(want, dtype=bool)
         has = occ >= 0
         if has.any():
@@ -154,7 +157,7 @@ def random_neutral(n: int, L: float | None = None, density: float = 1.0, hard_co
             alive = np.zeros(want, dtype=bool)
             alive[uidx] = True
             idx = np.nonzero(alive)[0]
-            nkey = (nx[idx] * g + ny[idx]) * g + nz[idx]    # [m, (2 reach + 1)^3]
+            nkey = nkey_all[idx]                           # [m, (2 reach + 1)^3]
             pos_ = np.searchsorted(ukey, nkey)
             pos_ = np.minimum(pos_, ukey.size - 1)
             hit = ukey[pos_] == nkey
@@ -202,9 +205,43 @@ def rocksalt_262144(seed: int = 1237):
 
 def random_2097152(seed: int = 1239):
     """N = 2,097,152 with charges +-1 (40 % each) and +-2 (10 % each), uniform at
-    density 1.0 (L = 128) with a 0.8 hard core."""
-    return random_neutral(2097152, density=1.0, hard_core=0.8,
-                          mix=((1.0, 0.4), (2.0, 0.1)), seed=seed)
+    density 1.0 (L = 128) with a 0.8 hard core.  Generation takes minutes, so the result
+    is kept in the on-disk cache (see :func:`_cached`)."""
+    return _cached(f"random_2097152_s{seed}",
+                   lambda: random_neutral(2097152, density=1.0, hard_core=0.8,
+                                          mix=((1.0, 0.4), (2.0, 0.1)), seed=seed))
+
+
+def _cache_dir() -> str:
+    d = os.environ.get("EWALD_WORKLOAD_CACHE")
+    if d:
+        return d
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "_build", "workloads")
+
+
+def _cached(key: str, make):
+    """Return make() = (pos, q, L), stored once as .npz under the cache directory
+    (EWALD_WORKLOAD_CACHE, default _build/workloads at the repository root).  The file
+    name carries a digest of this module's source, so an edited generator never reads an
+    older result."""
+    with open(os.path.abspath(__file__), "rb") as f:
+        tag = hashlib.sha256(f.read()).hexdigest()[:12]
+    path = os.path.join(_cache_dir(), f"{key}-{tag}.npz")
+    try:
+        with np.load(path) as z:
+            return np.ascontiguousarray(z["pos"]), np.ascontiguousarray(z["q"]), float(z["L"])
+    except (OSError, KeyError, ValueError):
+        pass
+    pos, q, L = make()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = f"{path}.tmp{os.getpid()}.npz"
+        np.savez(tmp, pos=pos, q=q, L=np.float64(L))
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return pos, q, L
 
 
 @dataclass

@@ -83,6 +83,7 @@ def test_null_handles_are_rejected():
     assert lib.ewald_server_destroy(None) == E.E_INVAL
     r = E._Result()
     assert lib.ewald_poll(None, 1, ctypes.byref(r)) == E.E_INVAL
+    assert lib.ewald_md(None, 4, None, None, None, None, 1e-3, 10, None, None, None) == E.E_INVAL
 
 
 def test_realspace_erfc_fit_meets_its_published_bound():

@@ -251,3 +251,26 @@ def test_pair_in_large_box_approaches_bare_coulomb():
     r = O.ewald(pos, q, L, beta, *_converged(L, beta))
     assert abs(r["E_total"] - (-1.0 / d)) < 1e-3
     assert abs(r["F"][0, 0] - (1.0 / d ** 2)) < 1e-3
+
+
+@pytest.mark.parametrize("n,L,rc,seed", [(3000, 15.0, 5.0, 3), (2000, 13.7, 4.1, 4), (1200, 11.0, 3.0, 5)])
+def test_cell_list_real_space_equals_all_pairs(n, L, rc, seed):
+    """The binned real-space sum visits exactly the pairs of the all-pairs loop: the results
+    agree to rounding (3 cells per side with L/r_c an integer, ragged cells, 3 cells at
+    L/r_c = 3.34, and particles given outside [0, L))."""
+    pos, q, L = W.random_neutral(n, L=L, hard_core=0.7, seed=seed, mix=((1.0, 0.4), (2.0, 0.1)))
+    pos = pos + L * np.random.default_rng(seed).integers(-2, 3, size=pos.shape)
+    e0, F0, p0 = O.real(pos, q, L, 0.9, rc)
+    e1, F1, p1 = O.real_cells(pos, q, L, 0.9, rc)
+    assert abs(e1 - e0) <= 1e-12 * abs(e0)
+    assert np.abs(F1 - F0).max() <= 1e-12 * np.abs(F0).max()
+    assert np.abs(p1 - p0).max() <= 1e-12 * np.abs(p0).max()
+    sub = np.array([0, 7, n // 2, n - 1])
+    _, Fs, ps = O.real_cells(pos, q, L, 0.9, rc, sub=sub)
+    assert np.array_equal(Fs, F1[sub]) and np.array_equal(ps, p1[sub])
+
+
+def test_cell_list_rejects_too_few_cells():
+    pos, q, L = W.rocksalt(4)
+    with pytest.raises(ValueError):
+        O.real_cells(pos, q, L, 1.0, 1.5)       # floor(4 / 1.5) = 2 cells per side
