@@ -24,15 +24,18 @@
 // Accumulation accuracy.  The rounding error of the tensor cores' FP32 accumulation grows
 // with the number of products summed into one accumulator, so the forward product (a sum
 // over all particles) accumulates only 128 particles per TMEM accumulator: two accumulator
-// buffers alternate, and drain warps add every finished buffer into an FP32 running sum in
-// shared memory (rounded to nearest) while the tensor cores fill the other.  The back-scatter
+// buffers alternate (one where tensor memory is short), and drain warps add every finished
+// buffer into an FP32 running sum, rounded to nearest, that is kept in another region of
+// tensor memory while the tensor cores fill the other buffer.  The back-scatter
 // (a sum over rows) processes rows in order of decreasing m_y^2 + m_z^2, so the coefficients
 // grow along the sum.
 //
 // Kernel structure (warp-specialised, mbarrier pipeline in shared memory):
-//   forward:      warps 0-7 generate A and B of each stage; warps 8-11 drain TMEM; warp 12
-//                 stages the particle data of each stage with a bulk TMA copy; warp 13
-//                 issues tcgen05.mma (one thread) and releases stages with tcgen05.commit.
+//   forward:      warps 0-7 generate A of each stage; warps 8-11 drain TMEM; warps 12 and
+//                 13 stream the particle data and the pre-built B operand of each stage by
+//                 bulk TMA into two separate rings; warp 14 issues tcgen05.mma (one thread)
+//                 and releases stages with tcgen05.commit.  Work is split evenly over one
+//                 CTA per SM ("stream-K" over (row group, particle stage) items).
 //   back-scatter: warps 0-7 generate A (one particle per thread) and then run the
 //                 epilogue; warp 8 streams the pre-packed G' tiles (with their row headers)
 //                 by bulk TMA; warp 9 issues tcgen05.mma.
@@ -47,6 +50,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "ewald_internal.cuh"
 
 namespace ew {
@@ -55,7 +60,7 @@ namespace {
 // ---- tiling ---------------------------------------------------------------------------
 constexpr int kFK = 32;        // forward: particles (K) per stage
 constexpr int kFChunk = 4;     // forward: stages per TMEM accumulator (128 particles)
-constexpr int kFThreads = 448; // forward: 14 warps
+constexpr int kFThreads = 480; // forward: 15 warps
 constexpr int kBK = 32;        // back-scatter: real K per stage (16 rows r)
 constexpr int kBStages = 3;
 constexpr int kBMT = 2;        // back-scatter: M tiles of 128 particles per CTA
@@ -212,55 +217,105 @@ __device__ __forceinline__ void st16(unsigned char *base, uint32_t off, uint32_t
 }
 
 // ---- forward: structure-factor partials ------------------------------------------------
-// grid (M groups of MT tiles of 64 rows r, K splits); block kFThreads.
-// Output Dpart[(ks * ntiles + tile) * NF * 128 + col * 128 + row] (FP32): row < 64 holds the
-// real part of A for row r = tile * 64 + row, row >= 64 the imaginary part.
+// Work partition ("stream-K"): the work items are (M group g of MT tiles of 64 rows,
+// 32-particle stage s), W = groups * stages of them in group-major order, and CTA c of the G
+// CTAs (one per SM) takes the contiguous items [floor(c W / G), floor((c + 1) W / G)).  A
+// CTA's items form one or a few segments, each inside one group; every segment yields one
+// partial sum ("piece") per tile, written to dpart[(tile * maxp + piece) * NF * 128 + ...]
+// with piece = c - (first CTA of the group).  Every SM gets the same number of items
+// whatever the group count.
+//
+// Roles (block kFThreads = 15 warps):
+//   warps 0-7   producers: A = e^{i(k_y y_j + k_z z_j)} of every stage (MT tiles, hi and lo
+//               terms) into the A ring; particle data comes from the P ring
+//   warps 8-11  drain: every TMEM accumulator buffer (kFChunk stages = 128 particles) is
+//               added into an FP32 running sum that also lives in TMEM; at the end of a
+//               segment the sum goes to dpart
+//   warp 12     bulk copies of (u_y, u_z) of every stage into the P ring
+//   warp 13     bulk copies of the B operand (q_j X_j[m], hi and lo) into the B ring
+//   warp 14     tcgen05.mma issue (one thread) and stage release by tcgen05.commit
+// TMEM columns: accumulator buffer b, tile mt at (b MT + mt) CT; running sum of tile mt at
+// (NBUF MT + mt) CT; CT = NF rounded up to 32.
+__host__ __device__ inline int64_t fwd_item0(int c, int64_t W, int G) { return (int64_t)c * W / G; }
+__host__ __device__ inline int fwd_cta_of(int64_t w, int64_t W, int G) { return (int)(((w + 1) * G - 1) / W); }
+
+__device__ __forceinline__ void tm_ld16r(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                   "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_st16r(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]),
+                   "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]),
+                   "r"(r[13]), "r"(r[14]), "r"(r[15]) : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Split a pair of FP32 values into packed FP16 hi and lo pairs: hi = rn(v), lo = rn(v - hi)
+// (v - hi is exact in FP32; the mixed-precision FMA forms it from the packed hi directly).
+__device__ __forceinline__ void split2_f16(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    __half2 h = __floats2half2_rn(a, b);
+    const unsigned short h0 = __half_as_ushort(__low2half(h)), h1 = __half_as_ushort(__high2half(h));
+    const unsigned short m1 = 0xbc00;          // -1.0 in FP16
+    float la, lb;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(la) : "h"(h0), "h"(m1), "f"(a));
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(lb) : "h"(h1), "h"(m1), "f"(b));
+    __half2 l = __floats2half2_rn(la, lb);
+    hi = *reinterpret_cast<uint32_t *>(&h);
+    lo = *reinterpret_cast<uint32_t *>(&l);
+}
+
 template <int MT, bool BF>
 __global__ void __launch_bounds__(kFThreads, 1)
-k_fwd_tc(int n, int R, int kmax, int NF, int per, int ntiles, int S, const RowInfo *__restrict__ rows,
-         const int *__restrict__ fperm, const unsigned char *__restrict__ xblob,
+k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, int SB, int SP,
+         int NBUF, int CT, const RowInfo *__restrict__ rows, const int *__restrict__ fperm,
+         const uint2 *__restrict__ yz, const unsigned char *__restrict__ bblob,
          float *__restrict__ dpart, int *__restrict__ status)
 {
-    // S: pipeline stages (2 or 3, as many as fit in shared memory)
-    constexpr int BUF = 256;                     // TMEM columns per accumulator buffer
-    constexpr int KC = kFK / 8;                  // K chunks per stage
+    constexpr int KC = kFK / 8;                  // K chunks of 8 per stage
+    constexpr int A_BYTES = 128 * kFK * 2;       // one 128 x 32 half tile
+    constexpr int A_STAGE = MT * 2 * A_BYTES;    // MT tiles, hi and lo
+    constexpr int P_STAGE = kFK * 8;             // (u_y, u_z) of 32 particles
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int A_BYTES = 128 * kFK * 2;
     const int B_BYTES = NF * kFK * 2;
-    const int P_OFF = MT * 2 * A_BYTES;          // stage blob: particles, then B hi, B lo
-    const int B_OFF = P_OFF + kFK * 16;
-    const int BLOB = kFK * 16 + 2 * B_BYTES;
-    const int STAGE = P_OFF + BLOB;
-    float *acc = reinterpret_cast<float *>(sm + S * STAGE);             // [MT][NF][128]
-    int2 *rowc = reinterpret_cast<int2 *>(acc + MT * NF * 128);         // [MT * 64]
-    uint64_t *pfull = reinterpret_cast<uint64_t *>(rowc + MT * 64);
-    uint64_t *full = pfull + S;
-    uint64_t *empty = full + S;
-    uint64_t *accf = empty + S;      // [2]
+    const int B_STAGE = 2 * B_BYTES;
+    unsigned char *smA = sm;
+    unsigned char *smB = smA + SA * A_STAGE;
+    unsigned char *smP = smB + SB * B_STAGE;
+    uint64_t *a_full = reinterpret_cast<uint64_t *>(smP + SP * P_STAGE);
+    uint64_t *a_empty = a_full + SA;
+    uint64_t *b_full = a_empty + SA;
+    uint64_t *b_empty = b_full + SB;
+    uint64_t *p_full = b_empty + SB;
+    uint64_t *p_empty = p_full + SP;
+    uint64_t *accf = p_empty + SP;   // [2]
     uint64_t *acce = accf + 2;       // [2]
     uint64_t *mmad = acce + 2;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mmad + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int mgroup = blockIdx.x, ks = blockIdx.y;
-    const int p0 = ks * per;
-    const int p1 = min(n, p0 + per);
-    const int nst = (p1 - p0 + kFK - 1) / kFK;
-    const int nch = (nst + kFChunk - 1) / kFChunk;
+    const int G = gridDim.x, c = blockIdx.x;
+    const int64_t w_begin = fwd_item0(c, W, G), w_end = fwd_item0(c + 1, W, G);
+    const int nit = (int)(w_end - w_begin);
 
     if (t == 0) {
-        for (int s = 0; s < S; ++s) { mb_init(&pfull[s], 1); mb_init(&full[s], 256); mb_init(&empty[s], 1); }
+        for (int s = 0; s < SA; ++s) { mb_init(&a_full[s], 256); mb_init(&a_empty[s], 1); }
+        for (int s = 0; s < SB; ++s) { mb_init(&b_full[s], 1); mb_init(&b_empty[s], 1); }
+        for (int s = 0; s < SP; ++s) { mb_init(&p_full[s], 1); mb_init(&p_empty[s], 256); }
         for (int b = 0; b < 2; ++b) { mb_init(&accf[b], 1); mb_init(&acce[b], 128); }
         mb_init(mmad, 1);
         *abort = 0;
         mb_fence_init();
-    }
-    for (int i = t; i < MT * 64; i += kFThreads) {
-        const int gr = mgroup * MT * 64 + i;
-        int2 v = make_int2(0, 0x40000000);   // padding rows: never continue a run, zero charge
-        if (gr < R) { const RowInfo ri = rows[fperm[gr]]; v = make_int2(ri.my, ri.mz); }
-        rowc[i] = v;
     }
     if (warp == 0) { tm_alloc(tslot, 512); tm_relinquish(); }
     tc_before();
@@ -269,121 +324,186 @@ k_fwd_tc(int n, int R, int kmax, int NF, int per, int ntiles, int S, const RowIn
     const uint32_t tmem = *tslot;
 
     if (t < 256) {
-        // ---- producers ----
-        // A: thread t owns row slot rl = t % 64 and particle chunk c = (t / 64) % 4 of every
-        //    M tile (MT units, computed together for instruction-level parallelism)
-        // (the charges q_j multiply the B operand, built by k_xgen)
-        const int rl = t & 63, c = (t >> 6) & 3;
+        // ---- producers: thread t owns row slot rl = t % 64 and particles 8c..8c+7 ----
+        const int rl = t & 63, pc = (t >> 6) & 3;
         int2 rc[MT];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) rc[mt] = rowc[mt * 64 + rl];
-        for (int it = 0; it < nst; ++it) {
-            const int s = it % S, u = it / S;
-            if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
-            if (!waitw(&pfull[s], u & 1, abort)) break;
-            unsigned char *st = sm + s * STAGE;
-            const uint4 *P = reinterpret_cast<const uint4 *>(st + P_OFF);
-            const int jn = p1 - (p0 + it * kFK);          // valid particles in this stage
-            {
-                float re[MT][8], im[MT][8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int j = 8 * c + e;
-                    const uint4 pj = P[j < jn ? j : 0];
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        float cs, sn;
-                        phase((uint32_t)rc[mt].x * pj.y + (uint32_t)rc[mt].y * pj.z, cs, sn);
-                        re[mt][e] = j < jn ? cs : 0.f; im[mt][e] = j < jn ? sn : 0.f;
-                    }
-                }
+        int gcur = -1;
+        for (int it = 0; it < nit; ++it) {
+            const int64_t w = w_begin + it;
+            const int g = (int)(w / nst_all);
+            if (g != gcur) {
+                gcur = g;
 #pragma unroll
                 for (int mt = 0; mt < MT; ++mt) {
-                    unsigned char *ahi = st + (mt * 2) * A_BYTES;
-                    uint32_t h[4], l[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) split2<BF>(re[mt][2 * e], re[mt][2 * e + 1], h[e], l[e]);
-                    st16(ahi, tile_off(rl, c, KC), h[0], h[1], h[2], h[3]);
-                    st16(ahi + A_BYTES, tile_off(rl, c, KC), l[0], l[1], l[2], l[3]);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) split2<BF>(im[mt][2 * e], im[mt][2 * e + 1], h[e], l[e]);
-                    st16(ahi, tile_off(64 + rl, c, KC), h[0], h[1], h[2], h[3]);
-                    st16(ahi + A_BYTES, tile_off(64 + rl, c, KC), l[0], l[1], l[2], l[3]);
+                    const int gr = (g * MT + mt) * 64 + rl;
+                    int2 v = make_int2(0, 0);          // padding rows: any finite phase
+                    if (gr < R) { const RowInfo ri = rows[fperm[gr]]; v = make_int2(ri.my, ri.mz); }
+                    rc[mt] = v;
                 }
+            }
+            const int sa = it % SA, ua = it / SA, sp = it % SP, up = it / SP;
+            if (ua > 0 && !waitw(&a_empty[sa], (ua - 1) & 1, abort)) break;
+            if (!waitw(&p_full[sp], up & 1, abort)) break;
+            uint32_t py[8], pz[8];
+            {
+                const uint4 *P4 = reinterpret_cast<const uint4 *>(smP + sp * P_STAGE) + 4 * pc;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint4 v = P4[i];
+                    py[2 * i] = v.x; pz[2 * i] = v.y; py[2 * i + 1] = v.z; pz[2 * i + 1] = v.w;
+                }
+            }
+            mb_arrive(&p_empty[sp]);
+            unsigned char *st = smA + sa * A_STAGE;
+            float re[MT][8], im[MT][8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+                    phase((uint32_t)rc[mt].x * py[e] + (uint32_t)rc[mt].y * pz[e], re[mt][e], im[mt][e]);
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                unsigned char *ahi = st + (mt * 2) * A_BYTES;
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (BF) split2<true>(re[mt][2 * e], re[mt][2 * e + 1], h[e], l[e]);
+                    else split2_f16(re[mt][2 * e], re[mt][2 * e + 1], h[e], l[e]);
+                }
+                st16(ahi, tile_off(rl, pc, KC), h[0], h[1], h[2], h[3]);
+                st16(ahi + A_BYTES, tile_off(rl, pc, KC), l[0], l[1], l[2], l[3]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (BF) split2<true>(im[mt][2 * e], im[mt][2 * e + 1], h[e], l[e]);
+                    else split2_f16(im[mt][2 * e], im[mt][2 * e + 1], h[e], l[e]);
+                }
+                st16(ahi, tile_off(64 + rl, pc, KC), h[0], h[1], h[2], h[3]);
+                st16(ahi + A_BYTES, tile_off(64 + rl, pc, KC), l[0], l[1], l[2], l[3]);
             }
             fence_async_smem();
-            mb_arrive(&full[s]);
+            mb_arrive(&a_full[sa]);
         }
     } else if (t < 384) {
-        // ---- drain warps: TMEM accumulator buffer -> FP32 running sum in shared memory ----
+        // ---- drain: TMEM accumulator buffer -> TMEM running sum -> dpart ----
         const int row = t - 256;                     // TMEM lane (warp 8 + q owns lanes 32q..)
-        for (int i = 0; i < MT * NF; ++i) acc[i * 128 + row] = 0.f;
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        for (int ch = 0; ch < nch; ++ch) {
-            const int b = ch & 1;
-            if (!waitw(&accf[b], (ch >> 1) & 1, abort)) break;
-            tc_after();
+        int gch = 0;
+        int64_t w = w_begin;
+        bool ok = true;
+        while (w < w_end && ok) {
+            const int g = (int)(w / nst_all);
+            const int64_t seg_end = min(w_end, (int64_t)(g + 1) * nst_all);
+            const int nchs = (int)((seg_end - w + kFChunk - 1) / kFChunk);
+            const int piece = c - fwd_cta_of((int64_t)g * nst_all, W, G);
+            for (int k = 0; k < nchs; ++k, ++gch) {
+                const int b = gch % NBUF;
+                if (!waitw(&accf[b], (gch / NBUF) & 1, abort)) { ok = false; break; }
+                tc_after();
+#pragma unroll 1
+                for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll 1
+                    for (int c0 = 0; c0 < NF; c0 += 16) {
+                        const uint32_t src = tmem + lanes + (uint32_t)((b * MT + mt) * CT + c0);
+                        const uint32_t dst = tmem + lanes + (uint32_t)((NBUF * MT + mt) * CT + c0);
+                        uint32_t v[16], s[16];
+                        tm_ld16r(src, v);
+                        if (k > 0) tm_ld16r(dst, s);
+                        tm_wait_ld();
+                        if (k > 0) {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                v[i] = __float_as_uint(__uint_as_float(s[i]) + __uint_as_float(v[i]));
+                        }
+                        tm_st16r(dst, v);
+                    }
+                }
+                tm_wait_st();
+                tc_before();
+                mb_arrive(&acce[b]);
+            }
+            if (!ok) break;
+            // the segment's partial sums -> dpart
 #pragma unroll 1
             for (int mt = 0; mt < MT; ++mt) {
+                const int tile = g * MT + mt;
+                if (tile >= ntiles) continue;
+                float *o = dpart + ((int64_t)tile * maxp + piece) * NF * 128;
 #pragma unroll 1
                 for (int c0 = 0; c0 < NF; c0 += 16) {
-                    float v[16];
-                    tm_ld16(tmem + lanes + b * BUF + mt * 128 + c0, v);
+                    uint32_t v[16];
+                    tm_ld16r(tmem + lanes + (uint32_t)((NBUF * MT + mt) * CT + c0), v);
+                    tm_wait_ld();
 #pragma unroll
-                    for (int jj = 0; jj < 16; ++jj) acc[(mt * NF + c0 + jj) * 128 + row] += v[jj];
+                    for (int i = 0; i < 16; ++i) o[(c0 + i) * 128 + row] = __uint_as_float(v[i]);
                 }
             }
-            tc_before();
-            mb_arrive(&acce[b]);
-        }
-        volatile int no_abort = 0;
-        waitw(mmad, 0, &no_abort);
-        if (!*abort) {
-            for (int mt = 0; mt < MT; ++mt) {
-                const int tile = mgroup * MT + mt;
-                if (tile >= ntiles) continue;
-                float *o = dpart + ((int64_t)ks * ntiles + tile) * NF * 128;
-                for (int col = 0; col < NF; ++col) o[col * 128 + row] = acc[(mt * NF + col) * 128 + row];
-            }
+            w = seg_end;
         }
     } else if (warp == 12) {
-        // ---- TMA: particle data of every stage ----
+        // ---- bulk copies: (u_y, u_z) of every stage ----
         int issued = 0;
-        for (int it = 0; it < nst; ++it) {
-            const int s = it % S, u = it / S;
-            if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
+        for (int it = 0; it < nit; ++it) {
+            const int sp = it % SP, up = it / SP;
+            if (up > 0 && !waitw(&p_empty[sp], (up - 1) & 1, abort)) break;
             if (lane == 0) {
-                const int64_t gst = (int64_t)(p0 / kFK) + it;        // global stage index
-                mb_expect_tx(&pfull[s], (uint32_t)BLOB);
-                tma_bulk(sm + s * STAGE + P_OFF, xblob + gst * BLOB, (uint32_t)BLOB, &pfull[s]);
+                const int64_t s = (w_begin + it) % nst_all;
+                mb_expect_tx(&p_full[sp], (uint32_t)P_STAGE);
+                tma_bulk(smP + sp * P_STAGE, yz + s * kFK, (uint32_t)P_STAGE, &p_full[sp]);
             }
             __syncwarp();
             issued = it + 1;
         }
-        for (int it = issued - S < 0 ? 0 : issued - S; it < issued; ++it) {
+        for (int it = issued - SP < 0 ? 0 : issued - SP; it < issued; ++it) {
             volatile int no_abort = 0;
-            waitw(&pfull[it % S], (it / S) & 1, &no_abort);
+            waitw(&p_full[it % SP], (it / SP) & 1, &no_abort);
         }
     } else if (warp == 13) {
+        // ---- bulk copies: B operand (hi, lo) of every stage ----
+        int issued = 0;
+        for (int it = 0; it < nit; ++it) {
+            const int sb = it % SB, ub = it / SB;
+            if (ub > 0 && !waitw(&b_empty[sb], (ub - 1) & 1, abort)) break;
+            if (lane == 0) {
+                const int64_t s = (w_begin + it) % nst_all;
+                mb_expect_tx(&b_full[sb], (uint32_t)B_STAGE);
+                tma_bulk(smB + sb * B_STAGE, bblob + s * B_STAGE, (uint32_t)B_STAGE, &b_full[sb]);
+            }
+            __syncwarp();
+            issued = it + 1;
+        }
+        for (int it = issued - SB < 0 ? 0 : issued - SB; it < issued; ++it) {
+            volatile int no_abort = 0;
+            waitw(&b_full[it % SB], (it / SB) & 1, &no_abort);
+        }
+    } else if (warp == 14) {
         // ---- MMA issuer ----
         const uint32_t idesc = idesc_f16(128, NF, BF);
         const uint32_t sbo = KC * 128;
-        for (int it = 0; it < nst; ++it) {
-            const int s = it % S, u = it / S;
-            const int ch = it / kFChunk, b = ch & 1;
-            const bool first = (it % kFChunk) == 0;
-            const bool last = (it % kFChunk) == kFChunk - 1 || it == nst - 1;
-            if (first && ch >= 2 && !waitw(&acce[b], ((ch >> 1) - 1) & 1, abort)) break;
-            if (!waitw(&full[s], u & 1, abort)) break;
-            if (!waitw(&pfull[s], u & 1, abort)) break;
+        int gch = -1;
+        int64_t seg_start = w_begin;
+        int gprev = -1;
+        for (int it = 0; it < nit; ++it) {
+            const int64_t w = w_begin + it;
+            const int g = (int)(w / nst_all);
+            if (g != gprev) { gprev = g; seg_start = w; }
+            const int64_t seg_end = min(w_end, (int64_t)(g + 1) * nst_all);
+            const int ls = (int)(w - seg_start);
+            const bool first = (ls % kFChunk) == 0;
+            const bool last = (ls % kFChunk) == kFChunk - 1 || w == seg_end - 1;
+            if (first) ++gch;
+            const int b = gch % NBUF;
+            const int sa = it % SA, ua = it / SA, sb = it % SB, ub = it / SB;
+            if (first && gch >= NBUF && !waitw(&acce[b], ((gch / NBUF) - 1) & 1, abort)) break;
+            if (!waitw(&a_full[sa], ua & 1, abort)) break;
+            if (!waitw(&b_full[sb], ub & 1, abort)) break;
             tc_after();
             if (lane == 0) {
-                const uint32_t st = su32(sm + s * STAGE);
-                const uint32_t bhi = st + B_OFF, blo = bhi + B_BYTES;
+                const uint32_t sA = su32(smA + sa * A_STAGE);
+                const uint32_t bhi = su32(smB + sb * B_STAGE), blo = bhi + B_BYTES;
 #pragma unroll
                 for (int mt = 0; mt < MT; ++mt) {
-                    const uint32_t ahi = st + (mt * 2) * A_BYTES, alo = ahi + A_BYTES;
-                    const uint32_t d = tmem + b * BUF + mt * 128;
+                    const uint32_t ahi = sA + (mt * 2) * A_BYTES, alo = ahi + A_BYTES;
+                    const uint32_t d = tmem + (uint32_t)((b * MT + mt) * CT);
 #pragma unroll
                     for (int kk = 0; kk < kFK / 16; ++kk) {
                         const uint32_t o = kk * 256;
@@ -392,13 +512,16 @@ k_fwd_tc(int n, int R, int kmax, int NF, int per, int ntiles, int S, const RowIn
                         umma(d, sdesc(alo + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, 1);
                     }
                 }
-                umma_commit(&empty[s]);
+                umma_commit(&a_empty[sa]);
+                umma_commit(&b_empty[sb]);
                 if (last) umma_commit(&accf[b]);
             }
             __syncwarp();
         }
         if (lane == 0) umma_commit(mmad);
         __syncwarp();
+        volatile int no_abort = 0;
+        waitw(mmad, 0, &no_abort);
     }
     if (t == 0 && *abort) atomicOr(status, kStTimeout);
     tc_before();
@@ -408,33 +531,35 @@ k_fwd_tc(int n, int R, int kmax, int NF, int per, int ntiles, int S, const RowIn
 }
 
 // ---- a5: B operand of the forward product, once per evaluation --------------------------
-// blob[stage] for every 32-particle stage: [32 x uint4 particle data][hi: NF x 32][lo: NF x 32]
-// with column m = Re(q_j X_j[m]), column k_max + m = Im(q_j X_j[m]) (m >= 1), zero padding
-// columns, in the core-matrix layout; X_j[m] = e^{i 2 pi m x_j / L}.  grid: stages, block 256.
+// For every 32-particle stage: yz[stage * 32 + j] = (u_y, u_z) of the particle (zero past n),
+// and bblob[stage] = [hi: NF x 32][lo: NF x 32] with column m = Re(q_j X_j[m]), column
+// k_max + m = Im(q_j X_j[m]) (m >= 1), zero padding columns, in the core-matrix layout;
+// X_j[m] = e^{i 2 pi m x_j / L}.  Particles past n have zero charge, so their B rows vanish
+// and the A rows the producers build for them (from (0, 0)) contribute nothing.
+// grid: stages, block 256.
 template <bool BF>
 __global__ void k_xgen(int n, int kmax, int NF, const uint4 *__restrict__ pu,
-                       unsigned char *__restrict__ xblob)
+                       uint2 *__restrict__ yz, unsigned char *__restrict__ bblob)
 {
     constexpr int KC = kFK / 8;
     const int B_BYTES = NF * kFK * 2;
-    const int BLOB = kFK * 16 + 2 * B_BYTES;
     const int stg = blockIdx.x;
     const int j0 = stg * kFK;
-    unsigned char *out = xblob + (int64_t)stg * BLOB;
-    uint4 *P = reinterpret_cast<uint4 *>(out);
-    unsigned char *bhi = out + kFK * 16;
+    unsigned char *bhi = bblob + (int64_t)stg * 2 * B_BYTES;
     if (threadIdx.x < kFK) {
         const int j = j0 + threadIdx.x;
-        P[threadIdx.x] = j < n ? pu[j] : make_uint4(0u, 0u, 0u, 0u);
+        uint2 v = make_uint2(0u, 0u);
+        if (j < n) { const uint4 p = pu[j]; v = make_uint2(p.y, p.z); }
+        yz[j] = v;
     }
     for (int unit = threadIdx.x; unit < NF * KC; unit += blockDim.x) {
-        const int col = unit / KC, c = unit % KC;
+        const int col = unit / KC, cc = unit % KC;
         const bool im = col > kmax;
         const int m = im ? col - kmax : col;
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int j = j0 + 8 * c + e;
+            const int j = j0 + 8 * cc + e;
             v[e] = 0.f;
             if (j < n && col <= 2 * kmax) {
                 const uint4 pj = pu[j];
@@ -446,18 +571,21 @@ __global__ void k_xgen(int n, int kmax, int NF, const uint4 *__restrict__ pu,
         uint32_t h[4], l[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split2<BF>(v[2 * e], v[2 * e + 1], h[e], l[e]);
-        st16(bhi, tile_off(col, c, KC), h[0], h[1], h[2], h[3]);
-        st16(bhi + B_BYTES, tile_off(col, c, KC), l[0], l[1], l[2], l[3]);
+        st16(bhi, tile_off(col, cc, KC), h[0], h[1], h[2], h[3]);
+        st16(bhi + B_BYTES, tile_off(col, cc, KC), l[0], l[1], l[2], l[3]);
     }
 }
 
 // ---- a6-a7: FP64 reduction of the forward partials, S(k), energy, G' ---------------------
 // grid (tiles of 64 rows in forward order, m = 0..k_max); block 64 (one row per thread).
+// The partial sums (pieces) of a tile are added in CTA order, so the result does not depend
+// on timing.
 // Writes S in K_half order, the energy of the 64 rows and one m as a fixed-order block sum
 // e_part[m * ntiles + tile], the coefficient matrix column-major
 // gmat_t[col * 2R + (2r | 2r + 1)], and the max |G'| (as int bits).
 __global__ void __launch_bounds__(64)
-k_sreduce_tc(int nks, int ntiles, int R, int kmax, int NF, const RowInfo *__restrict__ rows,
+k_sreduce_tc(int MT, int nst_all, int64_t W, int G, int maxp, int ntiles, int R, int kmax, int NF,
+             const RowInfo *__restrict__ rows,
              const int *__restrict__ fperm, const float *__restrict__ dpart,
              const double *__restrict__ gk, double *__restrict__ S, double *__restrict__ e_part,
              float *__restrict__ gmat_t, int *__restrict__ gmax)
@@ -475,9 +603,12 @@ k_sreduce_tc(int nks, int ntiles, int R, int kmax, int NF, const RowInfo *__rest
         const bool origin = ri.my == 0 && ri.mz == 0;
         const double wy = ri.my, wz = ri.mz;
         double t[4] = {0.0, 0.0, 0.0, 0.0};         // T_rr, T_ri, T_ir, T_ii
-        const int64_t stride = (int64_t)ntiles * NF * 128;
-        const float *o = dpart + (int64_t)tile * NF * 128;
-        for (int ks = 0; ks < nks; ++ks, o += stride) {
+        // the pieces of this tile: one per CTA that worked on its group, in CTA order
+        const int g = tile / MT;
+        const int npc = fwd_cta_of((int64_t)(g + 1) * nst_all - 1, W, G) -
+                        fwd_cta_of((int64_t)g * nst_all, W, G) + 1;
+        const float *o = dpart + (int64_t)tile * maxp * NF * 128;
+        for (int pc = 0; pc < npc; ++pc, o += (int64_t)NF * 128) {
             t[0] += (double)o[m * 128 + rl];
             t[2] += (double)o[m * 128 + 64 + rl];
             if (m >= 1) {
@@ -794,16 +925,20 @@ __global__ void k_bs_reduce(int64_t n, int npass, const float *__restrict__ bpar
 
 struct TcState {
     int nf = 0;           // forward N (2 k_max + 1 rounded up to 16)
-    int fmt = 2;          // forward M tiles per CTA (2 while N <= 128, else 1)
+    int fmt = 1;          // forward M tiles of 64 rows per group
+    int nbuf = 2;         // forward TMEM accumulator buffers
+    int ct = 0;           // forward TMEM columns per tile (nf rounded up to 32)
+    int sa = 0, sb = 0, sp = 0;   // forward ring depths: A, B, particle data
+    size_t fsmem = 0;     // forward dynamic shared memory
     int ntiles = 0;       // forward tiles of 64 rows
     int mgroups = 0;      // forward M groups
-    int ks = 0;           // forward K splits
-    int per = 0;          // forward particles per split
+    int maxp = 0;         // forward partial sums per tile (bound)
     int ncol = 0;         // back-scatter columns 3 (2 k_max + 1)
     int npass = 0, np = 0, nkb = 0;
-    float *dpart = nullptr;        // [ks][ntiles][nf][128]
-    unsigned char *xblob = nullptr; // [stages][particles + hi + lo] forward B operand
-    int nstg = 0;                  // 32-particle stages
+    float *dpart = nullptr;        // [ntiles][maxp][nf][128]
+    uint2 *yz = nullptr;           // [stages * 32] (u_y, u_z)
+    unsigned char *bblob = nullptr; // [stages][hi + lo] forward B operand
+    int nstg = 0;                  // 32-particle stages (capacity)
     float *gmat = nullptr;         // [ncol][2R]
     int *gmax = nullptr;
     float *gscale = nullptr;
@@ -811,38 +946,47 @@ struct TcState {
     float *bpart = nullptr;        // [npass][n][4]
 };
 
+constexpr size_t kSmemMax = 232448;   // opt-in shared memory per block (227 KB)
+constexpr int kTmemCols = 512;
+
+size_t fwd_bstage(int nf) { return (size_t)2 * nf * kFK * 2; }
+
+// Forward layout: tile stride in TMEM, M tiles per group, accumulator buffers (two while a
+// running sum fits beside them), and ring depths within the shared-memory limit.
+void fwd_config(TcState &s)
+{
+    s.ct = 32 * ((s.nf + 31) / 32);
+    if (6 * s.ct <= kTmemCols) { s.fmt = 2; s.nbuf = 2; }
+    else if (3 * s.ct <= kTmemCols) { s.fmt = 1; s.nbuf = 2; }
+    else { s.fmt = 1; s.nbuf = 1; }
+    s.sp = 8;
+    const size_t a_stage = (size_t)s.fmt * 2 * 128 * kFK * 2;
+    const size_t b_stage = fwd_bstage(s.nf);
+    s.sa = s.fmt == 2 ? 3 : 4;
+    auto total = [&](int sa, int sb) {
+        return sa * a_stage + sb * b_stage + (size_t)s.sp * kFK * 8 +
+               (size_t)(2 * sa + 2 * sb + 2 * s.sp + 5) * 8 + 64;
+    };
+    s.sb = 8;
+    while (s.sb > 2 && total(s.sa, s.sb) > kSmemMax) --s.sb;
+    while (s.sa > 2 && total(s.sa, s.sb) > kSmemMax) --s.sa;
+    s.fsmem = total(s.sa, s.sb);
+}
+
 void tc_shape(const Plan &p, int64_t n, TcState &s)
 {
     s.nf = 16 * ((2 * p.kmax + 1 + 15) / 16);
-    s.fmt = s.nf <= 128 ? 2 : 1;
+    fwd_config(s);
     s.ntiles = (p.R + 63) / 64;
     s.mgroups = (s.ntiles + s.fmt - 1) / s.fmt;
-    // one wave: as many K splits as fit next to the M groups on the GPU's SMs (a second,
-    // partial wave would double the kernel time)
-    const int nblk = (int)((n + kFK - 1) / kFK);
-    int want = p.num_sms / s.mgroups;
-    if (want > nblk) want = nblk;
-    if (want < 1) want = 1;
-    const int blk_per = (nblk + want - 1) / want;
-    s.per = blk_per * kFK;
-    s.ks = (nblk + blk_per - 1) / blk_per;
-    s.nstg = nblk;
+    s.maxp = p.num_sms / s.mgroups + 2;
+    s.nstg = (int)((n + kFK - 1) / kFK);
     s.ncol = 3 * (2 * p.kmax + 1);
     s.npass = (s.ncol + kPassMax - 1) / kPassMax;
     s.np = 16 * (((s.ncol + s.npass - 1) / s.npass + 15) / 16);
     s.nkb = (2 * p.R + kBK - 1) / kBK;
 }
 
-constexpr size_t kSmemMax = 232448;   // opt-in shared memory per block (227 KB)
-
-size_t fwd_blob(int nf) { return (size_t)kFK * 16 + 2 * (size_t)nf * kFK * 2; }
-size_t fwd_smem_s(int nf, int mt, int S)
-{
-    const size_t stage = (size_t)mt * 2 * 128 * kFK * 2 + fwd_blob(nf);
-    return S * stage + (size_t)mt * nf * 128 * 4 + (size_t)mt * 64 * 8 + 256;
-}
-int fwd_stages(int nf, int mt) { return fwd_smem_s(nf, mt, 3) <= kSmemMax ? 3 : 2; }
-size_t fwd_smem(int nf, int mt) { return fwd_smem_s(nf, mt, fwd_stages(nf, mt)); }
 size_t bs_blob(int np) { return kHdr + 2 * (size_t)np * kBK * 2; }
 size_t bs_smem(int np)
 {
@@ -851,14 +995,16 @@ size_t bs_smem(int np)
 }
 
 template <int MT, bool BF>
-cudaError_t launch_fwd(Plan &p, int64_t n, TcState &s, cudaStream_t st)
+cudaError_t launch_fwd(Plan &p, int nst_all, TcState &s, cudaStream_t st)
 {
-    const size_t fs = fwd_smem(s.nf, MT);
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<MT, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs);
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<MT, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)s.fsmem);
     if (e != cudaSuccess) return e;
-    k_fwd_tc<MT, BF><<<dim3(s.mgroups, s.ks), kFThreads, fs, st>>>(
-        (int)n, p.R, p.kmax, s.nf, s.per, s.ntiles, fwd_stages(s.nf, MT), p.rows_d, p.fperm_d,
-        s.xblob, s.dpart, p.d_status);
+    const int64_t W = (int64_t)s.mgroups * nst_all;
+    const int G = (int)std::min<int64_t>(p.num_sms, W);
+    k_fwd_tc<MT, BF><<<G, kFThreads, s.fsmem, st>>>(
+        p.R, s.nf, nst_all, W, s.maxp, s.ntiles, s.sa, s.sb, s.sp, s.nbuf, s.ct, p.rows_d,
+        p.fperm_d, s.yz, s.bblob, s.dpart, p.d_status);
     return cudaGetLastError();
 }
 
@@ -869,14 +1015,19 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
     Workspace &ws = p.ws;
     cudaError_t e;
     prof_mark(p, kEvRecipStart, st);
-    k_xgen<BF><<<s.nstg, 256, 0, st>>>((int)n, p.kmax, s.nf, ws.pu, s.xblob);
-    e = s.fmt == 2 ? launch_fwd<2, BF>(p, n, s, st) : launch_fwd<1, BF>(p, n, s, st);
+    const int nst_all = (int)((n + kFK - 1) / kFK);
+    k_xgen<BF><<<nst_all, 256, 0, st>>>((int)n, p.kmax, s.nf, ws.pu, s.yz, s.bblob);
+    e = s.fmt == 2 ? launch_fwd<2, BF>(p, nst_all, s, st) : launch_fwd<1, BF>(p, nst_all, s, st);
     if (e != cudaSuccess) return e;
     prof_mark(p, kEvFwdEnd, st);
     if ((e = cudaMemsetAsync(s.gmax, 0, sizeof(int), st)) != cudaSuccess) return e;
-    k_sreduce_tc<<<dim3(s.ntiles, p.kmax + 1), 64, 0, st>>>(s.ks, s.ntiles, p.R, p.kmax, s.nf, p.rows_d,
-                                                       p.fperm_d, s.dpart, p.g_d, p.S_d,
-                                                       p.e_recip_part, s.gmat, s.gmax);
+    {
+        const int64_t W = (int64_t)s.mgroups * nst_all;
+        const int G = (int)std::min<int64_t>(p.num_sms, W);
+        k_sreduce_tc<<<dim3(s.ntiles, p.kmax + 1), 64, 0, st>>>(
+            s.fmt, nst_all, W, G, s.maxp, s.ntiles, p.R, p.kmax, s.nf, p.rows_d, p.fperm_d,
+            s.dpart, p.g_d, p.S_d, p.e_recip_part, s.gmat, s.gmax);
+    }
     k_bpack<BF><<<dim3(s.nkb, s.npass), 256, 0, st>>>(p.R, s.ncol, s.np, s.nkb, p.rows_d, s.gmat,
                                                       s.gmax, s.gscale, s.blob);
     prof_mark(p, kEvCoefEnd, st);
@@ -903,8 +1054,8 @@ size_t recip_tc_bytes(const Plan &p, int64_t n)
     TcState s;
     tc_shape(p, n, s);
     size_t b = 0;
-    b += (size_t)s.ks * s.ntiles * s.nf * 128 * sizeof(float);
-    b += (size_t)s.nstg * fwd_blob(s.nf);
+    b += (size_t)s.ntiles * s.maxp * s.nf * 128 * sizeof(float);
+    b += (size_t)s.nstg * (fwd_bstage(s.nf) + kFK * sizeof(uint2));
     b += (size_t)2 * p.R * s.ncol * sizeof(float);
     b += (size_t)s.npass * s.nkb * bs_blob(s.np);
     b += (size_t)s.npass * n * 4 * sizeof(float);
@@ -919,9 +1070,10 @@ cudaError_t alloc_recip_tc(Plan &p, int64_t n)
     p.tc = s;
     cudaStream_t st = p.side_stream;
     cudaError_t e;
-    if ((e = pool_alloc((void **)&s->dpart, (size_t)s->ks * s->ntiles * s->nf * 128 * sizeof(float), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->dpart, (size_t)s->ntiles * s->maxp * s->nf * 128 * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->gmat, (size_t)2 * p.R * s->ncol * sizeof(float), st)) != cudaSuccess) return e;
-    if ((e = pool_alloc((void **)&s->xblob, (size_t)s->nstg * fwd_blob(s->nf), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->yz, (size_t)s->nstg * kFK * sizeof(uint2), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->bblob, (size_t)s->nstg * fwd_bstage(s->nf), st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->gmax, 64, st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->gscale, 64, st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->blob, (size_t)s->npass * s->nkb * bs_blob(s->np), st)) != cudaSuccess) return e;
@@ -935,7 +1087,7 @@ void free_recip_tc(Plan &p)
     if (!s) return;
     cudaStream_t st = p.side_stream;
     pool_free(s->dpart, st); pool_free(s->gmat, st); pool_free(s->gmax, st);
-    pool_free(s->xblob, st);
+    pool_free(s->yz, st); pool_free(s->bblob, st);
     pool_free(s->gscale, st); pool_free(s->blob, st); pool_free(s->bpart, st);
     delete s;
     p.tc = nullptr;
