@@ -236,6 +236,12 @@ __device__ __forceinline__ void st16(unsigned char *base, uint32_t off, uint32_t
 //   warp 14     tcgen05.mma issue (one thread) and stage release by tcgen05.commit
 // TMEM columns: accumulator buffer b, tile mt at (b MT + mt) CT; running sum of tile mt at
 // (NBUF MT + mt) CT; CT = NF rounded up to 32.
+// Position in a ring of `depth` slots: slot index and the number of completed laps.
+struct RingPos {
+    int slot = 0, lap = 0;
+    __device__ __forceinline__ void next(int depth) { if (++slot == depth) { slot = 0; ++lap; } }
+};
+
 __host__ __device__ inline int64_t fwd_item0(int c, int64_t W, int G) { return (int64_t)c * W / G; }
 __host__ __device__ inline int fwd_cta_of(int64_t w, int64_t W, int G) { return (int)(((w + 1) * G - 1) / W); }
 
@@ -328,9 +334,10 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
         const int rl = t & 63, pc = (t >> 6) & 3;
         int2 rc[MT];
         int gcur = -1;
-        for (int it = 0; it < nit; ++it) {
-            const int64_t w = w_begin + it;
-            const int g = (int)(w / nst_all);
+        int g = (int)(w_begin / nst_all), sg = (int)(w_begin % nst_all);   // item = (g, sg)
+        RingPos ra, rp;
+        for (int it = 0; it < nit; ++it, ++sg, ra.next(SA), rp.next(SP)) {
+            if (sg == nst_all) { sg = 0; ++g; }
             if (g != gcur) {
                 gcur = g;
 #pragma unroll
@@ -341,7 +348,7 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
                     rc[mt] = v;
                 }
             }
-            const int sa = it % SA, ua = it / SA, sp = it % SP, up = it / SP;
+            const int sa = ra.slot, ua = ra.lap, sp = rp.slot, up = rp.lap;
             if (ua > 0 && !waitw(&a_empty[sa], (ua - 1) & 1, abort)) break;
             if (!waitw(&p_full[sp], up & 1, abort)) break;
             uint32_t py[8], pz[8];
@@ -396,25 +403,35 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
             const int nchs = (int)((seg_end - w + kFChunk - 1) / kFChunk);
             const int piece = c - fwd_cta_of((int64_t)g * nst_all, W, G);
             for (int k = 0; k < nchs; ++k, ++gch) {
-                const int b = gch % NBUF;
-                if (!waitw(&accf[b], (gch / NBUF) & 1, abort)) { ok = false; break; }
+                const int b = NBUF == 2 ? (gch & 1) : 0, bl = NBUF == 2 ? (gch >> 1) : gch;
+                if (!waitw(&accf[b], bl & 1, abort)) { ok = false; break; }
                 tc_after();
+                // column blocks of 16 are taken two at a time (NF is a multiple of 16; an odd
+                // last block is taken alone), so that each TMEM load wait covers four loads
 #pragma unroll 1
                 for (int mt = 0; mt < MT; ++mt) {
 #pragma unroll 1
-                    for (int c0 = 0; c0 < NF; c0 += 16) {
+                    for (int c0 = 0; c0 < NF; c0 += 32) {
+                        const bool two = c0 + 16 < NF;
                         const uint32_t src = tmem + lanes + (uint32_t)((b * MT + mt) * CT + c0);
                         const uint32_t dst = tmem + lanes + (uint32_t)((NBUF * MT + mt) * CT + c0);
-                        uint32_t v[16], s[16];
-                        tm_ld16r(src, v);
-                        if (k > 0) tm_ld16r(dst, s);
+                        uint32_t v0[16], s0[16], v1[16], s1[16];
+                        tm_ld16r(src, v0);
+                        if (two) tm_ld16r(src + 16, v1);
+                        if (k > 0) {
+                            tm_ld16r(dst, s0);
+                            if (two) tm_ld16r(dst + 16, s1);
+                        }
                         tm_wait_ld();
                         if (k > 0) {
 #pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                v[i] = __float_as_uint(__uint_as_float(s[i]) + __uint_as_float(v[i]));
+                            for (int i = 0; i < 16; ++i) {
+                                v0[i] = __float_as_uint(__uint_as_float(s0[i]) + __uint_as_float(v0[i]));
+                                v1[i] = __float_as_uint(__uint_as_float(s1[i]) + __uint_as_float(v1[i]));
+                            }
                         }
-                        tm_st16r(dst, v);
+                        tm_st16r(dst, v0);
+                        if (two) tm_st16r(dst + 16, v1);
                     }
                 }
                 tm_wait_st();
@@ -442,13 +459,15 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
     } else if (warp == 12) {
         // ---- bulk copies: (u_y, u_z) of every stage ----
         int issued = 0;
-        for (int it = 0; it < nit; ++it) {
-            const int sp = it % SP, up = it / SP;
+        int sg = (int)(w_begin % nst_all);
+        RingPos rp;
+        for (int it = 0; it < nit; ++it, ++sg, rp.next(SP)) {
+            if (sg == nst_all) sg = 0;
+            const int sp = rp.slot, up = rp.lap;
             if (up > 0 && !waitw(&p_empty[sp], (up - 1) & 1, abort)) break;
             if (lane == 0) {
-                const int64_t s = (w_begin + it) % nst_all;
                 mb_expect_tx(&p_full[sp], (uint32_t)P_STAGE);
-                tma_bulk(smP + sp * P_STAGE, yz + s * kFK, (uint32_t)P_STAGE, &p_full[sp]);
+                tma_bulk(smP + sp * P_STAGE, yz + (int64_t)sg * kFK, (uint32_t)P_STAGE, &p_full[sp]);
             }
             __syncwarp();
             issued = it + 1;
@@ -460,13 +479,15 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
     } else if (warp == 13) {
         // ---- bulk copies: B operand (hi, lo) of every stage ----
         int issued = 0;
-        for (int it = 0; it < nit; ++it) {
-            const int sb = it % SB, ub = it / SB;
+        int sg = (int)(w_begin % nst_all);
+        RingPos rb;
+        for (int it = 0; it < nit; ++it, ++sg, rb.next(SB)) {
+            if (sg == nst_all) sg = 0;
+            const int sb = rb.slot, ub = rb.lap;
             if (ub > 0 && !waitw(&b_empty[sb], (ub - 1) & 1, abort)) break;
             if (lane == 0) {
-                const int64_t s = (w_begin + it) % nst_all;
                 mb_expect_tx(&b_full[sb], (uint32_t)B_STAGE);
-                tma_bulk(smB + sb * B_STAGE, bblob + s * B_STAGE, (uint32_t)B_STAGE, &b_full[sb]);
+                tma_bulk(smB + sb * B_STAGE, bblob + (int64_t)sg * B_STAGE, (uint32_t)B_STAGE, &b_full[sb]);
             }
             __syncwarp();
             issued = it + 1;
@@ -480,20 +501,17 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
         const uint32_t idesc = idesc_f16(128, NF, BF);
         const uint32_t sbo = KC * 128;
         int gch = -1;
-        int64_t seg_start = w_begin;
-        int gprev = -1;
-        for (int it = 0; it < nit; ++it) {
-            const int64_t w = w_begin + it;
-            const int g = (int)(w / nst_all);
-            if (g != gprev) { gprev = g; seg_start = w; }
-            const int64_t seg_end = min(w_end, (int64_t)(g + 1) * nst_all);
-            const int ls = (int)(w - seg_start);
+        int sg = (int)(w_begin % nst_all);     // stage of the item within its group
+        int ls = 0;                            // item index within the segment
+        RingPos ra, rb;
+        for (int it = 0; it < nit; ++it, ++sg, ++ls, ra.next(SA), rb.next(SB)) {
+            if (sg == nst_all) { sg = 0; ls = 0; }
             const bool first = (ls % kFChunk) == 0;
-            const bool last = (ls % kFChunk) == kFChunk - 1 || w == seg_end - 1;
+            const bool last = (ls % kFChunk) == kFChunk - 1 || sg == nst_all - 1 || it == nit - 1;
             if (first) ++gch;
-            const int b = gch % NBUF;
-            const int sa = it % SA, ua = it / SA, sb = it % SB, ub = it / SB;
-            if (first && gch >= NBUF && !waitw(&acce[b], ((gch / NBUF) - 1) & 1, abort)) break;
+            const int b = NBUF == 2 ? (gch & 1) : 0, bl = NBUF == 2 ? (gch >> 1) : gch;
+            const int sa = ra.slot, ua = ra.lap, sb = rb.slot, ub = rb.lap;
+            if (first && gch >= NBUF && !waitw(&acce[b], (bl - 1) & 1, abort)) break;
             if (!waitw(&a_full[sa], ua & 1, abort)) break;
             if (!waitw(&b_full[sb], ub & 1, abort)) break;
             tc_after();
@@ -957,6 +975,7 @@ void fwd_config(TcState &s)
 {
     s.ct = 32 * ((s.nf + 31) / 32);
     if (6 * s.ct <= kTmemCols) { s.fmt = 2; s.nbuf = 2; }
+    else if (4 * s.ct <= kTmemCols) { s.fmt = 2; s.nbuf = 1; }
     else if (3 * s.ct <= kTmemCols) { s.fmt = 1; s.nbuf = 2; }
     else { s.fmt = 1; s.nbuf = 1; }
     s.sp = 8;
