@@ -416,13 +416,10 @@ static cudaError_t plan_upload(Plan &p)
         }
     }
     if ((e = cudaMemcpyAsync(p.rows_d, p.rows_h.data(), sizeof(RowInfo) * p.R, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-    // forward order of the rows: (m_z, m_y) ascending, so that runs of m_y are consecutive
+    // forward order of the rows: decreasing n_x,max (the reverse of the row order), so that
+    // each 64-row tile of the forward product needs only the m_x columns of its first row
     std::vector<int> fperm(p.R);
-    for (int i = 0; i < p.R; ++i) fperm[i] = i;
-    std::sort(fperm.begin(), fperm.end(), [&](int a, int b) {
-        const RowInfo &x = p.rows_h[a], &y = p.rows_h[b];
-        return x.mz != y.mz ? x.mz < y.mz : x.my < y.my;
-    });
+    for (int i = 0; i < p.R; ++i) fperm[i] = p.R - 1 - i;
     if ((e = cudaMemcpyAsync(p.fperm_d, fperm.data(), sizeof(int) * p.R, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(p.kset_d, kset.data(), sizeof(int) * 3 * p.nk, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
     // g(k) = 4 pi exp(-k^2 / (4 beta^2)) / (V k^2) (C_k of Eq. 3), once per plan, K_half order

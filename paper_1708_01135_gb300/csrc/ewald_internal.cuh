@@ -90,7 +90,7 @@ struct Plan {
     int64_t nk = 0;
     std::vector<RowInfo> rows_h;
     RowInfo *rows_d = nullptr;
-    int *fperm_d = nullptr;      // [R] rows in (m_z, m_y) order -> row index (tensor-core forward)
+    int *fperm_d = nullptr;      // [R] forward order (decreasing n_x,max) -> row index (tensor-core forward)
     int *kset_d = nullptr;       // [nk][3]
     double *S_d = nullptr;       // [nk][2] last structure factor
     double *g_d = nullptr;       // [nk] g(k) = 4 pi exp(-k^2 / (4 beta^2)) / (V k^2), K_half order

@@ -7,8 +7,11 @@
 // algebra, including the pairing of +m_x with -m_x, is documented in recip_simt.cu):
 //
 //   forward  (a6):  D_f[(Re|Im) A[r], col] = sum_j A_j[r] X_j[col]
-//                   A_j[r] = q_j e^{i(k_y y_j + k_z z_j)},  cols: Re X_j[m], m = 0..k_max,
-//                   then Im X_j[m], m = 1..k_max;  M = 2R, N = 2 k_max + 1, K = particles
+//                   A_j[r] = e^{i(k_y y_j + k_z z_j)},  X_j carries q_j;  cols: Re X_j[0],
+//                   then Re X_j[m], Im X_j[m] for m = 1..k_max (column 2m - 1 and 2m), so
+//                   the first 2 m + 1 columns hold |m_x| <= m;  M = 2R, N = 2 k_max + 1,
+//                   K = particles.  Rows run in order of decreasing n_x,max, and every
+//                   tile of 64 rows multiplies only the columns its first row needs.
 //   back     (a8):  D_b[i, col] = sum_r (Re P_i[r], Im P_i[r]) . G'[(r, re|im), col]
 //                   P_i[r] = e^{i(k_y y_i + k_z z_i)};  M = particles, N = 3 (2 k_max + 1),
 //                   K = 2R
@@ -236,6 +239,19 @@ __device__ __forceinline__ void st16(unsigned char *base, uint32_t off, uint32_t
 //   warp 14     tcgen05.mma issue (one thread) and stage release by tcgen05.commit
 // TMEM columns: accumulator buffer b, tile mt at (b MT + mt) CT; running sum of tile mt at
 // (NBUF MT + mt) CT; CT = NF rounded up to 32.
+// Forward columns needed by M group g: |m_x| <= n_x,max of its first row (the largest, rows
+// run in order of decreasing n_x,max), rounded up to the MMA granule of 16.
+__device__ __forceinline__ int fwd_group_cols(int g, int MT, int R, int NF,
+                                              const RowInfo *__restrict__ rows,
+                                              const int *__restrict__ fperm)
+{
+    const int fr = g * MT * 64;
+    if (fr >= R) return 16;
+    const int nx = rows[fperm[fr]].nxmax;
+    const int nc = 16 * ((2 * nx + 1 + 15) / 16);
+    return nc < NF ? nc : NF;
+}
+
 // Position in a ring of `depth` slots: slot index and the number of completed laps.
 struct RingPos {
     int slot = 0, lap = 0;
@@ -402,6 +418,7 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
             const int64_t seg_end = min(w_end, (int64_t)(g + 1) * nst_all);
             const int nchs = (int)((seg_end - w + kFChunk - 1) / kFChunk);
             const int piece = c - fwd_cta_of((int64_t)g * nst_all, W, G);
+            const int NG = fwd_group_cols(g, MT, R, NF, rows, fperm);
             for (int k = 0; k < nchs; ++k, ++gch) {
                 const int b = NBUF == 2 ? (gch & 1) : 0, bl = NBUF == 2 ? (gch >> 1) : gch;
                 if (!waitw(&accf[b], bl & 1, abort)) { ok = false; break; }
@@ -411,8 +428,8 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
 #pragma unroll 1
                 for (int mt = 0; mt < MT; ++mt) {
 #pragma unroll 1
-                    for (int c0 = 0; c0 < NF; c0 += 32) {
-                        const bool two = c0 + 16 < NF;
+                    for (int c0 = 0; c0 < NG; c0 += 32) {
+                        const bool two = c0 + 16 < NG;
                         const uint32_t src = tmem + lanes + (uint32_t)((b * MT + mt) * CT + c0);
                         const uint32_t dst = tmem + lanes + (uint32_t)((NBUF * MT + mt) * CT + c0);
                         uint32_t v0[16], s0[16], v1[16], s1[16];
@@ -446,7 +463,7 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
                 if (tile >= ntiles) continue;
                 float *o = dpart + ((int64_t)tile * maxp + piece) * NF * 128;
 #pragma unroll 1
-                for (int c0 = 0; c0 < NF; c0 += 16) {
+                for (int c0 = 0; c0 < NG; c0 += 16) {
                     uint32_t v[16];
                     tm_ld16r(tmem + lanes + (uint32_t)((NBUF * MT + mt) * CT + c0), v);
                     tm_wait_ld();
@@ -479,15 +496,20 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
     } else if (warp == 13) {
         // ---- bulk copies: B operand (hi, lo) of every stage ----
         int issued = 0;
-        int sg = (int)(w_begin % nst_all);
+        int g = (int)(w_begin / nst_all), sg = (int)(w_begin % nst_all);
+        int NG = fwd_group_cols(g, MT, R, NF, rows, fperm);
         RingPos rb;
         for (int it = 0; it < nit; ++it, ++sg, rb.next(SB)) {
-            if (sg == nst_all) sg = 0;
+            if (sg == nst_all) { sg = 0; ++g; NG = fwd_group_cols(g, MT, R, NF, rows, fperm); }
             const int sb = rb.slot, ub = rb.lap;
             if (ub > 0 && !waitw(&b_empty[sb], (ub - 1) & 1, abort)) break;
             if (lane == 0) {
-                mb_expect_tx(&b_full[sb], (uint32_t)B_STAGE);
-                tma_bulk(smB + sb * B_STAGE, bblob + (int64_t)sg * B_STAGE, (uint32_t)B_STAGE, &b_full[sb]);
+                // the first NG columns of the hi and of the lo half (a prefix of each)
+                const uint32_t part = (uint32_t)NG * kFK * 2;
+                const unsigned char *src = bblob + (int64_t)sg * B_STAGE;
+                mb_expect_tx(&b_full[sb], 2 * part);
+                tma_bulk(smB + sb * B_STAGE, src, part, &b_full[sb]);
+                tma_bulk(smB + sb * B_STAGE + B_BYTES, src + B_BYTES, part, &b_full[sb]);
             }
             __syncwarp();
             issued = it + 1;
@@ -498,14 +520,18 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
         }
     } else if (warp == 14) {
         // ---- MMA issuer ----
-        const uint32_t idesc = idesc_f16(128, NF, BF);
         const uint32_t sbo = KC * 128;
+        int gm = (int)(w_begin / nst_all);
+        uint32_t idesc = idesc_f16(128, fwd_group_cols(gm, MT, R, NF, rows, fperm), BF);
         int gch = -1;
         int sg = (int)(w_begin % nst_all);     // stage of the item within its group
         int ls = 0;                            // item index within the segment
         RingPos ra, rb;
         for (int it = 0; it < nit; ++it, ++sg, ++ls, ra.next(SA), rb.next(SB)) {
-            if (sg == nst_all) { sg = 0; ls = 0; }
+            if (sg == nst_all) {
+                sg = 0; ls = 0; ++gm;
+                idesc = idesc_f16(128, fwd_group_cols(gm, MT, R, NF, rows, fperm), BF);
+            }
             const bool first = (ls % kFChunk) == 0;
             const bool last = (ls % kFChunk) == kFChunk - 1 || sg == nst_all - 1 || it == nit - 1;
             if (first) ++gch;
@@ -550,8 +576,9 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
 
 // ---- a5: B operand of the forward product, once per evaluation --------------------------
 // For every 32-particle stage: yz[stage * 32 + j] = (u_y, u_z) of the particle (zero past n),
-// and bblob[stage] = [hi: NF x 32][lo: NF x 32] with column m = Re(q_j X_j[m]), column
-// k_max + m = Im(q_j X_j[m]) (m >= 1), zero padding columns, in the core-matrix layout;
+// and bblob[stage] = [hi: NF x 32][lo: NF x 32] with column 0 = Re(q_j X_j[0]), column
+// 2m - 1 = Re(q_j X_j[m]), column 2m = Im(q_j X_j[m]) (m >= 1), zero padding columns, in the
+// core-matrix layout;
 // X_j[m] = e^{i 2 pi m x_j / L}.  Particles past n have zero charge, so their B rows vanish
 // and the A rows the producers build for them (from (0, 0)) contribute nothing.
 // grid: stages, block 256.
@@ -572,8 +599,8 @@ __global__ void k_xgen(int n, int kmax, int NF, const uint4 *__restrict__ pu,
     }
     for (int unit = threadIdx.x; unit < NF * KC; unit += blockDim.x) {
         const int col = unit / KC, cc = unit % KC;
-        const bool im = col > kmax;
-        const int m = im ? col - kmax : col;
+        const bool im = col > 0 && (col & 1) == 0;     // column 2m: Im X[m]; 2m - 1: Re X[m]
+        const int m = (col + 1) >> 1;
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
@@ -626,12 +653,15 @@ k_sreduce_tc(int MT, int nst_all, int64_t W, int G, int maxp, int ntiles, int R,
         const int npc = fwd_cta_of((int64_t)(g + 1) * nst_all - 1, W, G) -
                         fwd_cta_of((int64_t)g * nst_all, W, G) + 1;
         const float *o = dpart + (int64_t)tile * maxp * NF * 128;
-        for (int pc = 0; pc < npc; ++pc, o += (int64_t)NF * 128) {
-            t[0] += (double)o[m * 128 + rl];
-            t[2] += (double)o[m * 128 + 64 + rl];
-            if (m >= 1) {
-                t[1] += (double)o[(kmax + m) * 128 + rl];
-                t[3] += (double)o[(kmax + m) * 128 + 64 + rl];
+        const int cre = m == 0 ? 0 : 2 * m - 1, cim = 2 * m;   // columns of Re X[m], Im X[m]
+        if (m <= ri.nxmax) {
+            for (int pc = 0; pc < npc; ++pc, o += (int64_t)NF * 128) {
+                t[0] += (double)o[cre * 128 + rl];
+                t[2] += (double)o[cre * 128 + 64 + rl];
+                if (m >= 1) {
+                    t[1] += (double)o[cim * 128 + rl];
+                    t[3] += (double)o[cim * 128 + 64 + rl];
+                }
             }
         }
         const bool vp = m <= ri.nxmax && (!origin || m > 0);
@@ -688,6 +718,18 @@ k_sreduce_tc(int MT, int nst_all, int64_t W, int G, int maxp, int ntiles, int R,
     if (rl == 0) e_part[(int64_t)m * ntiles + tile] = ered[0] + ered[1];
 }
 
+// Back-scatter column order: |m_x| = m major, so that a pass (a range of columns) needs only
+// the rows with n_x,max >= the smallest m of its columns, a suffix of the row order.
+// Column gc: gc < 3 -> m = 0, block gc; else u = gc - 3: m = 1 + u / 6, block (u % 6) / 2,
+// kind 1 + (u & 1) (kind 1: coefficient column 2m - 1, kind 2: column 2m of the block).
+struct BsCol { int m, kind, blk; };
+__host__ __device__ inline BsCol bs_col(int gc)
+{
+    if (gc < 3) return {0, 0, gc};
+    const int u = gc - 3;
+    return {1 + u / 6, 1 + (u & 1), (u % 6) / 2};
+}
+
 // Pack G' (column-major FP32) into split half-precision tiles with a row header:
 // blob[pass][kb] = [16 x (m_y, m_z) int2][hi: NP x kBK][lo: NP x kBK], core-matrix layout.
 // One thread packs 8 consecutive K of one column: one 16-byte store per part.
@@ -714,14 +756,17 @@ __global__ void k_bpack(int R, int ncol, int NP, int nkb, const RowInfo *__restr
     unsigned char *hi = out + kHdr;
     unsigned char *lo = hi + NP * kBK * 2;
     const int64_t R2 = 2 * (int64_t)R;
+    const int NB = ncol / 3;
     for (int u = threadIdx.x; u < NP * (kBK / 8); u += blockDim.x) {
         const int col = u / (kBK / 8), kc = u % (kBK / 8);
         const int gc = pass * NP + col;
+        const BsCol bc = bs_col(gc);
+        const int64_t oc = (int64_t)bc.blk * NB + (bc.kind == 0 ? 0 : (bc.kind == 1 ? 2 * bc.m - 1 : 2 * bc.m));
         const int64_t gk0 = (int64_t)kb * kBK + 8 * kc;
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-            v[e] = (gk0 + e < R2 && gc < ncol) ? gmat_t[(int64_t)gc * R2 + gk0 + e] * scale : 0.f;
+            v[e] = (gk0 + e < R2 && gc < ncol) ? gmat_t[oc * R2 + gk0 + e] * scale : 0.f;
         uint32_t h[4], l[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) split2<BF>(v[2 * e], v[2 * e + 1], h[e], l[e]);
@@ -736,7 +781,7 @@ __global__ void k_bpack(int R, int ncol, int NP, int nkb, const RowInfo *__restr
 // bpart layout [pass][n] float4 = partial (F_x, F_y, F_z, phi) before q_i, 2 pi / L and scale.
 template <bool BF>
 __global__ void __launch_bounds__(kBThreads, 1)
-k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const uint4 *__restrict__ pu,
+k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, int4 kb0s, const uint4 *__restrict__ pu,
         const unsigned char *__restrict__ blob, float *__restrict__ bpart, int *__restrict__ status)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -757,7 +802,8 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const uint4 *__restri
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int pass = blockIdx.y;
     const int base = blockIdx.x * (kBMT * 128);
-    const int NB = 2 * kmax + 1;
+    // first K block of this pass: rows before it have n_x,max below every m of the pass
+    const int kb0 = pass == 0 ? kb0s.x : (pass == 1 ? kb0s.y : (pass == 2 ? kb0s.z : kb0s.w));
 
     if (t == 0) {
         for (int s = 0; s < kBStages; ++s) {
@@ -773,10 +819,8 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const uint4 *__restri
         const int gc = pass * NP + col;
         int d = 1 << 12;
         if (gc < ncol) {
-            const int blk = gc / NB, c = gc % NB;
-            const int m = (c + 1) / 2;
-            const int kind = c == 0 ? 0 : ((c & 1) ? 1 : 2);
-            d = m | (kind << 8) | (blk << 10);
+            const BsCol bc = bs_col(gc);
+            d = bc.m | (bc.kind << 8) | (bc.blk << 10);
         }
         coldesc[col] = d;
     }
@@ -792,8 +836,8 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const uint4 *__restri
         const int i = base + t;
         const bool valid = i < n;
         const uint4 pi = pu[valid ? i : 0];
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % kBStages, u = kb / kBStages;
+        for (int kb = kb0; kb < nkb; ++kb) {
+            const int s = (kb - kb0) % kBStages, u = (kb - kb0) / kBStages;
             if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
             if (!waitw(&full_b[s], u & 1, abort)) break;      // row header of this K block
             unsigned char *st = sm + s * STAGE;
@@ -823,26 +867,26 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const uint4 *__restri
     } else if (warp == 8) {
         // ---- TMA producer for the packed G' blobs ----
         int issued = 0;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % kBStages, u = kb / kBStages;
+        for (int kb = kb0; kb < nkb; ++kb) {
+            const int s = (kb - kb0) % kBStages, u = (kb - kb0) / kBStages;
             if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
             if (lane == 0) {
                 mb_expect_tx(&full_b[s], (uint32_t)BLOB);
                 tma_bulk(sm + s * STAGE + B_OFF, blob + ((int64_t)pass * nkb + kb) * BLOB, (uint32_t)BLOB, &full_b[s]);
             }
             __syncwarp();
-            issued = kb + 1;
+            issued = kb - kb0 + 1;
         }
-        for (int kb = issued - kBStages < 0 ? 0 : issued - kBStages; kb < issued; ++kb) {
+        for (int q = issued - kBStages < 0 ? 0 : issued - kBStages; q < issued; ++q) {
             volatile int no_abort = 0;
-            waitw(&full_b[kb % kBStages], (kb / kBStages) & 1, &no_abort);
+            waitw(&full_b[q % kBStages], (q / kBStages) & 1, &no_abort);
         }
     } else if (warp == 9) {
         // ---- MMA issuer ----
         const uint32_t idesc = idesc_f16(128, NP, BF);
         const uint32_t sbo = KC * 128;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % kBStages, u = kb / kBStages;
+        for (int kb = kb0; kb < nkb; ++kb) {
+            const int s = (kb - kb0) % kBStages, u = (kb - kb0) / kBStages;
             if (!waitw(&full_a[s], u & 1, abort)) break;
             if (!waitw(&full_b[s], u & 1, abort)) break;
             tc_after();
@@ -856,7 +900,7 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, const uint4 *__restri
 #pragma unroll
                     for (int kk = 0; kk < kBK / 16; ++kk) {
                         const uint32_t o = kk * 256;
-                        umma(d, sdesc(ahi + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, (kb | kk) != 0);
+                        umma(d, sdesc(ahi + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, (kb != kb0 || kk != 0) ? 1u : 0u);
                         umma(d, sdesc(ahi + o, 128, sbo), sdesc(blo + o, 128, sbo), idesc, 1);
                         umma(d, sdesc(alo + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, 1);
                     }
@@ -953,6 +997,7 @@ struct TcState {
     int maxp = 0;         // forward partial sums per tile (bound)
     int ncol = 0;         // back-scatter columns 3 (2 k_max + 1)
     int npass = 0, np = 0, nkb = 0;
+    int kb0[4] = {0, 0, 0, 0};     // back-scatter: first K block of every pass
     float *dpart = nullptr;        // [ntiles][maxp][nf][128]
     uint2 *yz = nullptr;           // [stages * 32] (u_y, u_z)
     unsigned char *bblob = nullptr; // [stages][hi + lo] forward B operand
@@ -1004,6 +1049,14 @@ void tc_shape(const Plan &p, int64_t n, TcState &s)
     s.npass = (s.ncol + kPassMax - 1) / kPassMax;
     s.np = 16 * (((s.ncol + s.npass - 1) / s.npass + 15) / 16);
     s.nkb = (2 * p.R + kBK - 1) / kBK;
+    // rows run in order of increasing n_x,max; pass q starts at the K block holding the first
+    // row that reaches the smallest m of its columns
+    for (int q = 0; q < s.npass && q < 4; ++q) {
+        const int mlo = bs_col(q * s.np).m;
+        int r = 0;
+        while (r < p.R && p.rows_h[r].nxmax < mlo) ++r;
+        s.kb0[q] = (r < p.R ? r : p.R - 1) / (kBK / 2);
+    }
 }
 
 size_t bs_blob(int np) { return kHdr + 2 * (size_t)np * kBK * 2; }
@@ -1054,9 +1107,9 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
     if ((e = cudaFuncSetAttribute(k_bs_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs)) != cudaSuccess)
         return e;
     const int ptiles = (int)((n + kBMT * 128 - 1) / (kBMT * 128));
-    k_bs_tc<BF><<<dim3(ptiles, s.npass), kBThreads, bs, st>>>((int)n, p.R, p.kmax, s.ncol, s.np,
-                                                              s.nkb, ws.pu, s.blob, s.bpart,
-                                                              p.d_status);
+    k_bs_tc<BF><<<dim3(ptiles, s.npass), kBThreads, bs, st>>>(
+        (int)n, p.R, p.kmax, s.ncol, s.np, s.nkb, make_int4(s.kb0[0], s.kb0[1], s.kb0[2], s.kb0[3]),
+        ws.pu, s.blob, s.bpart, p.d_status);
     k_bs_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s.npass, s.bpart, ws.pg, s.gscale,
                                                             p.L, ws.f_recip);
     prof_mark(p, kEvBackEnd, st);
