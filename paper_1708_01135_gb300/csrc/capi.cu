@@ -286,7 +286,7 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
                                                           parts, forces);
     p.launches += 2;
     prof_mark(p, kEvFinal, st);
-    p.prof_valid = p.prof && do_recip && (parts & EWALD_PART_REAL);
+    p.prof_valid = p.prof && do_recip;
     p.last_stream = st;
     return cudaGetLastError();
 }

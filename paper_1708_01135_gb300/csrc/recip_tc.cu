@@ -54,6 +54,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "ewald_internal.cuh"
 
@@ -63,7 +64,7 @@ namespace {
 // ---- tiling ---------------------------------------------------------------------------
 constexpr int kFK = 32;        // forward: particles (K) per stage
 constexpr int kFChunk = 4;     // forward: stages per TMEM accumulator (128 particles)
-constexpr int kFThreads = 480; // forward: 15 warps
+constexpr int kFThreads = 608; // forward: 19 warps
 constexpr int kBK = 32;        // back-scatter: real K per stage (16 rows r)
 constexpr int kBStages = 3;
 constexpr int kBMT = 2;        // back-scatter: M tiles of 128 particles per CTA
@@ -220,46 +221,39 @@ __device__ __forceinline__ void st16(unsigned char *base, uint32_t off, uint32_t
 }
 
 // ---- forward: structure-factor partials ------------------------------------------------
-// Work partition ("stream-K"): the work items are (M group g of MT tiles of 64 rows,
-// 32-particle stage s), W = groups * stages of them in group-major order, and CTA c of the G
-// CTAs (one per SM) takes the contiguous items [floor(c W / G), floor((c + 1) W / G)).  A
-// CTA's items form one or a few segments, each inside one group; every segment yields one
-// partial sum ("piece") per tile, written to dpart[(tile * maxp + piece) * NF * 128 + ...]
-// with piece = c - (first CTA of the group).  Every SM gets the same number of items
-// whatever the group count.
+// Transposed product.  A tcgen05.mma of M = 128, K = 16 takes the same time whatever its N
+// (up to 256), so the wide dimension of the forward product goes to N: per 32-particle stage,
+//   D[c, n] += sum_j X_j[c] P_j[n],   c = column (m_x slot, the MMA's M, from the pre-built
+//   operand), n = 0..127: Re P_j of row n, n = 128..255: Im P_j of row n - 128 (the MMA's N,
+//   generated by the producers), P_j[r] = e^{i(k_y y_j + k_z z_j)}.
+// Rows run in forward order (decreasing n_x,max) in groups of 128.  A group needs the columns
+// |m_x| <= n_x,max of its first row; where that is more than 128 columns, it is processed as
+// two "virtual groups" (column passes 0 and 1), each with one M tile of 128 columns.
 //
-// Roles (block kFThreads = 15 warps):
-//   warps 0-7   producers: A = e^{i(k_y y_j + k_z z_j)} of every stage (MT tiles, hi and lo
-//               terms) into the A ring; particle data comes from the P ring
-//   warps 8-11  drain: every TMEM accumulator buffer (kFChunk stages = 128 particles) is
-//               added into an FP32 running sum that also lives in TMEM; at the end of a
-//               segment the sum goes to dpart
-//   warp 12     bulk copies of (u_y, u_z) of every stage into the P ring
-//   warp 13     bulk copies of the B operand (q_j X_j[m], hi and lo) into the B ring
-//   warp 14     tcgen05.mma issue (one thread) and stage release by tcgen05.commit
-// TMEM columns: accumulator buffer b, tile mt at (b MT + mt) CT; running sum of tile mt at
-// (NBUF MT + mt) CT; CT = NF rounded up to 32.
-// Forward columns needed by M group g: |m_x| <= n_x,max of its first row (the largest, rows
-// run in order of decreasing n_x,max), rounded up to the MMA granule of 16.
-__device__ __forceinline__ int fwd_group_cols(int g, int MT, int R, int NF,
-                                              const RowInfo *__restrict__ rows,
-                                              const int *__restrict__ fperm)
-{
-    const int fr = g * MT * 64;
-    if (fr >= R) return 16;
-    const int nx = rows[fperm[fr]].nxmax;
-    const int nc = 16 * ((2 * nx + 1 + 15) / 16);
-    return nc < NF ? nc : NF;
-}
+// Work partition ("stream-K"): the items are (virtual group v, stage s), W = nvg * stages of
+// them in v-major order, and CTA c of the G CTAs (one per SM) takes the items
+// [floor(c W / G), floor((c + 1) W / G)).  A CTA's items form segments, each inside one
+// virtual group; every segment yields one partial sum ("piece"), written to
+// dpart[((v * maxp + piece) * 128 + c) * 256 + n] with piece = c - (first CTA of the group).
+//
+// Roles (block kFThreads = 19 warps):
+//   warps 0-7    producers: P of every stage (128 rows x 32 particles, Re and Im, hi and lo
+//                terms) into the P ring; particle coordinates come from the coordinate ring
+//   warps 8-15   drain: every kFChunk stages (128 particles) the TMEM accumulator
+//                (columns 0-255) is added into an FP32 running sum in TMEM columns 256-511;
+//                at the end of a segment the sum goes to dpart.  Warp 8 + q and 12 + q own
+//                TMEM lanes 32q..32q+31, columns 0-127 and 128-255 respectively.
+//   warp 16      bulk copies of (u_y, u_z) of every stage into the coordinate ring
+//   warp 17      bulk copies of the column operand (q_j X_j[c], hi and lo) into the X ring
+//   warp 18      tcgen05.mma issue (one thread) and stage release by tcgen05.commit
+__host__ __device__ inline int64_t fwd_item0(int c, int64_t W, int G) { return (int64_t)c * W / G; }
+__host__ __device__ inline int fwd_cta_of(int64_t w, int64_t W, int G) { return (int)(((w + 1) * G - 1) / W); }
 
 // Position in a ring of `depth` slots: slot index and the number of completed laps.
 struct RingPos {
     int slot = 0, lap = 0;
     __device__ __forceinline__ void next(int depth) { if (++slot == depth) { slot = 0; ++lap; } }
 };
-
-__host__ __device__ inline int64_t fwd_item0(int c, int64_t W, int G) { return (int64_t)c * W / G; }
-__host__ __device__ inline int fwd_cta_of(int64_t w, int64_t W, int G) { return (int)(((w + 1) * G - 1) / W); }
 
 __device__ __forceinline__ void tm_ld16r(uint32_t taddr, uint32_t (&r)[16])
 {
@@ -296,32 +290,42 @@ __device__ __forceinline__ void split2_f16(float a, float b, uint32_t &hi, uint3
     lo = *reinterpret_cast<uint32_t *>(&l);
 }
 
-template <int MT, bool BF>
+template <bool BF>
+__device__ __forceinline__ void split2x(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    if (BF) split2<true>(a, b, hi, lo);
+    else split2_f16(a, b, hi, lo);
+}
+
+// Virtual group descriptor: x = first forward row, y = column pass, z = columns (multiple of
+// 16, <= 128) copied for this pass.
+template <bool BF>
 __global__ void __launch_bounds__(kFThreads, 1)
-k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, int SB, int SP,
-         int NBUF, int CT, const RowInfo *__restrict__ rows, const int *__restrict__ fperm,
-         const uint2 *__restrict__ yz, const unsigned char *__restrict__ bblob,
-         float *__restrict__ dpart, int *__restrict__ status)
+k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int SA, int SX, int SP, int KCH,
+         const int4 *__restrict__ vgs, const RowInfo *__restrict__ rows,
+         const int *__restrict__ fperm, const uint2 *__restrict__ yz,
+         const unsigned char *__restrict__ bblob, float *__restrict__ dpart,
+         int *__restrict__ status)
 {
     constexpr int KC = kFK / 8;                  // K chunks of 8 per stage
-    constexpr int A_BYTES = 128 * kFK * 2;       // one 128 x 32 half tile
-    constexpr int A_STAGE = MT * 2 * A_BYTES;    // MT tiles, hi and lo
-    constexpr int P_STAGE = kFK * 8;             // (u_y, u_z) of 32 particles
+    constexpr int P_HALF = 256 * kFK * 2;        // one term of the phase tile: 256 rows x 32
+    constexpr int P_STAGE = 2 * P_HALF;          // hi and lo
+    constexpr int X_HALF = 128 * kFK * 2;        // one term of the column tile: 128 x 32
+    constexpr int X_STAGE = 2 * X_HALF;
+    constexpr int C_STAGE = kFK * 8;             // (u_y, u_z) of 32 particles
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int B_BYTES = NF * kFK * 2;
-    const int B_STAGE = 2 * B_BYTES;
-    unsigned char *smA = sm;
-    unsigned char *smB = smA + SA * A_STAGE;
-    unsigned char *smP = smB + SB * B_STAGE;
-    uint64_t *a_full = reinterpret_cast<uint64_t *>(smP + SP * P_STAGE);
+    unsigned char *smP = sm;
+    unsigned char *smX = smP + SA * P_STAGE;
+    unsigned char *smC = smX + SX * X_STAGE;
+    uint64_t *a_full = reinterpret_cast<uint64_t *>(smC + SP * C_STAGE);
     uint64_t *a_empty = a_full + SA;
-    uint64_t *b_full = a_empty + SA;
-    uint64_t *b_empty = b_full + SB;
-    uint64_t *p_full = b_empty + SB;
-    uint64_t *p_empty = p_full + SP;
-    uint64_t *accf = p_empty + SP;   // [2]
-    uint64_t *acce = accf + 2;       // [2]
-    uint64_t *mmad = acce + 2;
+    uint64_t *x_full = a_empty + SA;
+    uint64_t *x_empty = x_full + SX;
+    uint64_t *c_full = x_empty + SX;
+    uint64_t *c_empty = c_full + SP;
+    uint64_t *accf = c_empty + SP;
+    uint64_t *acce = accf + 1;
+    uint64_t *mmad = acce + 1;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(mmad + 1);
     volatile int *abort = reinterpret_cast<volatile int *>(tslot + 1);
 
@@ -329,12 +333,14 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
     const int G = gridDim.x, c = blockIdx.x;
     const int64_t w_begin = fwd_item0(c, W, G), w_end = fwd_item0(c + 1, W, G);
     const int nit = (int)(w_end - w_begin);
+    const int v0 = (int)(w_begin / nst_all), s0 = (int)(w_begin % nst_all);
 
     if (t == 0) {
         for (int s = 0; s < SA; ++s) { mb_init(&a_full[s], 256); mb_init(&a_empty[s], 1); }
-        for (int s = 0; s < SB; ++s) { mb_init(&b_full[s], 1); mb_init(&b_empty[s], 1); }
-        for (int s = 0; s < SP; ++s) { mb_init(&p_full[s], 1); mb_init(&p_empty[s], 256); }
-        for (int b = 0; b < 2; ++b) { mb_init(&accf[b], 1); mb_init(&acce[b], 128); }
+        for (int s = 0; s < SX; ++s) { mb_init(&x_full[s], 1); mb_init(&x_empty[s], 1); }
+        for (int s = 0; s < SP; ++s) { mb_init(&c_full[s], 1); mb_init(&c_empty[s], 256); }
+        mb_init(accf, 1);
+        mb_init(acce, 256);
         mb_init(mmad, 1);
         *abort = 0;
         mb_fence_init();
@@ -346,219 +352,185 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int ntiles, int SA, in
     const uint32_t tmem = *tslot;
 
     if (t < 256) {
-        // ---- producers: thread t owns row slot rl = t % 64 and particles 8c..8c+7 ----
-        const int rl = t & 63, pc = (t >> 6) & 3;
-        int2 rc[MT];
-        int gcur = -1;
-        int g = (int)(w_begin / nst_all), sg = (int)(w_begin % nst_all);   // item = (g, sg)
+        // ---- producers: thread t owns row rl = t % 128 and particles 16h..16h+15 ----
+        const int rl = t & 127, h = t >> 7;
+        int my = 0, mz = 0;
+        int vcur = -1;
+        int v = v0, sg = s0;
         RingPos ra, rp;
         for (int it = 0; it < nit; ++it, ++sg, ra.next(SA), rp.next(SP)) {
-            if (sg == nst_all) { sg = 0; ++g; }
-            if (g != gcur) {
-                gcur = g;
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const int gr = (g * MT + mt) * 64 + rl;
-                    int2 v = make_int2(0, 0);          // padding rows: any finite phase
-                    if (gr < R) { const RowInfo ri = rows[fperm[gr]]; v = make_int2(ri.my, ri.mz); }
-                    rc[mt] = v;
-                }
+            if (sg == nst_all) { sg = 0; ++v; }
+            if (v != vcur) {
+                vcur = v;
+                const int fr = vgs[v].x + rl;
+                my = 0; mz = 0;                    // padding rows: any finite phase
+                if (fr < R) { const RowInfo ri = rows[fperm[fr]]; my = ri.my; mz = ri.mz; }
             }
-            const int sa = ra.slot, ua = ra.lap, sp = rp.slot, up = rp.lap;
-            if (ua > 0 && !waitw(&a_empty[sa], (ua - 1) & 1, abort)) break;
-            if (!waitw(&p_full[sp], up & 1, abort)) break;
-            uint32_t py[8], pz[8];
+            if (ra.lap > 0 && !waitw(&a_empty[ra.slot], (ra.lap - 1) & 1, abort)) break;
+            if (!waitw(&c_full[rp.slot], rp.lap & 1, abort)) break;
+            uint32_t py[16], pz[16];
             {
-                const uint4 *P4 = reinterpret_cast<const uint4 *>(smP + sp * P_STAGE) + 4 * pc;
+                const uint4 *C4 = reinterpret_cast<const uint4 *>(smC + rp.slot * C_STAGE) + 8 * h;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint4 v = P4[i];
-                    py[2 * i] = v.x; pz[2 * i] = v.y; py[2 * i + 1] = v.z; pz[2 * i + 1] = v.w;
+                for (int i = 0; i < 8; ++i) {
+                    const uint4 q4 = C4[i];
+                    py[2 * i] = q4.x; pz[2 * i] = q4.y; py[2 * i + 1] = q4.z; pz[2 * i + 1] = q4.w;
                 }
             }
-            mb_arrive(&p_empty[sp]);
-            unsigned char *st = smA + sa * A_STAGE;
-            float re[MT][8], im[MT][8];
+            mb_arrive(&c_empty[rp.slot]);
+            float cs[16], sn[16];
 #pragma unroll
-            for (int e = 0; e < 8; ++e)
+            for (int e = 0; e < 16; ++e) phase((uint32_t)my * py[e] + (uint32_t)mz * pz[e], cs[e], sn[e]);
+            unsigned char *hi = smP + ra.slot * P_STAGE, *lo = hi + P_HALF;
 #pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-                    phase((uint32_t)rc[mt].x * py[e] + (uint32_t)rc[mt].y * pz[e], re[mt][e], im[mt][e]);
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                unsigned char *ahi = st + (mt * 2) * A_BYTES;
-                uint32_t h[4], l[4];
+            for (int q = 0; q < 2; ++q) {          // K chunk 2h + q: particles 16h + 8q ..
+                uint32_t ch[4], cl[4], sh[4], sl[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    if (BF) split2<true>(re[mt][2 * e], re[mt][2 * e + 1], h[e], l[e]);
-                    else split2_f16(re[mt][2 * e], re[mt][2 * e + 1], h[e], l[e]);
+                    split2x<BF>(cs[8 * q + 2 * e], cs[8 * q + 2 * e + 1], ch[e], cl[e]);
+                    split2x<BF>(sn[8 * q + 2 * e], sn[8 * q + 2 * e + 1], sh[e], sl[e]);
                 }
-                st16(ahi, tile_off(rl, pc, KC), h[0], h[1], h[2], h[3]);
-                st16(ahi + A_BYTES, tile_off(rl, pc, KC), l[0], l[1], l[2], l[3]);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (BF) split2<true>(im[mt][2 * e], im[mt][2 * e + 1], h[e], l[e]);
-                    else split2_f16(im[mt][2 * e], im[mt][2 * e + 1], h[e], l[e]);
-                }
-                st16(ahi, tile_off(64 + rl, pc, KC), h[0], h[1], h[2], h[3]);
-                st16(ahi + A_BYTES, tile_off(64 + rl, pc, KC), l[0], l[1], l[2], l[3]);
+                const uint32_t ore = tile_off(rl, 2 * h + q, KC), oim = tile_off(128 + rl, 2 * h + q, KC);
+                st16(hi, ore, ch[0], ch[1], ch[2], ch[3]);
+                st16(lo, ore, cl[0], cl[1], cl[2], cl[3]);
+                st16(hi, oim, sh[0], sh[1], sh[2], sh[3]);
+                st16(lo, oim, sl[0], sl[1], sl[2], sl[3]);
             }
             fence_async_smem();
-            mb_arrive(&a_full[sa]);
+            mb_arrive(&a_full[ra.slot]);
         }
-    } else if (t < 384) {
-        // ---- drain: TMEM accumulator buffer -> TMEM running sum -> dpart ----
-        const int row = t - 256;                     // TMEM lane (warp 8 + q owns lanes 32q..)
-        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+    } else if (t < 512) {
+        // ---- drain: TMEM accumulator -> TMEM running sum -> dpart ----
+        const int dq = warp & 3, dh = (warp - 8) >> 2;        // lane quadrant, column half
+        const uint32_t lanes = (uint32_t)(dq * 32) << 16;
+        const int cl = dq * 32 + lane;                         // this thread's column c
         int gch = 0;
         int64_t w = w_begin;
         bool ok = true;
         while (w < w_end && ok) {
-            const int g = (int)(w / nst_all);
-            const int64_t seg_end = min(w_end, (int64_t)(g + 1) * nst_all);
-            const int nchs = (int)((seg_end - w + kFChunk - 1) / kFChunk);
-            const int piece = c - fwd_cta_of((int64_t)g * nst_all, W, G);
-            const int NG = fwd_group_cols(g, MT, R, NF, rows, fperm);
+            const int v = (int)(w / nst_all);
+            const int64_t seg_end = min(w_end, (int64_t)(v + 1) * nst_all);
+            const int nchs = (int)((seg_end - w + KCH - 1) / KCH);
+            const int piece = c - fwd_cta_of((int64_t)v * nst_all, W, G);
             for (int k = 0; k < nchs; ++k, ++gch) {
-                const int b = NBUF == 2 ? (gch & 1) : 0, bl = NBUF == 2 ? (gch >> 1) : gch;
-                if (!waitw(&accf[b], bl & 1, abort)) { ok = false; break; }
+                if (!waitw(accf, gch & 1, abort)) { ok = false; break; }
                 tc_after();
-                // column blocks of 16 are taken two at a time (NF is a multiple of 16; an odd
-                // last block is taken alone), so that each TMEM load wait covers four loads
 #pragma unroll 1
-                for (int mt = 0; mt < MT; ++mt) {
-#pragma unroll 1
-                    for (int c0 = 0; c0 < NG; c0 += 32) {
-                        const bool two = c0 + 16 < NG;
-                        const uint32_t src = tmem + lanes + (uint32_t)((b * MT + mt) * CT + c0);
-                        const uint32_t dst = tmem + lanes + (uint32_t)((NBUF * MT + mt) * CT + c0);
-                        uint32_t v0[16], s0[16], v1[16], s1[16];
-                        tm_ld16r(src, v0);
-                        if (two) tm_ld16r(src + 16, v1);
-                        if (k > 0) {
-                            tm_ld16r(dst, s0);
-                            if (two) tm_ld16r(dst + 16, s1);
-                        }
-                        tm_wait_ld();
-                        if (k > 0) {
+                for (int c0 = 0; c0 < 128; c0 += 32) {
+                    const uint32_t src = tmem + lanes + (uint32_t)(dh * 128 + c0);
+                    const uint32_t dst = src + 256;
+                    uint32_t a0[16], a1[16], s0v[16], s1v[16];
+                    tm_ld16r(src, a0);
+                    tm_ld16r(src + 16, a1);
+                    if (k > 0) { tm_ld16r(dst, s0v); tm_ld16r(dst + 16, s1v); }
+                    tm_wait_ld();
+                    if (k > 0) {
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                v0[i] = __float_as_uint(__uint_as_float(s0[i]) + __uint_as_float(v0[i]));
-                                v1[i] = __float_as_uint(__uint_as_float(s1[i]) + __uint_as_float(v1[i]));
-                            }
+                        for (int i = 0; i < 16; ++i) {
+                            a0[i] = __float_as_uint(__uint_as_float(s0v[i]) + __uint_as_float(a0[i]));
+                            a1[i] = __float_as_uint(__uint_as_float(s1v[i]) + __uint_as_float(a1[i]));
                         }
-                        tm_st16r(dst, v0);
-                        if (two) tm_st16r(dst + 16, v1);
                     }
+                    tm_st16r(dst, a0);
+                    tm_st16r(dst + 16, a1);
                 }
                 tm_wait_st();
                 tc_before();
-                mb_arrive(&acce[b]);
+                mb_arrive(acce);
             }
             if (!ok) break;
-            // the segment's partial sums -> dpart
+            // the segment's partial sum -> dpart, columns c < the pass's column count only (the
+            // TMEM loads are warp-wide; a warp whose lanes are all past the count skips them)
+            const int ncv = vgs[v].z;
+            if (dq * 32 < ncv) {
+                float4 *o = reinterpret_cast<float4 *>(dpart + (((int64_t)v * maxp + piece) * 128 + cl) * 256 + dh * 128);
 #pragma unroll 1
-            for (int mt = 0; mt < MT; ++mt) {
-                const int tile = g * MT + mt;
-                if (tile >= ntiles) continue;
-                float *o = dpart + ((int64_t)tile * maxp + piece) * NF * 128;
-#pragma unroll 1
-                for (int c0 = 0; c0 < NG; c0 += 16) {
-                    uint32_t v[16];
-                    tm_ld16r(tmem + lanes + (uint32_t)((NBUF * MT + mt) * CT + c0), v);
+                for (int c0 = 0; c0 < 128; c0 += 16) {
+                    uint32_t r[16];
+                    tm_ld16r(tmem + lanes + (uint32_t)(256 + dh * 128 + c0), r);
                     tm_wait_ld();
+                    if (cl < ncv) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) o[(c0 + i) * 128 + row] = __uint_as_float(v[i]);
+                        for (int i = 0; i < 4; ++i)
+                            o[c0 / 4 + i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
+                                                        __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]));
+                    }
                 }
             }
             w = seg_end;
         }
-    } else if (warp == 12) {
+    } else if (warp == 16) {
         // ---- bulk copies: (u_y, u_z) of every stage ----
         int issued = 0;
-        int sg = (int)(w_begin % nst_all);
+        int sg = s0;
         RingPos rp;
         for (int it = 0; it < nit; ++it, ++sg, rp.next(SP)) {
             if (sg == nst_all) sg = 0;
-            const int sp = rp.slot, up = rp.lap;
-            if (up > 0 && !waitw(&p_empty[sp], (up - 1) & 1, abort)) break;
+            if (rp.lap > 0 && !waitw(&c_empty[rp.slot], (rp.lap - 1) & 1, abort)) break;
             if (lane == 0) {
-                mb_expect_tx(&p_full[sp], (uint32_t)P_STAGE);
-                tma_bulk(smP + sp * P_STAGE, yz + (int64_t)sg * kFK, (uint32_t)P_STAGE, &p_full[sp]);
+                mb_expect_tx(&c_full[rp.slot], (uint32_t)C_STAGE);
+                tma_bulk(smC + rp.slot * C_STAGE, yz + (int64_t)sg * kFK, (uint32_t)C_STAGE, &c_full[rp.slot]);
             }
             __syncwarp();
             issued = it + 1;
         }
         for (int it = issued - SP < 0 ? 0 : issued - SP; it < issued; ++it) {
             volatile int no_abort = 0;
-            waitw(&p_full[it % SP], (it / SP) & 1, &no_abort);
+            waitw(&c_full[it % SP], (it / SP) & 1, &no_abort);
         }
-    } else if (warp == 13) {
-        // ---- bulk copies: B operand (hi, lo) of every stage ----
+    } else if (warp == 17) {
+        // ---- bulk copies: column operand (hi, lo) of every stage, this pass's columns ----
+        const int B_BYTES = NF * kFK * 2;                      // one term of a stage of bblob
         int issued = 0;
-        int g = (int)(w_begin / nst_all), sg = (int)(w_begin % nst_all);
-        int NG = fwd_group_cols(g, MT, R, NF, rows, fperm);
-        RingPos rb;
-        for (int it = 0; it < nit; ++it, ++sg, rb.next(SB)) {
-            if (sg == nst_all) { sg = 0; ++g; NG = fwd_group_cols(g, MT, R, NF, rows, fperm); }
-            const int sb = rb.slot, ub = rb.lap;
-            if (ub > 0 && !waitw(&b_empty[sb], (ub - 1) & 1, abort)) break;
+        int v = v0, sg = s0;
+        int4 vd = vgs[v];
+        RingPos rx;
+        for (int it = 0; it < nit; ++it, ++sg, rx.next(SX)) {
+            if (sg == nst_all) { sg = 0; ++v; vd = vgs[v]; }
+            if (rx.lap > 0 && !waitw(&x_empty[rx.slot], (rx.lap - 1) & 1, abort)) break;
             if (lane == 0) {
-                // the first NG columns of the hi and of the lo half (a prefix of each)
-                const uint32_t part = (uint32_t)NG * kFK * 2;
-                const unsigned char *src = bblob + (int64_t)sg * B_STAGE;
-                mb_expect_tx(&b_full[sb], 2 * part);
-                tma_bulk(smB + sb * B_STAGE, src, part, &b_full[sb]);
-                tma_bulk(smB + sb * B_STAGE + B_BYTES, src + B_BYTES, part, &b_full[sb]);
+                const uint32_t part = (uint32_t)vd.z * kFK * 2;
+                const unsigned char *src = bblob + (int64_t)sg * 2 * B_BYTES + (int64_t)vd.y * X_HALF;
+                mb_expect_tx(&x_full[rx.slot], 2 * part);
+                tma_bulk(smX + rx.slot * X_STAGE, src, part, &x_full[rx.slot]);
+                tma_bulk(smX + rx.slot * X_STAGE + X_HALF, src + B_BYTES, part, &x_full[rx.slot]);
             }
             __syncwarp();
             issued = it + 1;
         }
-        for (int it = issued - SB < 0 ? 0 : issued - SB; it < issued; ++it) {
+        for (int it = issued - SX < 0 ? 0 : issued - SX; it < issued; ++it) {
             volatile int no_abort = 0;
-            waitw(&b_full[it % SB], (it / SB) & 1, &no_abort);
+            waitw(&x_full[it % SX], (it / SX) & 1, &no_abort);
         }
-    } else if (warp == 14) {
-        // ---- MMA issuer ----
+    } else if (warp == 18) {
+        // ---- MMA issuer: D[c, n] += X[c, k] P[n, k], three split products per K step ----
+        const uint32_t idesc = idesc_f16(128, 256, BF);
         const uint32_t sbo = KC * 128;
-        int gm = (int)(w_begin / nst_all);
-        uint32_t idesc = idesc_f16(128, fwd_group_cols(gm, MT, R, NF, rows, fperm), BF);
         int gch = -1;
-        int sg = (int)(w_begin % nst_all);     // stage of the item within its group
-        int ls = 0;                            // item index within the segment
-        RingPos ra, rb;
-        for (int it = 0; it < nit; ++it, ++sg, ++ls, ra.next(SA), rb.next(SB)) {
-            if (sg == nst_all) {
-                sg = 0; ls = 0; ++gm;
-                idesc = idesc_f16(128, fwd_group_cols(gm, MT, R, NF, rows, fperm), BF);
-            }
-            const bool first = (ls % kFChunk) == 0;
-            const bool last = (ls % kFChunk) == kFChunk - 1 || sg == nst_all - 1 || it == nit - 1;
+        int sg = s0, ls = 0;                 // stage within the virtual group, index in segment
+        RingPos ra, rx;
+        for (int it = 0; it < nit; ++it, ++sg, ++ls, ra.next(SA), rx.next(SX)) {
+            if (sg == nst_all) { sg = 0; ls = 0; }
+            const bool first = (ls % KCH) == 0;
+            const bool last = (ls % KCH) == KCH - 1 || sg == nst_all - 1 || it == nit - 1;
             if (first) ++gch;
-            const int b = NBUF == 2 ? (gch & 1) : 0, bl = NBUF == 2 ? (gch >> 1) : gch;
-            const int sa = ra.slot, ua = ra.lap, sb = rb.slot, ub = rb.lap;
-            if (first && gch >= NBUF && !waitw(&acce[b], (bl - 1) & 1, abort)) break;
-            if (!waitw(&a_full[sa], ua & 1, abort)) break;
-            if (!waitw(&b_full[sb], ub & 1, abort)) break;
+            if (first && gch >= 1 && !waitw(acce, (gch - 1) & 1, abort)) break;
+            if (!waitw(&a_full[ra.slot], ra.lap & 1, abort)) break;
+            if (!waitw(&x_full[rx.slot], rx.lap & 1, abort)) break;
             tc_after();
             if (lane == 0) {
-                const uint32_t sA = su32(smA + sa * A_STAGE);
-                const uint32_t bhi = su32(smB + sb * B_STAGE), blo = bhi + B_BYTES;
+                const uint32_t phi = su32(smP + ra.slot * P_STAGE), plo = phi + P_HALF;
+                const uint32_t xhi = su32(smX + rx.slot * X_STAGE), xlo = xhi + X_HALF;
 #pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const uint32_t ahi = sA + (mt * 2) * A_BYTES, alo = ahi + A_BYTES;
-                    const uint32_t d = tmem + (uint32_t)((b * MT + mt) * CT);
-#pragma unroll
-                    for (int kk = 0; kk < kFK / 16; ++kk) {
-                        const uint32_t o = kk * 256;
-                        umma(d, sdesc(ahi + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, (first && kk == 0) ? 0u : 1u);
-                        umma(d, sdesc(ahi + o, 128, sbo), sdesc(blo + o, 128, sbo), idesc, 1);
-                        umma(d, sdesc(alo + o, 128, sbo), sdesc(bhi + o, 128, sbo), idesc, 1);
-                    }
+                for (int kk = 0; kk < kFK / 16; ++kk) {
+                    const uint32_t o = kk * 256;
+                    umma(tmem, sdesc(xhi + o, 128, sbo), sdesc(phi + o, 128, sbo), idesc, (first && kk == 0) ? 0u : 1u);
+                    umma(tmem, sdesc(xhi + o, 128, sbo), sdesc(plo + o, 128, sbo), idesc, 1);
+                    umma(tmem, sdesc(xlo + o, 128, sbo), sdesc(phi + o, 128, sbo), idesc, 1);
                 }
-                umma_commit(&a_empty[sa]);
-                umma_commit(&b_empty[sb]);
-                if (last) umma_commit(&accf[b]);
+                umma_commit(&a_empty[ra.slot]);
+                umma_commit(&x_empty[rx.slot]);
+                if (last) umma_commit(accf);
             }
             __syncwarp();
         }
@@ -629,8 +601,8 @@ __global__ void k_xgen(int n, int kmax, int NF, const uint4 *__restrict__ pu,
 // e_part[m * ntiles + tile], the coefficient matrix column-major
 // gmat_t[col * 2R + (2r | 2r + 1)], and the max |G'| (as int bits).
 __global__ void __launch_bounds__(64)
-k_sreduce_tc(int MT, int nst_all, int64_t W, int G, int maxp, int ntiles, int R, int kmax, int NF,
-             const RowInfo *__restrict__ rows,
+k_sreduce_tc(int nst_all, int64_t W, int G, int maxp, const int2 *__restrict__ gvg, int ntiles,
+             int R, int kmax, int NF, const RowInfo *__restrict__ rows,
              const int *__restrict__ fperm, const float *__restrict__ dpart,
              const double *__restrict__ gk, double *__restrict__ S, double *__restrict__ e_part,
              float *__restrict__ gmat_t, int *__restrict__ gmax)
@@ -648,20 +620,26 @@ k_sreduce_tc(int MT, int nst_all, int64_t W, int G, int maxp, int ntiles, int R,
         const bool origin = ri.my == 0 && ri.mz == 0;
         const double wy = ri.my, wz = ri.mz;
         double t[4] = {0.0, 0.0, 0.0, 0.0};         // T_rr, T_ri, T_ir, T_ii
-        // the pieces of this tile: one per CTA that worked on its group, in CTA order
-        const int g = tile / MT;
-        const int npc = fwd_cta_of((int64_t)(g + 1) * nst_all - 1, W, G) -
-                        fwd_cta_of((int64_t)g * nst_all, W, G) + 1;
-        const float *o = dpart + (int64_t)tile * maxp * NF * 128;
         const int cre = m == 0 ? 0 : 2 * m - 1, cim = 2 * m;   // columns of Re X[m], Im X[m]
         if (m <= ri.nxmax) {
-            for (int pc = 0; pc < npc; ++pc, o += (int64_t)NF * 128) {
-                t[0] += (double)o[cre * 128 + rl];
-                t[2] += (double)o[cre * 128 + 64 + rl];
-                if (m >= 1) {
-                    t[1] += (double)o[cim * 128 + rl];
-                    t[3] += (double)o[cim * 128 + 64 + rl];
+            // the pieces of a column's virtual group: one per CTA that worked on it, in CTA
+            // order; n = row in the group (Re P) and 128 + row (Im P)
+            const int g = fr / 128, n = fr % 128;
+            const int2 gv = gvg[g];
+#pragma unroll
+            for (int which = 0; which < 2; ++which) {
+                if (which == 1 && m == 0) break;
+                const int col = which == 0 ? cre : cim;
+                const int v = gv.x + col / 128;
+                const int npc = fwd_cta_of((int64_t)(v + 1) * nst_all - 1, W, G) -
+                                fwd_cta_of((int64_t)v * nst_all, W, G) + 1;
+                const float *o = dpart + ((int64_t)v * maxp * 128 + col % 128) * 256;
+                double a = 0.0, b = 0.0;
+                for (int pc = 0; pc < npc; ++pc, o += (int64_t)128 * 256) {
+                    a += (double)o[n];
+                    b += (double)o[128 + n];
                 }
+                if (which == 0) { t[0] = a; t[2] = b; } else { t[1] = a; t[3] = b; }
             }
         }
         const bool vp = m <= ri.nxmax && (!origin || m > 0);
@@ -723,6 +701,14 @@ k_sreduce_tc(int MT, int nst_all, int64_t W, int G, int maxp, int ntiles, int R,
 // Column gc: gc < 3 -> m = 0, block gc; else u = gc - 3: m = 1 + u / 6, block (u % 6) / 2,
 // kind 1 + (u & 1) (kind 1: coefficient column 2m - 1, kind 2: column 2m of the block).
 struct BsCol { int m, kind, blk; };
+// Passes: pass q holds columns [q kPassMax, min(ncol, (q + 1) kPassMax)), padded to 16, so all
+// passes but the last use the full MMA width (an MMA costs the same whatever its N) and the
+// last, narrow one has the largest m and the shortest row range.
+__host__ __device__ inline int bs_pass_cols(int ncol, int pass)
+{
+    const int w = ncol - pass * kPassMax;
+    return 16 * (((w < kPassMax ? w : kPassMax) + 15) / 16);
+}
 __host__ __device__ inline BsCol bs_col(int gc)
 {
     if (gc < 3) return {0, 0, gc};
@@ -734,7 +720,7 @@ __host__ __device__ inline BsCol bs_col(int gc)
 // blob[pass][kb] = [16 x (m_y, m_z) int2][hi: NP x kBK][lo: NP x kBK], core-matrix layout.
 // One thread packs 8 consecutive K of one column: one 16-byte store per part.
 template <bool BF>
-__global__ void k_bpack(int R, int ncol, int NP, int nkb, const RowInfo *__restrict__ rows,
+__global__ void k_bpack(int R, int ncol, int NPS, int nkb, const RowInfo *__restrict__ rows,
                         const float *__restrict__ gmat_t, const int *__restrict__ gmax,
                         float *__restrict__ gscale, unsigned char *__restrict__ blob)
 {
@@ -745,7 +731,8 @@ __global__ void k_bpack(int R, int ncol, int NP, int nkb, const RowInfo *__restr
         if (mx > 0.f) scale = exp2f((float)(14 - ilogbf(mx)));
     }
     if (kb == 0 && pass == 0 && threadIdx.x == 0) gscale[0] = 1.f / scale;
-    const int64_t bsz = kHdr + 2 * (int64_t)NP * kBK * 2;
+    const int NP = bs_pass_cols(ncol, pass);            // columns of this pass
+    const int64_t bsz = kHdr + 2 * (int64_t)NPS * kBK * 2;  // slot stride: the widest pass
     unsigned char *out = blob + ((int64_t)pass * nkb + kb) * bsz;
     if (threadIdx.x < kBK / 2) {
         const int r = kb * (kBK / 2) + threadIdx.x;
@@ -759,7 +746,7 @@ __global__ void k_bpack(int R, int ncol, int NP, int nkb, const RowInfo *__restr
     const int NB = ncol / 3;
     for (int u = threadIdx.x; u < NP * (kBK / 8); u += blockDim.x) {
         const int col = u / (kBK / 8), kc = u % (kBK / 8);
-        const int gc = pass * NP + col;
+        const int gc = pass * kPassMax + col;
         const BsCol bc = bs_col(gc);
         const int64_t oc = (int64_t)bc.blk * NB + (bc.kind == 0 ? 0 : (bc.kind == 1 ? 2 * bc.m - 1 : 2 * bc.m));
         const int64_t gk0 = (int64_t)kb * kBK + 8 * kc;
@@ -781,16 +768,18 @@ __global__ void k_bpack(int R, int ncol, int NP, int nkb, const RowInfo *__restr
 // bpart layout [pass][n] float4 = partial (F_x, F_y, F_z, phi) before q_i, 2 pi / L and scale.
 template <bool BF>
 __global__ void __launch_bounds__(kBThreads, 1)
-k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, int4 kb0s, const uint4 *__restrict__ pu,
+k_bs_tc(int n, int R, int kmax, int ncol, int NPS, int nkb, int4 kb0s, const uint4 *__restrict__ pu,
         const unsigned char *__restrict__ blob, float *__restrict__ bpart, int *__restrict__ status)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     constexpr int KC = kBK / 8;
     const int A_BYTES = 128 * kBK * 2;          // 8 KB
+    const int NP = bs_pass_cols(ncol, blockIdx.y);   // columns (MMA N) of this pass
     const int B_BYTES = NP * kBK * 2;
-    const int BLOB = kHdr + 2 * B_BYTES;
+    const int BLOB = kHdr + 2 * B_BYTES;             // bytes copied per K block
     const int B_OFF = kBMT * 2 * A_BYTES;
-    const int STAGE = B_OFF + BLOB;
+    const int STAGE = B_OFF + kHdr + 2 * NPS * kBK * 2;   // stage layout sized for the widest pass
+    const int64_t SLOT = kHdr + 2 * (int64_t)NPS * kBK * 2;
     uint64_t *full_a = reinterpret_cast<uint64_t *>(sm + kBStages * STAGE);
     uint64_t *full_b = full_a + kBStages;
     uint64_t *empty = full_b + kBStages;
@@ -816,7 +805,7 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, int4 kb0s, const uint
     // column descriptors of this pass: bits 0-7 m, 8-9 kind (0: m = 0, 1: first, 2: second),
     // 10-11 block (x, y, z), bit 12 padding
     for (int col = t; col < NP; col += kBThreads) {
-        const int gc = pass * NP + col;
+        const int gc = pass * kPassMax + col;
         int d = 1 << 12;
         if (gc < ncol) {
             const BsCol bc = bs_col(gc);
@@ -872,7 +861,7 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NP, int nkb, int4 kb0s, const uint
             if (u > 0 && !waitw(&empty[s], (u - 1) & 1, abort)) break;
             if (lane == 0) {
                 mb_expect_tx(&full_b[s], (uint32_t)BLOB);
-                tma_bulk(sm + s * STAGE + B_OFF, blob + ((int64_t)pass * nkb + kb) * BLOB, (uint32_t)BLOB, &full_b[s]);
+                tma_bulk(sm + s * STAGE + B_OFF, blob + ((int64_t)pass * nkb + kb) * SLOT, (uint32_t)BLOB, &full_b[s]);
             }
             __syncwarp();
             issued = kb - kb0 + 1;
@@ -986,19 +975,22 @@ __global__ void k_bs_reduce(int64_t n, int npass, const float *__restrict__ bpar
 // ---- plan-side state ----------------------------------------------------------------------
 
 struct TcState {
-    int nf = 0;           // forward N (2 k_max + 1 rounded up to 16)
-    int fmt = 1;          // forward M tiles of 64 rows per group
-    int nbuf = 2;         // forward TMEM accumulator buffers
-    int ct = 0;           // forward TMEM columns per tile (nf rounded up to 32)
-    int sa = 0, sb = 0, sp = 0;   // forward ring depths: A, B, particle data
+    int nf = 0;           // forward columns (2 k_max + 1 rounded up to 16)
+    int sa = 0, sx = 0, sp = 0;   // forward ring depths: phases, columns, coordinates
+    int kch = kFChunk;    // forward stages per TMEM accumulation
     size_t fsmem = 0;     // forward dynamic shared memory
-    int ntiles = 0;       // forward tiles of 64 rows
-    int mgroups = 0;      // forward M groups
-    int maxp = 0;         // forward partial sums per tile (bound)
+    int ntiles = 0;       // tiles of 64 forward rows (reduction grid)
+    int ngroups = 0;      // forward groups of 128 rows
+    int nvg = 0;          // forward virtual groups (group, column pass)
+    int maxp = 0;         // forward partial sums per virtual group (bound)
+    std::vector<int4> vgs_h;      // (first row, pass, columns, 0) per virtual group
+    std::vector<int2> gvg_h;      // (first virtual group, passes) per group
+    int4 *vgs = nullptr;
+    int2 *gvg = nullptr;
     int ncol = 0;         // back-scatter columns 3 (2 k_max + 1)
     int npass = 0, np = 0, nkb = 0;
     int kb0[4] = {0, 0, 0, 0};     // back-scatter: first K block of every pass
-    float *dpart = nullptr;        // [ntiles][maxp][nf][128]
+    float *dpart = nullptr;        // [nvg][maxp][128 columns][256]
     uint2 *yz = nullptr;           // [stages * 32] (u_y, u_z)
     unsigned char *bblob = nullptr; // [stages][hi + lo] forward B operand
     int nstg = 0;                  // 32-particle stages (capacity)
@@ -1014,27 +1006,20 @@ constexpr int kTmemCols = 512;
 
 size_t fwd_bstage(int nf) { return (size_t)2 * nf * kFK * 2; }
 
-// Forward layout: tile stride in TMEM, M tiles per group, accumulator buffers (two while a
-// running sum fits beside them), and ring depths within the shared-memory limit.
+// Forward ring depths within the shared-memory limit: phase tiles 32 KB, column tiles 16 KB.
 void fwd_config(TcState &s)
 {
-    s.ct = 32 * ((s.nf + 31) / 32);
-    if (6 * s.ct <= kTmemCols) { s.fmt = 2; s.nbuf = 2; }
-    else if (4 * s.ct <= kTmemCols) { s.fmt = 2; s.nbuf = 1; }
-    else if (3 * s.ct <= kTmemCols) { s.fmt = 1; s.nbuf = 2; }
-    else { s.fmt = 1; s.nbuf = 1; }
+    const size_t p_stage = (size_t)2 * 256 * kFK * 2, x_stage = (size_t)2 * 128 * kFK * 2;
     s.sp = 8;
-    const size_t a_stage = (size_t)s.fmt * 2 * 128 * kFK * 2;
-    const size_t b_stage = fwd_bstage(s.nf);
-    s.sa = s.fmt == 2 ? 3 : 4;
-    auto total = [&](int sa, int sb) {
-        return sa * a_stage + sb * b_stage + (size_t)s.sp * kFK * 8 +
-               (size_t)(2 * sa + 2 * sb + 2 * s.sp + 5) * 8 + 64;
+    s.sa = 4;
+    s.sx = 5;
+    auto total = [&](int sa, int sx) {
+        return sa * p_stage + sx * x_stage + (size_t)s.sp * kFK * 8 +
+               (size_t)(2 * sa + 2 * sx + 2 * s.sp + 3) * 8 + 64;
     };
-    s.sb = 8;
-    while (s.sb > 2 && total(s.sa, s.sb) > kSmemMax) --s.sb;
-    while (s.sa > 2 && total(s.sa, s.sb) > kSmemMax) --s.sa;
-    s.fsmem = total(s.sa, s.sb);
+    while (s.sx > 2 && total(s.sa, s.sx) > kSmemMax) --s.sx;
+    while (s.sa > 2 && total(s.sa, s.sx) > kSmemMax) --s.sa;
+    s.fsmem = total(s.sa, s.sx);
 }
 
 void tc_shape(const Plan &p, int64_t n, TcState &s)
@@ -1042,17 +1027,32 @@ void tc_shape(const Plan &p, int64_t n, TcState &s)
     s.nf = 16 * ((2 * p.kmax + 1 + 15) / 16);
     fwd_config(s);
     s.ntiles = (p.R + 63) / 64;
-    s.mgroups = (s.ntiles + s.fmt - 1) / s.fmt;
-    s.maxp = p.num_sms / s.mgroups + 2;
+    s.ngroups = (p.R + 127) / 128;
+    // virtual groups: a group of 128 forward rows needs the columns |m_x| <= n_x,max of its
+    // first row (forward order = reverse row order), in passes of at most 128
+    s.vgs_h.clear();
+    s.gvg_h.clear();
+    for (int g = 0; g < s.ngroups; ++g) {
+        const int fr0 = g * 128;
+        const int nx = p.rows_h[p.R - 1 - fr0].nxmax;
+        int nc = 16 * ((2 * nx + 1 + 15) / 16);
+        if (nc > s.nf) nc = s.nf;
+        const int passes = (nc + 127) / 128;
+        s.gvg_h.push_back(make_int2((int)s.vgs_h.size(), passes));
+        for (int cp = 0; cp < passes; ++cp)
+            s.vgs_h.push_back(make_int4(fr0, cp, std::min(128, nc - 128 * cp), 0));
+    }
+    s.nvg = (int)s.vgs_h.size();
+    s.maxp = p.num_sms / s.nvg + 2;
     s.nstg = (int)((n + kFK - 1) / kFK);
     s.ncol = 3 * (2 * p.kmax + 1);
     s.npass = (s.ncol + kPassMax - 1) / kPassMax;
-    s.np = 16 * (((s.ncol + s.npass - 1) / s.npass + 15) / 16);
+    s.np = bs_pass_cols(s.ncol, 0);         // the widest pass: slot stride of the packed blobs
     s.nkb = (2 * p.R + kBK - 1) / kBK;
     // rows run in order of increasing n_x,max; pass q starts at the K block holding the first
     // row that reaches the smallest m of its columns
     for (int q = 0; q < s.npass && q < 4; ++q) {
-        const int mlo = bs_col(q * s.np).m;
+        const int mlo = bs_col(q * kPassMax).m;
         int r = 0;
         while (r < p.R && p.rows_h[r].nxmax < mlo) ++r;
         s.kb0[q] = (r < p.R ? r : p.R - 1) / (kBK / 2);
@@ -1066,17 +1066,17 @@ size_t bs_smem(int np)
     return kBStages * stage + 128 + 4 * (size_t)np;
 }
 
-template <int MT, bool BF>
+template <bool BF>
 cudaError_t launch_fwd(Plan &p, int nst_all, TcState &s, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<MT, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)s.fsmem);
     if (e != cudaSuccess) return e;
-    const int64_t W = (int64_t)s.mgroups * nst_all;
+    const int64_t W = (int64_t)s.nvg * nst_all;
     const int G = (int)std::min<int64_t>(p.num_sms, W);
-    k_fwd_tc<MT, BF><<<G, kFThreads, s.fsmem, st>>>(
-        p.R, s.nf, nst_all, W, s.maxp, s.ntiles, s.sa, s.sb, s.sp, s.nbuf, s.ct, p.rows_d,
-        p.fperm_d, s.yz, s.bblob, s.dpart, p.d_status);
+    k_fwd_tc<BF><<<G, kFThreads, s.fsmem, st>>>(
+        p.R, s.nf, nst_all, W, s.maxp, s.sa, s.sx, s.sp, s.kch, s.vgs, p.rows_d, p.fperm_d, s.yz,
+        s.bblob, s.dpart, p.d_status);
     return cudaGetLastError();
 }
 
@@ -1089,15 +1089,15 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
     prof_mark(p, kEvRecipStart, st);
     const int nst_all = (int)((n + kFK - 1) / kFK);
     k_xgen<BF><<<nst_all, 256, 0, st>>>((int)n, p.kmax, s.nf, ws.pu, s.yz, s.bblob);
-    e = s.fmt == 2 ? launch_fwd<2, BF>(p, nst_all, s, st) : launch_fwd<1, BF>(p, nst_all, s, st);
+    e = launch_fwd<BF>(p, nst_all, s, st);
     if (e != cudaSuccess) return e;
     prof_mark(p, kEvFwdEnd, st);
     if ((e = cudaMemsetAsync(s.gmax, 0, sizeof(int), st)) != cudaSuccess) return e;
     {
-        const int64_t W = (int64_t)s.mgroups * nst_all;
+        const int64_t W = (int64_t)s.nvg * nst_all;
         const int G = (int)std::min<int64_t>(p.num_sms, W);
         k_sreduce_tc<<<dim3(s.ntiles, p.kmax + 1), 64, 0, st>>>(
-            s.fmt, nst_all, W, G, s.maxp, s.ntiles, p.R, p.kmax, s.nf, p.rows_d, p.fperm_d,
+            nst_all, W, G, s.maxp, s.gvg, s.ntiles, p.R, p.kmax, s.nf, p.rows_d, p.fperm_d,
             s.dpart, p.g_d, p.S_d, p.e_recip_part, s.gmat, s.gmax);
     }
     k_bpack<BF><<<dim3(s.nkb, s.npass), 256, 0, st>>>(p.R, s.ncol, s.np, s.nkb, p.rows_d, s.gmat,
@@ -1126,7 +1126,8 @@ size_t recip_tc_bytes(const Plan &p, int64_t n)
     TcState s;
     tc_shape(p, n, s);
     size_t b = 0;
-    b += (size_t)s.ntiles * s.maxp * s.nf * 128 * sizeof(float);
+    b += (size_t)s.nvg * s.maxp * 128 * 256 * sizeof(float);
+    b += (size_t)s.nvg * sizeof(int4) + (size_t)s.ngroups * sizeof(int2);
     b += (size_t)s.nstg * (fwd_bstage(s.nf) + kFK * sizeof(uint2));
     b += (size_t)2 * p.R * s.ncol * sizeof(float);
     b += (size_t)s.npass * s.nkb * bs_blob(s.np);
@@ -1142,7 +1143,11 @@ cudaError_t alloc_recip_tc(Plan &p, int64_t n)
     p.tc = s;
     cudaStream_t st = p.side_stream;
     cudaError_t e;
-    if ((e = pool_alloc((void **)&s->dpart, (size_t)s->ntiles * s->maxp * s->nf * 128 * sizeof(float), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->dpart, (size_t)s->nvg * s->maxp * 128 * 256 * sizeof(float), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->vgs, (size_t)s->nvg * sizeof(int4), st)) != cudaSuccess) return e;
+    if ((e = pool_alloc((void **)&s->gvg, (size_t)s->ngroups * sizeof(int2), st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(s->vgs, s->vgs_h.data(), (size_t)s->nvg * sizeof(int4), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(s->gvg, s->gvg_h.data(), (size_t)s->ngroups * sizeof(int2), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->gmat, (size_t)2 * p.R * s->ncol * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->yz, (size_t)s->nstg * kFK * sizeof(uint2), st)) != cudaSuccess) return e;
     if ((e = pool_alloc((void **)&s->bblob, (size_t)s->nstg * fwd_bstage(s->nf), st)) != cudaSuccess) return e;
@@ -1159,6 +1164,7 @@ void free_recip_tc(Plan &p)
     if (!s) return;
     cudaStream_t st = p.side_stream;
     pool_free(s->dpart, st); pool_free(s->gmat, st); pool_free(s->gmax, st);
+    pool_free(s->vgs, st); pool_free(s->gvg, st);
     pool_free(s->yz, st); pool_free(s->bblob, st);
     pool_free(s->gscale, st); pool_free(s->blob, st); pool_free(s->bpart, st);
     delete s;
