@@ -336,9 +336,11 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int SA, int SX, int SP
     const int v0 = (int)(w_begin / nst_all), s0 = (int)(w_begin % nst_all);
 
     if (t == 0) {
-        for (int s = 0; s < SA; ++s) { mb_init(&a_full[s], 256); mb_init(&a_empty[s], 1); }
+        // producer barriers count one arrival per producer warp (lane 0, after the warp's
+        // stores are fenced for the async proxy and the warp has synchronised)
+        for (int s = 0; s < SA; ++s) { mb_init(&a_full[s], 8); mb_init(&a_empty[s], 1); }
         for (int s = 0; s < SX; ++s) { mb_init(&x_full[s], 1); mb_init(&x_empty[s], 1); }
-        for (int s = 0; s < SP; ++s) { mb_init(&c_full[s], 1); mb_init(&c_empty[s], 256); }
+        for (int s = 0; s < SP; ++s) { mb_init(&c_full[s], 1); mb_init(&c_empty[s], 8); }
         mb_init(accf, 1);
         mb_init(acce, 256);
         mb_init(mmad, 1);
@@ -377,7 +379,8 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int SA, int SX, int SP
                     py[2 * i] = q4.x; pz[2 * i] = q4.y; py[2 * i + 1] = q4.z; pz[2 * i + 1] = q4.w;
                 }
             }
-            mb_arrive(&c_empty[rp.slot]);
+            __syncwarp();
+            if (lane == 0) mb_arrive(&c_empty[rp.slot]);
             float cs[16], sn[16];
 #pragma unroll
             for (int e = 0; e < 16; ++e) phase((uint32_t)my * py[e] + (uint32_t)mz * pz[e], cs[e], sn[e]);
@@ -397,7 +400,8 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int SA, int SX, int SP
                 st16(lo, oim, sl[0], sl[1], sl[2], sl[3]);
             }
             fence_async_smem();
-            mb_arrive(&a_full[ra.slot]);
+            __syncwarp();
+            if (lane == 0) mb_arrive(&a_full[ra.slot]);
         }
     } else if (t < 512) {
         // ---- drain: TMEM accumulator -> TMEM running sum -> dpart ----
