@@ -23,6 +23,8 @@
 
 using namespace ew;
 
+static void cell_grid(double L, double rc, int64_t n, int &nc, int &w);
+
 
 namespace ew {
 namespace {
@@ -214,6 +216,10 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     if (e != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(p.side_stream)) != cudaSuccess) return e;
     free_workspace(p);
+    // the cell grid can depend on the density, known from here on
+    cell_grid(p.L, p.rc, n, p.nc, p.w);
+    p.ncells = p.nc * p.nc * p.nc;
+    p.cell_side = p.L / p.nc;
     Workspace &ws = p.ws;
     const int nb = binning_chunks(n);
     const int nrows = p.nc * p.nc;
@@ -304,10 +310,13 @@ cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, dou
 size_t plan_footprint(const Plan &p, int64_t n)
 {
     const int nb = binning_chunks(n);
-    const int64_t tiles = real_tile_capacity(p, n);
+    int nc = 1, w = 0;
+    cell_grid(p.L, p.rc, n, nc, w);
+    const size_t ncells = (size_t)nc * nc * nc;
+    const int64_t tiles = w == 0 ? (n + 31) / 32 : n / real_tile_size(p) + (int64_t)nc * nc + 1;
     size_t b = 0;
-    b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * p.ncells;
-    b += sizeof(int) * (2 * (size_t)p.ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * (p.nc * p.nc + 1);
+    b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * ncells;
+    b += sizeof(int) * (2 * ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * ((size_t)nc * nc + 1);
     b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
     b += sizeof(double) * 6 * (size_t)n + sizeof(double) * tiles + sizeof(double) * 3 * ((n + 255) / 256);
     b += uses_tc(p.precision) ? recip_tc_bytes(p, n) : recip_simt_bytes(p, n);
@@ -349,20 +358,33 @@ static void build_rows(Plan &p)
     p.nk = koff;
 }
 
+// Cell grid for n particles (n = 0 while the count is not known): cells of side >= r_c / w
+// with a (2w + 1)^3 stencil that does not wrap onto itself.  w = 3 where such cells still hold
+// 16 particles or more (dense systems with long cutoffs, where the finer stencil follows the
+// cutoff sphere more closely and the per-cell overhead stays small), else w = 2, 1, or 0
+// (all pairs with the minimum image).
+static void cell_grid(double L, double rc, int64_t n, int &nc_out, int &w_out)
+{
+    const double rho = n > 0 ? (double)n / (L * L * L) : 0.0;
+    w_out = 0;
+    nc_out = 1;
+    for (int w = 3; w >= 1; --w) {
+        int nc = (int)floor(L * w / rc * (1.0 - 1e-12));
+        if (nc > 256) nc = 256;
+        if (nc < 2 * w + 1) continue;
+        if (w == 3) {
+            const double side = L / nc;
+            if (rho * side * side * side < 16.0) continue;
+        }
+        w_out = w;
+        nc_out = nc;
+        return;
+    }
+}
+
 static void choose_cells(Plan &p)
 {
-    // cells of side >= r_c / w with a (2w + 1)^3 stencil that does not wrap onto itself
-    p.w = 0;
-    p.nc = 1;
-    for (int w = 2; w >= 1; --w) {
-        int nc = (int)floor(p.L * w / p.rc * (1.0 - 1e-12));
-        if (nc > 256) nc = 256;
-        if (nc >= 2 * w + 1) {
-            p.w = w;
-            p.nc = nc;
-            break;
-        }
-    }
+    cell_grid(p.L, p.rc, 0, p.nc, p.w);
     p.ncells = p.nc * p.nc * p.nc;
     p.cell_side = p.L / p.nc;
 }
