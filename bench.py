@@ -107,6 +107,25 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# ---- multi-rank aggregation --------------------------------------------------------------
+
+def max_over_ranks(ms, world, device=None):
+    """The job's step time is its slowest rank's: the max of a per-rank time over the ranks
+    of the default process group (the value itself when there is one rank)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ms, world):
+    """Units per second of the whole job: every rank processes units_per_rank in ms."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ---- clocks ------------------------------------------------------------------------------
 
 class ClockSampler:
@@ -334,17 +353,13 @@ def run_md(args, rank, world, local):
     clk = clocks.stop()
     if ew.status() != 0:
         raise RuntimeError("MD run reported an error")
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     lg = log.cpu().numpy()
     e_tot = lg[:, 5]
     drift = float(np.abs(e_tot - e_tot[0]).max() / abs(lg[0, 3]))
     if rank == 0:
         print(json.dumps({
-            "metric": "ewald_md_particle_steps_per_s", "value": world * n * steps / (ms * 1e-3),
+            "metric": "ewald_md_particle_steps_per_s", "value": whole_job_rate(n * steps, ms, world),
             "unit": "particle-steps/s", "n_gpus": world, "steps": steps, "warmup": w,
             "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
@@ -492,12 +507,8 @@ def main():
     ew.profile(0)
     if ew.status() != 0:
         raise RuntimeError("timed evaluation reported an error")
-    ms = float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)]))
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * n / (ms * 1e-3)
+    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)])), world, dev)
+    value = whole_job_rate(n, ms, world)
 
     # end to end through the host-buffer entry point (pinned host memory)
     hp = torch.tensor(pos).pin_memory().numpy()
@@ -511,7 +522,7 @@ def main():
         t0 = time.perf_counter()
         _, eh = ew.compute_host(hp, hq, hf)
         e_times.append(time.perf_counter() - t0)
-    e2e = world * n / float(np.mean(e_times))
+    e2e = whole_job_rate(n, max_over_ranks(1e3 * float(np.mean(e_times)), world, dev), world)
 
     pk, pk_kind = peaks()
     tc = args.precision in ("mixed", "mixed_bf16")
