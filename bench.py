@@ -55,30 +55,54 @@ def params_for(workload, n, L):
 
 # ---- roofline bookkeeping ---------------------------------------------------------------
 
+def row_nxmax(kmax):
+    """n_x,max of every row (m_y, m_z) of the half plane, in increasing order (the order the
+    library processes the rows of the back-scatter in)."""
+    out = []
+    for mz in range(kmax + 1):
+        for my in range(-kmax, kmax + 1):
+            if my * my + mz * mz <= kmax * kmax and (mz > 0 or my >= 0):
+                out.append(math.isqrt(kmax * kmax - my * my - mz * mz))
+    return sorted(out)
+
+
 def rows_count(kmax):
-    return sum(1 for mz in range(kmax + 1) for my in range(-kmax, kmax + 1)
-               if my * my + mz * mz <= kmax * kmax and (mz > 0 or my >= 0))
+    return len(row_nxmax(kmax))
 
 
 def tensor_flops(n, kmax):
-    """Issued tensor-core flops of one evaluation, three split-term products each: the
-    forward M = rows padded to 64-row tiles (x2 for re/im), N = 2 k_max + 1 padded to 16,
-    K = n padded to 32-particle stages; the back-scatter M = n padded to 256-particle CTA
-    tiles, K = 2R padded to 32, N = 3 (2 k_max + 1) split into passes of <= 256 columns
-    padded to 16."""
-    R = rows_count(kmax)
+    """Issued tensor-core flops of one evaluation (three split-term products each), following
+    the library's tiling.  Forward: per group of 128 rows (forward order: decreasing n_x,max)
+    one or two column passes, each an M = 128 x N = 256 product over K = n padded to
+    32-particle stages.  Back-scatter: M = n padded to 256-particle CTA tiles; columns in
+    passes of 256 (the last narrower, padded to 16), pass q over K = 32-deep blocks from the
+    block holding the first row with n_x,max >= the smallest |m_x| of its columns."""
+    nx = row_nxmax(kmax)
+    R = len(nx)
     nf = 16 * math.ceil((2 * kmax + 1) / 16)
+    kpad = 32 * math.ceil(n / 32)
+    fwd = 0.0
+    for g in range(math.ceil(R / 128)):
+        first = nx[R - 1 - 128 * g]                     # forward order = reverse row order
+        ncols = min(nf, 16 * math.ceil((2 * first + 1) / 16))
+        fwd += math.ceil(ncols / 128) * 2.0 * 128 * 256 * kpad * 3
     ncol = 3 * (2 * kmax + 1)
     npass = math.ceil(ncol / 256)
-    nb = npass * 16 * math.ceil(math.ceil(ncol / npass) / 16)
-    fwd = 2.0 * (2 * 64 * math.ceil(R / 64)) * nf * (32 * math.ceil(n / 32)) * 3
-    back = 2.0 * (256 * math.ceil(n / 256)) * (32 * math.ceil(2 * R / 32)) * nb * 3
+    nkb = math.ceil(2 * R / 32)
+    back = 0.0
+    for q in range(npass):
+        width = 16 * math.ceil(min(256, ncol - 256 * q) / 16)
+        gc = 256 * q
+        mlo = 0 if gc < 3 else 1 + (gc - 3) // 6
+        r = next((i for i, v in enumerate(nx) if v >= mlo), R - 1)
+        kb0 = r // 16
+        back += 2.0 * (256 * math.ceil(n / 256)) * (32 * (nkb - kb0)) * width * 3
     return fwd, back
 
 
 # DRAM bytes per launch of the back-scatter kernel from an ncu capture of the benchmark
 # workload, valid while the kernel source is unchanged (sha256 prefix of recip_tc.cu)
-BS_TRAFFIC = {("random_32768", "mixed", "1eedb42d53f14ee9"): 4229376}
+BS_TRAFFIC = {("random_32768", "mixed", "1b3b71d0c6e5e9a1"): 4227328}
 
 
 def bs_traffic(workload, precision):
