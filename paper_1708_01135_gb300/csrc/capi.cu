@@ -220,6 +220,7 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     cell_grid(p.L, p.rc, n, p.nc, p.w);
     p.ncells = p.nc * p.nc * p.nc;
     p.cell_side = p.L / p.nc;
+    p.real_tile = real_tile_for(p.w, (double)n / p.ncells);
     Workspace &ws = p.ws;
     const int nb = binning_chunks(n);
     const int nrows = p.nc * p.nc;
@@ -313,7 +314,7 @@ size_t plan_footprint(const Plan &p, int64_t n)
     int nc = 1, w = 0;
     cell_grid(p.L, p.rc, n, nc, w);
     const size_t ncells = (size_t)nc * nc * nc;
-    const int64_t tiles = w == 0 ? (n + 31) / 32 : n / real_tile_size(p) + (int64_t)nc * nc + 1;
+    const int64_t tiles = w == 0 ? (n + 31) / 32 : n / real_tile_for(w, (double)n / ncells) + (int64_t)nc * nc + 1;
     size_t b = 0;
     b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * ncells;
     b += sizeof(int) * (2 * ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * ((size_t)nc * nc + 1);

@@ -85,6 +85,7 @@ struct Plan {
     int w = 0;           // stencil half-width in cells (0: all pairs, minimum image)
     int ncells = 1;
     double cell_side = 0;
+    int real_tile = 16;          // targets per real-space warp tile (16 or 32)
     // reciprocal rows
     int R = 0;
     int64_t nk = 0;
@@ -132,7 +133,8 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
 // a4: real-space pairs into ws.f_real / ws.e_tile (sorted order).
 cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st);
 int64_t real_tile_capacity(const Plan &p, int64_t n);
-int real_tile_size(const Plan &p);          // particles per real-space tile (cell mode: 8)
+int real_tile_size(const Plan &p);          // particles per real-space tile
+int real_tile_for(int w, double cell_occupancy);   // tile size for a grid (particles per cell)
 // a5-a8 on CUDA cores (FP64 or FP32): S(k), energy, back-scatter into ws.f_recip.
 cudaError_t launch_recip_simt(Plan &p, int64_t n, cudaStream_t st);
 size_t recip_simt_bytes(const Plan &p, int64_t n);

@@ -6,14 +6,15 @@
 //   E_real = 1/2 sum_i q_i phi_i            (r_ij = r_i - r_j, minimum image)
 //
 // GPU design (templated on FP64 and FP32 arithmetic):
-//   * One warp owns a tile of up to 8 consecutive sorted particles of one row of cells
-//     (fixed c_y, c_z).  Lane = (target i, partner group g): the 8 targets each have 4
-//     lanes that take every 4th partner; the 4 partial sums of a target are combined with
-//     shuffles at the end, so every target's force is written by one lane and no two threads
-//     ever write the same particle (the paper's rule that a loop writes only its own particle,
-//     Section 3.2.3, with no atomics).  Narrow tiles keep the candidate set close to the
-//     cutoff sphere and give 4 warps per 32 particles, enough to hide the latency of the
-//     pair arithmetic.
+//   * One warp owns a tile of up to 16 (or 32) consecutive sorted particles of one row of
+//     cells (fixed c_y, c_z).  With 16, lane = (target i, partner group g): every target has
+//     2 lanes that take every other partner, and the 2 partial sums of a target are combined
+//     with a shuffle at the end; with 32 (cells of 16 particles or more) every lane owns one
+//     target.  Either way every target's force is written by one lane and no two threads ever
+//     write the same particle (the paper's rule that a loop writes only its own particle,
+//     Section 3.2.3, with no atomics).  The tile size per plan follows the cell occupancy:
+//     narrow tiles keep the candidate set close to the cutoff sphere where cells are sparse,
+//     wide ones amortise the candidate traffic where they are dense.
 //   * The candidate partners j of a tile are the cells of the neighbour rows (c_y + dy,
 //     c_z + dz), |dy|, |dz| <= w, in the x range of the tile widened by the reach left for
 //     that row.  A run of cells along x is a contiguous range of the sorted array, so it is
@@ -33,9 +34,11 @@ namespace ew {
 namespace {
 
 constexpr int kWarps = 4;      // warps (tiles) per block
-constexpr int kCap = 64;       // particles per staging buffer (cell mode)
+constexpr int kCap = 128;      // particles per staging buffer (cell mode)
 constexpr int kCapAll = 256;   // particles per staging buffer (all-pairs mode)
-constexpr int kTile = 8;       // targets per warp tile (cell mode)
+// Targets per warp tile in cell mode: 16 (two partner lanes per target) for sparse cells,
+// 32 (one lane per target) where cells hold 16 particles or more; chosen per plan.
+constexpr int kTileSparse = 16, kTileDense = 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -229,7 +232,7 @@ struct ChunkIter {
     }
 };
 
-template <class T>
+template <class T, int kTile>
 __global__ void __launch_bounds__(kWarps * 32)
 k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restrict__ key_sorted,
              const int *__restrict__ cell_start, const int2 *__restrict__ tiles,
@@ -258,7 +261,8 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     const int row = td.x, first = td.y;
     const int row_end = cell_start[(row + 1) * nc];
     const int last = min(first + kTile, row_end) - 1;
-    const int ti = lane & (kTile - 1), g = lane >> 3;   // target slot, partner group
+    constexpr int kGroups = 32 / kTile;             // partner lanes per target
+    const int ti = lane % kTile, g = lane / kTile;   // target slot, partner group
     const int i = first + ti;
     const bool valid = i <= last;
     const T4 pi = pl[valid ? i : last];
@@ -311,7 +315,7 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
                 const int jb = (cb > cur.g0 ? cb : cur.g0) - cur.g0;
                 const int je = (ce < cend ? ce : cend) - cur.g0;
                 const T xi = pi.x - T(u - cxi) * side;
-                for (int j = jb + g; j < je; j += 4) pair<T, T4>(acc, sb[j], xi, yi, zi, rc2, beta, nb2, two_b_rpi);
+                for (int j = jb + g; j < je; j += kGroups) pair<T, T4>(acc, sb[j], xi, yi, zi, rc2, beta, nb2, two_b_rpi);
             }
             if (ce >= cend) break;
             cb = ce;
@@ -329,9 +333,9 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         warp_wait(&bar[b ^ 1], phase[b ^ 1]);
         return;
     }
-    // combine the 4 partner groups of every target (lanes ti, ti + 8, ti + 16, ti + 24)
+    // combine the kGroups partner groups of every target (lanes ti, ti + kTile, ...)
 #pragma unroll
-    for (int o = 8; o < 32; o <<= 1) {
+    for (int o = kTile; o < 32; o <<= 1) {
         acc.fx += __shfl_xor_sync(0xffffffffu, acc.fx, o);
         acc.fy += __shfl_xor_sync(0xffffffffu, acc.fy, o);
         acc.fz += __shfl_xor_sync(0xffffffffu, acc.fz, o);
@@ -444,11 +448,11 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         k_real_allpairs<T><<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(
             pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.e_tile, p.d_status);
     } else {
-        e = cudaFuncSetAttribute(k_real_cells<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        auto kern = p.real_tile == kTileDense ? k_real_cells<T, kTileDense> : k_real_cells<T, kTileSparse>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int64_t tiles = real_tile_capacity(p, n);
-        k_real_cells<T><<<(unsigned)((tiles + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
+        kern<<<(unsigned)((tiles + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
             pl, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc, p.nc, p.w,
             (T)p.cell_side, rc2, beta, tbr, ws.f_real, ws.e_tile, p.d_status);
     }
@@ -461,10 +465,16 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
 int64_t real_tile_capacity(const Plan &p, int64_t n)
 {
     if (p.w == 0) return (n + 31) / 32;
-    return n / kTile + (int64_t)p.nc * p.nc + 1;
+    return n / real_tile_size(p) + (int64_t)p.nc * p.nc + 1;
 }
 
-int real_tile_size(const Plan &p) { return p.w == 0 ? 32 : kTile; }
+int real_tile_size(const Plan &p) { return p.w == 0 ? 32 : (p.real_tile == kTileDense ? kTileDense : kTileSparse); }
+
+int real_tile_for(int w, double cell_occupancy)
+{
+    if (w == 0) return 32;
+    return cell_occupancy >= 16.0 ? kTileDense : kTileSparse;
+}
 
 cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st)
 {

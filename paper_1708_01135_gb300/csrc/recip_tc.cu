@@ -416,11 +416,15 @@ k_fwd_tc(int R, int NF, int nst_all, int64_t W, int maxp, int SA, int SX, int SP
             const int64_t seg_end = min(w_end, (int64_t)(v + 1) * nst_all);
             const int nchs = (int)((seg_end - w + KCH - 1) / KCH);
             const int piece = c - fwd_cta_of((int64_t)v * nst_all, W, G);
+            // warps whose 32 lanes (columns) are all past the pass's column count have
+            // nothing to add (their sums are never read); they still take part in the
+            // barrier handshake
+            const bool work = dq * 32 < vgs[v].z;
             for (int k = 0; k < nchs; ++k, ++gch) {
                 if (!waitw(accf, gch & 1, abort)) { ok = false; break; }
                 tc_after();
 #pragma unroll 1
-                for (int c0 = 0; c0 < 128; c0 += 32) {
+                for (int c0 = 0; work && c0 < 128; c0 += 32) {
                     const uint32_t src = tmem + lanes + (uint32_t)(dh * 128 + c0);
                     const uint32_t dst = src + 256;
                     uint32_t a0[16], a1[16], s0v[16], s1v[16];
