@@ -136,8 +136,22 @@ bool uses_tc(int precision)
     return precision == EWALD_MIXED || precision == EWALD_MIXED_BF16;
 }
 
+// Drop the captured evaluation graph: its kernels hold pointers to the workspaces and the
+// plan's parameters, so it goes whenever either changes.
+void graph_reset(Plan &p)
+{
+    if (p.gexec) {
+        if (p.graph_stream) cudaStreamSynchronize(p.graph_stream);
+        cudaGraphExecDestroy(p.gexec);
+        p.gexec = nullptr;
+    }
+    p.gkey = Plan::EvalKey();
+    p.last_key = Plan::EvalKey();
+}
+
 void free_workspace(Plan &p)
 {
+    graph_reset(p);
     Workspace &ws = p.ws;
     void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
                     ws.tiles, ws.tile_count, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
@@ -300,12 +314,65 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
 
 }  // namespace
 
+// One evaluation.  An evaluation with the same arguments (sizes and buffers) as the one
+// before it is captured once into a CUDA graph, on the plan's graph stream, and replayed from
+// then on: the ~20 launches of the pipeline (two streams) become one graph launch.  A first
+// call, a call with new buffers, a call while profiling, and a call on a stream that is
+// itself being captured run the pipeline directly.
 cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
                      double *energy_dev, int parts, cudaStream_t st, bool clear_status)
 {
     cudaError_t e = grow_workspace(p, n);
     if (e != cudaSuccess) return e;
-    return pipeline(p, n, pos, q, forces, energy_dev, parts, st, clear_status);
+    Plan::EvalKey key;
+    key.n = n; key.pos = pos; key.q = q; key.forces = forces; key.energy = energy_dev;
+    key.parts = parts; key.clear = clear_status;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return e;
+    const bool repeat = key == p.last_key;
+    p.last_key = key;
+    if (p.prof || !p.graph_stream || cap != cudaStreamCaptureStatusNone || !repeat)
+        return pipeline(p, n, pos, q, forces, energy_dev, parts, st, clear_status);
+    if ((e = cudaEventRecord(p.ev_gin, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(p.graph_stream, p.ev_gin, 0)) != cudaSuccess) return e;
+    if (!(p.gexec && key == p.gkey)) {
+        // capture the pipeline on the graph stream
+        (void)cudaGetLastError();
+        cudaGraph_t g = nullptr;
+        if ((e = cudaStreamBeginCapture(p.graph_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return e;
+        cudaError_t ep = pipeline(p, n, pos, q, forces, energy_dev, parts, p.graph_stream, clear_status);
+        cudaError_t ec = cudaStreamEndCapture(p.graph_stream, &g);
+        if (ep != cudaSuccess || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            (void)cudaGetLastError();
+            p.gkey = Plan::EvalKey();
+            return ep != cudaSuccess ? ep : (ec != cudaSuccess ? ec : cudaErrorUnknown);
+        }
+        const int launches = p.launches;
+        bool ok = false;
+        if (p.gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            ok = cudaGraphExecUpdate(p.gexec, g, &info) == cudaSuccess;
+            if (!ok) {
+                (void)cudaGetLastError();
+                cudaGraphExecDestroy(p.gexec);
+                p.gexec = nullptr;
+            }
+        }
+        if (!ok) e = cudaGraphInstantiate(&p.gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { p.gexec = nullptr; p.gkey = Plan::EvalKey(); return e; }
+        p.gkey = key;
+        p.g_launches = launches;
+    }
+    if ((e = cudaGraphLaunch(p.gexec, p.graph_stream)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(p.ev_gout, p.graph_stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, p.ev_gout, 0)) != cudaSuccess) return e;
+    p.launches = p.g_launches;
+    p.prof_valid = false;
+    p.last_stream = st;
+    return cudaSuccess;
 }
 
 size_t plan_footprint(const Plan &p, int64_t n)
@@ -470,6 +537,7 @@ int plan_reconfigure(ewald_plan *h, double L, double beta, double rc, int kmax, 
     cudaStreamSynchronize(p.side_stream);
     const bool same_shape = probe.ncells == p.ncells && probe.nc == p.nc && probe.R == p.R &&
                             probe.kmax == p.kmax && probe.precision == p.precision;
+    graph_reset(p);
     if (!same_shape) free_workspace(p);
     plan_setup_host(p, L, beta, rc, kmax, precision);
     return cuda_status(plan_upload(p));
@@ -493,8 +561,12 @@ static void destroy_plan(ewald_plan *h)
         pool_free(p.ws.h_f, p.side_stream);
         cudaStreamSynchronize(p.side_stream);
     }
+    graph_reset(p);
     if (p.h_status) cudaFreeHost(p.h_status);
     if (p.side_stream) cudaStreamDestroy(p.side_stream);
+    if (p.graph_stream) cudaStreamDestroy(p.graph_stream);
+    if (p.ev_gin) cudaEventDestroy(p.ev_gin);
+    if (p.ev_gout) cudaEventDestroy(p.ev_gout);
     if (p.ev_fork) cudaEventDestroy(p.ev_fork);
     if (p.ev_join) cudaEventDestroy(p.ev_join);
     for (cudaEvent_t ev : p.ev)
@@ -522,6 +594,9 @@ extern "C" int ewald_create(double L, double beta, double r_c, int k_max, int pr
     EW_C(cudaStreamCreateWithFlags(&p.side_stream, cudaStreamNonBlocking));
     EW_C(cudaEventCreateWithFlags(&p.ev_fork, cudaEventDisableTiming));
     EW_C(cudaEventCreateWithFlags(&p.ev_join, cudaEventDisableTiming));
+    EW_C(cudaStreamCreateWithFlags(&p.graph_stream, cudaStreamNonBlocking));
+    EW_C(cudaEventCreateWithFlags(&p.ev_gin, cudaEventDisableTiming));
+    EW_C(cudaEventCreateWithFlags(&p.ev_gout, cudaEventDisableTiming));
     EW_C(cudaHostAlloc((void **)&p.h_status, sizeof(int), cudaHostAllocDefault));
     EW_C(pool_alloc((void **)&p.energy_d, sizeof(double) * 4, p.side_stream));
     EW_C(pool_alloc((void **)&p.d_status, sizeof(int), p.side_stream));
@@ -560,9 +635,7 @@ extern "C" int ewald_compute_async(ewald_plan_t plan, int64_t n, const double *p
         p.last_stream = st;
         return cuda_status(cudaGetLastError());
     }
-    cudaError_t e = grow_workspace(p, n);
-    if (e != cudaSuccess) return cuda_status(e);
-    e = pipeline(p, n, pos, q, forces, energy_dev, parts, st);
+    cudaError_t e = evaluate(p, n, pos, q, forces, energy_dev, parts, st, true);
     return cuda_status(e);
 }
 
@@ -725,13 +798,12 @@ extern "C" int ewald_tune(int64_t n, double L, double tol, double *r_c, double *
     const double p = sqrt(-log(tol));
     double rc = *r_c;
     if (!(rc > 0)) {
-        // Cost per particle, calibrated on GB300 with the EWALD_MIXED path: the real-space
-        // kernel visits ~18.75 r_c^3 rho candidates per target at ~4.2 ps each; the two
-        // reciprocal products cost ~0.06 ps per (particle, grid cell) over a cylinder of
-        // ~pi k_max^3 cells, k_max = p^2 L / (pi r_c).  Pick the r_c <= L/2 that minimises
-        // the sum on a grid.
+        // Cost per particle, calibrated on GB300 with the EWALD_MIXED path (262,144- and
+        // 2,097,152-ion systems): real space ~2.5e-11 s per r_c^3 rho, the two reciprocal
+        // products ~1.13e-13 s per k_max^3, k_max = p^2 L / (pi r_c).  Pick the r_c <= L/2
+        // that minimises the sum on a grid.
         const double rho = n / (L * L * L);
-        const double c_pair = 4.2e-12 * 18.75, c_mode = 6.0e-14 * kPi;
+        const double c_pair = 2.5e-11, c_mode = 1.13e-13;
         double best = 1e300, best_rc = 0.5 * L;
         for (int t = 1; t <= 400; ++t) {
             double x = 0.5 * L * t / 400.0;

@@ -105,6 +105,25 @@ struct Plan {
     cudaStream_t last_stream = nullptr;
     cudaStream_t side_stream = nullptr;  // reciprocal branch
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // CUDA-graph replay of repeated evaluations (see evaluate): the graph runs on the plan's
+    // own stream, ordered after and before the caller's stream by two events
+    cudaStream_t graph_stream = nullptr;
+    cudaEvent_t ev_gin = nullptr, ev_gout = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    struct EvalKey {
+        int64_t n = -1;
+        const void *pos = nullptr, *q = nullptr;
+        void *forces = nullptr, *energy = nullptr;
+        int parts = 0;
+        bool clear = false;
+        bool operator==(const EvalKey &o) const
+        {
+            return n == o.n && pos == o.pos && q == o.q && forces == o.forces &&
+                   energy == o.energy && parts == o.parts && clear == o.clear;
+        }
+    };
+    EvalKey gkey, last_key;      // key of the captured graph; key of the previous evaluation
+    int g_launches = 0;
     Workspace ws;
     // tensor-core path state (allocated lazily)
     void *tc = nullptr;

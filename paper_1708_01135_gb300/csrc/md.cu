@@ -65,9 +65,9 @@ __global__ void k_md_kick_ke(int64_t n, double *__restrict__ vel, const double *
 }
 
 // One block: E_kin = sum of the block partials (each thread a contiguous slice, then a
-// fixed tree); rec[4] = E_kin, rec[5] = rec[3] + E_kin.  rec[0..3] were written by the
-// evaluation of this step.
-__global__ void k_md_record(int nb, const double *__restrict__ ke_part, double *__restrict__ rec)
+// fixed tree); rec = (the four energies of this step's evaluation, E_kin, E_pot + E_kin).
+__global__ void k_md_record(int nb, const double *__restrict__ ke_part,
+                            const double *__restrict__ epot, double *__restrict__ rec)
 {
     __shared__ double red[kThreads];
     const int t = threadIdx.x;
@@ -82,8 +82,9 @@ __global__ void k_md_record(int nb, const double *__restrict__ ke_part, double *
         __syncthreads();
     }
     if (t == 0) {
+        for (int i = 0; i < 4; ++i) rec[i] = epot[i];
         rec[EWALD_MD_KIN] = red[0];
-        rec[EWALD_MD_TOTAL] = rec[EWALD_MD_POT] + red[0];
+        rec[EWALD_MD_TOTAL] = epot[EWALD_MD_POT] + red[0];
     }
 }
 
@@ -113,30 +114,33 @@ extern "C" int ewald_md(ewald_plan_t plan, int64_t n, double *pos, double *vel, 
         return cudaGetLastError() == cudaSuccess ? EWALD_OK : EWALD_E_CUDA;
     }
     const int nb = (int)((n + kThreads - 1) / kThreads);
-    double *scratch = nullptr;       // [nb] kinetic-energy partials + one record if no log
-    if ((e = ew::pool_alloc((void **)&scratch, sizeof(double) * (nb + EWALD_MD_RECORD), st)) != cudaSuccess)
+    // scratch: [nb] kinetic-energy partials, the energies of the current evaluation (a fixed
+    // buffer, so that repeated evaluations replay one captured graph), one record if no log
+    double *scratch = nullptr;
+    if ((e = ew::pool_alloc((void **)&scratch, sizeof(double) * (nb + 4 + EWALD_MD_RECORD), st)) != cudaSuccess)
         return EWALD_E_NOMEM;
-    double *ke_part = scratch;
+    double *ke_part = scratch, *epot = scratch + nb;
     auto record = [&](int s) {
-        return energy_log ? energy_log + (int64_t)s * EWALD_MD_RECORD : scratch + nb;
+        return energy_log ? energy_log + (int64_t)s * EWALD_MD_RECORD : scratch + nb + 4;
     };
     const unsigned gb3 = (unsigned)((3 * n + kThreads - 1) / kThreads);
     const double hdt = 0.5 * dt;
     int status = EWALD_OK;
-    // initial forces and energies
-    e = ew::evaluate(p, n, pos, q, forces, record(0), EWALD_PART_ALL, st, true);
+    // initial forces and energies; the device status collects every evaluation of the run
+    e = cudaMemsetAsync(p.d_status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = ew::evaluate(p, n, pos, q, forces, epot, EWALD_PART_ALL, st, false);
     if (e == cudaSuccess) {
         k_md_kick_ke<<<nb, kThreads, 0, st>>>(n, vel, forces, mass, 0.0, ke_part);
-        k_md_record<<<1, kThreads, 0, st>>>(nb, ke_part, record(0));
+        k_md_record<<<1, kThreads, 0, st>>>(nb, ke_part, epot, record(0));
         e = cudaGetLastError();
     }
     for (int s = 1; s <= steps && e == cudaSuccess; ++s) {
         k_md_kick_drift<<<gb3, kThreads, 0, st>>>(3 * n, pos, vel, forces, mass, hdt, dt);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
-        e = ew::evaluate(p, n, pos, q, forces, record(s), EWALD_PART_ALL, st, false);
+        e = ew::evaluate(p, n, pos, q, forces, epot, EWALD_PART_ALL, st, false);
         if (e != cudaSuccess) break;
         k_md_kick_ke<<<nb, kThreads, 0, st>>>(n, vel, forces, mass, hdt, ke_part);
-        k_md_record<<<1, kThreads, 0, st>>>(nb, ke_part, record(s));
+        k_md_record<<<1, kThreads, 0, st>>>(nb, ke_part, epot, record(s));
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) status = (e == cudaErrorMemoryAllocation) ? EWALD_E_NOMEM : EWALD_E_CUDA;

@@ -33,8 +33,8 @@ from paper_1708_01135_gb300 import workloads as W  # noqa: E402
 
 # (workload, r_c, beta, k_max, full reciprocal energy?)
 CASES = [
-    ("rocksalt_262144", 6.16, 0.6033964592288699, 46, True),
-    ("random_2097152", 8.64, 0.4301993274131757, 66, False),
+    ("rocksalt_262144", 6.8, 0.5466062042426233, 42, True),
+    ("random_2097152", 9.6, 0.3871793946718582, 59, False),
 ]
 
 
