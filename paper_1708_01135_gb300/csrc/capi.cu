@@ -30,21 +30,22 @@ namespace ew {
 namespace {
 
 // Sum of x[0..m) by one thread block of 256 threads in a fixed order: thread t sums the
-// contiguous slice t of the array (8 independent partial sums, combined in order), then a
-// fixed tree over the threads.  Every thread returns the total.
+// elements t, t + 256, t + 512, ... (coalesced loads) into 4 partial sums by position modulo
+// 4, combines them in order, then a fixed tree over the threads.  Every thread returns the
+// total.
 __device__ double block_sum_fixed(const double *__restrict__ x, int m, double *red)
 {
     const int t = threadIdx.x;
-    const int per = (m + 255) / 256;
-    const int b = t * per, e = min(m, b + per);
-    double p[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int i = b;
-    for (; i + 8 <= e; i += 8) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) p[u] += x[i + u];
+    double p[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = t;
+    for (; i + 3 * 256 < m; i += 4 * 256) {
+        p[0] += x[i];
+        p[1] += x[i + 256];
+        p[2] += x[i + 512];
+        p[3] += x[i + 768];
     }
-    for (int u = 0; i < e; ++i, ++u) p[u] += x[i];
-    double s = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    for (int u = 0; i < m; i += 256, ++u) p[u] += x[i];
+    double s = (p[0] + p[1]) + (p[2] + p[3]);
     red[t] = s;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
@@ -69,8 +70,7 @@ __global__ void k_energy(int ntile, const double *__restrict__ e_tile, int nq,
     // charge sums: qpart is [nq][3]
     const int t = threadIdx.x;
     double qs = 0.0, qa = 0.0, q2 = 0.0;
-    const int per = (nq + 255) / 256;
-    for (int i = t * per; i < min(nq, (t + 1) * per); ++i) {
+    for (int i = t; i < nq; i += 256) {
         qs += qpart[3 * i]; qa += qpart[3 * i + 1]; q2 += qpart[3 * i + 2];
     }
     qv[0][t] = qs; qv[1][t] = qa; qv[2][t] = q2;
@@ -168,9 +168,9 @@ void free_workspace(Plan &p)
 
 int binning_chunks(int64_t n)
 {
-    // chunks of at least 1024 particles and at most 16384 (the scatter keeps a chunk's keys
-    // in shared memory)
-    int64_t nb = (n + 1023) / 1024;
+    // chunks of at least 256 particles and at most 16384 (the scatter keeps a chunk's keys
+    // in shared memory), at most 128 of them
+    int64_t nb = (n + 255) / 256;
     if (nb > 128) nb = 128;
     if ((n + nb - 1) / nb > 16384) nb = (n + 16383) / 16384;
     return nb < 1 ? 1 : (int)nb;

@@ -643,6 +643,7 @@ k_sreduce_tc(int nst_all, int64_t W, int G, int maxp, const int2 *__restrict__ g
                                 fwd_cta_of((int64_t)v * nst_all, W, G) + 1;
                 const float *o = dpart + ((int64_t)v * maxp * 128 + col % 128) * 256;
                 double a = 0.0, b = 0.0;
+#pragma unroll 4
                 for (int pc = 0; pc < npc; ++pc, o += (int64_t)128 * 256) {
                     a += (double)o[n];
                     b += (double)o[128 + n];
