@@ -185,6 +185,7 @@ struct ChunkIter {
     int g, gend, run_u0, rowbase;
     bool in_run;
     bool started;
+    int part, split, rowctr;   // this warp takes the kept rows with index % split == part
     float side, rc2;     // geometry for culling (float is enough for the reach test)
 
     __device__ bool next_row()
@@ -196,6 +197,7 @@ struct ChunkIter {
             float my = ay > 0 ? (ay - 1) * side : 0.f, mz = az > 0 ? (az - 1) * side : 0.f;
             float rest = rc2 - my * my - mz * mz;
             if (rest <= 0.f) continue;
+            if ((rowctr++ % split) != part) continue;
             int r = (int)ceilf(sqrtf(rest) / side - 1e-6f);
             wx = r < w ? r : w;
             if (wx < 0) wx = 0;
@@ -237,12 +239,13 @@ __global__ void __launch_bounds__(kWarps * 32)
 k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restrict__ key_sorted,
              const int *__restrict__ cell_start, const int2 *__restrict__ tiles,
              const int *__restrict__ tile_total, int nc, int w, T side, T rc2, T beta,
-             T two_b_rpi, double *__restrict__ f_out, double *__restrict__ e_tile,
+             T two_b_rpi, int split, double *__restrict__ f_out, double *__restrict__ e_tile,
              int *__restrict__ status)
 {
     using T4 = typename Vec4<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kWarps][2];
+    __shared__ PairAcc<T> xacc[kWarps][32];     // partial sums handed between split warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T4 *buf[2];
     buf[0] = reinterpret_cast<T4 *>(smem_raw) + (size_t)warp * 2 * kCap;
@@ -254,13 +257,17 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         fence_mbar_init();
     }
     __syncwarp();
-    const int tile = blockIdx.x * kWarps + warp;
-    if (tile >= *tile_total) return;
+    // with split = 2 the two warps 2t and 2t + 1 of a block share a tile, each taking every
+    // other stencil row; their sums are added (in that order) at the end
+    const int part = warp % split;
+    const int tile = (blockIdx.x * kWarps + warp) / split;
+    const bool active = tile < *tile_total;
+    if (split == 1 && !active) return;
 
-    const int2 td = tiles[tile];
+    const int2 td = active ? tiles[tile] : make_int2(0, 0);
     const int row = td.x, first = td.y;
-    const int row_end = cell_start[(row + 1) * nc];
-    const int last = min(first + kTile, row_end) - 1;
+    const int row_end = active ? cell_start[(row + 1) * nc] : 1;
+    const int last = active ? min(first + kTile, row_end) - 1 : 0;
     constexpr int kGroups = 32 / kTile;             // partner lanes per target
     const int ti = lane % kTile, g = lane / kTile;   // target slot, partner group
     const int i = first + ti;
@@ -274,6 +281,7 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     it.xb = key_sorted[last] % nc;
     it.row_cy = row % nc; it.row_cz = row / nc;
     it.in_run = false; it.started = false;
+    it.part = part; it.split = split; it.rowctr = 0;
     it.side = (float)side; it.rc2 = (float)rc2;
     it.u = 0; it.uend = -1;
 
@@ -281,7 +289,7 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     const T nb2 = -beta * beta;
     uint32_t phase[2] = {0u, 0u};
     Chunk cur, nxt;
-    bool have_cur = it.next(cell_start, cur);
+    bool have_cur = active && it.next(cell_start, cur);
     bool ok = true;
     if (have_cur && lane == 0) {
         mbar_expect_tx(&bar[0], cur.cnt * (uint32_t)sizeof(T4));
@@ -331,7 +339,7 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         if (lane == 0) atomicOr(status, kStTimeout);
         // let a copy still in flight land before the warp leaves (bounded)
         warp_wait(&bar[b ^ 1], phase[b ^ 1]);
-        return;
+        if (split == 1) return;
     }
     // combine the kGroups partner groups of every target (lanes ti, ti + kTile, ...)
 #pragma unroll
@@ -340,6 +348,14 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         acc.fy += __shfl_xor_sync(0xffffffffu, acc.fy, o);
         acc.fz += __shfl_xor_sync(0xffffffffu, acc.fz, o);
         acc.phi += __shfl_xor_sync(0xffffffffu, acc.phi, o);
+    }
+    if (split == 2) {
+        // every warp of the block reaches this barrier (none has returned with split = 2)
+        if (part == 1) xacc[warp][lane] = acc;
+        __syncthreads();
+        if (part == 1 || !active) return;
+        const PairAcc<T> o = xacc[warp + 1][lane];
+        acc.fx += o.fx; acc.fy += o.fy; acc.fz += o.fz; acc.phi += o.phi;
     }
     const double qi = (double)pi.w;
     if (valid && g == 0) {
@@ -452,9 +468,11 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int64_t tiles = real_tile_capacity(p, n);
-        kern<<<(unsigned)((tiles + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
+        // two warps per tile when one warp per tile would leave the SMs short of warps
+        const int split = tiles < 16 * (int64_t)p.num_sms ? 2 : 1;
+        kern<<<(unsigned)((tiles * split + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
             pl, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc, p.nc, p.w,
-            (T)p.cell_side, rc2, beta, tbr, ws.f_real, ws.e_tile, p.d_status);
+            (T)p.cell_side, rc2, beta, tbr, split, ws.f_real, ws.e_tile, p.d_status);
     }
     p.launches += 1;
     return cudaGetLastError();
