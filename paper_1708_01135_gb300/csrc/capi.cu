@@ -2,6 +2,9 @@
 //
 // One evaluation (ewald_compute_async) on the caller's stream:
 //   a1-a3  binning: wrap, cell keys, stable counting sort, offsets, packing   (cells.cu)
+//   a5     the column operand of the forward product (tensor path), still on the caller's
+//          stream, so that the forward product and the real-space kernel become ready
+//          together and the forward's one-CTA-per-SM grid is placed first
 //   fork:  the reciprocal branch runs on the plan's side stream
 //   a4     real-space pairs                                                    (realspace.cu)
 //   a5-a8  phases, S(k), energy and coefficients, back-scatter    (recip_simt.cu / recip_tc.cu)
@@ -285,6 +288,8 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     if ((e = cudaMemsetAsync(ws.e_tile, 0, sizeof(double) * tiles, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.e_recip_part, 0, sizeof(double) * p.e_recip_count, st)) != cudaSuccess) return e;
     const bool do_recip = parts & EWALD_PART_RECIP;
+    if (do_recip && uses_tc(p.precision) && (e = launch_recip_tc_operands(p, n, st)) != cudaSuccess)
+        return e;
     if (do_recip) {
         if ((e = cudaEventRecord(p.ev_fork, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(p.side_stream, p.ev_fork, 0)) != cudaSuccess) return e;

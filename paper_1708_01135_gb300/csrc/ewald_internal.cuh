@@ -161,6 +161,9 @@ cudaError_t alloc_recip_simt(Plan &p, int64_t n);
 void free_recip_simt(Plan &p);
 // a5-a8 on the tcgen05 tensor cores (split FP16/BF16 operands).
 cudaError_t launch_recip_tc(Plan &p, int64_t n, cudaStream_t st);
+// a5 column operand of the forward product; launched before the fork, so that the forward
+// product is ready to start together with the real-space kernel and takes its SMs first
+cudaError_t launch_recip_tc_operands(Plan &p, int64_t n, cudaStream_t st);
 cudaError_t alloc_recip_tc(Plan &p, int64_t n);
 size_t recip_tc_bytes(const Plan &p, int64_t n);
 int recip_tc_energy_parts(const Plan &p);   // entries of the partial reciprocal energies

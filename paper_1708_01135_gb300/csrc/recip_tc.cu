@@ -1097,7 +1097,6 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
     cudaError_t e;
     prof_mark(p, kEvRecipStart, st);
     const int nst_all = (int)((n + kFK - 1) / kFK);
-    k_xgen<BF><<<nst_all, 256, 0, st>>>((int)n, p.kmax, s.nf, ws.pu, s.yz, s.bblob);
     e = launch_fwd<BF>(p, nst_all, s, st);
     if (e != cudaSuccess) return e;
     prof_mark(p, kEvFwdEnd, st);
@@ -1122,7 +1121,7 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
     k_bs_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s.npass, s.bpart, ws.pg, s.gscale,
                                                             p.L, ws.f_recip);
     prof_mark(p, kEvBackEnd, st);
-    p.launches += 6;
+    p.launches += 5;
     return cudaGetLastError();
 }
 
@@ -1178,6 +1177,19 @@ void free_recip_tc(Plan &p)
     pool_free(s->gscale, st); pool_free(s->blob, st); pool_free(s->bpart, st);
     delete s;
     p.tc = nullptr;
+}
+
+cudaError_t launch_recip_tc_operands(Plan &p, int64_t n, cudaStream_t st)
+{
+    if (!p.tc) return cudaErrorInvalidValue;
+    TcState &s = *static_cast<TcState *>(p.tc);
+    const int nst_all = (int)((n + kFK - 1) / kFK);
+    if (p.precision == EWALD_MIXED_BF16)
+        k_xgen<true><<<nst_all, 256, 0, st>>>((int)n, p.kmax, s.nf, p.ws.pu, s.yz, s.bblob);
+    else
+        k_xgen<false><<<nst_all, 256, 0, st>>>((int)n, p.kmax, s.nf, p.ws.pu, s.yz, s.bblob);
+    p.launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_recip_tc(Plan &p, int64_t n, cudaStream_t st)
