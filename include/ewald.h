@@ -137,6 +137,20 @@ int ewald_compute(ewald_plan_t plan, int64_t n, const double *pos, const double 
 int ewald_compute_async(ewald_plan_t plan, int64_t n, const double *pos, const double *q,
                         double *forces, double *energy_dev, int parts, void *stream);
 
+/*
+ * ewald_compute_phi_async - as ewald_compute_async, and also the electrostatic potential at
+ * every particle (the per-particle u of Algorithm 2 for the reciprocal part, phi of Eq. 4 for
+ * the real-space part):
+ *   phi_dev  dev float64 [n], caller order: phi_i = phi_i^real + phi_i^recip - 2 beta q_i /
+ *            sqrt(pi) over the selected parts, the potential at r_i of all other charges and of
+ *            all periodic images, so that the total energy is 1/2 sum_i q_i phi_i (the last
+ *            term is each particle's share of the self energy).
+ * Errors as ewald_compute_async; phi_dev may not be NULL when n > 0.
+ */
+int ewald_compute_phi_async(ewald_plan_t plan, int64_t n, const double *pos, const double *q,
+                            double *forces, double *phi_dev, double *energy_dev, int parts,
+                            void *stream);
+
 /* ewald_status_sync - synchronise the plan's last stream and return (and clear) the
  * device-side status of the last evaluation: EWALD_OK, EWALD_E_NONNEUTRAL,
  * EWALD_E_NONFINITE, EWALD_E_TIMEOUT or EWALD_E_CUDA. */

@@ -98,8 +98,14 @@ __global__ void k_energy(int ntile, const double *__restrict__ e_tile, int nq,
 }
 
 // a9: F[perm[s]] = F_real[s] + F_recip[s] (selected parts), caller order.
+// With phi_out: phi[perm[s]] = phi_real[s] + phi_recip[s] - 2 beta / sqrt(pi) q_s (selected
+// parts), the potential at every particle from all the others and their images, so that
+// E = 1/2 sum_i q_i phi_i (the self term -beta/sqrt(pi) sum q^2 is the last addend's share).
 __global__ void k_unsort(int64_t n, const int *__restrict__ perm, const double *__restrict__ fr,
-                         const double *__restrict__ fk, int parts, double *__restrict__ out)
+                         const double *__restrict__ fk, int parts, double *__restrict__ out,
+                         const double *__restrict__ pr, const double *__restrict__ pk,
+                         const double4_32a *__restrict__ pg, double beta,
+                         double *__restrict__ phi_out)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -111,6 +117,13 @@ __global__ void k_unsort(int64_t n, const int *__restrict__ perm, const double *
         if (ur) v += fr[3 * s + a];
         if (uk) v += fk[3 * s + a];
         out[3 * i + a] = v;
+    }
+    if (phi_out) {
+        double v = 0.0;
+        if (ur) v += pr[s];
+        if (uk) v += pk[s];
+        if (parts & EWALD_PART_SELF) v += -2.0 * beta / sqrt(kPi) * pg[s].w;
+        phi_out[i] = v;
     }
 }
 
@@ -158,7 +171,7 @@ void free_workspace(Plan &p)
     Workspace &ws = p.ws;
     void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
                     ws.tiles, ws.tile_count, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
-                    ws.f_real, ws.f_recip, ws.e_tile, ws.qpart};
+                    ws.f_real, ws.f_recip, ws.e_tile, ws.qpart, ws.phi_real, ws.phi_recip};
     for (void *q : ptrs) pool_free(q, p.side_stream);
     free_recip_simt(p);
     if (uses_tc(p.precision)) free_recip_tc(p);
@@ -258,6 +271,8 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     else EW_TRY(dmalloc(p, &ws.pl32, sizeof(float4) * n));
     EW_TRY(dmalloc(p, &ws.pu, sizeof(uint4) * n));
     EW_TRY(dmalloc(p, &ws.f_real, sizeof(double) * 3 * n));
+    EW_TRY(dmalloc(p, &ws.phi_real, sizeof(double) * n));
+    EW_TRY(dmalloc(p, &ws.phi_recip, sizeof(double) * n));
     EW_TRY(dmalloc(p, &ws.f_recip, sizeof(double) * 3 * n));
     EW_TRY(dmalloc(p, &ws.e_tile, sizeof(double) * tiles));
     EW_TRY(dmalloc(p, &ws.qpart, sizeof(double) * 3 * qblocks));
@@ -271,7 +286,8 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
 }
 
 cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
-                     double *energy_dev, int parts, cudaStream_t st, bool clear_status = true)
+                     double *energy_dev, int parts, cudaStream_t st, bool clear_status = true,
+                     double *phi = nullptr)
 {
     cudaError_t e;
     Workspace &ws = p.ws;
@@ -309,7 +325,8 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
                                 p.e_recip_count, p.e_recip_part, p.beta, parts, energy_dev,
                                 p.d_status);
     k_unsort<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ws.perm, ws.f_real, ws.f_recip,
-                                                          parts, forces);
+                                                          parts, forces, ws.phi_real,
+                                                          ws.phi_recip, ws.pg, p.beta, phi);
     p.launches += 2;
     prof_mark(p, kEvFinal, st);
     p.prof_valid = p.prof && do_recip;
@@ -325,19 +342,20 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
 // call, a call with new buffers, a call while profiling, and a call on a stream that is
 // itself being captured run the pipeline directly.
 cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
-                     double *energy_dev, int parts, cudaStream_t st, bool clear_status)
+                     double *energy_dev, int parts, cudaStream_t st, bool clear_status,
+                     double *phi)
 {
     cudaError_t e = grow_workspace(p, n);
     if (e != cudaSuccess) return e;
     Plan::EvalKey key;
     key.n = n; key.pos = pos; key.q = q; key.forces = forces; key.energy = energy_dev;
-    key.parts = parts; key.clear = clear_status;
+    key.parts = parts; key.clear = clear_status; key.phi = phi;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return e;
     const bool repeat = key == p.last_key;
     p.last_key = key;
     if (p.prof || !p.graph_stream || cap != cudaStreamCaptureStatusNone || !repeat)
-        return pipeline(p, n, pos, q, forces, energy_dev, parts, st, clear_status);
+        return pipeline(p, n, pos, q, forces, energy_dev, parts, st, clear_status, phi);
     if ((e = cudaEventRecord(p.ev_gin, st)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(p.graph_stream, p.ev_gin, 0)) != cudaSuccess) return e;
     if (!(p.gexec && key == p.gkey)) {
@@ -346,7 +364,8 @@ cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, dou
         cudaGraph_t g = nullptr;
         if ((e = cudaStreamBeginCapture(p.graph_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return e;
-        cudaError_t ep = pipeline(p, n, pos, q, forces, energy_dev, parts, p.graph_stream, clear_status);
+        cudaError_t ep = pipeline(p, n, pos, q, forces, energy_dev, parts, p.graph_stream,
+                                  clear_status, phi);
         cudaError_t ec = cudaStreamEndCapture(p.graph_stream, &g);
         if (ep != cudaSuccess || ec != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
@@ -642,6 +661,23 @@ extern "C" int ewald_compute_async(ewald_plan_t plan, int64_t n, const double *p
     }
     cudaError_t e = evaluate(p, n, pos, q, forces, energy_dev, parts, st, true);
     return cuda_status(e);
+}
+
+extern "C" int ewald_compute_phi_async(ewald_plan_t plan, int64_t n, const double *pos,
+                                       const double *q, double *forces, double *phi_dev,
+                                       double *energy_dev, int parts, void *stream)
+{
+    int s = validate_call(plan, n, pos, q, forces);
+    if (s != EWALD_OK) return s;
+    if (!energy_dev || (parts & ~EWALD_PART_ALL) || (n > 0 && !phi_dev)) return EWALD_E_INVAL;
+    Plan &p = plan->p;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        k_zero_energy<<<1, 32, 0, st>>>(energy_dev);
+        p.last_stream = st;
+        return cuda_status(cudaGetLastError());
+    }
+    return cuda_status(evaluate(p, n, pos, q, forces, energy_dev, parts, st, true, phi_dev));
 }
 
 extern "C" int ewald_status_sync(ewald_plan_t plan)

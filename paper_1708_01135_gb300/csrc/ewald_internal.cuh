@@ -59,6 +59,8 @@ struct Workspace {
     uint4 *pu = nullptr;         // 32-bit fixed-point fractions x/L, y/L, z/L + q (float bits)
     // outputs (sorted)
     double *f_real = nullptr;    // [n][3]
+    double *phi_real = nullptr;  // [n] real-space potential of every sorted particle
+    double *phi_recip = nullptr; // [n] reciprocal-space potential of every sorted particle
     double *f_recip = nullptr;   // [n][3]
     double *e_tile = nullptr;    // [max tiles] per-tile q_i phi_i sums
     double *qpart = nullptr;     // [qblocks][3]: sum q, sum |q|, sum q^2 partials
@@ -113,13 +115,13 @@ struct Plan {
     struct EvalKey {
         int64_t n = -1;
         const void *pos = nullptr, *q = nullptr;
-        void *forces = nullptr, *energy = nullptr;
+        void *forces = nullptr, *energy = nullptr, *phi = nullptr;
         int parts = 0;
         bool clear = false;
         bool operator==(const EvalKey &o) const
         {
             return n == o.n && pos == o.pos && q == o.q && forces == o.forces &&
-                   energy == o.energy && parts == o.parts && clear == o.clear;
+                   energy == o.energy && phi == o.phi && parts == o.parts && clear == o.clear;
         }
     };
     EvalKey gkey, last_key;      // key of the captured graph; key of the previous evaluation
@@ -172,7 +174,8 @@ void free_recip_tc(Plan &p);
 // clear_status false the plan's device status keeps the bits of earlier evaluations, so that
 // a sequence of evaluations reports every failure at the next ewald_status_sync.
 cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
-                     double *energy_dev, int parts, cudaStream_t st, bool clear_status);
+                     double *energy_dev, int parts, cudaStream_t st, bool clear_status,
+                     double *phi = nullptr);
 
 // Library memory pool (stream-ordered, retains freed memory for reuse).
 cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st);

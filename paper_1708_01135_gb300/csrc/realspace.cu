@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restrict__ key_sorted,
              const int *__restrict__ cell_start, const int2 *__restrict__ tiles,
              const int *__restrict__ tile_total, int nc, int w, T side, T rc2, T beta,
-             T two_b_rpi, int split, double *__restrict__ f_out, double *__restrict__ e_tile,
-             int *__restrict__ status)
+             T two_b_rpi, int split, double *__restrict__ f_out, double *__restrict__ phi_out,
+             double *__restrict__ e_tile, int *__restrict__ status)
 {
     using T4 = typename Vec4<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -362,6 +362,7 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         f_out[3 * (int64_t)i + 0] = qi * (double)acc.fx;
         f_out[3 * (int64_t)i + 1] = qi * (double)acc.fy;
         f_out[3 * (int64_t)i + 2] = qi * (double)acc.fz;
+        phi_out[i] = (double)acc.phi;
     }
     double e = (valid && g == 0) ? qi * (double)acc.phi : 0.0;
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
@@ -373,8 +374,8 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
 template <class T>
 __global__ void __launch_bounds__(kWarps * 32)
 k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2, T beta,
-                T two_b_rpi, double *__restrict__ f_out, double *__restrict__ e_tile,
-                int *__restrict__ status)
+                T two_b_rpi, double *__restrict__ f_out, double *__restrict__ phi_out,
+                double *__restrict__ e_tile, int *__restrict__ status)
 {
     using T4 = typename Vec4<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -442,6 +443,7 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
         f_out[3 * (int64_t)i + 0] = qi * (double)acc.fx;
         f_out[3 * (int64_t)i + 1] = qi * (double)acc.fy;
         f_out[3 * (int64_t)i + 2] = qi * (double)acc.fz;
+        phi_out[i] = (double)acc.phi;
     }
     double e = valid ? qi * (double)acc.phi : 0.0;
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
@@ -462,7 +464,7 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         if (e != cudaSuccess) return e;
         int tiles = (int)((n + 31) / 32);
         k_real_allpairs<T><<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(
-            pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.e_tile, p.d_status);
+            pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, p.d_status);
     } else {
         auto kern = p.real_tile == kTileDense ? k_real_cells<T, kTileDense> : k_real_cells<T, kTileSparse>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -472,7 +474,7 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         const int split = tiles < 16 * (int64_t)p.num_sms ? 2 : 1;
         kern<<<(unsigned)((tiles * split + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
             pl, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc, p.nc, p.w,
-            (T)p.cell_side, rc2, beta, tbr, split, ws.f_real, ws.e_tile, p.d_status);
+            (T)p.cell_side, rc2, beta, tbr, split, ws.f_real, ws.phi_real, ws.e_tile, p.d_status);
     }
     p.launches += 1;
     return cudaGetLastError();

@@ -319,7 +319,8 @@ k_bscat(int64_t n, int64_t cap, int R, int kmax, int ncol, int npass,
 
 // Sum the passes (fixed order) into the sorted reciprocal forces.
 __global__ void k_bscat_sum(int64_t n, int npass, const double *__restrict__ part,
-                            const double4_32a *__restrict__ pg, double L, double *__restrict__ f)
+                            const double4_32a *__restrict__ pg, double L, double *__restrict__ f,
+                            double *__restrict__ phi)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -329,6 +330,10 @@ __global__ void k_bscat_sum(int64_t n, int npass, const double *__restrict__ par
         for (int ps = 0; ps < npass; ++ps) v += part[(((int64_t)blk * npass + ps) * n + s) * 2];
         f[3 * s + blk] = qf * v;
     }
+    // the potential is carried by the x block (phi = Re U[0] + sum_m (...))
+    double v = 0.0;
+    for (int ps = 0; ps < npass; ++ps) v += part[((int64_t)ps * n + s) * 2 + 1];
+    phi[s] = v;
 }
 
 int bscat_passes(int kmax) { return (2 * kmax + 1 + kBC - 1) / kBC; }
@@ -369,7 +374,7 @@ cudaError_t launch_t(Plan &p, int64_t n, cudaStream_t st)
     k_bscat<T><<<gb, 256, 0, st>>>(n, cap, p.R, p.kmax, ncol, npass, p.rows_d, X, Y, Z,
                                    (const T *)ws.gmat, part);
     k_bscat_sum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, npass, part, ws.pg, p.L,
-                                                             ws.f_recip);
+                                                             ws.f_recip, ws.phi_recip);
     prof_mark(p, kEvBackEnd, st);
     p.launches += 5;
     return cudaGetLastError();

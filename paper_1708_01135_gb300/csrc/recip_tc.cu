@@ -963,22 +963,24 @@ k_bs_tc(int n, int R, int kmax, int ncol, int NPS, int nkb, int4 kb0s, const uin
     if (warp == 0) tm_dealloc(tmem, 512);
 }
 
-// Sum the passes (fixed order) into the sorted reciprocal forces.
+// Sum the passes (fixed order) into the sorted reciprocal forces and potentials.
 __global__ void k_bs_reduce(int64_t n, int npass, const float *__restrict__ bpart,
                             const double4_32a *__restrict__ pg, const float *__restrict__ gscale,
-                            double L, double *__restrict__ f)
+                            double L, double *__restrict__ f, double *__restrict__ phi)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const double qf = pg[s].w * (2.0 * kPi / L) * (double)gscale[0];
-    double a[3] = {0.0, 0.0, 0.0};
+    const double sc = (double)gscale[0];
+    const double qf = pg[s].w * (2.0 * kPi / L) * sc;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
     for (int ps = 0; ps < npass; ++ps) {
         const float4 v = reinterpret_cast<const float4 *>(bpart)[(int64_t)ps * n + s];
-        a[0] += v.x; a[1] += v.y; a[2] += v.z;
+        a[0] += v.x; a[1] += v.y; a[2] += v.z; a[3] += v.w;
     }
     f[3 * s + 0] = qf * a[0];
     f[3 * s + 1] = qf * a[1];
     f[3 * s + 2] = qf * a[2];
+    phi[s] = sc * a[3];
 }
 
 // ---- plan-side state ----------------------------------------------------------------------
@@ -1119,7 +1121,7 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
         (int)n, p.R, p.kmax, s.ncol, s.np, s.nkb, make_int4(s.kb0[0], s.kb0[1], s.kb0[2], s.kb0[3]),
         ws.pu, s.blob, s.bpart, p.d_status);
     k_bs_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s.npass, s.bpart, ws.pg, s.gscale,
-                                                            p.L, ws.f_recip);
+                                                            p.L, ws.f_recip, ws.phi_recip);
     prof_mark(p, kEvBackEnd, st);
     p.launches += 5;
     return cudaGetLastError();

@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
                 "ewald_destroy": (None, [_p]),
                 "ewald_compute": (_i, [_p, _i64, _p, _p, _p, _p, _p]),
                 "ewald_compute_async": (_i, [_p, _i64, _p, _p, _p, _p, _i, _p]),
+                "ewald_compute_phi_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
                 "ewald_status_sync": (_i, [_p]),
                 "ewald_compute_host": (_i, [_p, _i64, _p, _p, _p, _p, _p]),
                 "ewald_plan_info": (_i, [_p, _p]),
@@ -206,6 +207,15 @@ class Ewald:
                               float(dt), int(steps), _dev_f64(forces, (n, 3), "forces"),
                               None if log is None else _dev_f64(log, (int(steps) + 1, MD_RECORD), "log"),
                               _stream_handle(stream)), "ewald_md")
+
+    def compute_phi_async(self, pos, q, forces, phi, energy, parts=PART_ALL, stream=None):
+        """Asynchronous evaluation into device tensors forces [n,3], phi [n] (the potential at
+        every particle, so that E = 1/2 sum q_i phi_i) and energy [4]."""
+        n = int(q.shape[0])
+        _check(lib().ewald_compute_phi_async(self._h, n, _dev_f64(pos, (n, 3), "pos"),
+                                             _dev_f64(q, (n,), "q"), _dev_f64(forces, (n, 3), "forces"),
+                                             _dev_f64(phi, (n,), "phi"), _dev_f64(energy, (4,), "energy"),
+                                             int(parts), _stream_handle(stream)), "ewald_compute_phi_async")
 
     def status(self) -> int:
         """Synchronise and return the device-side status of the last evaluation."""
