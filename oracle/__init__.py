@@ -60,6 +60,10 @@ def lib():
             L.ewo_recip_energy.argtypes = [_i64, _p, _p, _d, _d, _p]
             L.ewo_recip_forces.restype = None
             L.ewo_recip_forces.argtypes = [_i64, _p, _p, _d, _d, _i64, _p, _p, _i64, _p, _p, _p]
+            L.ewo_virial_real.restype = None
+            L.ewo_virial_real.argtypes = [_i64, _p, _p, _d, _d, _d, _p]
+            L.ewo_virial_recip.restype = None
+            L.ewo_virial_recip.argtypes = [_i64, _p, _p, _d, _d, _p]
             L.ewo_self.restype = _d
             L.ewo_self.argtypes = [_i64, _p, _d]
             L.ewo_coulomb_cube.restype = None
@@ -151,6 +155,27 @@ def recip(pos, q, L, beta, kmax, sub=None, S=None):
     lib().ewo_recip_forces(len(q), _ptr(pos), _ptr(q), float(L), float(beta), len(m), _ptr(m),
                            _ptr(S2), 0 if sub is None else len(sub), _ptr(sub), _ptr(F), _ptr(phi))
     return e, F, phi, S, m
+
+
+def virial_real(pos, q, L, beta, rc) -> np.ndarray:
+    """Real-space virial tensor W_ab = -dE_real/d(eps_ab) at fixed beta ([3, 3])."""
+    pos, q = _f64(pos), _f64(q)
+    W = np.zeros(9)
+    lib().ewo_virial_real(len(q), _ptr(pos), _ptr(q), float(L), float(beta), float(rc), _ptr(W))
+    return W.reshape(3, 3)
+
+
+def virial_recip(pos, q, L, beta, kmax, S=None) -> np.ndarray:
+    """Reciprocal-space virial tensor W_ab = -dE_recip/d(eps_ab) at fixed beta over
+    K_half(kmax) ([3, 3]); S (complex, K_half order) is computed when not given."""
+    pos, q = _f64(pos), _f64(q)
+    m = kset_half(kmax)
+    if S is None:
+        S = structure_factor(pos, q, L, m)
+    S2 = np.ascontiguousarray(np.stack([S.real, S.imag], axis=1))
+    W = np.zeros(9)
+    lib().ewo_virial_recip(len(m), _ptr(m), _ptr(S2), float(L), float(beta), _ptr(W))
+    return W.reshape(3, 3)
 
 
 def self_energy(q, beta) -> float:

@@ -39,8 +39,10 @@
  * invariance of the total energy under beta at converged cutoffs, sum of forces = 0,
  * central finite differences of the energy, brute-force image sums of tiny neutral cells
  * (ewo_coulomb_cube), the exactly known S(k) of an unjittered rock-salt lattice,
- * lattice-point counts for the k-set, and equality of the cell-list real-space sum
- * (ewo_real_cells) with the all-pairs one (ewo_real).
+ * lattice-point counts for the k-set, equality of the cell-list real-space sum
+ * (ewo_real_cells) with the all-pairs one (ewo_real), and for the virial tensors: central
+ * finite differences of the energies under strain, the Coulomb virial identity
+ * tr W = E_total, invariance of W under beta, and the isotropic W = E/3 of rock-salt.
  */
 #include <math.h>
 #include <stddef.h>
@@ -369,6 +371,84 @@ void ewo_recip_forces(int64_t n, const double *pos, const double *q, double L, d
             F_out[3 * t + 2] = q[i] * fz;
         }
         if (phi_out) phi_out[t] = phi;
+    }
+}
+
+/*
+ * Real-space virial tensor: the strain derivative W_ab = -dE_real/d(eps_ab) of the real-space
+ * energy of Section 3.1.1 when every separation d_vec of Eq. 4 is strained to (1 + eps) d_vec
+ * at fixed beta.  With psi(d) = -d/dd [erfc(beta d)/d] = erfc(beta d)/d^2 +
+ * 2 beta/sqrt(pi) exp(-beta^2 d^2)/d (the radial factor of Eq. 4's force),
+ *   W_ab = 1/2 sum_i sum_{j,n} q_i q_j psi(d) d_a d_b / d,   d_vec = r_i - r_j - nL,
+ * i.e. 1/2 sum over ordered pairs of d_a F_b with F the pair force of Eq. 4.  The pairs and
+ * images are those of ewo_real (strict 0 < d < r_c).  W_out[3 a + b], row-major.  Each target
+ * accumulates its own row in parallel; the rows are added serially in target order.
+ */
+void ewo_virial_real(int64_t n, const double *pos, const double *q, double L, double beta,
+                     double rc, double *W_out)
+{
+    const double rc2 = rc * rc;
+    const double two_beta_rpi = 2.0 * beta / sqrt(EWO_PI);
+    const int min_image = (rc <= 0.5 * L);
+    const int ms = (int)ceil(rc / L);
+    double *rows = (double *)calloc((size_t)(n > 0 ? n : 1) * 9, sizeof(double));
+
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        const double xi = wrap1(pos[3 * i + 0], L);
+        const double yi = wrap1(pos[3 * i + 1], L);
+        const double zi = wrap1(pos[3 * i + 2], L);
+        double w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            const double dx0 = xi - wrap1(pos[3 * j + 0], L);
+            const double dy0 = yi - wrap1(pos[3 * j + 1], L);
+            const double dz0 = zi - wrap1(pos[3 * j + 2], L);
+            const int lo = min_image ? 0 : -ms, hi = min_image ? 0 : ms;
+            for (int sx = lo; sx <= hi; ++sx)
+                for (int sy = lo; sy <= hi; ++sy)
+                    for (int sz = lo; sz <= hi; ++sz) {
+                        if (j == i && sx == 0 && sy == 0 && sz == 0) continue;
+                        double d[3] = {dx0 - L * sx, dy0 - L * sy, dz0 - L * sz};
+                        if (min_image)
+                            for (int a = 0; a < 3; ++a) d[a] -= L * round(d[a] / L);
+                        const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        if (!(d2 < rc2)) continue;
+                        const double r = sqrt(d2);
+                        const double psi = erfc(beta * r) / d2 + two_beta_rpi * exp(-beta * beta * d2) / r;
+                        const double c = q[j] * psi / r;
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) w[3 * a + b] += c * d[a] * d[b];
+                    }
+        }
+        for (int u = 0; u < 9; ++u) rows[9 * i + u] = 0.5 * q[i] * w[u];
+    }
+    for (int u = 0; u < 9; ++u) W_out[u] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int u = 0; u < 9; ++u) W_out[u] += rows[9 * i + u];
+    free(rows);
+}
+
+/*
+ * Reciprocal-space virial tensor W_ab = -dE_recip/d(eps_ab) at fixed beta, given S(k) over a
+ * half-space k list.  Under the strain the box volume becomes V (1 + tr eps) and every k of
+ * Eq. 3 becomes (1 - eps) k while k.r_j, hence S(k), is unchanged; differentiating
+ * g(k) = 4 pi exp(-k^2/(4 beta^2)) / (V k^2) gives
+ *   W_ab = sum_{k in K_half} g(k) |S(k)|^2 [delta_ab - 2 k_a k_b (1/k^2 + 1/(4 beta^2))],
+ * summed serially in list order.  W_out[3 a + b], row-major.
+ */
+void ewo_virial_recip(int64_t nk, const int32_t *m, const double *S, double L, double beta,
+                      double *W_out)
+{
+    const double tpl = 2.0 * EWO_PI / L;
+    for (int u = 0; u < 9; ++u) W_out[u] = 0.0;
+    for (int64_t t = 0; t < nk; ++t) {
+        const double k[3] = {tpl * m[3 * t + 0], tpl * m[3 * t + 1], tpl * m[3 * t + 2]};
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        const double e = coef_g(m + 3 * t, L, beta) * (S[2 * t] * S[2 * t] + S[2 * t + 1] * S[2 * t + 1]);
+        const double c = 2.0 * (1.0 / k2 + 1.0 / (4.0 * beta * beta));
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                W_out[3 * a + b] += e * ((a == b ? 1.0 : 0.0) - c * k[a] * k[b]);
     }
 }
 
