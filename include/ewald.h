@@ -151,6 +151,30 @@ int ewald_compute_phi_async(ewald_plan_t plan, int64_t n, const double *pos, con
                             double *forces, double *phi_dev, double *energy_dev, int parts,
                             void *stream);
 
+/*
+ * ewald_compute_virial_async - as ewald_compute_async, and also the virial tensor of every
+ * part: W_ab = -dE/d(eps_ab), the derivative of the energy when the box and all positions
+ * are strained by (1 + eps) at fixed beta.  The configurational pressure tensor is W / V
+ * (V = L^3); the paper states the energies and forces (Section 3.1, Eqs. 2-4) and this is
+ * their strain derivative:
+ *   real:  W_ab = 1/2 sum_i sum_{j,n} q_i q_j psi(d) d_a d_b / d over the pairs of Eq. 4,
+ *          psi(d) = erfc(beta d)/d^2 + 2 beta/sqrt(pi) exp(-beta^2 d^2)/d, d_vec = r_i-r_j-nL;
+ *   recip: W_ab = sum_{k in K_half} g(k) |S(k)|^2 [delta_ab - 2 k_a k_b (1/k^2 + 1/(4 beta^2))]
+ *          (Eq. 3: V grows by tr eps, k shrinks by eps k, S(k) is unchanged);
+ *   self:  zero (the self energy does not change under the strain at fixed beta).
+ *   virial_dev  dev float64 [4][3][3]: the real, reciprocal and self tensors and their sum
+ *               (selected parts only; unselected parts are zero), row-major and symmetric.
+ *               For converged cutoffs tr W = E_total (the Coulomb energy is homogeneous of
+ *               degree -1 in the coordinates).
+ * The real-space kernel accumulates the six tensor entries next to the force in FP32 (mixed
+ * precisions) or FP64; the reciprocal tensor is an FP64 sum over the modes of S(k).  Sums are
+ * in a fixed order, so repeated calls give identical bits.
+ * Errors as ewald_compute_async; virial_dev may not be NULL.
+ */
+int ewald_compute_virial_async(ewald_plan_t plan, int64_t n, const double *pos,
+                               const double *q, double *forces, double *virial_dev,
+                               double *energy_dev, int parts, void *stream);
+
 /* ewald_status_sync - synchronise the plan's last stream and return (and clear) the
  * device-side status of the last evaluation: EWALD_OK, EWALD_E_NONNEUTRAL,
  * EWALD_E_NONFINITE, EWALD_E_TIMEOUT or EWALD_E_CUDA. */

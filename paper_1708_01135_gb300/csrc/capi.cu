@@ -127,9 +127,77 @@ __global__ void k_unsort(int64_t n, const int *__restrict__ perm, const double *
     }
 }
 
+// Reciprocal virial tensor from S(k) (the strain derivative of E_recip = sum_{K_half} g |S|^2
+// at fixed beta; under a strain eps the volume grows by tr eps and k shrinks by eps k while
+// S(k) is unchanged):
+//   W_ab = sum_{k in K_half} g(k) |S(k)|^2 [delta_ab - 2 k_a k_b (1/k^2 + 1/(4 beta^2))].
+// Block b sums the modes b * 256 + t + j * (gridDim.x * 256) of thread t in order, then a
+// fixed tree; part[c * gridDim.x + b] for c = xx, yy, zz, xy, xz, yz.
+__global__ void __launch_bounds__(256)
+k_recip_virial(int64_t nk, const int *__restrict__ kset, const double *__restrict__ g,
+               const double *__restrict__ S, double kf, double c4, double *__restrict__ part)
+{
+    __shared__ double red[6][256];
+    const int t = threadIdx.x;
+    double w[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t u = (int64_t)blockIdx.x * 256 + t; u < nk; u += (int64_t)gridDim.x * 256) {
+        const double kx = kf * kset[3 * u], ky = kf * kset[3 * u + 1], kz = kf * kset[3 * u + 2];
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        const double sr = S[2 * u], si = S[2 * u + 1];
+        const double e = g[u] * (sr * sr + si * si);
+        const double c = 2.0 * e * (1.0 / k2 + c4);
+        w[0] += e - c * kx * kx;
+        w[1] += e - c * ky * ky;
+        w[2] += e - c * kz * kz;
+        w[3] -= c * kx * ky;
+        w[4] -= c * kx * kz;
+        w[5] -= c * ky * kz;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) red[c][t] = w[c];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) red[c][t] += red[c][t + o];
+        }
+        __syncthreads();
+    }
+    if (t < 6) part[t * gridDim.x + blockIdx.x] = red[t][0];
+}
+
+// Virial tensors (one block, fixed order): vir[0..8] real, vir[9..17] reciprocal,
+// vir[18..26] self (zero: the self energy does not depend on the positions or the box at
+// fixed beta), vir[27..35] their sum; each 3 x 3 row-major and symmetric.
+__global__ void k_virial(int ntile, const double *__restrict__ vir_tile, int64_t vcap,
+                         int nblk, const double *__restrict__ vir_part, int parts,
+                         double *__restrict__ vir)
+{
+    __shared__ double red[256];
+    double wr[6], wk[6];
+    for (int c = 0; c < 6; ++c) {
+        wr[c] = (parts & EWALD_PART_REAL) ? block_sum_fixed(vir_tile + c * vcap, ntile, red) : 0.0;
+        wk[c] = (parts & EWALD_PART_RECIP) ? block_sum_fixed(vir_part + c * nblk, nblk, red) : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        const int ix[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};   // (a, b) -> xx yy zz xy xz yz
+        for (int u = 0; u < 9; ++u) {
+            vir[u] = wr[ix[u]];
+            vir[9 + u] = wk[ix[u]];
+            vir[18 + u] = 0.0;
+            vir[27 + u] = wr[ix[u]] + wk[ix[u]];
+        }
+    }
+}
+
 __global__ void k_zero_energy(double *e)
 {
     if (threadIdx.x < 4) e[threadIdx.x] = 0.0;
+}
+
+__global__ void k_zero(double *x, int m)
+{
+    for (int i = threadIdx.x; i < m; i += blockDim.x) x[i] = 0.0;
 }
 
 int status_from_bits(int bits)
@@ -171,7 +239,8 @@ void free_workspace(Plan &p)
     Workspace &ws = p.ws;
     void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
                     ws.tiles, ws.tile_count, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
-                    ws.f_real, ws.f_recip, ws.e_tile, ws.qpart, ws.phi_real, ws.phi_recip};
+                    ws.f_real, ws.f_recip, ws.e_tile, ws.qpart, ws.phi_real, ws.phi_recip,
+                    ws.vir_tile, ws.vir_part};
     for (void *q : ptrs) pool_free(q, p.side_stream);
     free_recip_simt(p);
     if (uses_tc(p.precision)) free_recip_tc(p);
@@ -275,6 +344,8 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     EW_TRY(dmalloc(p, &ws.phi_recip, sizeof(double) * n));
     EW_TRY(dmalloc(p, &ws.f_recip, sizeof(double) * 3 * n));
     EW_TRY(dmalloc(p, &ws.e_tile, sizeof(double) * tiles));
+    EW_TRY(dmalloc(p, &ws.vir_tile, sizeof(double) * 6 * tiles));
+    EW_TRY(dmalloc(p, &ws.vir_part, sizeof(double) * 6 * kVirBlocks));
     EW_TRY(dmalloc(p, &ws.qpart, sizeof(double) * 3 * qblocks));
     ws.cap_n = n;
     ws.nb = nb;
@@ -287,7 +358,7 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
 
 cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
                      double *energy_dev, int parts, cudaStream_t st, bool clear_status = true,
-                     double *phi = nullptr)
+                     double *phi = nullptr, double *vir = nullptr)
 {
     cudaError_t e;
     Workspace &ws = p.ws;
@@ -302,6 +373,8 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     prof_mark(p, kEvBinned, st);
     const int64_t tiles = real_tile_capacity(p, n);
     if ((e = cudaMemsetAsync(ws.e_tile, 0, sizeof(double) * tiles, st)) != cudaSuccess) return e;
+    if (vir && (e = cudaMemsetAsync(ws.vir_tile, 0, sizeof(double) * 6 * tiles, st)) != cudaSuccess)
+        return e;
     if ((e = cudaMemsetAsync(p.e_recip_part, 0, sizeof(double) * p.e_recip_count, st)) != cudaSuccess) return e;
     const bool do_recip = parts & EWALD_PART_RECIP;
     if (do_recip && uses_tc(p.precision) && (e = launch_recip_tc_operands(p, n, st)) != cudaSuccess)
@@ -312,10 +385,16 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
         e = uses_tc(p.precision) ? launch_recip_tc(p, n, p.side_stream)
                                  : launch_recip_simt(p, n, p.side_stream);
         if (e != cudaSuccess) return e;
+        if (vir) {
+            k_recip_virial<<<kVirBlocks, 256, 0, p.side_stream>>>(
+                p.nk, p.kset_d, p.g_d, p.S_d, 2.0 * kPi / p.L, 0.25 / (p.beta * p.beta),
+                ws.vir_part);
+            p.launches += 1;
+        }
         if ((e = cudaEventRecord(p.ev_join, p.side_stream)) != cudaSuccess) return e;
     }
     if (parts & EWALD_PART_REAL) {
-        if ((e = launch_real(p, n, st)) != cudaSuccess) return e;
+        if ((e = launch_real(p, n, st, vir != nullptr)) != cudaSuccess) return e;
     }
     prof_mark(p, kEvRealEnd, st);
     if (do_recip) {
@@ -328,6 +407,11 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
                                                           parts, forces, ws.phi_real,
                                                           ws.phi_recip, ws.pg, p.beta, phi);
     p.launches += 2;
+    if (vir) {
+        k_virial<<<1, 256, 0, st>>>((int)tiles, ws.vir_tile, tiles, kVirBlocks, ws.vir_part,
+                                    parts, vir);
+        p.launches += 1;
+    }
     prof_mark(p, kEvFinal, st);
     p.prof_valid = p.prof && do_recip;
     p.last_stream = st;
@@ -343,19 +427,19 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
 // itself being captured run the pipeline directly.
 cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
                      double *energy_dev, int parts, cudaStream_t st, bool clear_status,
-                     double *phi)
+                     double *phi, double *vir)
 {
     cudaError_t e = grow_workspace(p, n);
     if (e != cudaSuccess) return e;
     Plan::EvalKey key;
     key.n = n; key.pos = pos; key.q = q; key.forces = forces; key.energy = energy_dev;
-    key.parts = parts; key.clear = clear_status; key.phi = phi;
+    key.parts = parts; key.clear = clear_status; key.phi = phi; key.vir = vir;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return e;
     const bool repeat = key == p.last_key;
     p.last_key = key;
     if (p.prof || !p.graph_stream || cap != cudaStreamCaptureStatusNone || !repeat)
-        return pipeline(p, n, pos, q, forces, energy_dev, parts, st, clear_status, phi);
+        return pipeline(p, n, pos, q, forces, energy_dev, parts, st, clear_status, phi, vir);
     if ((e = cudaEventRecord(p.ev_gin, st)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(p.graph_stream, p.ev_gin, 0)) != cudaSuccess) return e;
     if (!(p.gexec && key == p.gkey)) {
@@ -365,7 +449,7 @@ cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, dou
         if ((e = cudaStreamBeginCapture(p.graph_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return e;
         cudaError_t ep = pipeline(p, n, pos, q, forces, energy_dev, parts, p.graph_stream,
-                                  clear_status, phi);
+                                  clear_status, phi, vir);
         cudaError_t ec = cudaStreamEndCapture(p.graph_stream, &g);
         if (ep != cudaSuccess || ec != cudaSuccess || !g) {
             if (g) cudaGraphDestroy(g);
@@ -410,7 +494,8 @@ size_t plan_footprint(const Plan &p, int64_t n)
     b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * ncells;
     b += sizeof(int) * (2 * ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * ((size_t)nc * nc + 1);
     b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
-    b += sizeof(double) * 6 * (size_t)n + sizeof(double) * tiles + sizeof(double) * 3 * ((n + 255) / 256);
+    b += sizeof(double) * 8 * (size_t)n + sizeof(double) * 7 * tiles + sizeof(double) * 3 * ((n + 255) / 256);
+    b += sizeof(double) * 6 * kVirBlocks;
     b += uses_tc(p.precision) ? recip_tc_bytes(p, n) : recip_simt_bytes(p, n);
     b += sizeof(double) * 3 * (size_t)p.nk + sizeof(int) * 3 * (size_t)p.nk + sizeof(RowInfo) * p.R;
     b += sizeof(double) * 32 * (size_t)p.R;
@@ -678,6 +763,25 @@ extern "C" int ewald_compute_phi_async(ewald_plan_t plan, int64_t n, const doubl
         return cuda_status(cudaGetLastError());
     }
     return cuda_status(evaluate(p, n, pos, q, forces, energy_dev, parts, st, true, phi_dev));
+}
+
+extern "C" int ewald_compute_virial_async(ewald_plan_t plan, int64_t n, const double *pos,
+                                          const double *q, double *forces, double *virial_dev,
+                                          double *energy_dev, int parts, void *stream)
+{
+    int s = validate_call(plan, n, pos, q, forces);
+    if (s != EWALD_OK) return s;
+    if (!energy_dev || !virial_dev || (parts & ~EWALD_PART_ALL)) return EWALD_E_INVAL;
+    Plan &p = plan->p;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        k_zero_energy<<<1, 32, 0, st>>>(energy_dev);
+        k_zero<<<1, 64, 0, st>>>(virial_dev, 36);
+        p.last_stream = st;
+        return cuda_status(cudaGetLastError());
+    }
+    return cuda_status(evaluate(p, n, pos, q, forces, energy_dev, parts, st, true, nullptr,
+                                virial_dev));
 }
 
 extern "C" int ewald_status_sync(ewald_plan_t plan)

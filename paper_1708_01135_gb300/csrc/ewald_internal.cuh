@@ -63,6 +63,8 @@ struct Workspace {
     double *phi_recip = nullptr; // [n] reciprocal-space potential of every sorted particle
     double *f_recip = nullptr;   // [n][3]
     double *e_tile = nullptr;    // [max tiles] per-tile q_i phi_i sums
+    double *vir_tile = nullptr;  // [6][max tiles] per-tile real-space virial sums (xx yy zz xy xz yz)
+    double *vir_part = nullptr;  // [6][kVirBlocks] block sums of the reciprocal virial
     double *qpart = nullptr;     // [qblocks][3]: sum q, sum |q|, sum q^2 partials
     // staging for the host-buffer entry point
     double *h_pos = nullptr, *h_q = nullptr, *h_f = nullptr, *h_e = nullptr;
@@ -115,13 +117,14 @@ struct Plan {
     struct EvalKey {
         int64_t n = -1;
         const void *pos = nullptr, *q = nullptr;
-        void *forces = nullptr, *energy = nullptr, *phi = nullptr;
+        void *forces = nullptr, *energy = nullptr, *phi = nullptr, *vir = nullptr;
         int parts = 0;
         bool clear = false;
         bool operator==(const EvalKey &o) const
         {
             return n == o.n && pos == o.pos && q == o.q && forces == o.forces &&
-                   energy == o.energy && phi == o.phi && parts == o.parts && clear == o.clear;
+                   energy == o.energy && phi == o.phi && vir == o.vir && parts == o.parts &&
+                   clear == o.clear;
         }
     };
     EvalKey gkey, last_key;      // key of the captured graph; key of the previous evaluation
@@ -151,8 +154,9 @@ inline void prof_mark(Plan &p, int which, cudaStream_t st)
 // a1-a3: wrap, cell keys, stable counting sort, cell offsets, packing.
 cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *q,
                            cudaStream_t st);
-// a4: real-space pairs into ws.f_real / ws.e_tile (sorted order).
-cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st);
+// a4: real-space pairs into ws.f_real / ws.phi_real / ws.e_tile (sorted order), and with
+// virial the per-tile virial sums into ws.vir_tile.
+cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st, bool virial);
 int64_t real_tile_capacity(const Plan &p, int64_t n);
 int real_tile_size(const Plan &p);          // particles per real-space tile
 int real_tile_for(int w, double cell_occupancy);   // tile size for a grid (particles per cell)
@@ -173,9 +177,11 @@ void free_recip_tc(Plan &p);
 // One whole evaluation on `st` (grows the workspaces for n first; n > 0).  With
 // clear_status false the plan's device status keeps the bits of earlier evaluations, so that
 // a sequence of evaluations reports every failure at the next ewald_status_sync.
+// phi (optional, [n] caller order) receives the potentials; vir (optional, [4][9]) the
+// virial tensors of the real, reciprocal and self parts and their total.
 cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, double *forces,
                      double *energy_dev, int parts, cudaStream_t st, bool clear_status,
-                     double *phi = nullptr);
+                     double *phi = nullptr, double *vir = nullptr);
 
 // Library memory pool (stream-ordered, retains freed memory for reuse).
 cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st);
@@ -192,6 +198,9 @@ int plan_reconfigure(struct ::ewald_plan *h, double L, double beta, double rc, i
 
 // Footprint of a plan's workspaces for n particles (serving admission).
 size_t plan_footprint(const Plan &p, int64_t n);
+
+// Blocks of the reciprocal virial reduction (each sums a fixed stride of the modes).
+constexpr int kVirBlocks = 128;
 
 // Bounded spin limit for mbarrier waits inside kernels (iterations of try_wait).
 constexpr long long kSpinLimit = 1ll << 26;

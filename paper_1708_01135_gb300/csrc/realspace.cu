@@ -119,10 +119,61 @@ __device__ __forceinline__ double exp_t(double x) { return exp(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 
-template <class T>
+// Per-target sums of one warp lane: force / q_i, potential, and with kVir the six
+// independent entries of sum_j s_ij d_a d_b (xx, yy, zz, xy, xz, yz), s_ij d_vec being the
+// force / q_i that partner j exerts, so that the target's share of the virial tensor is
+// 1/2 q_i times that sum.
+template <class T, bool kVir>
 struct PairAcc {
+    static constexpr bool vir = false;
     T fx, fy, fz, phi;
 };
+template <class T>
+struct PairAcc<T, true> {
+    static constexpr bool vir = true;
+    T fx, fy, fz, phi;
+    T w[6];
+};
+
+template <class A>
+__device__ __forceinline__ void acc_shfl_add(A &a, int o)
+{
+    a.fx += __shfl_xor_sync(0xffffffffu, a.fx, o);
+    a.fy += __shfl_xor_sync(0xffffffffu, a.fy, o);
+    a.fz += __shfl_xor_sync(0xffffffffu, a.fz, o);
+    a.phi += __shfl_xor_sync(0xffffffffu, a.phi, o);
+    if constexpr (A::vir) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.w[c] += __shfl_xor_sync(0xffffffffu, a.w[c], o);
+    }
+}
+
+template <class A>
+__device__ __forceinline__ void acc_add(A &a, const A &o)
+{
+    a.fx += o.fx; a.fy += o.fy; a.fz += o.fz; a.phi += o.phi;
+    if constexpr (A::vir) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.w[c] += o.w[c];
+    }
+}
+
+// Writes the tile's share of the six virial sums, vir_tile[c * vcap + tile] = sum over the
+// tile's targets of 1/2 q_i w_c (a fixed shuffle tree over the lanes).
+template <class A>
+__device__ __forceinline__ void acc_store_virial(const A &a, bool mine, double qi, int lane,
+                                                 double *__restrict__ vir_tile, int64_t vcap,
+                                                 int64_t tile)
+{
+    if constexpr (A::vir) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            double v = mine ? 0.5 * qi * (double)a.w[c] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) vir_tile[c * vcap + tile] = v;
+        }
+    }
+}
 
 // erfc(x) = exp(-x^2) * t * exp(P(t)), t = 1 / (1 + x / 2), x >= 0: the Chebyshev fit
 // "erfcc" of Numerical Recipes in C (2nd ed., Sec. 6.2), fractional error below 1.2e-7 in
@@ -145,8 +196,8 @@ __device__ __forceinline__ float erfc_from_gauss(float x, float g)
 }
 
 // One candidate pair: target at the origin shifted by (xi, yi, zi), partner p.
-template <class T, class T4>
-__device__ __forceinline__ void pair(PairAcc<T> &a, const T4 &p, T xi, T yi, T zi, T rc2,
+template <class T, class T4, class A>
+__device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
                                      T beta, T nb2, T two_b_rpi)
 {
     const T dx = xi - p.x, dy = yi - p.y, dz = zi - p.z;   // r_i - r_j
@@ -160,9 +211,14 @@ __device__ __forceinline__ void pair(PairAcc<T> &a, const T4 &p, T xi, T yi, T z
         else e = erfc_t(beta * r) * rinv;
         const T s = p.w * (e + two_b_rpi * g) * rinv * rinv;
         a.phi += p.w * e;
-        a.fx += s * dx;
-        a.fy += s * dy;
-        a.fz += s * dz;
+        const T sx = s * dx, sy = s * dy, sz = s * dz;
+        a.fx += sx;
+        a.fy += sy;
+        a.fz += sz;
+        if constexpr (A::vir) {
+            a.w[0] += sx * dx; a.w[1] += sy * dy; a.w[2] += sz * dz;
+            a.w[3] += sx * dy; a.w[4] += sx * dz; a.w[5] += sy * dz;
+        }
     }
 }
 
@@ -234,18 +290,20 @@ struct ChunkIter {
     }
 };
 
-template <class T, int kTile>
+template <class T, int kTile, bool kVir>
 __global__ void __launch_bounds__(kWarps * 32)
 k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restrict__ key_sorted,
              const int *__restrict__ cell_start, const int2 *__restrict__ tiles,
              const int *__restrict__ tile_total, int nc, int w, T side, T rc2, T beta,
              T two_b_rpi, int split, double *__restrict__ f_out, double *__restrict__ phi_out,
-             double *__restrict__ e_tile, int *__restrict__ status)
+             double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap,
+             int *__restrict__ status)
 {
     using T4 = typename Vec4<T>::type;
+    using Acc = PairAcc<T, kVir>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kWarps][2];
-    __shared__ PairAcc<T> xacc[kWarps][32];     // partial sums handed between split warps
+    __shared__ Acc xacc[kWarps][32];            // partial sums handed between split warps
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T4 *buf[2];
     buf[0] = reinterpret_cast<T4 *>(smem_raw) + (size_t)warp * 2 * kCap;
@@ -285,7 +343,7 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     it.side = (float)side; it.rc2 = (float)rc2;
     it.u = 0; it.uend = -1;
 
-    PairAcc<T> acc{T(0), T(0), T(0), T(0)};
+    Acc acc{};
     const T nb2 = -beta * beta;
     uint32_t phase[2] = {0u, 0u};
     Chunk cur, nxt;
@@ -343,19 +401,13 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     }
     // combine the kGroups partner groups of every target (lanes ti, ti + kTile, ...)
 #pragma unroll
-    for (int o = kTile; o < 32; o <<= 1) {
-        acc.fx += __shfl_xor_sync(0xffffffffu, acc.fx, o);
-        acc.fy += __shfl_xor_sync(0xffffffffu, acc.fy, o);
-        acc.fz += __shfl_xor_sync(0xffffffffu, acc.fz, o);
-        acc.phi += __shfl_xor_sync(0xffffffffu, acc.phi, o);
-    }
+    for (int o = kTile; o < 32; o <<= 1) acc_shfl_add(acc, o);
     if (split == 2) {
         // every warp of the block reaches this barrier (none has returned with split = 2)
         if (part == 1) xacc[warp][lane] = acc;
         __syncthreads();
         if (part == 1 || !active) return;
-        const PairAcc<T> o = xacc[warp + 1][lane];
-        acc.fx += o.fx; acc.fy += o.fy; acc.fz += o.fz; acc.phi += o.phi;
+        acc_add(acc, xacc[warp + 1][lane]);
     }
     const double qi = (double)pi.w;
     if (valid && g == 0) {
@@ -367,15 +419,17 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     double e = (valid && g == 0) ? qi * (double)acc.phi : 0.0;
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
     if (lane == 0) e_tile[tile] = e;
+    acc_store_virial(acc, valid && g == 0, qi, lane, vir_tile, vcap, tile);
 }
 
 // All pairs with the minimum image (boxes too small for a cell stencil): one tile of 32
 // targets per warp, every particle staged through the same double-buffered TMA path.
-template <class T>
+template <class T, bool kVir>
 __global__ void __launch_bounds__(kWarps * 32)
 k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2, T beta,
                 T two_b_rpi, double *__restrict__ f_out, double *__restrict__ phi_out,
-                double *__restrict__ e_tile, int *__restrict__ status)
+                double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap,
+                int *__restrict__ status)
 {
     using T4 = typename Vec4<T>::type;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -397,7 +451,7 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
     const bool valid = i < n;
     const T4 pi = pl[valid ? i : n - 1];
     const T invL = T(1) / L;
-    PairAcc<T> acc{T(0), T(0), T(0), T(0)};
+    PairAcc<T, kVir> acc{};
     const T nb2 = -beta * beta;
     uint32_t phase[2] = {0u, 0u};
     const int nchunks = (n + kCapAll - 1) / kCapAll;
@@ -448,25 +502,30 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
     double e = valid ? qi * (double)acc.phi : 0.0;
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
     if (lane == 0) e_tile[tile] = e;
+    acc_store_virial(acc, valid, qi, lane, vir_tile, vcap, tile);
 }
 
-template <class T>
+template <class T, bool kVir>
 cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, cudaStream_t st)
 {
     Workspace &ws = p.ws;
+    double *vir = kVir ? ws.vir_tile : nullptr;
+    const int64_t vcap = real_tile_capacity(p, n);
     const size_t smem = (size_t)kWarps * 2 * (p.w == 0 ? kCapAll : kCap) * sizeof(typename Vec4<T>::type);
     const T beta = (T)p.beta, rc2 = (T)(p.rc * p.rc);
     const T tbr = (T)(2.0 * p.beta / sqrt(kPi));
     cudaError_t e;
     if (p.w == 0) {
-        e = cudaFuncSetAttribute(k_real_allpairs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_real_allpairs<T, kVir>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e != cudaSuccess) return e;
         int tiles = (int)((n + 31) / 32);
-        k_real_allpairs<T><<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(
-            pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, p.d_status);
+        k_real_allpairs<T, kVir><<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(
+            pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap,
+            p.d_status);
     } else {
-        auto kern = p.real_tile == kTileDense ? k_real_cells<T, kTileDense> : k_real_cells<T, kTileSparse>;
+        auto kern = p.real_tile == kTileDense ? k_real_cells<T, kTileDense, kVir>
+                                              : k_real_cells<T, kTileSparse, kVir>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int64_t tiles = real_tile_capacity(p, n);
@@ -474,7 +533,8 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         const int split = tiles < 16 * (int64_t)p.num_sms ? 2 : 1;
         kern<<<(unsigned)((tiles * split + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
             pl, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc, p.nc, p.w,
-            (T)p.cell_side, rc2, beta, tbr, split, ws.f_real, ws.phi_real, ws.e_tile, p.d_status);
+            (T)p.cell_side, rc2, beta, tbr, split, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap,
+            p.d_status);
     }
     p.launches += 1;
     return cudaGetLastError();
@@ -496,10 +556,13 @@ int real_tile_for(int w, double cell_occupancy)
     return cell_occupancy >= 16.0 ? kTileDense : kTileSparse;
 }
 
-cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st)
+cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st, bool virial)
 {
-    if (p.precision == EWALD_FP64) return launch_real_t<double>(p, n, p.ws.pl64, st);
-    return launch_real_t<float>(p, n, p.ws.pl32, st);
+    if (p.precision == EWALD_FP64)
+        return virial ? launch_real_t<double, true>(p, n, p.ws.pl64, st)
+                      : launch_real_t<double, false>(p, n, p.ws.pl64, st);
+    return virial ? launch_real_t<float, true>(p, n, p.ws.pl32, st)
+                  : launch_real_t<float, false>(p, n, p.ws.pl32, st);
 }
 
 }  // namespace ew

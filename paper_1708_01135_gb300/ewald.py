@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
                 "ewald_compute": (_i, [_p, _i64, _p, _p, _p, _p, _p]),
                 "ewald_compute_async": (_i, [_p, _i64, _p, _p, _p, _p, _i, _p]),
                 "ewald_compute_phi_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
+                "ewald_compute_virial_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
                 "ewald_status_sync": (_i, [_p]),
                 "ewald_compute_host": (_i, [_p, _i64, _p, _p, _p, _p, _p]),
                 "ewald_plan_info": (_i, [_p, _p]),
@@ -216,6 +217,16 @@ class Ewald:
                                              _dev_f64(q, (n,), "q"), _dev_f64(forces, (n, 3), "forces"),
                                              _dev_f64(phi, (n,), "phi"), _dev_f64(energy, (4,), "energy"),
                                              int(parts), _stream_handle(stream)), "ewald_compute_phi_async")
+
+    def compute_virial_async(self, pos, q, forces, virial, energy, parts=PART_ALL, stream=None):
+        """Asynchronous evaluation into device tensors forces [n,3], virial [4,3,3] (the real,
+        reciprocal and self virial tensors W_ab = -dE/d(eps_ab) and their sum) and energy [4]."""
+        n = int(q.shape[0])
+        _check(lib().ewald_compute_virial_async(self._h, n, _dev_f64(pos, (n, 3), "pos"),
+                                                _dev_f64(q, (n,), "q"), _dev_f64(forces, (n, 3), "forces"),
+                                                _dev_f64(virial, (4, 3, 3), "virial"),
+                                                _dev_f64(energy, (4,), "energy"), int(parts),
+                                                _stream_handle(stream)), "ewald_compute_virial_async")
 
     def status(self) -> int:
         """Synchronise and return the device-side status of the last evaluation."""
