@@ -64,6 +64,8 @@ def lib():
             L.ewo_virial_real.argtypes = [_i64, _p, _p, _d, _d, _d, _p]
             L.ewo_virial_recip.restype = None
             L.ewo_virial_recip.argtypes = [_i64, _p, _p, _d, _d, _p]
+            L.ewo_lj.restype = ctypes.c_int
+            L.ewo_lj.argtypes = [_i64, _p, _p, ctypes.c_int, _p, _p, _d, _d, _p, _p, _p]
             L.ewo_self.restype = _d
             L.ewo_self.argtypes = [_i64, _p, _d]
             L.ewo_coulomb_cube.restype = None
@@ -176,6 +178,23 @@ def virial_recip(pos, q, L, beta, kmax, S=None) -> np.ndarray:
     W = np.zeros(9)
     lib().ewo_virial_recip(len(m), _ptr(m), _ptr(S2), float(L), float(beta), _ptr(W))
     return W.reshape(3, 3)
+
+
+def lj(pos, types, eps, sigma, L, rc):
+    """Truncated and shifted Lennard-Jones pairs inside r_c (minimum image): (E, F [n, 3],
+    W [3, 3]).  types int [n] in [0, T); eps and sigma symmetric [T, T]."""
+    pos = _f64(pos)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    eps, sigma = _f64(eps), _f64(sigma)
+    T = eps.shape[0]
+    F = np.zeros((len(types), 3))
+    Wv = np.zeros(9)
+    e = _d(0.0)
+    r = lib().ewo_lj(len(types), _ptr(pos), _ptr(types), int(T), _ptr(eps), _ptr(sigma),
+                     float(L), float(rc), _ptr(F), ctypes.byref(e), _ptr(Wv))
+    if r != 0:
+        raise ValueError("lj needs r_c <= L/2 and types in [0, T)")
+    return e.value, F, Wv.reshape(3, 3)
 
 
 def self_energy(q, beta) -> float:

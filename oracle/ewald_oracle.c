@@ -42,7 +42,10 @@
  * lattice-point counts for the k-set, equality of the cell-list real-space sum
  * (ewo_real_cells) with the all-pairs one (ewo_real), and for the virial tensors: central
  * finite differences of the energies under strain, the Coulomb virial identity
- * tr W = E_total, invariance of W under beta, and the isotropic W = E/3 of rock-salt.
+ * tr W = E_total, invariance of W under beta, and the isotropic W = E/3 of rock-salt;
+ * for the Lennard-Jones pairs (ewo_lj): the minimum and zero of the pair potential, the
+ * simple-cubic lattice sum of (sigma/d)^12, finite differences of the energy under
+ * displacement and strain, and invariance under a relabelling of the types.
  */
 #include <math.h>
 #include <stddef.h>
@@ -450,6 +453,67 @@ void ewo_virial_recip(int64_t nk, const int32_t *m, const double *S, double L, d
             for (int b = 0; b < 3; ++b)
                 W_out[3 * a + b] += e * ((a == b ? 1.0 : 0.0) - c * k[a] * k[b]);
     }
+}
+
+/*
+ * Short-range Lennard-Jones pairs, the repulsion that the paper's NaCl benchmark adds to
+ * the Coulomb sum (Section 4; its force-field parameters are not printed).  Every particle
+ * has a type t_i in [0, ntypes); eps and sigma are symmetric [ntypes][ntypes] tables.  For
+ * 0 < d < r_c (minimum image, the cutoff of the real-space sum) a pair contributes the
+ * truncated and shifted potential
+ *   u(d) = 4 eps [(sigma/d)^12 - (sigma/d)^6] - 4 eps [(sigma/r_c)^12 - (sigma/r_c)^6],
+ * its force on i, F = -du/dd d_vec/d = 24 eps [2 (sigma/d)^12 - (sigma/d)^6] d_vec / d^2,
+ * and the strain derivative -du/d(eps_ab) = 1/2 of d_a F_b per ordered pair (as the virial of
+ * ewo_virial_real).  Outputs (each may be NULL): F_out [n][3], *e_out = 1/2 sum_i sum_j u,
+ * W_out [9] row-major.  Per-target rows in parallel, totals summed serially in index order.
+ * Returns 0, or -1 (nothing written) when r_c > L/2 or a type is out of range.
+ */
+int ewo_lj(int64_t n, const double *pos, const int32_t *type, int ntypes, const double *eps,
+           const double *sigma, double L, double rc, double *F_out, double *e_out,
+           double *W_out)
+{
+    if (!(rc <= 0.5 * L) || ntypes < 1) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        if (type[i] < 0 || type[i] >= ntypes) return -1;
+    const double rc2 = rc * rc;
+    double *rows = (double *)calloc((size_t)(n > 0 ? n : 1) * 13, sizeof(double));
+
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double *row = rows + 13 * i;   /* F[3], u, W[9] */
+        const double xi = wrap1(pos[3 * i + 0], L);
+        const double yi = wrap1(pos[3 * i + 1], L);
+        const double zi = wrap1(pos[3 * i + 2], L);
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3] = {xi - wrap1(pos[3 * j + 0], L), yi - wrap1(pos[3 * j + 1], L),
+                           zi - wrap1(pos[3 * j + 2], L)};
+            for (int a = 0; a < 3; ++a) d[a] -= L * round(d[a] / L);
+            const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(d2 < rc2)) continue;
+            const int t = type[i] * ntypes + type[j];
+            const double e = eps[t], s2 = sigma[t] * sigma[t];
+            const double x6 = (s2 / d2) * (s2 / d2) * (s2 / d2);
+            const double c6 = (s2 / rc2) * (s2 / rc2) * (s2 / rc2);
+            const double f = 24.0 * e * (2.0 * x6 * x6 - x6) / d2;
+            row[3] += 4.0 * e * (x6 * x6 - x6) - 4.0 * e * (c6 * c6 - c6);
+            for (int a = 0; a < 3; ++a) {
+                row[a] += f * d[a];
+                for (int b = 0; b < 3; ++b) row[4 + 3 * a + b] += 0.5 * f * d[a] * d[b];
+            }
+        }
+    }
+    double e = 0.0, W[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        const double *row = rows + 13 * i;
+        if (F_out) for (int a = 0; a < 3; ++a) F_out[3 * i + a] = row[a];
+        e += 0.5 * row[3];
+        for (int u = 0; u < 9; ++u) W[u] += row[4 + u];
+    }
+    if (e_out) *e_out = e;
+    if (W_out) for (int u = 0; u < 9; ++u) W_out[u] = W[u];
+    free(rows);
+    return 0;
 }
 
 /* E_self = -beta / sqrt(pi) * sum_i q_i^2 (Section 3.2.2, amortised self-energy). */
