@@ -59,6 +59,9 @@ typedef enum ewald_status {
     EWALD_E_UNSUPPORTED = -10   /* parameters outside what this build implements           */
 } ewald_status;
 
+/* Most particle types of the Lennard-Jones pair table (ewald_set_lj). */
+#define EWALD_LJ_MAX_TYPES 8
+
 typedef enum ewald_precision {
     /* FP64 everywhere on CUDA cores: real-space pairs, per-axis phase recurrences,
      * structure factors and back-scatter as FP64 products.  The plain FP64 GPU Ewald. */
@@ -174,6 +177,31 @@ int ewald_compute_phi_async(ewald_plan_t plan, int64_t n, const double *pos, con
 int ewald_compute_virial_async(ewald_plan_t plan, int64_t n, const double *pos,
                                const double *q, double *forces, double *virial_dev,
                                double *energy_dev, int parts, void *stream);
+
+/*
+ * ewald_set_lj - fuse short-range Lennard-Jones pairs into the real-space kernel of every
+ * later evaluation of this plan (the paper's NaCl benchmark adds such a repulsion to the
+ * Coulomb sum, Section 4; its parameters are not printed, so they are the caller's).
+ *   ntypes    0 (switch the pairs off; the other arguments are ignored) or
+ *             1..EWALD_LJ_MAX_TYPES
+ *   epsilon   host float64 [ntypes][ntypes], symmetric, >= 0 and finite (copied)
+ *   sigma     host float64 [ntypes][ntypes], symmetric, > 0 and finite (copied)
+ *   type_dev  dev int32 [n], the type of every particle in caller order, for the n of each
+ *             later call.  NOT copied: the caller keeps it alive and unchanged while the plan
+ *             evaluates with it (a type outside [0, ntypes) makes that evaluation report
+ *             EWALD_E_INVAL through its device status, with the type taken as 0).
+ * Every pair with 0 < d < r_c (the real-space cutoff, minimum image) adds the truncated and
+ * shifted potential u(d) = 4 eps [(sigma/d)^12 - (sigma/d)^6] - u_0 with u_0 its value at r_c,
+ * evaluated in the arithmetic of the real-space pairs (FP32 on the mixed and FP32 paths).
+ * The Lennard-Jones force is part of the returned forces, its energy part of energy[3] (the
+ * total potential energy) but not of energy[0..2], so E_LJ = energy[3] - energy[0] -
+ * energy[1] - energy[2]; likewise its virial is part of the sum tensor of
+ * ewald_compute_virial_async only.  The pairs are evaluated whenever EWALD_PART_REAL is
+ * selected, and ewald_md integrates with them.
+ * Synchronises the plan's streams.  Returns EWALD_E_INVAL for bad arguments.
+ */
+int ewald_set_lj(ewald_plan_t plan, int ntypes, const double *epsilon, const double *sigma,
+                 const int32_t *type_dev);
 
 /* ewald_status_sync - synchronise the plan's last stream and return (and clear) the
  * device-side status of the last evaluation: EWALD_OK, EWALD_E_NONNEUTRAL,

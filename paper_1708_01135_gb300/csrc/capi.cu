@@ -61,15 +61,18 @@ __device__ double block_sum_fixed(const double *__restrict__ x, int m, double *r
 }
 
 // a9: energies (one block, fixed order) and the neutrality check.
+// With elj_tile (Lennard-Jones pairs on), their energy is part of energy[3] only.
 __global__ void k_energy(int ntile, const double *__restrict__ e_tile, int nq,
                          const double *__restrict__ qpart, int R,
                          const double *__restrict__ e_row, double beta, int parts,
+                         const double *__restrict__ elj_tile,
                          double *__restrict__ energy, int *__restrict__ status)
 {
     __shared__ double red[256];
     __shared__ double qv[3][256];
     const double er = block_sum_fixed(e_tile, ntile, red);
     const double ek = block_sum_fixed(e_row, R, red);
+    const double elj = elj_tile ? block_sum_fixed(elj_tile, ntile, red) : 0.0;
     // charge sums: qpart is [nq][3]
     const int t = threadIdx.x;
     double qs = 0.0, qa = 0.0, q2 = 0.0;
@@ -93,8 +96,23 @@ __global__ void k_energy(int ntile, const double *__restrict__ e_tile, int nq,
         energy[0] = e_real;
         energy[1] = e_recip;
         energy[2] = e_self;
-        energy[3] = (e_real + e_recip) + e_self;
+        energy[3] = ((e_real + e_recip) + e_self) + elj;
     }
+}
+
+// Lennard-Jones types in sorted order; a type outside [0, ntypes) is replaced by 0 and
+// flagged.
+__global__ void k_gather_type(int64_t n, const int *__restrict__ perm, const int *__restrict__ type,
+                              int ntypes, int *__restrict__ tsort, int *__restrict__ status)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int t = type[perm[s]];
+    if (t < 0 || t >= ntypes) {
+        atomicOr(status, kStBadType);
+        t = 0;
+    }
+    tsort[s] = t;
 }
 
 // a9: F[perm[s]] = F_real[s] + F_recip[s] (selected parts), caller order.
@@ -169,15 +187,18 @@ k_recip_virial(int64_t nk, const int *__restrict__ kset, const double *__restric
 // Virial tensors (one block, fixed order): vir[0..8] real, vir[9..17] reciprocal,
 // vir[18..26] self (zero: the self energy does not depend on the positions or the box at
 // fixed beta), vir[27..35] their sum; each 3 x 3 row-major and symmetric.
+// With Lennard-Jones pairs (lj), their virial (rows 6-11 of vir_tile) is part of the sum
+// only.
 __global__ void k_virial(int ntile, const double *__restrict__ vir_tile, int64_t vcap,
-                         int nblk, const double *__restrict__ vir_part, int parts,
+                         int nblk, const double *__restrict__ vir_part, int parts, int lj,
                          double *__restrict__ vir)
 {
     __shared__ double red[256];
-    double wr[6], wk[6];
+    double wr[6], wk[6], wl[6];
     for (int c = 0; c < 6; ++c) {
         wr[c] = (parts & EWALD_PART_REAL) ? block_sum_fixed(vir_tile + c * vcap, ntile, red) : 0.0;
         wk[c] = (parts & EWALD_PART_RECIP) ? block_sum_fixed(vir_part + c * nblk, nblk, red) : 0.0;
+        wl[c] = lj ? block_sum_fixed(vir_tile + (6 + c) * vcap, ntile, red) : 0.0;
     }
     if (threadIdx.x == 0) {
         const int ix[9] = {0, 3, 4, 3, 1, 5, 4, 5, 2};   // (a, b) -> xx yy zz xy xz yz
@@ -185,7 +206,7 @@ __global__ void k_virial(int ntile, const double *__restrict__ vir_tile, int64_t
             vir[u] = wr[ix[u]];
             vir[9 + u] = wk[ix[u]];
             vir[18 + u] = 0.0;
-            vir[27 + u] = wr[ix[u]] + wk[ix[u]];
+            vir[27 + u] = (wr[ix[u]] + wk[ix[u]]) + wl[ix[u]];
         }
     }
 }
@@ -205,6 +226,7 @@ int status_from_bits(int bits)
     if (bits & kStNonFinite) return EWALD_E_NONFINITE;
     if (bits & kStTimeout) return EWALD_E_TIMEOUT;
     if (bits & kStNonNeutral) return EWALD_E_NONNEUTRAL;
+    if (bits & kStBadType) return EWALD_E_INVAL;
     return EWALD_OK;
 }
 
@@ -240,7 +262,7 @@ void free_workspace(Plan &p)
     void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
                     ws.tiles, ws.tile_count, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
                     ws.f_real, ws.f_recip, ws.e_tile, ws.qpart, ws.phi_real, ws.phi_recip,
-                    ws.vir_tile, ws.vir_part};
+                    ws.vir_tile, ws.vir_part, ws.type_sorted, ws.elj_tile};
     for (void *q : ptrs) pool_free(q, p.side_stream);
     free_recip_simt(p);
     if (uses_tc(p.precision)) free_recip_tc(p);
@@ -344,7 +366,9 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     EW_TRY(dmalloc(p, &ws.phi_recip, sizeof(double) * n));
     EW_TRY(dmalloc(p, &ws.f_recip, sizeof(double) * 3 * n));
     EW_TRY(dmalloc(p, &ws.e_tile, sizeof(double) * tiles));
-    EW_TRY(dmalloc(p, &ws.vir_tile, sizeof(double) * 6 * tiles));
+    EW_TRY(dmalloc(p, &ws.vir_tile, sizeof(double) * 12 * tiles));
+    EW_TRY(dmalloc(p, &ws.elj_tile, sizeof(double) * tiles));
+    EW_TRY(dmalloc(p, &ws.type_sorted, sizeof(int) * n));
     EW_TRY(dmalloc(p, &ws.vir_part, sizeof(double) * 6 * kVirBlocks));
     EW_TRY(dmalloc(p, &ws.qpart, sizeof(double) * 3 * qblocks));
     ws.cap_n = n;
@@ -370,10 +394,19 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     if (clear_status && (e = cudaMemsetAsync(p.d_status, 0, sizeof(int), st)) != cudaSuccess)
         return e;
     if ((e = launch_binning(p, n, pos, q, st)) != cudaSuccess) return e;
+    const bool lj = p.lj_ntypes > 0 && (parts & EWALD_PART_REAL);
+    if (lj) {
+        k_gather_type<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ws.perm, p.lj_type,
+                                                                   p.lj_ntypes, ws.type_sorted,
+                                                                   p.d_status);
+        p.launches += 1;
+    }
     prof_mark(p, kEvBinned, st);
     const int64_t tiles = real_tile_capacity(p, n);
     if ((e = cudaMemsetAsync(ws.e_tile, 0, sizeof(double) * tiles, st)) != cudaSuccess) return e;
-    if (vir && (e = cudaMemsetAsync(ws.vir_tile, 0, sizeof(double) * 6 * tiles, st)) != cudaSuccess)
+    if (vir && (e = cudaMemsetAsync(ws.vir_tile, 0, sizeof(double) * (lj ? 12 : 6) * tiles, st)) != cudaSuccess)
+        return e;
+    if (lj && (e = cudaMemsetAsync(ws.elj_tile, 0, sizeof(double) * tiles, st)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(p.e_recip_part, 0, sizeof(double) * p.e_recip_count, st)) != cudaSuccess) return e;
     const bool do_recip = parts & EWALD_PART_RECIP;
@@ -401,15 +434,15 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
         if ((e = cudaStreamWaitEvent(st, p.ev_join, 0)) != cudaSuccess) return e;
     }
     k_energy<<<1, 256, 0, st>>>((int)tiles, ws.e_tile, (int)((n + 255) / 256), ws.qpart,
-                                p.e_recip_count, p.e_recip_part, p.beta, parts, energy_dev,
-                                p.d_status);
+                                p.e_recip_count, p.e_recip_part, p.beta, parts,
+                                lj ? ws.elj_tile : nullptr, energy_dev, p.d_status);
     k_unsort<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ws.perm, ws.f_real, ws.f_recip,
                                                           parts, forces, ws.phi_real,
                                                           ws.phi_recip, ws.pg, p.beta, phi);
     p.launches += 2;
     if (vir) {
         k_virial<<<1, 256, 0, st>>>((int)tiles, ws.vir_tile, tiles, kVirBlocks, ws.vir_part,
-                                    parts, vir);
+                                    parts, lj ? 1 : 0, vir);
         p.launches += 1;
     }
     prof_mark(p, kEvFinal, st);
@@ -494,7 +527,8 @@ size_t plan_footprint(const Plan &p, int64_t n)
     b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * ncells;
     b += sizeof(int) * (2 * ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * ((size_t)nc * nc + 1);
     b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
-    b += sizeof(double) * 8 * (size_t)n + sizeof(double) * 7 * tiles + sizeof(double) * 3 * ((n + 255) / 256);
+    b += sizeof(double) * 8 * (size_t)n + sizeof(double) * 14 * tiles + sizeof(double) * 3 * ((n + 255) / 256);
+    b += sizeof(int) * (size_t)n;
     b += sizeof(double) * 6 * kVirBlocks;
     b += uses_tc(p.precision) ? recip_tc_bytes(p, n) : recip_simt_bytes(p, n);
     b += sizeof(double) * 3 * (size_t)p.nk + sizeof(int) * 3 * (size_t)p.nk + sizeof(RowInfo) * p.R;
@@ -666,6 +700,7 @@ static void destroy_plan(ewald_plan *h)
         pool_free(p.S_d, p.side_stream); pool_free(p.e_recip_part, p.side_stream);
         pool_free(p.g_d, p.side_stream);
         pool_free(p.energy_d, p.side_stream); pool_free(p.d_status, p.side_stream);
+        pool_free(p.lj_tab_d, p.side_stream);
         pool_free(p.ws.h_pos, p.side_stream); pool_free(p.ws.h_q, p.side_stream);
         pool_free(p.ws.h_f, p.side_stream);
         cudaStreamSynchronize(p.side_stream);
@@ -782,6 +817,48 @@ extern "C" int ewald_compute_virial_async(ewald_plan_t plan, int64_t n, const do
     }
     return cuda_status(evaluate(p, n, pos, q, forces, energy_dev, parts, st, true, nullptr,
                                 virial_dev));
+}
+
+extern "C" int ewald_set_lj(ewald_plan_t plan, int ntypes, const double *epsilon,
+                            const double *sigma, const int32_t *type_dev)
+{
+    if (!plan || ntypes < 0 || ntypes > EWALD_LJ_MAX_TYPES) return EWALD_E_INVAL;
+    Plan &p = plan->p;
+    if (ntypes == 0) {
+        if (p.last_stream) cudaStreamSynchronize(p.last_stream);
+        graph_reset(p);
+        p.lj_ntypes = 0;
+        p.lj_type = nullptr;
+        return EWALD_OK;
+    }
+    if (!epsilon || !sigma || !type_dev) return EWALD_E_INVAL;
+    double tab[EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES * 4];
+    for (int a = 0; a < ntypes; ++a)
+        for (int b = 0; b < ntypes; ++b) {
+            const double e = epsilon[a * ntypes + b], s = sigma[a * ntypes + b];
+            if (!(e >= 0) || !isfinite(e) || !(s > 0) || !isfinite(s)) return EWALD_E_INVAL;
+            if (e != epsilon[b * ntypes + a] || s != sigma[b * ntypes + a]) return EWALD_E_INVAL;
+            double *t = tab + 4 * (a * ntypes + b);
+            t[0] = s * s;
+            t[1] = 4.0 * e;
+            t[2] = 24.0 * e;
+            t[3] = 0.0;
+        }
+    // the graph of the last evaluation and a running evaluation may still read the old table
+    if (p.last_stream) cudaStreamSynchronize(p.last_stream);
+    cudaStreamSynchronize(p.side_stream);
+    graph_reset(p);
+    cudaError_t e = cudaSuccess;
+    if (!p.lj_tab_d) {
+        e = pool_alloc((void **)&p.lj_tab_d, sizeof(tab), p.side_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p.side_stream);
+        if (e != cudaSuccess) { p.lj_tab_d = nullptr; return cuda_status(e); }
+    }
+    e = cudaMemcpy(p.lj_tab_d, tab, sizeof(double) * 4 * ntypes * ntypes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_status(e);
+    p.lj_ntypes = ntypes;
+    p.lj_type = reinterpret_cast<const int *>(type_dev);
+    return EWALD_OK;
 }
 
 extern "C" int ewald_status_sync(ewald_plan_t plan)

@@ -31,6 +31,7 @@ enum : int {
     kStNonFinite = 1,
     kStTimeout = 2,
     kStNonNeutral = 4,
+    kStBadType = 8,      // a Lennard-Jones type outside [0, ntypes)
 };
 
 // Row of the reciprocal grid: (m_y, m_z), nxmax, and the offset of its first mode in the
@@ -63,7 +64,10 @@ struct Workspace {
     double *phi_recip = nullptr; // [n] reciprocal-space potential of every sorted particle
     double *f_recip = nullptr;   // [n][3]
     double *e_tile = nullptr;    // [max tiles] per-tile q_i phi_i sums
-    double *vir_tile = nullptr;  // [6][max tiles] per-tile real-space virial sums (xx yy zz xy xz yz)
+    double *vir_tile = nullptr;  // [12][max tiles] per-tile real-space virial sums (xx yy zz xy xz
+                                 // yz; rows 0-5 Coulomb, 6-11 Lennard-Jones)
+    int *type_sorted = nullptr;  // [n] Lennard-Jones types in sorted order
+    double *elj_tile = nullptr;  // [max tiles] per-tile Lennard-Jones energies
     double *vir_part = nullptr;  // [6][kVirBlocks] block sums of the reciprocal virial
     double *qpart = nullptr;     // [qblocks][3]: sum q, sum |q|, sum q^2 partials
     // staging for the host-buffer entry point
@@ -90,6 +94,10 @@ struct Plan {
     int ncells = 1;
     double cell_side = 0;
     int real_tile = 16;          // targets per real-space warp tile (16 or 32)
+    // Lennard-Jones pairs fused into the real-space kernel (off when lj_ntypes == 0)
+    int lj_ntypes = 0;
+    const int *lj_type = nullptr;    // caller-owned [n] types, caller order
+    double *lj_tab_d = nullptr;      // [T][T][4]: sigma^2, 4 eps, 24 eps, 0
     // reciprocal rows
     int R = 0;
     int64_t nk = 0;

@@ -119,20 +119,23 @@ __device__ __forceinline__ double exp_t(double x) { return exp(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 
-// Per-target sums of one warp lane: force / q_i, potential, and with kVir the six
-// independent entries of sum_j s_ij d_a d_b (xx, yy, zz, xy, xz, yz), s_ij d_vec being the
+// Per-target sums of one warp lane: force / q_i and potential; with kVir the six
+// independent entries (xx, yy, zz, xy, xz, yz) of sum_j s_ij d_a d_b, s_ij d_vec being the
 // force / q_i that partner j exerts, so that the target's share of the virial tensor is
-// 1/2 q_i times that sum.
-template <class T, bool kVir>
-struct PairAcc {
-    static constexpr bool vir = false;
-    T fx, fy, fz, phi;
-};
-template <class T>
-struct PairAcc<T, true> {
-    static constexpr bool vir = true;
-    T fx, fy, fz, phi;
-    T w[6];
+// 1/2 q_i times that sum; with kLJ the Lennard-Jones force and pair-energy sums (and with
+// both, the Lennard-Jones virial sums, whose share is 1/2 of the sum).
+// (The optional sums are empty base classes when off, so they take no registers or shared
+// memory in the variants that do not use them.)
+template <class T> struct AccBase { T fx, fy, fz, phi; };
+template <class T, bool on> struct AccVir {};
+template <class T> struct AccVir<T, true> { T w[6]; };
+template <class T, bool on> struct AccLJ {};
+template <class T> struct AccLJ<T, true> { T lj_f[4]; };
+template <class T, bool on> struct AccLJVir {};
+template <class T> struct AccLJVir<T, true> { T lj_w[6]; };
+template <class T, bool kVir, bool kLJ>
+struct PairAcc : AccBase<T>, AccVir<T, kVir>, AccLJ<T, kLJ>, AccLJVir<T, kVir && kLJ> {
+    static constexpr bool vir = kVir, lj = kLJ;
 };
 
 template <class A>
@@ -146,6 +149,14 @@ __device__ __forceinline__ void acc_shfl_add(A &a, int o)
 #pragma unroll
         for (int c = 0; c < 6; ++c) a.w[c] += __shfl_xor_sync(0xffffffffu, a.w[c], o);
     }
+    if constexpr (A::lj) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a.lj_f[c] += __shfl_xor_sync(0xffffffffu, a.lj_f[c], o);
+    }
+    if constexpr (A::vir && A::lj) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.lj_w[c] += __shfl_xor_sync(0xffffffffu, a.lj_w[c], o);
+    }
 }
 
 template <class A>
@@ -156,23 +167,76 @@ __device__ __forceinline__ void acc_add(A &a, const A &o)
 #pragma unroll
         for (int c = 0; c < 6; ++c) a.w[c] += o.w[c];
     }
+    if constexpr (A::lj) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a.lj_f[c] += o.lj_f[c];
+    }
+    if constexpr (A::vir && A::lj) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.lj_w[c] += o.lj_w[c];
+    }
 }
 
-// Writes the tile's share of the six virial sums, vir_tile[c * vcap + tile] = sum over the
-// tile's targets of 1/2 q_i w_c (a fixed shuffle tree over the lanes).
+// Fixed shuffle tree over the 32 lanes; lane 0 holds the warp's sum.
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The tile's shares of the virial sums: vir_tile[c * vcap + tile] = sum over the tile's
+// targets of 1/2 q_i w_c (c < 6), and with Lennard-Jones pairs 1/2 lj_w_c (rows 6..11); the
+// Lennard-Jones energy 1/2 sum of the pair energies into e_lj[tile].
 template <class A>
-__device__ __forceinline__ void acc_store_virial(const A &a, bool mine, double qi, int lane,
-                                                 double *__restrict__ vir_tile, int64_t vcap,
-                                                 int64_t tile)
+__device__ __forceinline__ void acc_store_tile(const A &a, bool mine, double qi, int lane,
+                                               double *__restrict__ vir_tile, int64_t vcap,
+                                               double *__restrict__ e_lj, int64_t tile)
 {
     if constexpr (A::vir) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            double v = mine ? 0.5 * qi * (double)a.w[c] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            const double v = warp_sum(mine ? 0.5 * qi * (double)a.w[c] : 0.0);
             if (lane == 0) vir_tile[c * vcap + tile] = v;
         }
     }
+    if constexpr (A::lj) {
+        const double v = warp_sum(mine ? 0.5 * (double)a.lj_f[3] : 0.0);
+        if (lane == 0) e_lj[tile] = v;
+    }
+    if constexpr (A::vir && A::lj) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const double v = warp_sum(mine ? 0.5 * (double)a.lj_w[c] : 0.0);
+            if (lane == 0) vir_tile[(6 + c) * vcap + tile] = v;
+        }
+    }
+}
+
+// Lennard-Jones arguments of the real-space kernels: sorted types, the [T][T] table of
+// (sigma^2, 4 eps, 24 eps, -) and the per-tile energy output.
+struct LJArgs {
+    const int *tsort;
+    const double *tab;
+    int ntypes;
+    double *e_tile;
+};
+
+// Shared-memory copy of the pair table with the shift u(r_c) of every pair type in the
+// fourth entry; every thread of the block takes part (call before any thread returns).
+template <class T, class T4>
+__device__ __forceinline__ void load_lj_table(T4 *ljs, const LJArgs &lj, double rc2)
+{
+    for (int u = threadIdx.x; u < lj.ntypes * lj.ntypes; u += blockDim.x) {
+        const double s2 = lj.tab[4 * u], e4 = lj.tab[4 * u + 1];
+        const double x2 = s2 / rc2, x6 = x2 * x2 * x2;
+        T4 c;
+        c.x = (T)s2;
+        c.y = (T)e4;
+        c.z = (T)lj.tab[4 * u + 2];
+        c.w = (T)(e4 * (x6 * x6 - x6));
+        ljs[u] = c;
+    }
+    __syncthreads();
 }
 
 // erfc(x) = exp(-x^2) * t * exp(P(t)), t = 1 / (1 + x / 2), x >= 0: the Chebyshev fit
@@ -195,10 +259,11 @@ __device__ __forceinline__ float erfc_from_gauss(float x, float g)
     return t * g * __expf(p);
 }
 
-// One candidate pair: target at the origin shifted by (xi, yi, zi), partner p.
+// One candidate pair: target at the origin shifted by (xi, yi, zi), partner p; with
+// Lennard-Jones pairs, ljrow is the target type's row of the table and tj the partner's type.
 template <class T, class T4, class A>
 __device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
-                                     T beta, T nb2, T two_b_rpi)
+                                     T beta, T nb2, T two_b_rpi, const T4 *ljrow, int tj)
 {
     const T dx = xi - p.x, dy = yi - p.y, dz = zi - p.z;   // r_i - r_j
     const T r2 = dx * dx + dy * dy + dz * dz;
@@ -218,6 +283,22 @@ __device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
         if constexpr (A::vir) {
             a.w[0] += sx * dx; a.w[1] += sy * dy; a.w[2] += sz * dz;
             a.w[3] += sx * dy; a.w[4] += sx * dz; a.w[5] += sy * dz;
+        }
+        if constexpr (A::lj) {
+            // u = 4 eps (x^12 - x^6) - u(r_c), x = sigma / r; -du/dr / r = 24 eps (2 x^12 - x^6) / r^2
+            const T4 c = ljrow[tj];
+            const T inv2 = rinv * rinv;
+            const T x2 = c.x * inv2, x6 = x2 * x2 * x2;
+            const T fl = c.z * (T(2) * x6 * x6 - x6) * inv2;
+            const T lx = fl * dx, ly = fl * dy, lz = fl * dz;
+            a.lj_f[0] += lx;
+            a.lj_f[1] += ly;
+            a.lj_f[2] += lz;
+            a.lj_f[3] += c.y * (x6 * x6 - x6) - c.w;
+            if constexpr (A::vir) {
+                a.lj_w[0] += lx * dx; a.lj_w[1] += ly * dy; a.lj_w[2] += lz * dz;
+                a.lj_w[3] += lx * dy; a.lj_w[4] += lx * dz; a.lj_w[5] += ly * dz;
+            }
         }
     }
 }
@@ -290,17 +371,18 @@ struct ChunkIter {
     }
 };
 
-template <class T, int kTile, bool kVir>
+template <class T, int kTile, bool kVir, bool kLJ>
 __global__ void __launch_bounds__(kWarps * 32)
 k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restrict__ key_sorted,
              const int *__restrict__ cell_start, const int2 *__restrict__ tiles,
              const int *__restrict__ tile_total, int nc, int w, T side, T rc2, T beta,
              T two_b_rpi, int split, double *__restrict__ f_out, double *__restrict__ phi_out,
              double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap,
-             int *__restrict__ status)
+             LJArgs lj, int *__restrict__ status)
 {
     using T4 = typename Vec4<T>::type;
-    using Acc = PairAcc<T, kVir>;
+    using Acc = PairAcc<T, kVir, kLJ>;
+    __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kWarps][2];
     __shared__ Acc xacc[kWarps][32];            // partial sums handed between split warps
@@ -315,6 +397,7 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         fence_mbar_init();
     }
     __syncwarp();
+    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2);
     // with split = 2 the two warps 2t and 2t + 1 of a block share a tile, each taking every
     // other stencil row; their sums are added (in that order) at the end
     const int part = warp % split;
@@ -332,6 +415,7 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     const bool valid = i <= last;
     const T4 pi = pl[valid ? i : last];
     const int cxi = key_sorted[valid ? i : last] % nc;
+    const T4 *ljrow = kLJ ? ljs + lj.tsort[valid ? i : last] * lj.ntypes : nullptr;
 
     ChunkIter it;
     it.w = w; it.nc = nc;
@@ -381,7 +465,9 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
                 const int jb = (cb > cur.g0 ? cb : cur.g0) - cur.g0;
                 const int je = (ce < cend ? ce : cend) - cur.g0;
                 const T xi = pi.x - T(u - cxi) * side;
-                for (int j = jb + g; j < je; j += kGroups) pair<T, T4>(acc, sb[j], xi, yi, zi, rc2, beta, nb2, two_b_rpi);
+                for (int j = jb + g; j < je; j += kGroups)
+                    pair<T, T4>(acc, sb[j], xi, yi, zi, rc2, beta, nb2, two_b_rpi, ljrow,
+                                kLJ ? lj.tsort[cur.g0 + j] : 0);
             }
             if (ce >= cend) break;
             cb = ce;
@@ -411,27 +497,33 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
     }
     const double qi = (double)pi.w;
     if (valid && g == 0) {
-        f_out[3 * (int64_t)i + 0] = qi * (double)acc.fx;
-        f_out[3 * (int64_t)i + 1] = qi * (double)acc.fy;
-        f_out[3 * (int64_t)i + 2] = qi * (double)acc.fz;
+        double f[3] = {qi * (double)acc.fx, qi * (double)acc.fy, qi * (double)acc.fz};
+        if constexpr (kLJ) {
+            f[0] += (double)acc.lj_f[0];
+            f[1] += (double)acc.lj_f[1];
+            f[2] += (double)acc.lj_f[2];
+        }
+        f_out[3 * (int64_t)i + 0] = f[0];
+        f_out[3 * (int64_t)i + 1] = f[1];
+        f_out[3 * (int64_t)i + 2] = f[2];
         phi_out[i] = (double)acc.phi;
     }
-    double e = (valid && g == 0) ? qi * (double)acc.phi : 0.0;
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    const double e = warp_sum((valid && g == 0) ? qi * (double)acc.phi : 0.0);
     if (lane == 0) e_tile[tile] = e;
-    acc_store_virial(acc, valid && g == 0, qi, lane, vir_tile, vcap, tile);
+    acc_store_tile(acc, valid && g == 0, qi, lane, vir_tile, vcap, lj.e_tile, tile);
 }
 
 // All pairs with the minimum image (boxes too small for a cell stencil): one tile of 32
 // targets per warp, every particle staged through the same double-buffered TMA path.
-template <class T, bool kVir>
+template <class T, bool kVir, bool kLJ>
 __global__ void __launch_bounds__(kWarps * 32)
 k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2, T beta,
                 T two_b_rpi, double *__restrict__ f_out, double *__restrict__ phi_out,
                 double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap,
-                int *__restrict__ status)
+                LJArgs lj, int *__restrict__ status)
 {
     using T4 = typename Vec4<T>::type;
+    __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kWarps][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -445,13 +537,15 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
         fence_mbar_init();
     }
     __syncwarp();
+    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2);
     const int tile = blockIdx.x * kWarps + warp;
     if (tile * 32 >= n) return;
     const int i = tile * 32 + lane;
     const bool valid = i < n;
     const T4 pi = pl[valid ? i : n - 1];
+    const T4 *ljrow = kLJ ? ljs + lj.tsort[valid ? i : n - 1] * lj.ntypes : nullptr;
     const T invL = T(1) / L;
-    PairAcc<T, kVir> acc{};
+    PairAcc<T, kVir, kLJ> acc{};
     const T nb2 = -beta * beta;
     uint32_t phase[2] = {0u, 0u};
     const int nchunks = (n + kCapAll - 1) / kCapAll;
@@ -482,7 +576,8 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
             // evaluate the pair at the minimum image: shift the partner, keep the target
             T4 pj = p;
             pj.x = pi.x - dx; pj.y = pi.y - dy; pj.z = pi.z - dz;
-            pair<T, T4>(acc, pj, pi.x, pi.y, pi.z, rc2, beta, nb2, two_b_rpi);
+            pair<T, T4>(acc, pj, pi.x, pi.y, pi.z, rc2, beta, nb2, two_b_rpi, ljrow,
+                        kLJ ? lj.tsort[c * kCapAll + j] : 0);
         }
         __syncwarp();
         b ^= 1;
@@ -494,38 +589,44 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
     }
     const double qi = (double)pi.w;
     if (valid) {
-        f_out[3 * (int64_t)i + 0] = qi * (double)acc.fx;
-        f_out[3 * (int64_t)i + 1] = qi * (double)acc.fy;
-        f_out[3 * (int64_t)i + 2] = qi * (double)acc.fz;
+        double f[3] = {qi * (double)acc.fx, qi * (double)acc.fy, qi * (double)acc.fz};
+        if constexpr (kLJ) {
+            f[0] += (double)acc.lj_f[0];
+            f[1] += (double)acc.lj_f[1];
+            f[2] += (double)acc.lj_f[2];
+        }
+        f_out[3 * (int64_t)i + 0] = f[0];
+        f_out[3 * (int64_t)i + 1] = f[1];
+        f_out[3 * (int64_t)i + 2] = f[2];
         phi_out[i] = (double)acc.phi;
     }
-    double e = valid ? qi * (double)acc.phi : 0.0;
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    const double e = warp_sum(valid ? qi * (double)acc.phi : 0.0);
     if (lane == 0) e_tile[tile] = e;
-    acc_store_virial(acc, valid, qi, lane, vir_tile, vcap, tile);
+    acc_store_tile(acc, valid, qi, lane, vir_tile, vcap, lj.e_tile, tile);
 }
 
-template <class T, bool kVir>
+template <class T, bool kVir, bool kLJ>
 cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, cudaStream_t st)
 {
     Workspace &ws = p.ws;
     double *vir = kVir ? ws.vir_tile : nullptr;
     const int64_t vcap = real_tile_capacity(p, n);
+    LJArgs lj{ws.type_sorted, p.lj_tab_d, p.lj_ntypes, ws.elj_tile};
     const size_t smem = (size_t)kWarps * 2 * (p.w == 0 ? kCapAll : kCap) * sizeof(typename Vec4<T>::type);
     const T beta = (T)p.beta, rc2 = (T)(p.rc * p.rc);
     const T tbr = (T)(2.0 * p.beta / sqrt(kPi));
     cudaError_t e;
     if (p.w == 0) {
-        e = cudaFuncSetAttribute(k_real_allpairs<T, kVir>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        auto kern = k_real_allpairs<T, kVir, kLJ>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int tiles = (int)((n + 31) / 32);
-        k_real_allpairs<T, kVir><<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(
-            pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap,
+        kern<<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(
+            pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap, lj,
             p.d_status);
     } else {
-        auto kern = p.real_tile == kTileDense ? k_real_cells<T, kTileDense, kVir>
-                                              : k_real_cells<T, kTileSparse, kVir>;
+        auto kern = p.real_tile == kTileDense ? k_real_cells<T, kTileDense, kVir, kLJ>
+                                              : k_real_cells<T, kTileSparse, kVir, kLJ>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int64_t tiles = real_tile_capacity(p, n);
@@ -534,10 +635,19 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         kern<<<(unsigned)((tiles * split + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
             pl, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc, p.nc, p.w,
             (T)p.cell_side, rc2, beta, tbr, split, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap,
-            p.d_status);
+            lj, p.d_status);
     }
     p.launches += 1;
     return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_real_p(Plan &p, int64_t n, const typename Vec4<T>::type *pl, cudaStream_t st,
+                          bool virial)
+{
+    const bool lj = p.lj_ntypes > 0;
+    if (virial) return lj ? launch_real_t<T, true, true>(p, n, pl, st) : launch_real_t<T, true, false>(p, n, pl, st);
+    return lj ? launch_real_t<T, false, true>(p, n, pl, st) : launch_real_t<T, false, false>(p, n, pl, st);
 }
 
 }  // namespace
@@ -558,11 +668,8 @@ int real_tile_for(int w, double cell_occupancy)
 
 cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st, bool virial)
 {
-    if (p.precision == EWALD_FP64)
-        return virial ? launch_real_t<double, true>(p, n, p.ws.pl64, st)
-                      : launch_real_t<double, false>(p, n, p.ws.pl64, st);
-    return virial ? launch_real_t<float, true>(p, n, p.ws.pl32, st)
-                  : launch_real_t<float, false>(p, n, p.ws.pl32, st);
+    if (p.precision == EWALD_FP64) return launch_real_p<double>(p, n, p.ws.pl64, st, virial);
+    return launch_real_p<float>(p, n, p.ws.pl32, st, virial);
 }
 
 }  // namespace ew

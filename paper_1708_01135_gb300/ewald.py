@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
                 "ewald_compute_async": (_i, [_p, _i64, _p, _p, _p, _p, _i, _p]),
                 "ewald_compute_phi_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
                 "ewald_compute_virial_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
+                "ewald_set_lj": (_i, [_p, _i, _p, _p, _p]),
                 "ewald_status_sync": (_i, [_p]),
                 "ewald_compute_host": (_i, [_p, _i64, _p, _p, _p, _p, _p]),
                 "ewald_plan_info": (_i, [_p, _p]),
@@ -227,6 +228,27 @@ class Ewald:
                                                 _dev_f64(virial, (4, 3, 3), "virial"),
                                                 _dev_f64(energy, (4,), "energy"), int(parts),
                                                 _stream_handle(stream)), "ewald_compute_virial_async")
+
+    def set_lj(self, epsilon=None, sigma=None, types=None):
+        """Fuse truncated and shifted Lennard-Jones pairs into the real-space kernel
+        (ewald_set_lj): epsilon and sigma symmetric [T, T] host arrays, types a CUDA int32
+        tensor [n] in particle order that must stay alive while the plan uses it.  No
+        arguments: switch the pairs off."""
+        import torch
+        if epsilon is None:
+            _check(lib().ewald_set_lj(self._h, 0, None, None, None), "ewald_set_lj")
+            self._lj_types = None
+            return
+        eps = np.ascontiguousarray(epsilon, dtype=np.float64)
+        sig = np.ascontiguousarray(sigma, dtype=np.float64)
+        if eps.ndim != 2 or eps.shape[0] != eps.shape[1] or sig.shape != eps.shape:
+            raise ValueError("epsilon and sigma must be square tables of one shape")
+        if not isinstance(types, torch.Tensor) or not types.is_cuda or types.dtype != torch.int32 \
+                or not types.is_contiguous():
+            raise TypeError("types must be a contiguous CUDA int32 tensor")
+        _check(lib().ewald_set_lj(self._h, int(eps.shape[0]), eps.ctypes.data, sig.ctypes.data,
+                                  types.data_ptr()), "ewald_set_lj")
+        self._lj_types = types      # keep the caller's tensor alive with the plan
 
     def status(self) -> int:
         """Synchronise and return the device-side status of the last evaluation."""
