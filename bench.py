@@ -6,7 +6,7 @@ one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload random_32768]
                   [--precision mixed|fp64|fp32|mixed_bf16] [--impl ours|reference]
-                  [--md STEPS [--dt DT]]
+                  [--md STEPS [--dt DT] [--lj] [--kT KT]]
 
 Timing: inputs resident in HBM; before every step a 512 MiB buffer is written to flush
 the L2 (129 MB); every step is bracketed by CUDA events on the launching stream and the
@@ -345,13 +345,24 @@ def run_md(args, rank, world, local):
     steps, dt = args.md, args.dt
     log = torch.empty((steps + 1, MD_RECORD), dtype=torch.float64, device=dev)
     ew = Ewald(L, beta, rc, kmax, args.precision)
+    lj_cfg = None
+    if args.lj:
+        # one Lennard-Jones type for every pair, sigma = the rock-salt spacing and eps that
+        # about balances the Madelung pressure there (reduced NaCl-like units)
+        lj_cfg = {"types": 1, "sigma": 1.0, "epsilon": 0.0182, "cutoff": rc, "shifted": True}
+        t_types = torch.zeros(n, dtype=torch.int32, device=dev)
+        ew.set_lj(np.full((1, 1), lj_cfg["epsilon"]), np.full((1, 1), lj_cfg["sigma"]), t_types)
+    v0 = np.zeros((n, 3))
+    if args.kT > 0:
+        v0 = np.random.default_rng(2024).normal(0.0, np.sqrt(args.kT), size=(n, 3))
+        v0 -= v0.mean(axis=0)
     clocks = ClockSampler(local)
     clocks.start()
     t_warm = time.perf_counter()
     w = 0
     while w < args.warmup or time.perf_counter() - t_warm < 0.5:
         tp = torch.tensor(pos, device=dev)
-        tv = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+        tv = torch.tensor(v0, device=dev)
         ew.md(tp, tv, tq, F, dt, 1)
         w += 1
         torch.cuda.synchronize()
@@ -362,7 +373,7 @@ def run_md(args, rank, world, local):
     _, per_eval = ew.profile(-1)
     ew.profile(0)
     tp = torch.tensor(pos, device=dev)
-    tv = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+    tv = torch.tensor(v0, device=dev)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
@@ -388,7 +399,7 @@ def run_md(args, rank, world, local):
             "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "L": L, "r_c": rc, "beta": beta,
-                       "k_max": kmax, "dt": dt, "mass": 1.0, "v0": 0.0,
+                       "k_max": kmax, "dt": dt, "mass": 1.0, "kT0": args.kT, "lj": lj_cfg,
                        "precision": args.precision,
                        "l2": "not flushed: the MD state stays resident from step to step",
                        "parallelism": f"replicas x{world}"},
@@ -460,6 +471,8 @@ def main():
                     help="time the FP64 GPU path beside the line up to this N")
     ap.add_argument("--md", type=int, default=0, help="velocity-Verlet MD steps (0: single evaluations)")
     ap.add_argument("--dt", type=float, default=1e-3)
+    ap.add_argument("--lj", action="store_true", help="MD with Lennard-Jones pairs (sigma 1, eps 0.0182)")
+    ap.add_argument("--kT", type=float, default=0.0, help="MD initial Maxwell velocities (unit masses)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
