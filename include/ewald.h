@@ -203,6 +203,27 @@ int ewald_compute_virial_async(ewald_plan_t plan, int64_t n, const double *pos,
 int ewald_set_lj(ewald_plan_t plan, int ntypes, const double *epsilon, const double *sigma,
                  const int32_t *type_dev);
 
+/*
+ * ewald_set_spme - compute the reciprocal part of every later evaluation of this plan by
+ * smooth particle-mesh Ewald (Essmann et al., J. Chem. Phys. 103, 8577 (1995)), the
+ * successor that the paper names for large N (Sections 1 and 5), instead of the classical
+ * sum over the k set of Eq. 3.  The real-space and self parts, the energies layout, the
+ * forces, potentials, virial, Lennard-Jones pairs and ewald_md are unchanged; k_max is not
+ * used while SPME is on, and ewald_structure_factor returns EWALD_E_UNSUPPORTED.
+ *   K      mesh points per side (even order <= K <= 1024), or 0 to return to the classical sum
+ *   order  B-spline order p: 4, 6, 8, 10 or 12
+ * Charges are spread with p^3 weights per particle onto a fixed-point mesh (64-bit integer
+ * atomics, 2^-36 resolution), so results repeat bit for bit; an evaluation with
+ * sum |q| >= 2^26 reports EWALD_E_UNSUPPORTED (the mesh could overflow).  The mesh, its
+ * transforms (cuFFT) and the particle-side splines are FP32 on the mixed and FP32 plans,
+ * FP64 on the FP64 plan.  The error of the mesh approximation falls with K and p (about
+ * (beta L / (pi K))^p); it adds to the real-space and k-space truncation errors.
+ * Synchronises the plan's streams; allocates the mesh (about 8 + 4 (or 8) x 2 bytes per
+ * mesh point) and two cuFFT plans.  Returns EWALD_E_INVAL, EWALD_E_NOMEM,
+ * EWALD_E_UNSUPPORTED (cuFFT plan failure) or EWALD_E_CUDA.
+ */
+int ewald_set_spme(ewald_plan_t plan, int K, int order);
+
 /* ewald_status_sync - synchronise the plan's last stream and return (and clear) the
  * device-side status of the last evaluation: EWALD_OK, EWALD_E_NONNEUTRAL,
  * EWALD_E_NONFINITE, EWALD_E_TIMEOUT or EWALD_E_CUDA. */

@@ -2,7 +2,8 @@
 
 Every translation unit under csrc/ is compiled in parallel to an object file under
 ``_build/`` (git-ignored), then linked into ``paper_1708_01135_gb300/libewald.so``.  The
-CUDA runtime is linked statically, so the library needs only the driver at run time.
+CUDA runtime is linked statically; the one shared dependency is cuFFT (the SPME mesh
+transforms), found through an rpath to the toolkit's lib64.
 
     python -m paper_1708_01135_gb300.build          # build (incremental)
     python -m paper_1708_01135_gb300.build --force  # rebuild everything
@@ -57,7 +58,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + [
+            "-L", cudalib, "-lcufft", "-Xlinker", f"-rpath,{cudalib}", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

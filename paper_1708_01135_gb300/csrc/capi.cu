@@ -65,7 +65,7 @@ __device__ double block_sum_fixed(const double *__restrict__ x, int m, double *r
 __global__ void k_energy(int ntile, const double *__restrict__ e_tile, int nq,
                          const double *__restrict__ qpart, int R,
                          const double *__restrict__ e_row, double beta, int parts,
-                         const double *__restrict__ elj_tile,
+                         const double *__restrict__ elj_tile, int spme,
                          double *__restrict__ energy, int *__restrict__ status)
 {
     __shared__ double red[256];
@@ -90,6 +90,7 @@ __global__ void k_energy(int ntile, const double *__restrict__ e_tile, int nq,
     if (t == 0) {
         qs = qv[0][0]; qa = qv[1][0]; q2 = qv[2][0];
         if (fabs(qs) > 1e-10 * qa) atomicOr(status, kStNonNeutral);
+        if (spme && !(qa < kSpmeMaxAbsCharge)) atomicOr(status, kStRange);
         const double e_real = (parts & EWALD_PART_REAL) ? 0.5 * er : 0.0;
         const double e_recip = (parts & EWALD_PART_RECIP) ? ek : 0.0;
         const double e_self = (parts & EWALD_PART_SELF) ? -beta / sqrt(kPi) * q2 : 0.0;
@@ -227,6 +228,7 @@ int status_from_bits(int bits)
     if (bits & kStTimeout) return EWALD_E_TIMEOUT;
     if (bits & kStNonNeutral) return EWALD_E_NONNEUTRAL;
     if (bits & kStBadType) return EWALD_E_INVAL;
+    if (bits & kStRange) return EWALD_E_UNSUPPORTED;
     return EWALD_OK;
 }
 
@@ -410,15 +412,18 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
         return e;
     if ((e = cudaMemsetAsync(p.e_recip_part, 0, sizeof(double) * p.e_recip_count, st)) != cudaSuccess) return e;
     const bool do_recip = parts & EWALD_PART_RECIP;
-    if (do_recip && uses_tc(p.precision) && (e = launch_recip_tc_operands(p, n, st)) != cudaSuccess)
+    const bool spme = p.spme != nullptr;
+    if (do_recip && !spme && uses_tc(p.precision) &&
+        (e = launch_recip_tc_operands(p, n, st)) != cudaSuccess)
         return e;
     if (do_recip) {
         if ((e = cudaEventRecord(p.ev_fork, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(p.side_stream, p.ev_fork, 0)) != cudaSuccess) return e;
-        e = uses_tc(p.precision) ? launch_recip_tc(p, n, p.side_stream)
-                                 : launch_recip_simt(p, n, p.side_stream);
+        e = spme ? launch_recip_spme(p, n, p.side_stream)
+                 : uses_tc(p.precision) ? launch_recip_tc(p, n, p.side_stream)
+                                        : launch_recip_simt(p, n, p.side_stream);
         if (e != cudaSuccess) return e;
-        if (vir) {
+        if (vir && !spme) {   // (the SPME spectrum pass writes its own virial partials)
             k_recip_virial<<<kVirBlocks, 256, 0, p.side_stream>>>(
                 p.nk, p.kset_d, p.g_d, p.S_d, 2.0 * kPi / p.L, 0.25 / (p.beta * p.beta),
                 ws.vir_part);
@@ -433,9 +438,13 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     if (do_recip) {
         if ((e = cudaStreamWaitEvent(st, p.ev_join, 0)) != cudaSuccess) return e;
     }
+    int erc = p.e_recip_count;
+    const double *erp = p.e_recip_part;
+    if (spme) erp = spme_energy_parts(p, &erc);
     k_energy<<<1, 256, 0, st>>>((int)tiles, ws.e_tile, (int)((n + 255) / 256), ws.qpart,
-                                p.e_recip_count, p.e_recip_part, p.beta, parts,
-                                lj ? ws.elj_tile : nullptr, energy_dev, p.d_status);
+                                erc, erp, p.beta, parts,
+                                lj ? ws.elj_tile : nullptr, (spme && do_recip) ? 1 : 0,
+                                energy_dev, p.d_status);
     k_unsort<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ws.perm, ws.f_real, ws.f_recip,
                                                           parts, forces, ws.phi_real,
                                                           ws.phi_recip, ws.pg, p.beta, phi);
@@ -471,7 +480,8 @@ cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, dou
     if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return e;
     const bool repeat = key == p.last_key;
     p.last_key = key;
-    if (p.prof || !p.graph_stream || cap != cudaStreamCaptureStatusNone || !repeat)
+    // (SPME evaluations run directly: their transforms are library calls)
+    if (p.prof || !p.graph_stream || cap != cudaStreamCaptureStatusNone || !repeat || p.spme)
         return pipeline(p, n, pos, q, forces, energy_dev, parts, st, clear_status, phi, vir);
     if ((e = cudaEventRecord(p.ev_gin, st)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(p.graph_stream, p.ev_gin, 0)) != cudaSuccess) return e;
@@ -706,6 +716,7 @@ static void destroy_plan(ewald_plan *h)
         cudaStreamSynchronize(p.side_stream);
     }
     graph_reset(p);
+    spme_free(p);
     if (p.h_status) cudaFreeHost(p.h_status);
     if (p.side_stream) cudaStreamDestroy(p.side_stream);
     if (p.graph_stream) cudaStreamDestroy(p.graph_stream);
@@ -861,6 +872,16 @@ extern "C" int ewald_set_lj(ewald_plan_t plan, int ntypes, const double *epsilon
     return EWALD_OK;
 }
 
+extern "C" int ewald_set_spme(ewald_plan_t plan, int K, int order)
+{
+    if (!plan || K < 0) return EWALD_E_INVAL;
+    Plan &p = plan->p;
+    if (p.last_stream) cudaStreamSynchronize(p.last_stream);
+    if (p.side_stream) cudaStreamSynchronize(p.side_stream);
+    graph_reset(p);
+    return spme_set(p, K, order);
+}
+
 extern "C" int ewald_status_sync(ewald_plan_t plan)
 {
     if (!plan) return EWALD_E_INVAL;
@@ -992,6 +1013,7 @@ extern "C" int ewald_structure_factor(ewald_plan_t plan, double *S_dev, void *st
 {
     if (!plan || !S_dev) return EWALD_E_INVAL;
     const Plan &p = plan->p;
+    if (p.spme) return EWALD_E_UNSUPPORTED;
     return cuda_status(cudaMemcpyAsync(S_dev, p.S_d, sizeof(double) * 2 * p.nk,
                                        cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
 }

@@ -32,7 +32,12 @@ enum : int {
     kStTimeout = 2,
     kStNonNeutral = 4,
     kStBadType = 8,      // a Lennard-Jones type outside [0, ntypes)
+    kStRange = 16,       // sum |q| beyond the range of the SPME fixed-point charge mesh
 };
+
+// Largest sum |q| for which no point of the SPME fixed-point mesh (2^-36 resolution in a
+// signed 64-bit integer) can overflow: every particle adds at most |q| to a point.
+constexpr double kSpmeMaxAbsCharge = 67108864.0;   // 2^26
 
 // Row of the reciprocal grid: (m_y, m_z), nxmax, and the offset of its first mode in the
 // K_half ordering.
@@ -140,6 +145,8 @@ struct Plan {
     Workspace ws;
     // tensor-core path state (allocated lazily)
     void *tc = nullptr;
+    // smooth particle-mesh Ewald state (ewald_set_spme); the reciprocal part uses it when set
+    void *spme = nullptr;
     // profiling: events at stage boundaries (see ewald_profile), kernel launch counter
     bool prof = false;
     bool prof_valid = false;
@@ -182,6 +189,13 @@ cudaError_t alloc_recip_tc(Plan &p, int64_t n);
 size_t recip_tc_bytes(const Plan &p, int64_t n);
 int recip_tc_energy_parts(const Plan &p);   // entries of the partial reciprocal energies
 void free_recip_tc(Plan &p);
+// Smooth particle-mesh Ewald reciprocal part into ws.f_recip / ws.phi_recip, its energy
+// partials (spme_energy_parts) and virial partials (ws.vir_part).
+int spme_set(Plan &p, int K, int order);     // K = 0: back to the classical sum
+void spme_free(Plan &p);
+cudaError_t launch_recip_spme(Plan &p, int64_t n, cudaStream_t st);
+const double *spme_energy_parts(const Plan &p, int *count);
+size_t spme_bytes(const Plan &p);
 // One whole evaluation on `st` (grows the workspaces for n first; n > 0).  With
 // clear_status false the plan's device status keeps the bits of earlier evaluations, so that
 // a sequence of evaluations reports every failure at the next ewald_status_sync.

@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
                 "ewald_compute_phi_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
                 "ewald_compute_virial_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
                 "ewald_set_lj": (_i, [_p, _i, _p, _p, _p]),
+                "ewald_set_spme": (_i, [_p, _i, _i]),
                 "ewald_status_sync": (_i, [_p]),
                 "ewald_compute_host": (_i, [_p, _i64, _p, _p, _p, _p, _p]),
                 "ewald_plan_info": (_i, [_p, _p]),
@@ -249,6 +250,11 @@ class Ewald:
         _check(lib().ewald_set_lj(self._h, int(eps.shape[0]), eps.ctypes.data, sig.ctypes.data,
                                   types.data_ptr()), "ewald_set_lj")
         self._lj_types = types      # keep the caller's tensor alive with the plan
+
+    def set_spme(self, K: int = 0, order: int = 6):
+        """Reciprocal part by smooth particle-mesh Ewald on a K^3 mesh with B-splines of the
+        given even order (ewald_set_spme); K = 0 returns to the classical k-space sum."""
+        _check(lib().ewald_set_spme(self._h, int(K), int(order)), "ewald_set_spme")
 
     def status(self) -> int:
         """Synchronise and return the device-side status of the last evaluation."""
