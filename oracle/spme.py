@@ -99,30 +99,42 @@ def _weights(pos, L, K, p):
     return np.mod(k, K), bspline(p, t), bspline_deriv(p, t)
 
 
-def charge_mesh(pos, q, L, K, p) -> np.ndarray:
-    """Q(k) on the K^3 mesh."""
+def charge_mesh(pos, q, L, K, p, block: int = 4096) -> np.ndarray:
+    """Q(k) on the K^3 mesh: every particle adds q_i M_p M_p M_p to its p^3 points (in
+    blocks of particles, each an unbuffered np.add.at over their flattened point indices)."""
     idx, w, _ = _weights(pos, L, K, p)
-    Q = np.zeros((K, K, K))
-    for i in range(len(q)):
-        wq = q[i] * w[i, 0][:, None, None] * w[i, 1][None, :, None] * w[i, 2][None, None, :]
-        np.add.at(Q, np.ix_(idx[i, 0], idx[i, 1], idx[i, 2]), wq)
-    return Q
+    q = np.asarray(q, dtype=np.float64)
+    Q = np.zeros(K * K * K)
+    for s in range(0, len(q), block):
+        e = min(len(q), s + block)
+        wq = (q[s:e, None, None, None] * w[s:e, 0][:, :, None, None] *
+              w[s:e, 1][:, None, :, None] * w[s:e, 2][:, None, None, :])
+        flat = ((idx[s:e, 0][:, :, None, None] * K + idx[s:e, 1][:, None, :, None]) * K +
+                idx[s:e, 2][:, None, None, :])
+        np.add.at(Q, flat.ravel(), wq.ravel())
+    return Q.reshape(K, K, K)
 
 
-def recip(pos, q, L, beta, K, p):
-    """SPME reciprocal part: dict with E, F [n, 3], phi [n], W [3, 3], Q, phi_mesh."""
+def recip(pos, q, L, beta, K, p, sub=None, Q=None):
+    """SPME reciprocal part: dict with E, F [n, 3], phi [n], W [3, 3], Q, phi_mesh.  With
+    `sub` (particle indices) F and phi hold only those particles, in that order; the mesh
+    still takes every particle.  Q, if given, is charge_mesh(pos, q, L, K, p) computed
+    before."""
     _check(K, p)
     q = np.asarray(q, dtype=np.float64)
     G = influence(K, p, L, beta)
-    Q = charge_mesh(pos, q, L, K, p)
+    if Q is None:
+        Q = charge_mesh(pos, q, L, K, p)
     FQ = np.fft.fftn(Q)                     # conj(F(Q)) for real Q; |.|^2 is the same
     A = G * np.abs(FQ) ** 2
     E = 0.5 * float(A.sum())
     phi_mesh = np.real(np.fft.ifftn(G * FQ)) * K ** 3
-    idx, w, dw = _weights(pos, L, K, p)
-    n = len(q)
+    sel = np.arange(len(q)) if sub is None else np.asarray(sub)
+    idx, w, dw = _weights(np.asarray(pos)[sel], L, K, p)
+    n = len(sel)
     F = np.zeros((n, 3))
     phi = np.zeros(n)
+    qs = q[sel]
     for i in range(n):
         P = phi_mesh[np.ix_(idx[i, 0], idx[i, 1], idx[i, 2])]
         wx, wy, wz = w[i]
@@ -131,7 +143,7 @@ def recip(pos, q, L, beta, K, p):
         g = np.array([np.einsum("a,b,c,abc->", dx, wy, wz, P),
                       np.einsum("a,b,c,abc->", wx, dy, wz, P),
                       np.einsum("a,b,c,abc->", wx, wy, dz, P)])
-        F[i] = -q[i] * (K / L) * g
+        F[i] = -qs[i] * (K / L) * g
     s = _signed(K) / L
     M = [s[:, None, None] + 0 * s[None, :, None] + 0 * s[None, None, :],
          0 * s[:, None, None] + s[None, :, None] + 0 * s[None, None, :],

@@ -87,3 +87,17 @@ def test_potential_energy_identity_and_mesh_shift():
     # an odd order is refused (its Euler spline vanishes at m = K/2)
     with pytest.raises(ValueError):
         spme.recip(pos, q, L, beta, K, 5)
+
+
+def test_subset_and_blocked_mesh_match_the_whole():
+    """Forces of a particle subset equal those rows of the full evaluation, and the charge
+    mesh does not depend on how many particles are added per block (one point at a time per
+    particle, in particle order, either way)."""
+    pos, q, L = W.random_neutral(300, density=1.0, hard_core=0.8, seed=41)
+    full = spme.recip(pos, q, L, 1.1, 20, 6)
+    sub = np.array([7, 3, 250, 0])
+    part = spme.recip(pos, q, L, 1.1, 20, 6, sub=sub)
+    assert np.array_equal(part["F"], full["F"][sub])
+    assert np.array_equal(part["phi"], full["phi"][sub])
+    assert part["E"] == full["E"]
+    assert np.array_equal(spme.charge_mesh(pos, q, L, 20, 6, block=1), full["Q"])
