@@ -6,7 +6,7 @@ one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload random_32768]
                   [--precision mixed|fp64|fp32|mixed_bf16] [--impl ours|reference]
-                  [--md STEPS [--dt DT] [--lj] [--kT KT]]
+                  [--md STEPS [--dt DT] [--lj] [--kT KT]] [--spme auto|K,p [--spme-rc RC]]
 
 Timing: inputs resident in HBM; before every step a 512 MiB buffer is written to flush
 the L2 (129 MB); every step is bracketed by CUDA events on the launching stream and the
@@ -42,6 +42,37 @@ WORKLOADS = {
     "rocksalt_262144": (W.rocksalt_262144, None),
     "random_2097152": (W.random_2097152, None),
 }
+
+
+# Smooth particle-mesh Ewald: the mesh spacing h = L / K that keeps the mesh error of the
+# forces at about 1e-6 of the RMS force, as beta * h for each B-spline order p.  Calibrated
+# against the FP64 oracle (SPME reciprocal forces against the converged classical sum, random
+# ionic systems at density 1, beta 0.93 and 1.2): the error depends on beta * h and p only.
+SPME_BETA_H = {6: 0.22, 8: 0.33, 10: 0.39, 12: 0.43}
+
+
+def fft_size(k):
+    """Smallest even K >= k whose prime factors are 2, 3, 5 and 7 (sizes cuFFT handles with
+    its fastest kernels)."""
+    k = max(4, int(math.ceil(k)))
+    while True:
+        if k % 2 == 0:
+            r = k
+            for f in (2, 3, 5, 7):
+                while r % f == 0:
+                    r //= f
+            if r == 1:
+                return k
+        k += 1
+
+
+def spme_params(spec, beta, L):
+    """(K, p) from --spme: 'K,p', or 'auto' / 'auto:p' (mesh from SPME_BETA_H)."""
+    if spec.startswith("auto"):
+        p = int(spec.split(":")[1]) if ":" in spec else 8
+        return fft_size(beta * L / SPME_BETA_H[p]), p
+    K, p = (int(x) for x in spec.split(","))
+    return K, p
 
 
 def params_for(workload, n, L):
@@ -121,6 +152,12 @@ def simt_flops(n, kmax):
     fwd = 2.0 * 4 * R * (kmax + 1) * n
     back = 2.0 * n * (2 * R) * 3 * (2 * kmax + 1)
     return fwd, back
+
+
+def fp32_peak(pk):
+    """FP32 CUDA-core peak in TFLOP/s: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x the maximum
+    SM clock (MEASURED_PEAKS.json's sm_max_mhz, else 2070 MHz)."""
+    return 152 * 128 * 2 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
 
 
 def peaks():
@@ -240,6 +277,32 @@ def oracle_sample(pos, q, L, beta, rc, kmax, n_targets, seed=0, S_given=None,
     t2 = time.perf_counter()
     full = t_s + (t2 - t1) * n / len(sub)
     return full, (t2 - t0), len(sub), sub, Fr + Fk, note
+
+
+def spme_oracle_sample(pos, q, L, beta, rc, K, order, n_targets, seed=0):
+    """Time the FP64 oracle's SPME evaluation on a bounded sample and scale it: the charge
+    mesh of all particles and its transforms once, then real-space and SPME reciprocal forces
+    of `n_targets` random particles (the full time is t_mesh + (N / n_targets) t_targets).
+    Returns (full time, CPU seconds spent, targets, target indices, oracle forces, note)."""
+    import oracle
+    from oracle import spme as ospme
+    n = len(q)
+    rng = np.random.default_rng(seed)
+    sub = np.sort(rng.choice(n, size=min(n_targets, n), replace=False))
+    t0 = time.perf_counter()
+    Q = ospme.charge_mesh(pos, q, L, K, order)
+    t1 = time.perf_counter()
+    ospme.recip(pos, q, L, beta, K, order, sub=sub[:1], Q=Q)     # transforms + one target
+    t2 = time.perf_counter()
+    _, Fr, _ = oracle.real(pos, q, L, beta, rc, sub=sub)
+    Fk = ospme.recip(pos, q, L, beta, K, order, sub=sub, Q=Q)["F"]
+    t3 = time.perf_counter()
+    t_once = (t1 - t0) + (t2 - t1)                  # mesh and transforms
+    t_targets = max((t3 - t2) - (t2 - t1), 0.0)     # per-target work of all the targets
+    full = t_once + t_targets * n / len(sub)
+    note = (f"SPME oracle: charge mesh of all {n} particles and its transforms on a {K}^3 mesh "
+            f"(p = {order})")
+    return full, (t3 - t0), len(sub), sub, Fr + Fk, note
 
 
 # ---- main ---------------------------------------------------------------------------------
@@ -473,6 +536,10 @@ def main():
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--lj", action="store_true", help="MD with Lennard-Jones pairs (sigma 1, eps 0.0182)")
     ap.add_argument("--kT", type=float, default=0.0, help="MD initial Maxwell velocities (unit masses)")
+    ap.add_argument("--spme", default="", help="reciprocal part by smooth particle-mesh Ewald: "
+                    "'auto' (order 8), 'auto:P' or 'K,P'")
+    ap.add_argument("--spme-rc", type=float, default=0.0,
+                    help="real-space cutoff of the SPME line (beta from the tuner at this r_c)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -495,6 +562,19 @@ def main():
     pos, q, L = gen()
     n = len(q)
     rc, beta, kmax = params_for(args.workload, n, L)
+    spme = None
+    if args.spme:
+        from paper_1708_01135_gb300 import tune
+        if args.spme_rc:
+            # beta r_c = sqrt(-ln tol), as the tuner's rule; the classical k_max at this beta
+            # (for the accuracy check) may exceed the library's limit, in which case the plan
+            # carries an unused k_max and the check is skipped
+            rc = args.spme_rc
+            beta = math.sqrt(-math.log(TOL)) / rc
+            kmax = int(math.ceil(math.sqrt(-math.log(TOL)) * beta * L / math.pi))
+        K, order = spme_params(args.spme, beta, L)
+        spme = {"K": K, "order": order, "beta_h": beta * L / K, "classical_k_max": kmax}
+        kmax = min(kmax, 127)
     dev = torch.device("cuda", local)
     tp = torch.tensor(pos, device=dev)
     tq = torch.tensor(q, device=dev)
@@ -503,6 +583,8 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ew = Ewald(L, beta, rc, kmax, args.precision)
+    if spme:
+        ew.set_spme(spme["K"], spme["order"])
 
     # the clock sampler runs through the warm-up (at least ~0.5 s of back-to-back steps) and
     # the timed steps, so that its samples see the GPU under this workload's load
@@ -570,7 +652,22 @@ def main():
     tc = args.precision in ("mixed", "mixed_bf16")
     back_ms = float(np.median(stage["recip_back"]))
     fwd_ms = float(np.median(stage["recip_forward"]))
-    if tc:
+    if spme:
+        # the dominant kernel of an SPME step is the real-space pair kernel (FP32 on the mixed
+        # path): 40 flop per pair evaluation within r_c, each pair evaluated from both sides
+        # (no atomics), N (4 pi / 3) r_c^3 rho pairs per side for density rho
+        real_ms = float(np.median(stage["real"]))
+        pairs = n * (4.0 * math.pi / 3.0) * rc ** 3 * (n / L ** 3)
+        achieved = 40.0 * pairs / (real_ms * 1e-3) / 1e12
+        fp32 = args.precision != "fp64"
+        peak = fp32_peak(pk) if fp32 else 1.25
+        roof = {"bound": "alu", "kernel": "real-space pairs (a4)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "work": "40 flop per pair evaluation within r_c (both sides of every pair)",
+                "peak_kind": ("FP32 CUDA-core rate from unit counts and the maximum SM clock "
+                              "(152 SMs x 128 lanes x 2 flop x 2.07 GHz)" if fp32 else
+                              "nominal FP64 rate")}
+    elif tc:
         fwd_f, back_f = tensor_flops(n, kmax)
         achieved = back_f / (back_ms * 1e-3) / 1e12
         peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
@@ -614,19 +711,34 @@ def main():
     accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        Sg = ew.structure_factor()
-        full, wall, nt, sub, Fo, note = oracle_sample(pos, q, L, beta, rc, kmax, args.cpu_targets,
-                                                      S_given=Sg)
+        Fg = hf                 # forces of the last end-to-end evaluation (same input)
+        if spme:
+            full, wall, nt, sub, Fo, note = spme_oracle_sample(pos, q, L, beta, rc, spme["K"],
+                                                               spme["order"], args.cpu_targets)
+            ref_note = ("FP64 oracle at the same (beta, r_c, K, p): real-space pairs plus "
+                        "the SPME reciprocal part; arithmetic error of this path (the mesh "
+                        "error of (K, p) is the separate spme_vs_classical figure)")
+        else:
+            full, wall, nt, sub, Fo, note = oracle_sample(pos, q, L, beta, rc, kmax,
+                                                          args.cpu_targets,
+                                                          S_given=ew.structure_factor())
+            ref_note = ("FP64 oracle at the same (beta, r_c, k_max): arithmetic error of this "
+                        "path; the truncation error of the parameters is stated separately")
         cpu = {"value": n / full, "unit": "particles/s", "cores": oracle.num_threads(),
                "kind": "oracle", "sample": f"{note}; forces of {nt} random particles, scaled "
                                            f"to {n} ({wall:.1f} s of CPU work)"}
-        Fg = hf[sub]        # forces of the last end-to-end evaluation (same input)
-        accuracy = {"rel_force_rms_vs_oracle": float(np.sqrt(((Fg - Fo) ** 2).sum() / (Fo ** 2).sum())),
-                    "particles": int(nt),
-                    "reference": "FP64 oracle at the same (beta, r_c, k_max): arithmetic error "
-                                 "of this path; the truncation error of the parameters is "
-                                 "stated separately",
-                    "oracle_sample": note}
+        accuracy = {"rel_force_rms_vs_oracle": float(np.sqrt(((Fg[sub] - Fo) ** 2).sum() /
+                                                             (Fo ** 2).sum())),
+                    "particles": int(nt), "reference": ref_note, "oracle_sample": note}
+    if rank == 0 and spme and spme["classical_k_max"] <= 127:
+        # the mesh error of SPME: its forces against the classical k-space sum at the same
+        # beta and r_c (the tensor-core path, itself within ~1e-6 of the oracle)
+        with Ewald(L, beta, rc, kmax, "mixed") as ewc:
+            Fc = torch.empty_like(F)
+            ewc.compute_async(tp, tq, Fc, torch.empty_like(E))
+            Fc = Fc.cpu().numpy()
+        Fs = hf
+        spme["vs_classical_rel_force_rms"] = float(np.sqrt(((Fs - Fc) ** 2).sum() / (Fc ** 2).sum()))
     if rank == 0:
         line = {
             "metric": "ewald_particles_per_s", "value": value, "unit": "particles/s",
@@ -638,6 +750,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "L": L, "r_c": rc, "beta": beta,
                        "k_max": kmax, "tol": TOL, "precision": args.precision,
+                       "reciprocal": ({"method": "spme", **spme} if spme else
+                                      {"method": "classical k-space sum"}),
                        "l2": "flushed before every step (512 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e, "unit": "particles/s", "h2d_bytes_per_step": 32 * n,

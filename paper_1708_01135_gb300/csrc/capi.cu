@@ -450,8 +450,11 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
                                                           ws.phi_recip, ws.pg, p.beta, phi);
     p.launches += 2;
     if (vir) {
-        k_virial<<<1, 256, 0, st>>>((int)tiles, ws.vir_tile, tiles, kVirBlocks, ws.vir_part,
-                                    parts, lj ? 1 : 0, vir);
+        int vrc = kVirBlocks;
+        const double *vrp = ws.vir_part;
+        if (spme) vrp = spme_virial_parts(p, &vrc);
+        k_virial<<<1, 256, 0, st>>>((int)tiles, ws.vir_tile, tiles, vrc, vrp, parts, lj ? 1 : 0,
+                                    vir);
         p.launches += 1;
     }
     prof_mark(p, kEvFinal, st);

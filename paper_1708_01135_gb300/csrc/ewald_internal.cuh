@@ -190,11 +190,12 @@ size_t recip_tc_bytes(const Plan &p, int64_t n);
 int recip_tc_energy_parts(const Plan &p);   // entries of the partial reciprocal energies
 void free_recip_tc(Plan &p);
 // Smooth particle-mesh Ewald reciprocal part into ws.f_recip / ws.phi_recip, its energy
-// partials (spme_energy_parts) and virial partials (ws.vir_part).
+// partials (spme_energy_parts) and virial partials (spme_virial_parts).
 int spme_set(Plan &p, int K, int order);     // K = 0: back to the classical sum
 void spme_free(Plan &p);
 cudaError_t launch_recip_spme(Plan &p, int64_t n, cudaStream_t st);
-const double *spme_energy_parts(const Plan &p, int *count);
+const double *spme_energy_parts(const Plan &p, int *count);   // [count] energy partials
+const double *spme_virial_parts(const Plan &p, int *count);   // [6][count] virial partials
 size_t spme_bytes(const Plan &p);
 // One whole evaluation on `st` (grows the workspaces for n first; n > 0).  With
 // clear_status false the plan's device status keeps the bits of earlier evaluations, so that

@@ -11,17 +11,24 @@
 //   phi_i = sum_k M phi_mesh (so that E = 1/2 sum q_i phi_i).
 //
 // GPU design:
-//   * spread: one thread per (sorted) particle computes its 3 x p spline weights and adds
-//     q w_x w_y w_z to the p^3 mesh points with 64-bit integer atomics on a fixed-point mesh
-//     (2^-36 resolution).  Integer addition is associative, so the mesh, and everything
-//     after it, is bit-identical from run to run whatever order the atomics land in;
+//   * spread: one block per brick of cells of the real-space cell grid (the particles are
+//     sorted by cell) spreads the brick's charges into a tile of the mesh held in shared
+//     memory, with no atomics: warp w of the p warps owns the tile planes x = w (mod p), so
+//     every tile point is updated by one warp, particle after particle in slot order.  The
+//     tile is then added to a fixed-point mesh (2^-36 resolution) with one 64-bit integer
+//     atomic per nonzero point.  Integer addition is associative, so the mesh, and
+//     everything after it, is bit-identical from run to run whatever order the bricks
+//     finish in.  (A grid too coarse for tiles falls back to one thread per particle with
+//     p^3 atomics, e.g. a single cell on a small box);
 //   * convert (fixed point -> FP64/FP32, and re-zero the fixed-point mesh for the next call),
 //     cuFFT real-to-complex transform (a plain library FFT);
 //   * influence: G is the product of three per-axis tables and 1 / |m~|^2, computed on the
-//     fly (no K^3 coefficient array); the same pass forms the energy and virial partials
-//     (fixed-order block sums) and scales the spectrum by G;
-//   * cuFFT complex-to-real transform, then gather: one thread per particle reads its p^3
-//     mesh values and writes its own force and potential (no atomics).
+//     fly (no K^3 coefficient array, FP32 arithmetic on the FP32 mesh); the same pass forms
+//     the energy and virial partials (fixed-order sums, FP64 across groups of 16 entries)
+//     and scales the spectrum by G;
+//   * cuFFT complex-to-real transform, then gather: per brick, the tile of the potential
+//     mesh is copied to shared memory, and one thread per particle sums over its p^3 points
+//     and writes its own force and potential (no atomics).
 // The mixed and FP32 plans use FP32 splines, mesh and FFT; the FP64 plan FP64 throughout.
 #include <cuda_runtime.h>
 #include <cufft.h>
@@ -45,8 +52,13 @@ struct SpmeState {
     void *mesh = nullptr;                 // [K^3] real mesh (charges, then potentials)
     void *spec = nullptr;                 // [K][K][K/2 + 1] complex spectrum
     double2 *axis = nullptr;              // [K]: (|b(m)|^2 exp(-pi^2 s^2 / (beta L)^2), s / L)
-    double *epart = nullptr;              // [kVirBlocks] energy partials
+    double *part = nullptr;               // [7][nblk] energy and virial partials
+    int nblk = 0;                         // blocks of the spectrum pass
     double axis_beta = 0, axis_L = 0;     // parameters the axis table was built for
+    // brick tiling of the spreading for the plan's current cell grid (tile_nc = -1: not
+    // chosen yet; bc = 0: no tile fits, spread particle by particle)
+    int tile_nc = -1, bc = 0, nbk = 0, W = 0, chunk = 0;
+    size_t smem = 0, smem_g = 0;          // dynamic shared memory of the spread / gather tiles
 };
 
 namespace {
@@ -89,14 +101,11 @@ __device__ __forceinline__ void axis_pos(double x, double kl, int K, int &base, 
     if (base >= K) base -= K;
 }
 
+// One particle's P^3 charge weights, added to the fixed-point mesh with integer atomics.
 template <class T, int P>
-__global__ void __launch_bounds__(kThreads)
-k_spme_spread(int64_t n, const double4_32a *__restrict__ pg, int K, double kl,
-              unsigned long long *__restrict__ qfix)
+__device__ void spread_one(const double4_32a &r, int K, double kl,
+                           unsigned long long *__restrict__ qfix)
 {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    const double4_32a r = pg[i];
     int b[3];
     double w[3];
     axis_pos(r.x, kl, K, b[0], w[0]);
@@ -128,6 +137,131 @@ k_spme_spread(int64_t n, const double4_32a *__restrict__ pg, int K, double kl,
     }
 }
 
+// Spreading particle by particle (grids with no room for tiles).
+template <class T, int P>
+__global__ void __launch_bounds__(kThreads)
+k_spme_spread(int64_t n, const double4_32a *__restrict__ pg, int K, double kl,
+              unsigned long long *__restrict__ qfix)
+{
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    spread_one<T, P>(pg[i], K, kl, qfix);
+}
+
+// Tiled spreading (see the file comment).  Block b is the brick (bx, by, bz) of bc^3 cells;
+// its particles are the slot ranges of its cell rows.  The tile covers mesh points
+// [o, o + W) per axis with o = floor(c0 K / nc) - P: every particle of cells [c0, c1) has
+// its mesh base floor(u) in [o + P, floor(c1 K / nc)], up to rounding, and W leaves one
+// point of margin at each end; a particle found outside all the same is spread directly
+// into the global mesh.  Shared memory: the tile T[W][W][W], then per particle of the
+// current chunk its 3 x P weights, its charge and its packed local base.
+template <class T, int P>
+__global__ void __launch_bounds__(P * 32)
+k_spme_spread_tile(const double4_32a *__restrict__ pg, const int *__restrict__ cell_start,
+                   int nc, int bc, int nbk, int W, int chunk, int K, double kl,
+                   unsigned long long *__restrict__ qfix)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int rfirst[64], rpre[65];
+    const int W3 = W * W * W;
+    T *tile = reinterpret_cast<T *>(smraw);
+    T *wts = tile + W3;
+    T *qs = wts + (size_t)chunk * 3 * P;
+    int *lb = reinterpret_cast<int *>(qs + chunk);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nth = P * 32;
+    const int b = blockIdx.x;
+    const int bx = b % nbk, by = (b / nbk) % nbk, bz = b / (nbk * nbk);
+    const int cx0 = bx * bc, cy0 = by * bc, cz0 = bz * bc;
+    const int cx1 = min(nc, cx0 + bc), cy1 = min(nc, cy0 + bc), cz1 = min(nc, cz0 + bc);
+    const int o[3] = {(int)(((int64_t)cx0 * K) / nc) - P, (int)(((int64_t)cy0 * K) / nc) - P,
+                      (int)(((int64_t)cz0 * K) / nc) - P};
+    const int nry = cy1 - cy0, nr = nry * (cz1 - cz0);
+    if (tid < nr) {
+        const int base = ((cz0 + tid / nry) * nc + cy0 + tid % nry) * nc;
+        const int f = cell_start[base + cx0];
+        rfirst[tid] = f;
+        rpre[tid + 1] = cell_start[base + cx1] - f;
+    }
+    for (int t = tid; t < W3; t += nth) tile[t] = T(0);
+    __syncthreads();
+    if (tid == 0) {
+        rpre[0] = 0;
+        for (int r = 0; r < nr; ++r) rpre[r + 1] += rpre[r];
+    }
+    __syncthreads();
+    const int total = rpre[nr];
+    for (int c0 = 0; c0 < total; c0 += chunk) {
+        const int cnt = min(chunk, total - c0);
+        if (tid < cnt) {
+            const int f = c0 + tid;
+            int r = 0;
+            while (rpre[r + 1] <= f) ++r;
+            const double4_32a pr = pg[rfirst[r] + (f - rpre[r])];
+            const double u[3] = {pr.x * kl, pr.y * kl, pr.z * kl};
+            int l[3];
+            T w[3];
+            bool inside = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double fl = floor(u[a]);
+                l[a] = (int)fl - o[a];
+                w[a] = (T)(u[a] - fl);
+                inside = inside && l[a] >= P - 1 && l[a] < W;
+            }
+            T *wp = wts + (size_t)tid * 3 * P;
+            if (inside) {
+                T c[P], d[P];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    spline<T, P, false>(w[a], c, d);
+#pragma unroll
+                    for (int j = 0; j < P; ++j) wp[a * P + j] = c[j];
+                }
+                qs[tid] = (T)pr.w;
+                lb[tid] = l[0] | (l[1] << 10) | (l[2] << 20);
+            } else {
+                spread_one<T, P>(pr, K, kl, qfix);
+#pragma unroll
+                for (int j = 0; j < 3 * P; ++j) wp[j] = T(0);
+                qs[tid] = T(0);
+                lb[tid] = (P - 1) | ((P - 1) << 10) | ((P - 1) << 20);
+            }
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+            const int pk = lb[j];
+            const int lx0 = pk & 1023, ly0 = (pk >> 10) & 1023, lz0 = pk >> 20;
+            int a = (lx0 - warp) % P;
+            if (a < 0) a += P;
+            const T *wp = wts + (size_t)j * 3 * P;
+            const T qa = qs[j] * wp[a];
+            T *plane = tile + (size_t)(lx0 - a) * W * W + (size_t)ly0 * W + lz0;
+#pragma unroll
+            for (int i = 0; i < (P * P + 31) / 32; ++i) {
+                const int idx = lane + 32 * i;
+                if (idx < P * P) {
+                    const int bb = idx / P, cc = idx % P;
+                    plane[-bb * W - cc] += qa * wp[P + bb] * wp[2 * P + cc];
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < W3; t += nth) {
+        const T v = tile[t];
+        if (v != T(0)) {
+            int gx = (o[0] + t / (W * W)) % K, gy = (o[1] + (t / W) % W) % K, gz = (o[2] + t % W) % K;
+            if (gx < 0) gx += K;
+            if (gy < 0) gy += K;
+            if (gz < 0) gz += K;
+            atomicAdd(qfix + ((int64_t)gx * K + gy) * K + gz,
+                      (unsigned long long)llrint((double)v * kFixScale));
+        }
+    }
+}
+
 template <class T>
 __global__ void k_spme_convert(int64_t m, unsigned long long *__restrict__ qfix, T *__restrict__ mesh)
 {
@@ -139,52 +273,66 @@ __global__ void k_spme_convert(int64_t m, unsigned long long *__restrict__ qfix,
 
 // Spectrum pass over the K x K x (K/2 + 1) half spectrum: energy and virial partials of
 // 1/2 sum_m G |F(Q)|^2 (entries m_z = 0 and m_z = K/2 stand for themselves, the others also
-// for their conjugate partners) and spec <- G spec.  Block b takes the entries
-// b * 256 + t + j * (gridDim.x * 256) in order, then a fixed tree.
-template <class T2>
+// for their conjugate partners) and spec <- G spec.  Arithmetic in the mesh type T; each
+// thread adds its terms in T over groups of 16 entries and the group sums in FP64.  Block b
+// takes the entries b * 256 + t + j * (gridDim.x * 256) in order, then a fixed tree; part
+// holds [7][gridDim.x] block sums (energy, then the virial xx yy zz xy xz yz).
+template <class T, class T2>
 __global__ void __launch_bounds__(kThreads)
 k_spme_influence(int K, const double2 *__restrict__ axis, double inv_piV, double pi2_b2,
-                 T2 *__restrict__ spec, double *__restrict__ epart, double *__restrict__ vpart)
+                 T2 *__restrict__ spec, double *__restrict__ part)
 {
     __shared__ double red[7][kThreads];
     const int Kh = K / 2 + 1;
     const int64_t tot = (int64_t)K * K * Kh;
     const int t = threadIdx.x;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    T grp[7] = {0, 0, 0, 0, 0, 0, 0};
+    int ng = 0;
+    const T ipv = (T)inv_piV, pb = (T)pi2_b2;
     for (int64_t e = (int64_t)blockIdx.x * kThreads + t; e < tot; e += (int64_t)gridDim.x * kThreads) {
         const int mz = (int)(e % Kh);
         const int64_t r = e / Kh;
         const int my = (int)(r % K), mx = (int)(r / K);
         const double2 ax = axis[mx], ay = axis[my], az = axis[mz];
-        const double m2 = ax.y * ax.y + ay.y * ay.y + az.y * az.y;
-        const double G = e == 0 ? 0.0 : ax.x * ay.x * az.x * inv_piV / m2;
+        const T sx = (T)ax.y, sy = (T)ay.y, sz = (T)az.y;
+        const T m2 = sx * sx + sy * sy + sz * sz;
         T2 v = spec[e];
-        const double a = G * ((double)v.x * (double)v.x + (double)v.y * (double)v.y);
-        const bool single = mz == 0 || 2 * mz == K;    // stands for itself only
-        const double hw = single ? 0.5 * a : a;         // 1/2 x (1 or 2)
         if (e != 0) {
-            const double c = 2.0 * (1.0 / m2 + pi2_b2);
+            const T G = (T)ax.x * (T)ay.x * (T)az.x * ipv / m2;
+            const T a = G * (v.x * v.x + v.y * v.y);
+            const bool single = mz == 0 || 2 * mz == K;    // stands for itself only
+            const T hw = single ? T(0.5) * a : a;           // 1/2 x (1 or 2)
+            const T c = T(2) * (T(1) / m2 + pb);
             // an entry that also stands for its conjugate partner (-m): the partner's signed
             // frequencies are -s, except on a Nyquist index K/2, which is +K/2 for both
             // (the mesh cannot tell +K/2 from -K/2), so there the off-diagonal products of
             // the pair cancel
             const bool nx = 2 * mx == K, ny = 2 * my == K;
-            const double fxy = (!single && nx != ny) ? 0.0 : 1.0;
-            const double fxz = (!single && nx) ? 0.0 : 1.0, fyz = (!single && ny) ? 0.0 : 1.0;
-            acc[0] += hw;
-            acc[1] += hw * (1.0 - c * ax.y * ax.y);
-            acc[2] += hw * (1.0 - c * ay.y * ay.y);
-            acc[3] += hw * (1.0 - c * az.y * az.y);
-            acc[4] -= fxy * hw * c * ax.y * ay.y;
-            acc[5] -= fxz * hw * c * ax.y * az.y;
-            acc[6] -= fyz * hw * c * ay.y * az.y;
+            const T fxy = (!single && nx != ny) ? T(0) : T(1);
+            const T fxz = (!single && nx) ? T(0) : T(1), fyz = (!single && ny) ? T(0) : T(1);
+            grp[0] += hw;
+            grp[1] += hw * (T(1) - c * sx * sx);
+            grp[2] += hw * (T(1) - c * sy * sy);
+            grp[3] += hw * (T(1) - c * sz * sz);
+            grp[4] -= fxy * hw * c * sx * sy;
+            grp[5] -= fxz * hw * c * sx * sz;
+            grp[6] -= fyz * hw * c * sy * sz;
+            v.x *= G;
+            v.y *= G;
+        } else {
+            v.x = 0;
+            v.y = 0;
         }
-        v.x = (decltype(v.x))((double)v.x * G);
-        v.y = (decltype(v.y))((double)v.y * G);
         spec[e] = v;
+        if (++ng == 16) {
+#pragma unroll
+            for (int c = 0; c < 7; ++c) { acc[c] += (double)grp[c]; grp[c] = T(0); }
+            ng = 0;
+        }
     }
 #pragma unroll
-    for (int c = 0; c < 7; ++c) red[c][t] = acc[c];
+    for (int c = 0; c < 7; ++c) red[c][t] = acc[c] + (double)grp[c];
     __syncthreads();
     for (int o = kThreads / 2; o > 0; o >>= 1) {
         if (t < o) {
@@ -193,43 +341,31 @@ k_spme_influence(int K, const double2 *__restrict__ axis, double inv_piV, double
         }
         __syncthreads();
     }
-    if (t == 0) epart[blockIdx.x] = red[0][0];
-    if (t < 6) vpart[t * gridDim.x + blockIdx.x] = red[1 + t][0];
+    if (t < 7) part[t * gridDim.x + blockIdx.x] = red[t][0];
 }
 
+// Potential and mesh-gradient sums of one particle over its P^3 mesh points: m[ox[a] +
+// oy[b] + oz[c]] is the potential at the point (base - a, base - b, base - c).
 template <class T, int P>
-__global__ void __launch_bounds__(kThreads)
-k_spme_gather(int64_t n, const double4_32a *__restrict__ pg, int K, double kl,
-              const T *__restrict__ mesh, double *__restrict__ f, double *__restrict__ phi)
+__device__ __forceinline__ void gather_core(const T *__restrict__ m, const int (&ox)[P],
+                                            const int (&oy)[P], const int (&oz)[P],
+                                            const double (&w)[3], T &s, T &gx, T &gy, T &gz)
 {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    const double4_32a r = pg[i];
-    int b[3];
-    double w[3];
-    axis_pos(r.x, kl, K, b[0], w[0]);
-    axis_pos(r.y, kl, K, b[1], w[1]);
-    axis_pos(r.z, kl, K, b[2], w[2]);
     T cx[P], cy[P], cz[P], dx[P], dy[P], dz[P];
     spline<T, P, true>((T)w[0], cx, dx);
     spline<T, P, true>((T)w[1], cy, dy);
     spline<T, P, true>((T)w[2], cz, dz);
-    int iz[P];
+    s = gx = gy = gz = T(0);
 #pragma unroll
-    for (int c = 0; c < P; ++c) iz[c] = b[2] - c < 0 ? b[2] - c + K : b[2] - c;
-    T s = T(0), gx = T(0), gy = T(0), gz = T(0);
-#pragma unroll 1
     for (int a = 0; a < P; ++a) {
-        const int ix = b[0] - a < 0 ? b[0] - a + K : b[0] - a;
         T sa = T(0), ga = T(0), gza = T(0);
-#pragma unroll 1
+#pragma unroll
         for (int bb = 0; bb < P; ++bb) {
-            const int iy = b[1] - bb < 0 ? b[1] - bb + K : b[1] - bb;
-            const T *row = mesh + ((int64_t)ix * K + iy) * K;
+            const T *row = m + ox[a] + oy[bb];
             T sz = T(0), dzs = T(0);
 #pragma unroll
             for (int c = 0; c < P; ++c) {
-                const T v = row[iz[c]];
+                const T v = row[oz[c]];
                 sz += cz[c] * v;
                 dzs += dz[c] * v;
             }
@@ -242,11 +378,122 @@ k_spme_gather(int64_t n, const double4_32a *__restrict__ pg, int K, double kl,
         gy += cx[a] * ga;
         gz += cx[a] * gza;
     }
+}
+
+// One particle from the global mesh (periodic indices).
+template <class T, int P>
+__device__ void gather_one(const double4_32a &r, int K, double kl, const T *__restrict__ mesh,
+                           double *__restrict__ f, double *__restrict__ phi)
+{
+    int b[3];
+    double w[3];
+    axis_pos(r.x, kl, K, b[0], w[0]);
+    axis_pos(r.y, kl, K, b[1], w[1]);
+    axis_pos(r.z, kl, K, b[2], w[2]);
+    int ox[P], oy[P], oz[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+        ox[c] = (b[0] - c < 0 ? b[0] - c + K : b[0] - c) * K * K;
+        oy[c] = (b[1] - c < 0 ? b[1] - c + K : b[1] - c) * K;
+        oz[c] = b[2] - c < 0 ? b[2] - c + K : b[2] - c;
+    }
+    T s, gx, gy, gz;
+    gather_core<T, P>(mesh, ox, oy, oz, w, s, gx, gy, gz);
     const double qk = -(double)r.w * kl;
-    f[3 * i + 0] = qk * (double)gx;
-    f[3 * i + 1] = qk * (double)gy;
-    f[3 * i + 2] = qk * (double)gz;
-    phi[i] = (double)s;
+    f[0] = qk * (double)gx;
+    f[1] = qk * (double)gy;
+    f[2] = qk * (double)gz;
+    *phi = (double)s;
+}
+
+// Gather particle by particle from the global mesh (grids with no room for tiles).
+template <class T, int P>
+__global__ void __launch_bounds__(kThreads)
+k_spme_gather(int64_t n, const double4_32a *__restrict__ pg, int K, double kl,
+              const T *__restrict__ mesh, double *__restrict__ f, double *__restrict__ phi)
+{
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    gather_one<T, P>(pg[i], K, kl, mesh, f + 3 * i, phi + i);
+}
+
+// Tiled gather: the brick decomposition of the spreading; the block first copies the W^3
+// tile of the potential mesh that its particles reach into shared memory (coalesced along
+// z), then every thread takes particles of the brick and sums over the tile.  A particle
+// found outside the tile reads the global mesh instead.
+template <class T, int P>
+__global__ void __launch_bounds__(kThreads)
+k_spme_gather_tile(const double4_32a *__restrict__ pg, const int *__restrict__ cell_start,
+                   int nc, int bc, int nbk, int W, int K, double kl, const T *__restrict__ mesh,
+                   double *__restrict__ f, double *__restrict__ phi)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int rfirst[64], rpre[65];
+    const int W3 = W * W * W;
+    T *tile = reinterpret_cast<T *>(smraw);
+    const int tid = threadIdx.x;
+    const int b = blockIdx.x;
+    const int bx = b % nbk, by = (b / nbk) % nbk, bz = b / (nbk * nbk);
+    const int cx0 = bx * bc, cy0 = by * bc, cz0 = bz * bc;
+    const int cx1 = min(nc, cx0 + bc), cy1 = min(nc, cy0 + bc), cz1 = min(nc, cz0 + bc);
+    const int o[3] = {(int)(((int64_t)cx0 * K) / nc) - P, (int)(((int64_t)cy0 * K) / nc) - P,
+                      (int)(((int64_t)cz0 * K) / nc) - P};
+    const int nry = cy1 - cy0, nr = nry * (cz1 - cz0);
+    if (tid < nr) {
+        const int base = ((cz0 + tid / nry) * nc + cy0 + tid % nry) * nc;
+        const int f0 = cell_start[base + cx0];
+        rfirst[tid] = f0;
+        rpre[tid + 1] = cell_start[base + cx1] - f0;
+    }
+    for (int t = tid; t < W3; t += kThreads) {
+        int gx = (o[0] + t / (W * W)) % K, gy = (o[1] + (t / W) % W) % K, gz = (o[2] + t % W) % K;
+        if (gx < 0) gx += K;
+        if (gy < 0) gy += K;
+        if (gz < 0) gz += K;
+        tile[t] = mesh[((int64_t)gx * K + gy) * K + gz];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        rpre[0] = 0;
+        for (int r = 0; r < nr; ++r) rpre[r + 1] += rpre[r];
+    }
+    __syncthreads();
+    const int total = rpre[nr];
+    int r = 0;
+    for (int fi = tid; fi < total; fi += kThreads) {
+        while (rpre[r + 1] <= fi) ++r;
+        const int slot = rfirst[r] + (fi - rpre[r]);
+        const double4_32a pr = pg[slot];
+        const double u[3] = {pr.x * kl, pr.y * kl, pr.z * kl};
+        int l[3];
+        double w[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double fl = floor(u[a]);
+            l[a] = (int)fl - o[a];
+            w[a] = u[a] - fl;
+            inside = inside && l[a] >= P - 1 && l[a] < W;
+        }
+        if (!inside) {
+            gather_one<T, P>(pr, K, kl, mesh, f + 3 * (int64_t)slot, phi + slot);
+            continue;
+        }
+        int ox[P], oy[P], oz[P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            ox[c] = (l[0] - c) * W * W;
+            oy[c] = (l[1] - c) * W;
+            oz[c] = l[2] - c;
+        }
+        T s, gx, gy, gz;
+        gather_core<T, P>(tile, ox, oy, oz, w, s, gx, gy, gz);
+        const double qk = -(double)pr.w * kl;
+        f[3 * (int64_t)slot + 0] = qk * (double)gx;
+        f[3 * (int64_t)slot + 1] = qk * (double)gy;
+        f[3 * (int64_t)slot + 2] = qk * (double)gz;
+        phi[slot] = (double)s;
+    }
 }
 
 // Host B-spline M_p(u) by the order recursion (for the Euler-spline moduli).
@@ -278,6 +525,55 @@ cudaError_t upload_axis(Plan &p, SpmeState &s, cudaStream_t st)
     return e;
 }
 
+// Brick size of the tiled spreading for the plan's cell grid: the largest bc (cells per
+// brick side, <= 8) whose tile and chunk fit in half of an SM's shared memory (two blocks per
+// SM) while the bricks still fill every SM once; else the largest that fits in one SM's
+// shared memory with that many bricks; else the smallest brick that fits at all (small
+// grids); bc = 0 when none does (e.g. the single cell of a small box).
+template <class T, int P>
+void choose_tiling(Plan &p, SpmeState &s)
+{
+    const int nc = p.nc, K = s.K;
+    const int chunk = sizeof(T) == 4 ? 128 : 64;
+    const size_t max_smem = 227 * 1024 - 1024;
+    int pick[3] = {0, 0, 0};
+    size_t pick_smem[3] = {0, 0, 0};
+    int pick_W[3] = {0, 0, 0};
+    for (int bc = 1; bc <= 8 && bc <= nc && p.w > 0; ++bc) {
+        const int nbk = (nc + bc - 1) / bc;
+        int W = 0;
+        for (int b = 0; b < nbk; ++b) {
+            const int c0 = b * bc, c1 = c0 + bc < nc ? c0 + bc : nc;
+            const int w = (int)(((int64_t)c1 * K) / nc - ((int64_t)c0 * K) / nc) + P + 2;
+            if (w > W) W = w;
+        }
+        const size_t smem = (size_t)W * W * W * sizeof(T) + (size_t)chunk * (3 * P + 1) * sizeof(T) +
+                            (size_t)chunk * sizeof(int);
+        if (W > 1023 || smem > max_smem) break;
+        const bool fill = (int64_t)nbk * nbk * nbk >= p.num_sms;
+        if (fill && smem <= max_smem / 2) { pick[0] = bc; pick_smem[0] = smem; pick_W[0] = W; }
+        if (fill) { pick[1] = bc; pick_smem[1] = smem; pick_W[1] = W; }
+        if (!pick[2]) { pick[2] = bc; pick_smem[2] = smem; pick_W[2] = W; }
+    }
+    const int k = pick[0] ? 0 : pick[1] ? 1 : 2;
+    s.tile_nc = nc;
+    s.bc = pick[k];
+    s.nbk = s.bc ? (nc + s.bc - 1) / s.bc : 0;
+    s.W = pick_W[k];
+    s.chunk = chunk;
+    s.smem = pick_smem[k];
+    s.smem_g = (size_t)s.W * s.W * s.W * sizeof(T);
+    if (s.bc && (cudaFuncSetAttribute(k_spme_spread_tile<T, P>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)s.smem) != cudaSuccess ||
+                 cudaFuncSetAttribute(k_spme_gather_tile<T, P>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)s.smem_g) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        s.bc = 0;
+    }
+}
+
 template <class T, int P>
 cudaError_t launch_spme_p(Plan &p, SpmeState &s, int64_t n, cudaStream_t st)
 {
@@ -287,7 +583,12 @@ cudaError_t launch_spme_p(Plan &p, SpmeState &s, int64_t n, cudaStream_t st)
     const double kl = K / p.L;
     const unsigned gb = (unsigned)((n + kThreads - 1) / kThreads);
     prof_mark(p, kEvRecipStart, st);
-    k_spme_spread<T, P><<<gb, kThreads, 0, st>>>(n, p.ws.pg, K, kl, s.qfix);
+    if (s.tile_nc != p.nc) choose_tiling<T, P>(p, s);
+    if (s.bc > 0)
+        k_spme_spread_tile<T, P><<<(unsigned)((int64_t)s.nbk * s.nbk * s.nbk), P * 32, s.smem, st>>>(
+            p.ws.pg, p.ws.cell_start, p.nc, s.bc, s.nbk, s.W, s.chunk, K, kl, s.qfix);
+    else
+        k_spme_spread<T, P><<<gb, kThreads, 0, st>>>(n, p.ws.pg, K, kl, s.qfix);
     k_spme_convert<T><<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, st>>>(m, s.qfix, (T *)s.mesh);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -299,16 +600,21 @@ cudaError_t launch_spme_p(Plan &p, SpmeState &s, int64_t n, cudaStream_t st)
     if (fr != CUFFT_SUCCESS) return cudaErrorUnknown;
     prof_mark(p, kEvFwdEnd, st);
     const double V = p.L * p.L * p.L;
-    k_spme_influence<T2><<<kVirBlocks, kThreads, 0, st>>>(K, s.axis, 1.0 / (kPi * V),
-                                                        kPi * kPi / (p.beta * p.beta),
-                                                        (T2 *)s.spec, s.epart, p.ws.vir_part);
+    k_spme_influence<T, T2><<<s.nblk, kThreads, 0, st>>>(K, s.axis, 1.0 / (kPi * V),
+                                                       kPi * kPi / (p.beta * p.beta),
+                                                       (T2 *)s.spec, s.part);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     prof_mark(p, kEvCoefEnd, st);
     if (sizeof(T) == 4) fr = cufftExecC2R(s.inv, (cufftComplex *)s.spec, (cufftReal *)s.mesh);
     else fr = cufftExecZ2D(s.inv, (cufftDoubleComplex *)s.spec, (cufftDoubleReal *)s.mesh);
     if (fr != CUFFT_SUCCESS) return cudaErrorUnknown;
-    k_spme_gather<T, P><<<gb, kThreads, 0, st>>>(n, p.ws.pg, K, kl, (const T *)s.mesh,
-                                                 p.ws.f_recip, p.ws.phi_recip);
+    if (s.bc > 0)
+        k_spme_gather_tile<T, P><<<(unsigned)((int64_t)s.nbk * s.nbk * s.nbk), kThreads, s.smem_g, st>>>(
+            p.ws.pg, p.ws.cell_start, p.nc, s.bc, s.nbk, s.W, K, kl, (const T *)s.mesh,
+            p.ws.f_recip, p.ws.phi_recip);
+    else
+        k_spme_gather<T, P><<<gb, kThreads, 0, st>>>(n, p.ws.pg, K, kl, (const T *)s.mesh,
+                                                     p.ws.f_recip, p.ws.phi_recip);
     prof_mark(p, kEvBackEnd, st);
     p.launches += 6;   // 4 kernels + 2 transforms (cuFFT kernels counted as one each)
     return cudaGetLastError();
@@ -336,7 +642,7 @@ void destroy_state(SpmeState *s)
     cudaFree(s->mesh);
     cudaFree(s->spec);
     cudaFree(s->axis);
-    cudaFree(s->epart);
+    cudaFree(s->part);
     delete s;
 }
 
@@ -367,7 +673,8 @@ int spme_set(Plan &p, int K, int order)
     if (e == cudaSuccess) e = cudaMalloc(&s->mesh, real * m);
     if (e == cudaSuccess) e = cudaMalloc(&s->spec, 2 * real * h);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s->axis, sizeof(double2) * K);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&s->epart, sizeof(double) * kVirBlocks);
+    s->nblk = 4 * p.num_sms;
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s->part, sizeof(double) * 7 * s->nblk);
     if (e == cudaSuccess) e = cudaMemset(s->qfix, 0, sizeof(unsigned long long) * m);
     if (e != cudaSuccess) {
         destroy_state(s);
@@ -404,8 +711,16 @@ cudaError_t launch_recip_spme(Plan &p, int64_t n, cudaStream_t st)
 
 const double *spme_energy_parts(const Plan &p, int *count)
 {
-    *count = kVirBlocks;
-    return static_cast<const SpmeState *>(p.spme)->epart;
+    const SpmeState *s = static_cast<const SpmeState *>(p.spme);
+    *count = s->nblk;
+    return s->part;
+}
+
+const double *spme_virial_parts(const Plan &p, int *count)
+{
+    const SpmeState *s = static_cast<const SpmeState *>(p.spme);
+    *count = s->nblk;
+    return s->part + s->nblk;
 }
 
 size_t spme_bytes(const Plan &p)

@@ -113,3 +113,21 @@ def test_spme_md_conserves_energy():
         d_spme, ke = _md_drift(ew, pos, q)
     print(f"MD drift over 200 steps: classical {d_classic:.2e}, SPME {d_spme:.2e}")
     assert ke > 0 and d_spme < 1e-7 and d_classic < 1e-7
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spme_single_cell_grid_spreads_particle_by_particle(precision):
+    """r_c = L/2 on a small box leaves the real-space grid a single cell (all pairs), too
+    coarse for brick tiles, so the charges are spread particle by particle; the result is the
+    same SPME sum (oracle) as with tiles."""
+    need_gpu()
+    pos, q, L = W.random_neutral(500, density=1.0, hard_core=0.8, seed=64)
+    beta, rc = 0.9, 0.5 * L
+    ref = ospme.recip(pos, q, L, beta, 24, 6)
+    with Ewald(L, beta, rc, 8, precision) as ew:
+        ew.set_spme(24, 6)
+        F, phi, V, E = _eval(ew, pos, q, PART_RECIP)
+    tol = TOL[precision]
+    assert rel(E[1], ref["E"]) < tol
+    assert rel_rms(F, ref["F"]) < tol
+    assert rel_rms(phi, ref["phi"]) < tol
