@@ -57,8 +57,12 @@ struct SpmeState {
     double axis_beta = 0, axis_L = 0;     // parameters the axis table was built for
     // brick tiling of the spreading for the plan's current cell grid (tile_nc = -1: not
     // chosen yet; bc = 0: no tile fits, spread particle by particle)
-    int tile_nc = -1, bc = 0, nbk = 0, W = 0, chunk = 0;
-    size_t smem = 0, smem_g = 0;          // dynamic shared memory of the spread / gather tiles
+    int tile_nc = -1, bc = 0, nbk = 0, W = 0, S = 24, chunk = 0;
+    size_t smem = 0;                      // dynamic shared memory of the spreading blocks
+    // the gather's bricks (larger: one thread per particle wants >= 128 particles a block)
+    int bc_g = 0, nbk_g = 0, W_g = 0;
+    int64_t tile_n = -1;                  // particle count the gather's bricks were chosen for
+    size_t smem_g = 0;
 };
 
 namespace {
@@ -148,14 +152,28 @@ k_spme_spread(int64_t n, const double4_32a *__restrict__ pg, int K, double kl,
     spread_one<T, P>(pg[i], K, kl, qfix);
 }
 
+// Mesh index o + l wrapped into [0, K), for o + l in [-K, 2K).
+__device__ __forceinline__ int wrap_mesh(int g, int K)
+{
+    return g < 0 ? g + K : (g >= K ? g - K : g);
+}
+
+// The fixed-point value of a tile sum (2^-36 resolution, round to nearest even).  The
+// scaling by 2^36 is exact in either precision, so both give llrint(v * 2^36).
+__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * 68719476736.0f); }
+__device__ __forceinline__ long long to_fix(double v) { return __double2ll_rn(v * kFixScale); }
+
 // Tiled spreading (see the file comment).  Block b is the brick (bx, by, bz) of bc^3 cells;
 // its particles are the slot ranges of its cell rows.  The tile covers mesh points
 // [o, o + W) per axis with o = floor(c0 K / nc) - P: every particle of cells [c0, c1) has
 // its mesh base floor(u) in [o + P, floor(c1 K / nc)], up to rounding, and W leaves one
 // point of margin at each end; a particle found outside all the same is spread directly
-// into the global mesh.  Shared memory: the tile T[W][W][W], then per particle of the
-// current chunk its 3 x P weights, its charge and its packed local base.
-template <class T, int P>
+// into the global mesh.  The tile is stored [W][W][S] (S >= W a compile-time row pitch, so
+// that offsets inside one plane of a particle's footprint are constants; S = 24 or 40 keeps
+// the P x P points a warp updates in distinct shared-memory banks for P = 8).  After the tile, per
+// particle of the current chunk: its 3 x P weights (the x weights times its charge), then
+// its tile offset and its x base modulo P.
+template <class T, int P, int S>
 __global__ void __launch_bounds__(P * 32)
 k_spme_spread_tile(const double4_32a *__restrict__ pg, const int *__restrict__ cell_start,
                    int nc, int bc, int nbk, int W, int chunk, int K, double kl,
@@ -163,13 +181,15 @@ k_spme_spread_tile(const double4_32a *__restrict__ pg, const int *__restrict__ c
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int rfirst[64], rpre[65];
-    const int W3 = W * W * W;
+    const int S2 = W * S;          // plane stride
+    const int TV = W * S2;
     T *tile = reinterpret_cast<T *>(smraw);
-    T *wts = tile + W3;
-    T *qs = wts + (size_t)chunk * 3 * P;
-    int *lb = reinterpret_cast<int *>(qs + chunk);
+    T *wts = tile + TV;
+    int2 *info = reinterpret_cast<int2 *>(
+        smraw + (((TV + (size_t)chunk * 3 * P) * sizeof(T) + 7) & ~(size_t)7));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nth = P * 32;
+    constexpr int NI = (P * P + 31) / 32;
     const int b = blockIdx.x;
     const int bx = b % nbk, by = (b / nbk) % nbk, bz = b / (nbk * nbk);
     const int cx0 = bx * bc, cy0 = by * bc, cz0 = bz * bc;
@@ -183,7 +203,20 @@ k_spme_spread_tile(const double4_32a *__restrict__ pg, const int *__restrict__ c
         rfirst[tid] = f;
         rpre[tid + 1] = cell_start[base + cx1] - f;
     }
-    for (int t = tid; t < W3; t += nth) tile[t] = T(0);
+    for (int t = tid; t < TV; t += nth) tile[t] = T(0);
+    // this lane's points (b, c) of a particle's P x P footprint in one plane: offsets from
+    // the particle's base point and the positions of their weights
+    int off[NI], wy_i[NI], wz_i[NI];
+    bool has[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int idx = lane + 32 * i;
+        has[i] = idx < P * P;
+        const int bb = has[i] ? idx / P : 0, cc = has[i] ? idx % P : 0;
+        off[i] = -bb * S - cc;
+        wy_i[i] = P + bb;
+        wz_i[i] = 2 * P + cc;
+    }
     __syncthreads();
     if (tid == 0) {
         rpre[0] = 0;
@@ -191,11 +224,11 @@ k_spme_spread_tile(const double4_32a *__restrict__ pg, const int *__restrict__ c
     }
     __syncthreads();
     const int total = rpre[nr];
+    int r = 0;
     for (int c0 = 0; c0 < total; c0 += chunk) {
         const int cnt = min(chunk, total - c0);
         if (tid < cnt) {
             const int f = c0 + tid;
-            int r = 0;
             while (rpre[r + 1] <= f) ++r;
             const double4_32a pr = pg[rfirst[r] + (f - rpre[r])];
             const double u[3] = {pr.x * kl, pr.y * kl, pr.z * kl};
@@ -212,52 +245,50 @@ k_spme_spread_tile(const double4_32a *__restrict__ pg, const int *__restrict__ c
             T *wp = wts + (size_t)tid * 3 * P;
             if (inside) {
                 T c[P], d[P];
+                const T q = (T)pr.w;
+                spline<T, P, false>(w[0], c, d);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
+                for (int j = 0; j < P; ++j) wp[j] = q * c[j];
+#pragma unroll
+                for (int a = 1; a < 3; ++a) {
                     spline<T, P, false>(w[a], c, d);
 #pragma unroll
                     for (int j = 0; j < P; ++j) wp[a * P + j] = c[j];
                 }
-                qs[tid] = (T)pr.w;
-                lb[tid] = l[0] | (l[1] << 10) | (l[2] << 20);
+                info[tid] = make_int2(l[0] * S2 + l[1] * S + l[2], l[0] % P);
             } else {
                 spread_one<T, P>(pr, K, kl, qfix);
 #pragma unroll
                 for (int j = 0; j < 3 * P; ++j) wp[j] = T(0);
-                qs[tid] = T(0);
-                lb[tid] = (P - 1) | ((P - 1) << 10) | ((P - 1) << 20);
+                info[tid] = make_int2((P - 1) * (S2 + S + 1), P - 1);
             }
         }
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
-            const int pk = lb[j];
-            const int lx0 = pk & 1023, ly0 = (pk >> 10) & 1023, lz0 = pk >> 20;
-            int a = (lx0 - warp) % P;
+            const int2 in = info[j];
+            int a = in.y - warp;
             if (a < 0) a += P;
             const T *wp = wts + (size_t)j * 3 * P;
-            const T qa = qs[j] * wp[a];
-            T *plane = tile + (size_t)(lx0 - a) * W * W + (size_t)ly0 * W + lz0;
+            const T qa = wp[a];
+            T *pt = tile + (in.x - a * S2);
 #pragma unroll
-            for (int i = 0; i < (P * P + 31) / 32; ++i) {
-                const int idx = lane + 32 * i;
-                if (idx < P * P) {
-                    const int bb = idx / P, cc = idx % P;
-                    plane[-bb * W - cc] += qa * wp[P + bb] * wp[2 * P + cc];
-                }
-            }
+            for (int i = 0; i < NI; ++i)
+                if (has[i]) pt[off[i]] += qa * wp[wy_i[i]] * wp[wz_i[i]];
             __syncwarp();
         }
         __syncthreads();
     }
-    for (int t = tid; t < W3; t += nth) {
-        const T v = tile[t];
-        if (v != T(0)) {
-            int gx = (o[0] + t / (W * W)) % K, gy = (o[1] + (t / W) % W) % K, gz = (o[2] + t % W) % K;
-            if (gx < 0) gx += K;
-            if (gy < 0) gy += K;
-            if (gz < 0) gz += K;
-            atomicAdd(qfix + ((int64_t)gx * K + gy) * K + gz,
-                      (unsigned long long)llrint((double)v * kFixScale));
+    // the tile into the global mesh: warps step over the rows (x, y), lanes along z
+    for (int lx = 0; lx < W; ++lx) {
+        const int gx = wrap_mesh(o[0] + lx, K);
+        for (int ly = warp; ly < W; ly += P) {
+            unsigned long long *dst = qfix + ((int64_t)gx * K + wrap_mesh(o[1] + ly, K)) * K;
+            const T *src = tile + lx * S2 + ly * S;
+            for (int lz = lane; lz < W; lz += 32) {
+                const T v = src[lz];
+                if (v != T(0))
+                    atomicAdd(dst + wrap_mesh(o[2] + lz, K), (unsigned long long)to_fix(v));
+            }
         }
     }
 }
@@ -344,43 +375,17 @@ k_spme_influence(int K, const double2 *__restrict__ axis, double inv_piV, double
     if (t < 7) part[t * gridDim.x + blockIdx.x] = red[t][0];
 }
 
-// Potential and mesh-gradient sums of one particle over its P^3 mesh points: m[ox[a] +
-// oy[b] + oz[c]] is the potential at the point (base - a, base - b, base - c).
+// Shift the weights of one axis down by one (after plane a, entry 0 holds plane a + 1's):
+// keeps the plane loop rolled without indexing register arrays by the loop counter.
 template <class T, int P>
-__device__ __forceinline__ void gather_core(const T *__restrict__ m, const int (&ox)[P],
-                                            const int (&oy)[P], const int (&oz)[P],
-                                            const double (&w)[3], T &s, T &gx, T &gy, T &gz)
+__device__ __forceinline__ void shift_down(T (&c)[P], T (&d)[P])
 {
-    T cx[P], cy[P], cz[P], dx[P], dy[P], dz[P];
-    spline<T, P, true>((T)w[0], cx, dx);
-    spline<T, P, true>((T)w[1], cy, dy);
-    spline<T, P, true>((T)w[2], cz, dz);
-    s = gx = gy = gz = T(0);
 #pragma unroll
-    for (int a = 0; a < P; ++a) {
-        T sa = T(0), ga = T(0), gza = T(0);
-#pragma unroll
-        for (int bb = 0; bb < P; ++bb) {
-            const T *row = m + ox[a] + oy[bb];
-            T sz = T(0), dzs = T(0);
-#pragma unroll
-            for (int c = 0; c < P; ++c) {
-                const T v = row[oz[c]];
-                sz += cz[c] * v;
-                dzs += dz[c] * v;
-            }
-            sa += cy[bb] * sz;
-            ga += dy[bb] * sz;
-            gza += cy[bb] * dzs;
-        }
-        s += cx[a] * sa;
-        gx += dx[a] * sa;
-        gy += cx[a] * ga;
-        gz += cx[a] * gza;
-    }
+    for (int j = 0; j + 1 < P; ++j) { c[j] = c[j + 1]; d[j] = d[j + 1]; }
 }
 
-// One particle from the global mesh (periodic indices).
+// One particle from the global mesh (periodic indices; grids with no room for tiles and
+// particles outside their tile).
 template <class T, int P>
 __device__ void gather_one(const double4_32a &r, int K, double kl, const T *__restrict__ mesh,
                            double *__restrict__ f, double *__restrict__ phi)
@@ -390,15 +395,42 @@ __device__ void gather_one(const double4_32a &r, int K, double kl, const T *__re
     axis_pos(r.x, kl, K, b[0], w[0]);
     axis_pos(r.y, kl, K, b[1], w[1]);
     axis_pos(r.z, kl, K, b[2], w[2]);
-    int ox[P], oy[P], oz[P];
+    T cx[P], cy[P], cz[P], dx[P], dy[P], dz[P];
+    spline<T, P, true>((T)w[0], cx, dx);
+    spline<T, P, true>((T)w[1], cy, dy);
+    spline<T, P, true>((T)w[2], cz, dz);
+    int iz[P], iy[P];
 #pragma unroll
     for (int c = 0; c < P; ++c) {
-        ox[c] = (b[0] - c < 0 ? b[0] - c + K : b[0] - c) * K * K;
-        oy[c] = (b[1] - c < 0 ? b[1] - c + K : b[1] - c) * K;
-        oz[c] = b[2] - c < 0 ? b[2] - c + K : b[2] - c;
+        iz[c] = b[2] - c < 0 ? b[2] - c + K : b[2] - c;
+        iy[c] = (b[1] - c < 0 ? b[1] - c + K : b[1] - c) * K;
     }
-    T s, gx, gy, gz;
-    gather_core<T, P>(mesh, ox, oy, oz, w, s, gx, gy, gz);
+    T s = T(0), gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll 1
+    for (int a = 0; a < P; ++a) {
+        const int ix = b[0] - a < 0 ? b[0] - a + K : b[0] - a;
+        const T *pl = mesh + (int64_t)ix * K * K;
+        T sa = T(0), ga = T(0), gza = T(0);
+#pragma unroll
+        for (int bb = 0; bb < P; ++bb) {
+            const T *row = pl + iy[bb];
+            T sz = T(0), dzs = T(0);
+#pragma unroll
+            for (int c = 0; c < P; ++c) {
+                const T v = row[iz[c]];
+                sz += cz[c] * v;
+                dzs += dz[c] * v;
+            }
+            sa += cy[bb] * sz;
+            ga += dy[bb] * sz;
+            gza += cy[bb] * dzs;
+        }
+        s += cx[0] * sa;
+        gx += dx[0] * sa;
+        gy += cx[0] * ga;
+        gz += cx[0] * gza;
+        shift_down<T, P>(cx, dx);
+    }
     const double qk = -(double)r.w * kl;
     f[0] = qk * (double)gx;
     f[1] = qk * (double)gy;
@@ -417,10 +449,12 @@ k_spme_gather(int64_t n, const double4_32a *__restrict__ pg, int K, double kl,
     gather_one<T, P>(pg[i], K, kl, mesh, f + 3 * i, phi + i);
 }
 
-// Tiled gather: the brick decomposition of the spreading; the block first copies the W^3
-// tile of the potential mesh that its particles reach into shared memory (coalesced along
-// z), then every thread takes particles of the brick and sums over the tile.  A particle
-// found outside the tile reads the global mesh instead.
+// Tiled gather: bricks of cells as for the spreading (larger ones: one thread per particle
+// wants >= 128 particles a block).  The block first copies the W^3 tile of the potential
+// mesh that its particles reach into shared memory (rows along z, coalesced), then every
+// thread takes particles of the brick and sums over the tile, one plane of the footprint at
+// a time (row offsets inside a plane are multiples of W, points along a row constants).  A
+// particle found outside the tile reads the global mesh instead.
 template <class T, int P>
 __global__ void __launch_bounds__(kThreads)
 k_spme_gather_tile(const double4_32a *__restrict__ pg, const int *__restrict__ cell_start,
@@ -429,9 +463,10 @@ k_spme_gather_tile(const double4_32a *__restrict__ pg, const int *__restrict__ c
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int rfirst[64], rpre[65];
-    const int W3 = W * W * W;
+    const int W2 = W * W;
     T *tile = reinterpret_cast<T *>(smraw);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nw = kThreads / 32;
     const int b = blockIdx.x;
     const int bx = b % nbk, by = (b / nbk) % nbk, bz = b / (nbk * nbk);
     const int cx0 = bx * bc, cy0 = by * bc, cz0 = bz * bc;
@@ -445,12 +480,13 @@ k_spme_gather_tile(const double4_32a *__restrict__ pg, const int *__restrict__ c
         rfirst[tid] = f0;
         rpre[tid + 1] = cell_start[base + cx1] - f0;
     }
-    for (int t = tid; t < W3; t += kThreads) {
-        int gx = (o[0] + t / (W * W)) % K, gy = (o[1] + (t / W) % W) % K, gz = (o[2] + t % W) % K;
-        if (gx < 0) gx += K;
-        if (gy < 0) gy += K;
-        if (gz < 0) gz += K;
-        tile[t] = mesh[((int64_t)gx * K + gy) * K + gz];
+    for (int lx = 0; lx < W; ++lx) {
+        const T *pl = mesh + (int64_t)wrap_mesh(o[0] + lx, K) * K * K;
+        for (int ly = warp; ly < W; ly += nw) {
+            const T *src = pl + (int64_t)wrap_mesh(o[1] + ly, K) * K;
+            T *dst = tile + lx * W2 + ly * W;
+            for (int lz = lane; lz < W; lz += 32) dst[lz] = src[wrap_mesh(o[2] + lz, K)];
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -466,28 +502,49 @@ k_spme_gather_tile(const double4_32a *__restrict__ pg, const int *__restrict__ c
         const double4_32a pr = pg[slot];
         const double u[3] = {pr.x * kl, pr.y * kl, pr.z * kl};
         int l[3];
-        double w[3];
+        T w[3];
         bool inside = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const double fl = floor(u[a]);
             l[a] = (int)fl - o[a];
-            w[a] = u[a] - fl;
+            w[a] = (T)(u[a] - fl);
             inside = inside && l[a] >= P - 1 && l[a] < W;
         }
         if (!inside) {
             gather_one<T, P>(pr, K, kl, mesh, f + 3 * (int64_t)slot, phi + slot);
             continue;
         }
-        int ox[P], oy[P], oz[P];
+        T cx[P], cy[P], cz[P], dx[P], dy[P], dz[P];
+        spline<T, P, true>(w[0], cx, dx);
+        spline<T, P, true>(w[1], cy, dy);
+        spline<T, P, true>(w[2], cz, dz);
+        const T *base = tile + l[0] * W2 + l[1] * W + l[2];
+        T s = T(0), gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll 1
+        for (int a = 0; a < P; ++a) {
+            const T *pl = base - a * W2;
+            T sa = T(0), ga = T(0), gza = T(0);
 #pragma unroll
-        for (int c = 0; c < P; ++c) {
-            ox[c] = (l[0] - c) * W * W;
-            oy[c] = (l[1] - c) * W;
-            oz[c] = l[2] - c;
+            for (int bb = 0; bb < P; ++bb) {
+                const T *row = pl - bb * W;
+                T sz = T(0), dzs = T(0);
+#pragma unroll
+                for (int c = 0; c < P; ++c) {
+                    const T v = row[-c];
+                    sz += cz[c] * v;
+                    dzs += dz[c] * v;
+                }
+                sa += cy[bb] * sz;
+                ga += dy[bb] * sz;
+                gza += cy[bb] * dzs;
+            }
+            s += cx[0] * sa;
+            gx += dx[0] * sa;
+            gy += cx[0] * ga;
+            gz += cx[0] * gza;
+            shift_down<T, P>(cx, dx);
         }
-        T s, gx, gy, gz;
-        gather_core<T, P>(tile, ox, oy, oz, w, s, gx, gy, gz);
         const double qk = -(double)pr.w * kl;
         f[3 * (int64_t)slot + 0] = qk * (double)gx;
         f[3 * (int64_t)slot + 1] = qk * (double)gy;
@@ -525,53 +582,96 @@ cudaError_t upload_axis(Plan &p, SpmeState &s, cudaStream_t st)
     return e;
 }
 
-// Brick size of the tiled spreading for the plan's cell grid: the largest bc (cells per
-// brick side, <= 8) whose tile and chunk fit in half of an SM's shared memory (two blocks per
+// Tile side (mesh points) of bricks of bc cells per side on an nc-cell grid with K mesh
+// points per side and splines of order P: the largest brick's mesh extent plus P + 2.
+static int tile_side(int nc, int K, int P, int bc)
+{
+    int W = 0;
+    for (int b = 0; b * bc < nc; ++b) {
+        const int c0 = b * bc, c1 = c0 + bc < nc ? c0 + bc : nc;
+        const int w = (int)(((int64_t)c1 * K) / nc - ((int64_t)c0 * K) / nc) + P + 2;
+        if (w > W) W = w;
+    }
+    return W;
+}
+
+// Brick sizes for the plan's cell grid (bc = 0: no tile fits, e.g. the single cell of a
+// small box).  Spreading: the largest bc (cells per brick side, <= 8) whose tile (W <= 40,
+// row pitch S = 24 or 40) and chunk fit in half of an SM's shared memory (two blocks per
 // SM) while the bricks still fill every SM once; else the largest that fits in one SM's
-// shared memory with that many bricks; else the smallest brick that fits at all (small
-// grids); bc = 0 when none does (e.g. the single cell of a small box).
+// shared memory with that many bricks; else the smallest brick that fits.  Gather: the
+// smallest bc whose bricks hold >= 128 particles on average (one thread per particle), if
+// its tile fits in half of an SM's shared memory and the bricks
+// fill the SMs; else the spreading's bricks.  (The gather's tile is W^3 with no padding.)
 template <class T, int P>
-void choose_tiling(Plan &p, SpmeState &s)
+void choose_tiling(Plan &p, SpmeState &s, int64_t n)
 {
     const int nc = p.nc, K = s.K;
     const int chunk = sizeof(T) == 4 ? 128 : 64;
     const size_t max_smem = 227 * 1024 - 1024;
+    auto pitch = [](int W) { return W <= 24 ? 24 : 40; };
+    auto spread_smem = [&](int W) {
+        return (((size_t)W * W * pitch(W) + (size_t)chunk * 3 * P) * sizeof(T) + 7) / 8 * 8 +
+               (size_t)chunk * sizeof(int2);
+    };
     int pick[3] = {0, 0, 0};
-    size_t pick_smem[3] = {0, 0, 0};
-    int pick_W[3] = {0, 0, 0};
     for (int bc = 1; bc <= 8 && bc <= nc && p.w > 0; ++bc) {
         const int nbk = (nc + bc - 1) / bc;
-        int W = 0;
-        for (int b = 0; b < nbk; ++b) {
-            const int c0 = b * bc, c1 = c0 + bc < nc ? c0 + bc : nc;
-            const int w = (int)(((int64_t)c1 * K) / nc - ((int64_t)c0 * K) / nc) + P + 2;
-            if (w > W) W = w;
-        }
-        const size_t smem = (size_t)W * W * W * sizeof(T) + (size_t)chunk * (3 * P + 1) * sizeof(T) +
-                            (size_t)chunk * sizeof(int);
-        if (W > 1023 || smem > max_smem) break;
+        const int W = tile_side(nc, K, P, bc);
+        if (W > 40 || spread_smem(W) > max_smem) break;
         const bool fill = (int64_t)nbk * nbk * nbk >= p.num_sms;
-        if (fill && smem <= max_smem / 2) { pick[0] = bc; pick_smem[0] = smem; pick_W[0] = W; }
-        if (fill) { pick[1] = bc; pick_smem[1] = smem; pick_W[1] = W; }
-        if (!pick[2]) { pick[2] = bc; pick_smem[2] = smem; pick_W[2] = W; }
+        if (fill && spread_smem(W) <= max_smem / 2) pick[0] = bc;
+        if (fill) pick[1] = bc;
+        if (!pick[2]) pick[2] = bc;
     }
-    const int k = pick[0] ? 0 : pick[1] ? 1 : 2;
+    const int bc = pick[0] ? pick[0] : pick[1] ? pick[1] : pick[2];
     s.tile_nc = nc;
-    s.bc = pick[k];
-    s.nbk = s.bc ? (nc + s.bc - 1) / s.bc : 0;
-    s.W = pick_W[k];
+    s.bc = bc;
+    s.nbk = bc ? (nc + bc - 1) / bc : 0;
+    s.W = bc ? tile_side(nc, K, P, bc) : 0;
+    s.S = pitch(s.W);
     s.chunk = chunk;
-    s.smem = pick_smem[k];
-    s.smem_g = (size_t)s.W * s.W * s.W * sizeof(T);
-    if (s.bc && (cudaFuncSetAttribute(k_spme_spread_tile<T, P>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)s.smem) != cudaSuccess ||
-                 cudaFuncSetAttribute(k_spme_gather_tile<T, P>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)s.smem_g) != cudaSuccess)) {
-        (void)cudaGetLastError();
-        s.bc = 0;
+    s.smem = bc ? spread_smem(s.W) : 0;
+    s.bc_g = bc;
+    for (int g = bc; g >= 1 && g <= 8 && g <= nc; ++g) {
+        const int nbk = (nc + g - 1) / g;
+        const int W = tile_side(nc, K, P, g);
+        if (W > 40 || (size_t)W * W * W * sizeof(T) > max_smem / 2 ||
+            (int64_t)nbk * nbk * nbk < p.num_sms)
+            break;
+        s.bc_g = g;
+        if ((double)n / ((double)nbk * nbk * nbk) >= 128.0) break;
     }
+    s.nbk_g = s.bc_g ? (nc + s.bc_g - 1) / s.bc_g : 0;
+    s.W_g = s.bc_g ? tile_side(nc, K, P, s.bc_g) : 0;
+    s.smem_g = (size_t)s.W_g * s.W_g * s.W_g * sizeof(T);
+    if (!bc) return;
+    cudaError_t e = s.S == 24
+        ? cudaFuncSetAttribute(k_spme_spread_tile<T, P, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem)
+        : cudaFuncSetAttribute(k_spme_spread_tile<T, P, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spme_gather_tile<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s.smem_g);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        s.bc = s.bc_g = 0;
+    }
+}
+
+template <class T, int P, int S>
+void launch_spread_tile(Plan &p, SpmeState &s, double kl, cudaStream_t st)
+{
+    k_spme_spread_tile<T, P, S><<<(unsigned)((int64_t)s.nbk * s.nbk * s.nbk), P * 32, s.smem, st>>>(
+        p.ws.pg, p.ws.cell_start, p.nc, s.bc, s.nbk, s.W, s.chunk, s.K, kl, s.qfix);
+}
+
+template <class T, int P>
+void launch_gather_tile(Plan &p, SpmeState &s, double kl, cudaStream_t st)
+{
+    k_spme_gather_tile<T, P><<<(unsigned)((int64_t)s.nbk_g * s.nbk_g * s.nbk_g), kThreads,
+                               s.smem_g, st>>>(
+        p.ws.pg, p.ws.cell_start, p.nc, s.bc_g, s.nbk_g, s.W_g, s.K, kl, (const T *)s.mesh,
+        p.ws.f_recip, p.ws.phi_recip);
 }
 
 template <class T, int P>
@@ -583,10 +683,10 @@ cudaError_t launch_spme_p(Plan &p, SpmeState &s, int64_t n, cudaStream_t st)
     const double kl = K / p.L;
     const unsigned gb = (unsigned)((n + kThreads - 1) / kThreads);
     prof_mark(p, kEvRecipStart, st);
-    if (s.tile_nc != p.nc) choose_tiling<T, P>(p, s);
-    if (s.bc > 0)
-        k_spme_spread_tile<T, P><<<(unsigned)((int64_t)s.nbk * s.nbk * s.nbk), P * 32, s.smem, st>>>(
-            p.ws.pg, p.ws.cell_start, p.nc, s.bc, s.nbk, s.W, s.chunk, K, kl, s.qfix);
+    if (s.tile_nc != p.nc || s.tile_n != n) choose_tiling<T, P>(p, s, n);
+    s.tile_n = n;
+    if (s.bc > 0 && s.S == 24) launch_spread_tile<T, P, 24>(p, s, kl, st);
+    else if (s.bc > 0) launch_spread_tile<T, P, 40>(p, s, kl, st);
     else
         k_spme_spread<T, P><<<gb, kThreads, 0, st>>>(n, p.ws.pg, K, kl, s.qfix);
     k_spme_convert<T><<<(unsigned)((m + kThreads - 1) / kThreads), kThreads, 0, st>>>(m, s.qfix, (T *)s.mesh);
@@ -608,10 +708,7 @@ cudaError_t launch_spme_p(Plan &p, SpmeState &s, int64_t n, cudaStream_t st)
     if (sizeof(T) == 4) fr = cufftExecC2R(s.inv, (cufftComplex *)s.spec, (cufftReal *)s.mesh);
     else fr = cufftExecZ2D(s.inv, (cufftDoubleComplex *)s.spec, (cufftDoubleReal *)s.mesh);
     if (fr != CUFFT_SUCCESS) return cudaErrorUnknown;
-    if (s.bc > 0)
-        k_spme_gather_tile<T, P><<<(unsigned)((int64_t)s.nbk * s.nbk * s.nbk), kThreads, s.smem_g, st>>>(
-            p.ws.pg, p.ws.cell_start, p.nc, s.bc, s.nbk, s.W, K, kl, (const T *)s.mesh,
-            p.ws.f_recip, p.ws.phi_recip);
+    if (s.bc_g > 0) launch_gather_tile<T, P>(p, s, kl, st);
     else
         k_spme_gather<T, P><<<gb, kThreads, 0, st>>>(n, p.ws.pg, K, kl, (const T *)s.mesh,
                                                      p.ws.f_recip, p.ws.phi_recip);
