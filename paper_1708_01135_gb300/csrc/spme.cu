@@ -158,9 +158,22 @@ __device__ __forceinline__ int wrap_mesh(int g, int K)
     return g < 0 ? g + K : (g >= K ? g - K : g);
 }
 
-// The fixed-point value of a tile sum (2^-36 resolution, round to nearest even).  The
-// scaling by 2^36 is exact in either precision, so both give llrint(v * 2^36).
-__device__ __forceinline__ long long to_fix(float v) { return __float2ll_rn(v * 68719476736.0f); }
+// The fixed-point value of a tile sum (2^-36 resolution, round to nearest even), equal to
+// llrint(v * 2^36) in either precision.  For FP32 it is put together from 32-bit conversions
+// (a 64-bit conversion runs on the FP64 units): with s = 16 |v| and h = floor(s),
+// |v| 2^36 = h 2^32 + r, r = (s - h) 2^32 in [0, 2^32), where s, h, the fraction s - h
+// (s >= 0) and r are exact in FP32 (r is a float below 2^32, so it rounds to at most
+// 2^32 - 256), and h 2^32 is an even integer, so rounding r rounds |v| 2^36 (ties to even
+// included); rounding to nearest even is odd-symmetric, so the sign is applied last.
+// |v| < 2^26 keeps h in int range.
+__device__ __forceinline__ long long to_fix(float v)
+{
+    const float s = fabsf(v) * 16.0f;
+    const float h = floorf(s);
+    const float r = (s - h) * 4294967296.0f;
+    const long long m = (long long)(int)h * 4294967296ll + (long long)__float2uint_rn(r);
+    return v < 0.0f ? -m : m;
+}
 __device__ __forceinline__ long long to_fix(double v) { return __double2ll_rn(v * kFixScale); }
 
 // Tiled spreading (see the file comment).  Block b is the brick (bx, by, bz) of bc^3 cells;
@@ -480,14 +493,20 @@ k_spme_gather_tile(const double4_32a *__restrict__ pg, const int *__restrict__ c
         rfirst[tid] = f0;
         rpre[tid + 1] = cell_start[base + cx1] - f0;
     }
+    // asynchronous element copies (cp.async): every load of the tile is in flight at once
     for (int lx = 0; lx < W; ++lx) {
         const T *pl = mesh + (int64_t)wrap_mesh(o[0] + lx, K) * K * K;
         for (int ly = warp; ly < W; ly += nw) {
             const T *src = pl + (int64_t)wrap_mesh(o[1] + ly, K) * K;
             T *dst = tile + lx * W2 + ly * W;
-            for (int lz = lane; lz < W; lz += 32) dst[lz] = src[wrap_mesh(o[2] + lz, K)];
+            for (int lz = lane; lz < W; lz += 32)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                                 (uint32_t)__cvta_generic_to_shared(dst + lz)),
+                             "l"(src + wrap_mesh(o[2] + lz, K)), "n"((int)sizeof(T))
+                             : "memory");
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
         rpre[0] = 0;
