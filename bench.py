@@ -7,6 +7,7 @@ one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload random_32768]
                   [--precision mixed|fp64|fp32|mixed_bf16] [--impl ours|reference]
                   [--md STEPS [--dt DT] [--lj] [--kT KT]] [--spme auto|K,p [--spme-rc RC]]
+  (--spme applies to single evaluations and to --md runs)
 
 Timing: inputs resident in HBM; before every step a 512 MiB buffer is written to flush
 the L2 (129 MB); every step is bracketed by CUDA events on the launching stream and the
@@ -74,6 +75,24 @@ def spme_params(spec, beta, L):
         return fft_size(beta * L / SPME_BETA_H[p]), p
     K, p = (int(x) for x in spec.split(","))
     return K, p
+
+
+def run_params(args, n, L):
+    """(r_c, beta, k_max, spme) of a run: the tuned classical parameters, or with --spme the
+    SPME mesh (K, p) at the same beta, or at beta r_c = sqrt(-ln tol) for --spme-rc; the
+    classical k_max at that beta (for the accuracy check) may exceed the library's limit, in
+    which case the plan carries an unused k_max and the classical comparison is skipped."""
+    rc, beta, kmax = params_for(args.workload, n, L)
+    spme = None
+    if args.spme:
+        if args.spme_rc:
+            rc = args.spme_rc
+            beta = math.sqrt(-math.log(TOL)) / rc
+            kmax = int(math.ceil(math.sqrt(-math.log(TOL)) * beta * L / math.pi))
+        K, order = spme_params(args.spme, beta, L)
+        spme = {"K": K, "order": order, "beta_h": beta * L / K, "classical_k_max": kmax}
+        kmax = min(kmax, 127)
+    return rc, beta, kmax, spme
 
 
 def params_for(workload, n, L):
@@ -402,13 +421,15 @@ def run_md(args, rank, world, local):
     gen, _ = WORKLOADS[args.workload]
     pos, q, L = gen()
     n = len(q)
-    rc, beta, kmax = params_for(args.workload, n, L)
+    rc, beta, kmax, spme = run_params(args, n, L)
     dev = torch.device("cuda", local)
     tq = torch.tensor(q, device=dev)
     F = torch.empty((n, 3), dtype=torch.float64, device=dev)
     steps, dt = args.md, args.dt
     log = torch.empty((steps + 1, MD_RECORD), dtype=torch.float64, device=dev)
     ew = Ewald(L, beta, rc, kmax, args.precision)
+    if spme:
+        ew.set_spme(spme["K"], spme["order"])
     lj_cfg = None
     if args.lj:
         # one Lennard-Jones type for every pair, sigma = the rock-salt spacing and eps that
@@ -464,6 +485,8 @@ def run_md(args, rank, world, local):
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": args.workload, "n": n, "L": L, "r_c": rc, "beta": beta,
                        "k_max": kmax, "dt": dt, "mass": 1.0, "kT0": args.kT, "lj": lj_cfg,
+                       "reciprocal": ({"method": "spme", **spme} if spme else
+                                      {"method": "classical k-space sum"}),
                        "precision": args.precision,
                        "l2": "not flushed: the MD state stays resident from step to step",
                        "parallelism": f"replicas x{world}"},
@@ -562,20 +585,7 @@ def main():
     gen, _ = WORKLOADS[args.workload]
     pos, q, L = gen()
     n = len(q)
-    rc, beta, kmax = params_for(args.workload, n, L)
-    spme = None
-    if args.spme:
-        from paper_1708_01135_gb300 import tune
-        if args.spme_rc:
-            # beta r_c = sqrt(-ln tol), as the tuner's rule; the classical k_max at this beta
-            # (for the accuracy check) may exceed the library's limit, in which case the plan
-            # carries an unused k_max and the check is skipped
-            rc = args.spme_rc
-            beta = math.sqrt(-math.log(TOL)) / rc
-            kmax = int(math.ceil(math.sqrt(-math.log(TOL)) * beta * L / math.pi))
-        K, order = spme_params(args.spme, beta, L)
-        spme = {"K": K, "order": order, "beta_h": beta * L / K, "classical_k_max": kmax}
-        kmax = min(kmax, 127)
+    rc, beta, kmax, spme = run_params(args, n, L)
     dev = torch.device("cuda", local)
     tp = torch.tensor(pos, device=dev)
     tq = torch.tensor(q, device=dev)
