@@ -20,7 +20,10 @@ namespace {
 __device__ __forceinline__ double wrap_box(double x, double L)
 {
     // x - L floor(x / L), with explicit rounding steps (no fused multiply-add) so that the
-    // result is reproducible on any IEEE machine; a result equal to L maps to 0.
+    // result is reproducible on any IEEE machine; a result equal to L maps to 0.  A position
+    // already in [0, L) gives the same result without the FP64 division: x / L rounds to at
+    // most 1 - 2^-53 there, so the floor is 0 and the result is x - 0 (+0 for x = -0).
+    if (x >= 0.0 && x < L) return __dadd_rn(x, 0.0);
     double w = __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
     return (w >= L) ? 0.0 : w;
 }
@@ -148,7 +151,21 @@ __global__ void k_scatter(int64_t n, int64_t chunk, int ncells, const int *__res
     int *keys = sh;                              // [chunk]
     int *row = hist + (int64_t)b * ncells;
     int *off = use_smem ? sh + chunk : row;
-    for (int c = threadIdx.x; c < ncells; c += blockDim.x) off[c] = row[c] + cell_start[c];
+    // (eight cells per thread per step, so that the loads overlap)
+    for (int c0 = threadIdx.x; c0 < ncells; c0 += 8 * blockDim.x) {
+        int r[8], s[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = c0 + u * blockDim.x;
+            r[u] = c < ncells ? row[c] : 0;
+            s[u] = c < ncells ? cell_start[c] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = c0 + u * blockDim.x;
+            if (c < ncells) off[c] = r[u] + s[u];
+        }
+    }
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) keys[i] = key[beg + i];
     __syncthreads();
     if (threadIdx.x >= 32) return;
