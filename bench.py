@@ -515,16 +515,35 @@ def run_reference(args, rank, world):
     pos, q, L = gen()
     n = len(q)
     rc, beta, kmax = params_for(args.workload, n, L)
-    targets = args.cpu_targets
+    nk = len(oracle.kset_half(kmax))
+    S0 = np.zeros(nk, dtype=complex)
+    # every step times a sample sized so that the whole run takes about two and a half
+    # minutes (between 0.5 s and 10 s of oracle work a step): a small probe measures the
+    # oracle's rates, then each step takes S(k) over the modes and the forces of the targets
+    # that fill half of its budget each (see oracle_sample for the scaling to the full N)
+    budget = min(10.0, max(0.5, 150.0 / (args.warmup + args.steps)))
+    ms = oracle.kset_half(kmax)[: max(1, min(nk, int(2e7 // n)))]
+    t0 = time.perf_counter()
+    oracle.structure_factor(pos, q, L, ms)
+    c_s = max(1e-13, (time.perf_counter() - t0) / (len(ms) * n))      # s per (mode, particle)
+    probe = np.arange(min(16, n))
+    t0 = time.perf_counter()
+    oracle.real(pos, q, L, beta, rc, sub=probe)
+    oracle.recip(pos, q, L, beta, kmax, sub=probe, S=S0)
+    c_t = max(1e-9, (time.perf_counter() - t0) / len(probe))          # s per target
+    targets = int(min(args.cpu_targets, max(16, 0.5 * budget / c_t)))
+    max_terms = max(float(n), 0.5 * budget / c_s)
     times = []
     for s in range(args.warmup + args.steps):
         full, wall, nt, _, _, note = oracle_sample(pos, q, L, beta, rc, kmax, targets, seed=s,
-                                                   S_given=np.zeros(len(oracle.kset_half(kmax)),
-                                                                    dtype=complex))
+                                                   S_given=S0, max_sk_terms=max_terms)
         if s >= args.warmup:
             times.append(full)
     t = float(np.mean(times))
     value = n / t
+    note = note.replace("(reciprocal forces from the GPU's S(k))",
+                        "(reciprocal forces of the targets timed against a stand-in S(k) of "
+                        "the same size)")
     line = {
         "impl": "reference", "metric": "ewald_particles_per_s", "value": value,
         "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
