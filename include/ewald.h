@@ -212,14 +212,16 @@ int ewald_set_lj(ewald_plan_t plan, int ntypes, const double *epsilon, const dou
  * used while SPME is on, and ewald_structure_factor returns EWALD_E_UNSUPPORTED.
  *   K      mesh points per side (even order <= K <= 1024), or 0 to return to the classical sum
  *   order  B-spline order p: 4, 6, 8, 10 or 12
- * Charges are spread with p^3 weights per particle onto a fixed-point mesh (64-bit integer
- * atomics, 2^-36 resolution), so results repeat bit for bit; an evaluation with
- * sum |q| >= 2^26 reports EWALD_E_UNSUPPORTED (the mesh could overflow).  The mesh, its
+ * Charges are spread with p^3 weights per particle, brick by brick of the cell grid in shared
+ * memory, and the brick sums are added to a fixed-point mesh (64-bit integer atomics, 2^-36
+ * resolution), so results repeat bit for bit; an evaluation with sum |q| >= 2^26 reports
+ * EWALD_E_UNSUPPORTED (the mesh could overflow).  The mesh, its
  * transforms (cuFFT) and the particle-side splines are FP32 on the mixed and FP32 plans,
  * FP64 on the FP64 plan.  The error of the mesh approximation falls with K and p (about
  * (beta L / (pi K))^p); it adds to the real-space and k-space truncation errors.
  * Synchronises the plan's streams; allocates the mesh (about 8 + 4 (or 8) x 2 bytes per
- * mesh point) and two cuFFT plans.  Returns EWALD_E_INVAL, EWALD_E_NOMEM,
+ * mesh point) and two cuFFT plans.  The first evaluation after a change of the particle
+ * count or cell grid also sets the brick sizes of the spreading (host work only).  Returns EWALD_E_INVAL, EWALD_E_NOMEM,
  * EWALD_E_UNSUPPORTED (cuFFT plan failure) or EWALD_E_CUDA.
  */
 int ewald_set_spme(ewald_plan_t plan, int K, int order);
