@@ -84,6 +84,8 @@ def test_null_handles_are_rejected():
     r = E._Result()
     assert lib.ewald_poll(None, 1, ctypes.byref(r)) == E.E_INVAL
     assert lib.ewald_md(None, 4, None, None, None, None, 1e-3, 10, None, None, None) == E.E_INVAL
+    assert lib.ewald_set_spme(None, 32, 8) == E.E_INVAL
+    assert lib.ewald_set_lj(None, 1, None, None, None) == E.E_INVAL
 
 
 def test_realspace_erfc_fit_meets_its_published_bound():
