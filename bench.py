@@ -117,6 +117,23 @@ def row_nxmax(kmax):
     return sorted(out)
 
 
+def len_kset_half(kmax):
+    """|K_half|: integer m != 0 with |m|^2 <= k_max^2 in the half space (m_z > 0, or m_z = 0
+    and m_y > 0, or m_z = m_y = 0 and m_x > 0)."""
+    cnt = 0
+    for mz in range(kmax + 1):
+        for my in range(-kmax, kmax + 1):
+            r = kmax * kmax - my * my - mz * mz
+            if r < 0:
+                continue
+            nx = math.isqrt(r)
+            if mz > 0 or my > 0:
+                cnt += 2 * nx + 1
+            elif my == 0 and mz == 0:
+                cnt += nx
+    return cnt
+
+
 def rows_count(kmax):
     return len(row_nxmax(kmax))
 
@@ -714,6 +731,17 @@ def main():
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_kind": "nominal FP64/FP32 CUDA-core rate (unit counts x clock)"}
     stages_ms = {k: float(np.median(v)) for k, v in stage.items()}
+    # the method's own work per evaluation, whatever the kernels issue: 40 flop per pair
+    # evaluation within r_c (each pair from both sides, N (4 pi / 3) r_c^3 rho of them) and,
+    # for the classical sum, 18 flop per (particle, mode) term (one complex multiply-add for
+    # S(k), ~10 flop for the back-scatter), over the whole step time
+    pairs = n * (4.0 * math.pi / 3.0) * rc ** 3 * (n / L ** 3)
+    nk = 0 if spme else len_kset_half(kmax)
+    algo = {"real_pair_evaluations": pairs, "recip_terms": float(n) * nk,
+            "flop": 40.0 * pairs + 18.0 * n * nk,
+            "tflops_over_step": (40.0 * pairs + 18.0 * n * nk) / (ms * 1e-3) / 1e12,
+            "note": ("SPME mesh work not counted" if spme else
+                     "classical k-space sum over the half-space modes")}
 
     # the plain FP64 GPU path on the same system and parameters
     fp64 = None
@@ -789,6 +817,7 @@ def main():
             "gpu_launches": launches,
             "roofline": roof,
             "stages_ms": stages_ms,
+            "algorithmic": algo,
             "clocks": clk,
             "cpu_baseline": cpu,
             "accuracy": accuracy,

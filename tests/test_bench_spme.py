@@ -1,5 +1,5 @@
-"""Host-side helpers of the SPME benchmark line (no GPU): FFT-friendly mesh sizes and the
-mesh rule of bench.spme_params."""
+"""Host-side helpers of the benchmark (no GPU): FFT-friendly mesh sizes, the SPME mesh rule
+of bench.spme_params, and the half-space mode count of the algorithmic work figure."""
 import math
 
 import bench
@@ -25,3 +25,9 @@ def test_spme_params_auto_and_explicit():
         assert K == bench.fft_size(beta * L / bh)
     assert bench.spme_params("auto", beta, L)[1] == 8
     assert bench.spme_params("64,10", beta, L) == (64, 10)
+
+
+def test_half_space_mode_count_matches_the_oracle_k_set():
+    import oracle
+    for k in (1, 2, 5, 8, 10, 36):
+        assert bench.len_kset_half(k) == len(oracle.kset_half(k))
