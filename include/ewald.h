@@ -226,6 +226,17 @@ int ewald_set_lj(ewald_plan_t plan, int ntypes, const double *epsilon, const dou
  */
 int ewald_set_spme(ewald_plan_t plan, int K, int order);
 
+/*
+ * ewald_probe_timeout - diagnostic of the failure path of the device-side waits (not part of
+ * the paper's method).  Every wait of the library's kernels on an asynchronous copy gives up
+ * after about one second and records EWALD_E_TIMEOUT in the plan's status instead of hanging
+ * the GPU.  This call launches, on `stream`, one warp that waits in the same way on a
+ * barrier that nothing completes, so the next ewald_status_sync of the plan returns
+ * EWALD_E_TIMEOUT (about one second later) and the device stays usable.  Returns
+ * EWALD_E_INVAL for a null plan, EWALD_E_CUDA if the launch fails.
+ */
+int ewald_probe_timeout(ewald_plan_t plan, void *stream);
+
 /* ewald_status_sync - synchronise the plan's last stream and return (and clear) the
  * device-side status of the last evaluation: EWALD_OK, EWALD_E_NONNEUTRAL,
  * EWALD_E_NONFINITE, EWALD_E_TIMEOUT or EWALD_E_CUDA. */

@@ -885,6 +885,12 @@ extern "C" int ewald_set_spme(ewald_plan_t plan, int K, int order)
     return spme_set(p, K, order);
 }
 
+extern "C" int ewald_probe_timeout(ewald_plan_t plan, void *stream)
+{
+    if (!plan) return EWALD_E_INVAL;
+    return cuda_status(launch_wait_probe(plan->p, (cudaStream_t)stream));
+}
+
 extern "C" int ewald_status_sync(ewald_plan_t plan)
 {
     if (!plan) return EWALD_E_INVAL;

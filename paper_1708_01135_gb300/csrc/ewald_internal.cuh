@@ -172,6 +172,8 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
 // a4: real-space pairs into ws.f_real / ws.phi_real / ws.e_tile (sorted order), and with
 // virial the per-tile virial sums into ws.vir_tile.
 cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st, bool virial);
+// One bounded device wait that cannot complete (the timeout path of the staged copies).
+cudaError_t launch_wait_probe(Plan &p, cudaStream_t st);
 int64_t real_tile_capacity(const Plan &p, int64_t n);
 int real_tile_size(const Plan &p);          // particles per real-space tile
 int real_tile_for(int w, double cell_occupancy);   // tile size for a grid (particles per cell)

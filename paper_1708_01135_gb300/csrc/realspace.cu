@@ -109,6 +109,20 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
     }
 }
 
+// The failure path of the bounded waits: one warp waits on an mbarrier phase that nothing
+// completes (no copy is issued and nobody arrives), gives up after ~1 s exactly as a pair
+// kernel whose staged copy never lands, and sets the timeout bit of the status word.
+__global__ void k_wait_probe(int *__restrict__ status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if (!warp_wait(&bar, 0u) && threadIdx.x == 0) atomicOr(status, kStTimeout);
+}
+
 template <class T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4_32a; };
@@ -664,6 +678,13 @@ int real_tile_for(int w, double cell_occupancy)
 {
     if (w == 0) return 32;
     return cell_occupancy >= 16.0 ? kTileDense : kTileSparse;
+}
+
+cudaError_t launch_wait_probe(Plan &p, cudaStream_t st)
+{
+    k_wait_probe<<<1, 32, 0, st>>>(p.d_status);
+    p.last_stream = st;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st, bool virial)

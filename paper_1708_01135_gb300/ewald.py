@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
                 "ewald_compute_virial_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
                 "ewald_set_lj": (_i, [_p, _i, _p, _p, _p]),
                 "ewald_set_spme": (_i, [_p, _i, _i]),
+                "ewald_probe_timeout": (_i, [_p, _p]),
                 "ewald_status_sync": (_i, [_p]),
                 "ewald_compute_host": (_i, [_p, _i64, _p, _p, _p, _p, _p]),
                 "ewald_plan_info": (_i, [_p, _p]),
@@ -255,6 +256,11 @@ class Ewald:
         """Reciprocal part by smooth particle-mesh Ewald on a K^3 mesh with B-splines of the
         given even order (ewald_set_spme); K = 0 returns to the classical k-space sum."""
         _check(lib().ewald_set_spme(self._h, int(K), int(order)), "ewald_set_spme")
+
+    def probe_timeout(self, stream=None):
+        """One device wait that cannot complete (ewald_probe_timeout): the next status() is
+        the timeout status, about one second later."""
+        _check(lib().ewald_probe_timeout(self._h, _stream_handle(stream)), "ewald_probe_timeout")
 
     def status(self) -> int:
         """Synchronise and return the device-side status of the last evaluation."""

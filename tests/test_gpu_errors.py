@@ -1,6 +1,7 @@
 """Edge cases and error statuses of the C ABI on the GPU: empty input, tiny systems,
 non-neutral and non-finite input reported as status codes, and the paper's degenerate
-cases (a single neutral pair, r_c = L/2 exactly on a lattice)."""
+cases (a single neutral pair, r_c = L/2 exactly on a lattice), and the timeout path of the
+bounded device waits."""
 import math
 
 import numpy as np
@@ -73,3 +74,25 @@ def test_unjittered_lattice_at_half_box_cutoff():
         F, e = ew.compute(dev(pos), dev(q))
     assert rel(e[0], ref["E_real"]) < 1e-12
     assert np.abs(F.cpu().numpy()).max() < 1e-10
+
+
+def test_bounded_device_wait_times_out_and_the_device_stays_usable():
+    """A device wait that can never complete (a barrier nothing arrives at, the way a staged
+    copy that never landed would look) gives up after about a second and reports
+    EWALD_E_TIMEOUT through the plan's status; the next evaluation on the same plan is
+    correct, so the context survived."""
+    need_gpu()
+    import time
+    pos, q, L = W.rocksalt_512()
+    ref = oracle.ewald(pos, q, L, 1.0, 4.0, 10)
+    with Ewald(L, 1.0, 4.0, 10, "mixed") as ew:
+        t0 = time.perf_counter()
+        ew.probe_timeout()
+        st = ew.status()
+        dt = time.perf_counter() - t0
+        assert st == E.E_TIMEOUT
+        assert 0.5 < dt < 60.0
+        F, e = ew.compute(dev(pos), dev(q))
+        assert ew.status() == 0
+    assert rel_rms(F.cpu().numpy(), ref["F"]) < 1e-5
+    assert rel(e[3], ref["E_total"]) < 1e-5
