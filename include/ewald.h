@@ -439,6 +439,22 @@ int ewald_server_stats(ewald_server_t srv, int64_t stats[5]);
  * poll results are dropped), stop the scheduler and free everything. */
 int ewald_server_destroy(ewald_server_t srv);
 
+/*
+ * ewald_server_simulate - replay the server's admission policy on the host with a simulated
+ * executor (no device work; the policy function is the one the scheduler thread runs).
+ * Request i (0 <= i < n, arrivals in non-decreasing t_arrive, index order at equal times)
+ * holds footprint[i] bytes (<= budget) and runs for duration[i] seconds once admitted; a
+ * finished slot keeps its memory until the policy reclaims it.  After every arrival or
+ * completion the admission pass runs: first fit in arrival order on the idle slot holding the
+ * most memory, idle slots' memory reclaimed while a request does not fit, and at most 64
+ * admissions past a waiting head of the queue.  Writes order[k] = the k-th admitted request,
+ * t_admit[i] = its admission time and *peak_held = the largest total held.  Returns
+ * EWALD_E_INVAL for bad arguments.
+ */
+int ewald_server_simulate(int max_slots, int64_t budget, int n, const int64_t *footprint,
+                          const double *t_arrive, const double *duration, int64_t *order,
+                          double *t_admit, int64_t *peak_held);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,41 @@ int cuda_st(cudaError_t e)
     return e == cudaErrorMemoryAllocation ? EWALD_E_NOMEM : EWALD_E_CUDA;
 }
 
+// One step of the admission policy for the queued request at the front of the scan (pure
+// host logic: the scheduler and ewald_server_simulate share it).  The request (footprint
+// fp, is_head when it is the first in the queue) would run on the idle slot that holds the
+// most memory (the first such slot); if the held total with it exceeds the budget, the
+// idle slots other than that one give back their workspaces, in slot order, until it fits
+// (they are reclaimed even if it still does not).  Returns kAdmitStop when no slot is idle,
+// or when the request fits but is not the head and the head has already been passed over
+// max_bypass times; kAdmitSkip when it does not fit (the scan goes on with the next
+// request); kAdmitTake when it is admitted on *slot.
+enum AdmitAction { kAdmitStop = 0, kAdmitSkip = 1, kAdmitTake = 2 };
+struct AdmitSlot {
+    bool busy;
+    int64_t held;
+};
+int admit_step(int64_t fp, bool is_head, const std::vector<AdmitSlot> &slots, int64_t held_total,
+               int64_t budget, int head_bypass, int max_bypass, int *slot,
+               std::vector<int> *reclaim)
+{
+    reclaim->clear();
+    int fs = -1;
+    for (int i = 0; i < (int)slots.size(); ++i)
+        if (!slots[i].busy && (fs < 0 || slots[i].held > slots[fs].held)) fs = i;
+    if (fs < 0) return kAdmitStop;
+    int64_t after = held_total - slots[fs].held + fp;
+    for (int i = 0; i < (int)slots.size() && after > budget; ++i) {
+        if (slots[i].busy || i == fs || slots[i].held == 0) continue;
+        reclaim->push_back(i);
+        after -= slots[i].held;
+    }
+    if (after > budget) return kAdmitSkip;
+    if (!is_head && head_bypass >= max_bypass) return kAdmitStop;
+    *slot = fs;
+    return kAdmitTake;
+}
+
 }  // namespace
 
 struct ewald_server {
@@ -180,43 +215,39 @@ void scheduler(ewald_server *s)
         // first reclaims the workspaces of idle slots; once the head of the queue has been
         // passed over kMaxBypass times, nothing behind it is admitted before it.
         if (!s->stop) {
+            std::vector<AdmitSlot> view(s->slots.size());
+            std::vector<int> reclaim;
             for (auto it = s->queue.begin(); it != s->queue.end();) {
-                Slot *free_slot = nullptr;
-                for (Slot &sl : s->slots)
-                    if (!sl.busy && (!free_slot || sl.held > free_slot->held)) free_slot = &sl;
-                if (!free_slot) break;
+                for (size_t i = 0; i < s->slots.size(); ++i)
+                    view[i] = AdmitSlot{s->slots[i].busy, (int64_t)s->slots[i].held};
                 const bool is_head = it == s->queue.begin();
-                int64_t after = s->held_total - (int64_t)free_slot->held + (int64_t)it->footprint;
-                if (after > (int64_t)s->budget) {
-                    for (Slot &sl : s->slots) {
-                        if (after <= (int64_t)s->budget) break;
-                        if (sl.busy || &sl == free_slot || sl.held == 0) continue;
-                        lk.unlock();
-                        if (sl.plan) { ewald_destroy(sl.plan); sl.plan = nullptr; }
-                        lk.lock();
-                        s->held_total -= (int64_t)sl.held;
-                        after -= (int64_t)sl.held;
-                        sl.held = 0;
-                    }
+                int si = -1;
+                const int act = admit_step((int64_t)it->footprint, is_head, view, s->held_total,
+                                           (int64_t)s->budget, s->head_bypass, kMaxBypass, &si,
+                                           &reclaim);
+                for (int r : reclaim) {
+                    Slot &sl = s->slots[r];
+                    lk.unlock();
+                    if (sl.plan) { ewald_destroy(sl.plan); sl.plan = nullptr; }
+                    lk.lock();
+                    s->held_total -= (int64_t)sl.held;
+                    sl.held = 0;
                 }
-                if (after > (int64_t)s->budget) {   // does not fit now: try the next one
+                if (act == kAdmitStop) break;
+                if (act == kAdmitSkip) {   // does not fit now: try the next one
                     ++it;
                     continue;
                 }
-                if (is_head) {
-                    s->head_bypass = 0;
-                } else {
-                    if (s->head_bypass >= kMaxBypass) break;   // the head has waited long enough
-                    ++s->head_bypass;
-                }
+                if (is_head) s->head_bypass = 0;
+                else ++s->head_bypass;
                 Pending pd = *it;
                 it = s->queue.erase(it);
-                Slot &sl = *free_slot;
+                Slot &sl = s->slots[si];
                 sl.busy = true;
                 sl.ticket = pd.ticket;
                 sl.t_submit = pd.t_submit;
                 sl.footprint = pd.footprint;
-                s->held_total = after;
+                s->held_total += (int64_t)pd.footprint - (int64_t)sl.held;
                 sl.held = pd.footprint;
                 if (s->held_total > s->peak_held) s->peak_held = s->held_total;
                 s->state[pd.ticket] = 1;
@@ -364,5 +395,68 @@ extern "C" int ewald_server_destroy(ewald_server_t s)
         if (sl.status_h) cudaFreeHost(sl.status_h);
     }
     delete s;
+    return EWALD_OK;
+}
+
+// Host-only replay of the admission policy with a simulated executor (no device work): the
+// requests arrive at t_arrive (in index order at equal times), each runs for its duration
+// once admitted, a finished slot keeps its memory until reclaimed, and after every event the
+// scheduler's admission pass runs (first fit in arrival order, restarted from the head after
+// every admission) with the same admit_step.  Writes the admission order (request indices)
+// and times, and the peak of the held total.
+extern "C" int ewald_server_simulate(int max_slots, int64_t budget, int n,
+                                     const int64_t *footprint, const double *t_arrive,
+                                     const double *duration, int64_t *order, double *t_admit,
+                                     int64_t *peak_held)
+{
+    if (max_slots < 1 || max_slots > 64 || budget < 0 || n < 0 || (n > 0 && (!footprint ||
+        !t_arrive || !duration || !order || !t_admit)) || !peak_held)
+        return EWALD_E_INVAL;
+    for (int i = 0; i < n; ++i)
+        if (footprint[i] < 0 || footprint[i] > budget || !(duration[i] >= 0) ||
+            !(t_arrive[i] >= 0) || (i > 0 && t_arrive[i] < t_arrive[i - 1]))
+            return EWALD_E_INVAL;
+    std::vector<AdmitSlot> slots(max_slots, AdmitSlot{false, 0});
+    std::vector<double> ends(max_slots, 0.0);
+    std::deque<int> queue;
+    std::vector<int> reclaim;
+    int64_t held = 0, peak = 0;
+    int bypass = 0, next = 0, admitted = 0;
+    double t = 0.0;
+    while (admitted < n) {
+        // next event: an arrival or the end of a running request
+        double tn = next < n ? t_arrive[next] : 1e300;
+        for (int i = 0; i < max_slots; ++i)
+            if (slots[i].busy && ends[i] < tn) tn = ends[i];
+        if (tn >= 1e300) return EWALD_E_INVAL;   // nothing can ever be admitted
+        t = tn;
+        for (int i = 0; i < max_slots; ++i)
+            if (slots[i].busy && ends[i] <= t) slots[i].busy = false;
+        while (next < n && t_arrive[next] <= t) queue.push_back(next++);
+        for (size_t k = 0; k < queue.size();) {
+            int si = -1;
+            const int act = admit_step(footprint[queue[k]], k == 0, slots, held, budget, bypass,
+                                       kMaxBypass, &si, &reclaim);
+            for (int r : reclaim) {
+                held -= slots[r].held;
+                slots[r].held = 0;
+            }
+            if (act == kAdmitStop) break;
+            if (act == kAdmitSkip) { ++k; continue; }
+            bypass = k == 0 ? 0 : bypass + 1;
+            const int i = queue[k];
+            queue.erase(queue.begin() + k);
+            held += footprint[i] - slots[si].held;
+            slots[si].held = footprint[i];
+            slots[si].busy = true;
+            ends[si] = t + duration[i];
+            if (held > peak) peak = held;
+            order[admitted] = i;
+            t_admit[i] = t;
+            ++admitted;
+            k = 0;
+        }
+    }
+    *peak_held = peak;
     return EWALD_OK;
 }

@@ -85,6 +85,8 @@ def lib() -> ctypes.CDLL:
                 "ewald_wait": (_i, [_p, ctypes.c_uint64, _d, ctypes.POINTER(_Result)]),
                 "ewald_server_stats": (_i, [_p, _p]),
                 "ewald_server_destroy": (_i, [_p]),
+                "ewald_server_simulate": (_i, [_i, _i64, _i, _p, _p, _p, _p, _p,
+                                               ctypes.POINTER(_i64)]),
                 "ewald_real_noalloc": (_i, [_d, _d, _d, _i64, _p, _p, _p, _p, _p]),
                 "ewald_md": (_i, [_p, _i64, _p, _p, _p, _p, _d, _i, _p, _p, _p]),
             }
@@ -94,6 +96,23 @@ def lib() -> ctypes.CDLL:
                 f.argtypes = args
             _lib = L
     return _lib
+
+
+def simulate_admission(max_slots: int, budget: int, footprint, t_arrive, duration):
+    """Replay of the server's admission policy on the host (ewald_server_simulate): returns
+    (admission order, admission times, peak held bytes)."""
+    fp = np.ascontiguousarray(footprint, dtype=np.int64)
+    ta = np.ascontiguousarray(t_arrive, dtype=np.float64)
+    du = np.ascontiguousarray(duration, dtype=np.float64)
+    n = len(fp)
+    order = np.zeros(n, dtype=np.int64)
+    tad = np.zeros(n, dtype=np.float64)
+    peak = _i64(0)
+    _check(lib().ewald_server_simulate(int(max_slots), int(budget), n, fp.ctypes.data,
+                                       ta.ctypes.data, du.ctypes.data, order.ctypes.data,
+                                       tad.ctypes.data, ctypes.byref(peak)),
+           "ewald_server_simulate")
+    return order, tad, peak.value
 
 
 def strerror(status: int) -> str:
