@@ -335,6 +335,11 @@ int ewald_md(ewald_plan_t plan, int64_t n, double *pos, double *vel, const doubl
  * Both truncation errors decay as exp(-p^2) with p = beta r_c = pi k_max / (beta L)
  * (Section 3.1.3: r_c ~ alpha^-1/2, k_c ~ alpha^1/2); p is set from tol.  With r_c free,
  * the tuner picks r_c <= L/2 minimising a cost model of pair candidates plus k modes.
+ * The tolerance is relative to the RMS force, and both the truncation errors and the RMS
+ * force scale with the charges squared, so no sum of q^2 enters (the absolute-error forms
+ * of the estimates that Section 3.1.3 points to carry one; for a relative target it
+ * cancels).  r_c is an in/out argument so that a caller can fix the cutoff (a cell grid, a
+ * Lennard-Jones range) and have beta and k_max follow.
  */
 int ewald_tune(int64_t n, double L, double tol, double *r_c, double *beta, int *k_max);
 
@@ -365,8 +370,12 @@ int ewald_tune(int64_t n, double L, double tol, double *r_c, double *beta, int *
  * partials for EWALD_NOALLOC_MAX_N particles, about 516 KB), present on every GPU that loads
  * the library until the process exits.  Every call shares it: calls whose GPU work overlaps
  * (different streams, or unordered calls from several host threads) race and give undefined
- * results.  The first call on a device looks up the array's device address (and may load the
- * library's device code into the context), so make it before any stream capture.
+ * results.  Every call looks up the array's device address in the current context (a host
+ * lookup that allocates nothing) and asks for its kernels' attributes, which loads them into
+ * the context if they are not loaded yet; the first call on a device, with any n (n = 0
+ * included), may therefore load the library's device code, so make it before any stream
+ * capture.  A launch failure of this call returns EWALD_E_CUDA; errors left pending by other
+ * work are not reported or cleared.
  */
 #define EWALD_NOALLOC_MAX_N 16384
 int ewald_real_noalloc(double L, double beta, double r_c, int64_t n, const double *pos,

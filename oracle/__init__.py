@@ -51,7 +51,7 @@ def lib():
             L.ewo_kset_half.restype = _i64
             L.ewo_kset_half.argtypes = [ctypes.c_int, _p, _i64]
             L.ewo_real.restype = None
-            L.ewo_real.argtypes = [_i64, _p, _p, _d, _d, _d, _i64, _p, _p, _p, _p]
+            L.ewo_real.argtypes = [_i64, _p, _p, _d, _d, _d, _i64, _p, _p, _p, _p, ctypes.c_int]
             L.ewo_real_cells.restype = ctypes.c_int
             L.ewo_real_cells.argtypes = [_i64, _p, _p, _d, _d, _d, _i64, _p, _p, _p, _p]
             L.ewo_structure_factor.restype = None
@@ -105,8 +105,10 @@ def _sub(sub):
     return None if sub is None else np.ascontiguousarray(sub, dtype=np.int64)
 
 
-def real(pos, q, L, beta, rc, sub=None):
-    """Real-space part: (E_real or None when sub is given, F [nt, 3], phi [nt])."""
+def real(pos, q, L, beta, rc, sub=None, images=False):
+    """Real-space part: (E_real or None when sub is given, F [nt, 3], phi [nt]).  With
+    images=True the sum runs over explicit image shifts even where r_c <= L/2 would take
+    the minimum image directly (the same sum; used to check one branch against the other)."""
     pos, q, sub = _f64(pos), _f64(q), _sub(sub)
     nt = len(q) if sub is None else len(sub)
     F = np.zeros((nt, 3))
@@ -114,7 +116,7 @@ def real(pos, q, L, beta, rc, sub=None):
     e = _d(0.0)
     lib().ewo_real(len(q), _ptr(pos), _ptr(q), float(L), float(beta), float(rc),
                    0 if sub is None else len(sub), _ptr(sub), _ptr(F), _ptr(phi),
-                   ctypes.byref(e) if sub is None else None)
+                   ctypes.byref(e) if sub is None else None, int(bool(images)))
     return (e.value if sub is None else None), F, phi
 
 

@@ -123,15 +123,19 @@ int64_t ewo_kset_half(int kmax, int32_t *m_out, int64_t cap)
  * Pairs are counted when 0 < d < r_c (strict, as Listing 1's mask).  For r_c <= L/2 only the
  * nearest image along every axis can lie inside the cutoff, so that image is taken directly;
  * otherwise every shift n with |n_a| <= ceil(r_c / L) is visited (including the particle's
- * own images, which add energy but no net force).
+ * own images, which add energy but no net force).  With force_images != 0 the image loop is
+ * taken whatever r_c is: for r_c <= L/2 it visits the 27 shifts |n_a| <= 1 and keeps those
+ * within r_c, which is the same sum as the minimum image term by term (the tests compare
+ * the two branches this way).
  */
 void ewo_real(int64_t n, const double *pos, const double *q, double L, double beta, double rc,
-              int64_t nsub, const int64_t *sub, double *F_out, double *phi_out, double *e_real)
+              int64_t nsub, const int64_t *sub, double *F_out, double *phi_out, double *e_real,
+              int force_images)
 {
     const int64_t nt = sub ? nsub : n;
     const double rc2 = rc * rc;
     const double two_beta_rpi = 2.0 * beta / sqrt(EWO_PI);
-    const int min_image = (rc <= 0.5 * L);
+    const int min_image = (rc <= 0.5 * L) && !force_images;
     const int ms = (int)ceil(rc / L);
     /* phi is needed for the energy even when the caller does not want it */
     double *phi_tmp = phi_out;

@@ -21,14 +21,17 @@
 // ordering) race on the scratch and give undefined results.
 //
 // In host code the array's name is only a host-side stand-in for the device symbol; its
-// device address comes from cudaGetSymbolAddress, looked up once per device (with that
-// device current) by the first call made on that device.  That first call may also load the
-// library's device code into the context, so it should come before any stream capture.
+// device address comes from cudaGetSymbolAddress, looked up on every call with the caller's
+// device current (a host-side lookup that allocates nothing), so an address never outlives
+// the context it belongs to (after cudaDeviceReset, or for another context on the same
+// device).  Every call also asks for the attributes of its three kernels, which makes the
+// runtime load them into the context if lazy loading has not done so yet; the first call on
+// a device may therefore load the library's device code, and it should come before any
+// stream capture.  Each launch is checked by its own return code, so an error left pending
+// by some unrelated earlier launch is neither reported as this call's nor cleared.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
-
-#include <mutex>
 
 #include "ewald_internal.cuh"
 
@@ -41,9 +44,6 @@ constexpr size_t kPackBytes = sizeof(double4_32a) * (size_t)kMaxN;
 constexpr size_t kScratchBytes = kPackBytes + sizeof(double) * (size_t)kTiles;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-
-std::mutex g_mu;
-void *g_scratch_addr[256] = {};   // per device ordinal: device address of g_scratch
 
 // Wrap into [0, L) and pack (x, y, z, q) as FP64.
 __global__ void k_na_pack(int n, const double *__restrict__ pos, const double *__restrict__ q,
@@ -121,6 +121,16 @@ __global__ void k_na_energy(int ntiles, const double *__restrict__ e_tile,
     }
 }
 
+// Launch with the launch's own status (cudaLaunchKernel returns the error of this launch).
+template <class T> struct same { using type = T; };
+template <class... A>
+cudaError_t launch(void (*k)(A...), unsigned grid, unsigned block, cudaStream_t st,
+                   typename same<A>::type... a)
+{
+    void *args[] = {(void *)&a...};
+    return cudaLaunchKernel((const void *)k, dim3(grid), dim3(block), args, 0, st);
+}
+
 }  // namespace
 
 extern "C" int ewald_real_noalloc(double L, double beta, double r_c, int64_t n, const double *pos,
@@ -132,27 +142,30 @@ extern "C" int ewald_real_noalloc(double L, double beta, double r_c, int64_t n, 
     if (n < 0 || !energy_dev) return EWALD_E_INVAL;
     if (n > kMaxN) return EWALD_E_UNSUPPORTED;
     if (n > 0 && (!pos || !q || !forces)) return EWALD_E_INVAL;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return EWALD_E_CUDA;
+    // every kernel of this entry point is loaded into the current context now, whatever n is
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_na_pack) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_na_pairs) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_na_energy) != cudaSuccess)
+        return EWALD_E_CUDA;
     void *base = nullptr;
-    {
-        std::lock_guard<std::mutex> g(g_mu);
-        if (!g_scratch_addr[dev]) {
-            void *a = nullptr;
-            if (cudaGetSymbolAddress(&a, g_scratch) != cudaSuccess || !a) return EWALD_E_CUDA;
-            g_scratch_addr[dev] = a;
-        }
-        base = g_scratch_addr[dev];
-    }
+    if (cudaGetSymbolAddress(&base, g_scratch) != cudaSuccess || !base) return EWALD_E_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     double4_32a *packed = reinterpret_cast<double4_32a *>(base);
     double *e_tile = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + kPackBytes);
-    const int ntiles = (int)((n + kTile - 1) / kTile);
-    if (n > 0) {
-        k_na_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((int)n, pos, q, L, packed);
-        k_na_pairs<<<(unsigned)((ntiles * 32 + 127) / 128), 128, 0, st>>>(
-            (int)n, packed, L, r_c * r_c, beta, 2.0 * beta / sqrt(ew::kPi), forces, e_tile);
+    const int ni = (int)n;
+    const int ntiles = (ni + kTile - 1) / kTile;
+    if (ni > 0) {
+        if (launch(k_na_pack, (unsigned)((ni + 255) / 256), 256u, st, ni, pos, q, L, packed) !=
+            cudaSuccess)
+            return EWALD_E_CUDA;
+        if (launch(k_na_pairs, (unsigned)((ntiles * 32 + 127) / 128), 128u, st, ni,
+                   (const double4_32a *)packed, L, r_c * r_c, beta, 2.0 * beta / sqrt(ew::kPi),
+                   forces, e_tile) != cudaSuccess)
+            return EWALD_E_CUDA;
     }
-    k_na_energy<<<1, 256, 0, st>>>(ntiles, e_tile, energy_dev);
-    return cudaGetLastError() == cudaSuccess ? EWALD_OK : EWALD_E_CUDA;
+    if (launch(k_na_energy, 1u, 256u, st, ntiles, (const double *)e_tile, energy_dev) !=
+        cudaSuccess)
+        return EWALD_E_CUDA;
+    return EWALD_OK;
 }

@@ -73,10 +73,11 @@ int cuda_st(cudaError_t e)
 // fp, is_head when it is the first in the queue) would run on the idle slot that holds the
 // most memory (the first such slot); if the held total with it exceeds the budget, the
 // idle slots other than that one give back their workspaces, in slot order, until it fits
-// (they are reclaimed even if it still does not).  Returns kAdmitStop when no slot is idle,
-// or when the request fits but is not the head and the head has already been passed over
-// max_bypass times; kAdmitSkip when it does not fit (the scan goes on with the next
-// request); kAdmitTake when it is admitted on *slot.
+// (they are reclaimed even if it still does not).  Returns kAdmitStop, with nothing to
+// reclaim, when no slot is idle, or when the request is not the head and the head has
+// already been passed over max_bypass times (then nothing behind the head may run, so no
+// idle workspace is given up for it); kAdmitSkip when it does not fit (the scan goes on with
+// the next request); kAdmitTake when it is admitted on *slot.
 enum AdmitAction { kAdmitStop = 0, kAdmitSkip = 1, kAdmitTake = 2 };
 struct AdmitSlot {
     bool busy;
@@ -91,6 +92,7 @@ int admit_step(int64_t fp, bool is_head, const std::vector<AdmitSlot> &slots, in
     for (int i = 0; i < (int)slots.size(); ++i)
         if (!slots[i].busy && (fs < 0 || slots[i].held > slots[fs].held)) fs = i;
     if (fs < 0) return kAdmitStop;
+    if (!is_head && head_bypass >= max_bypass) return kAdmitStop;
     int64_t after = held_total - slots[fs].held + fp;
     for (int i = 0; i < (int)slots.size() && after > budget; ++i) {
         if (slots[i].busy || i == fs || slots[i].held == 0) continue;
@@ -98,7 +100,6 @@ int admit_step(int64_t fp, bool is_head, const std::vector<AdmitSlot> &slots, in
         after -= slots[i].held;
     }
     if (after > budget) return kAdmitSkip;
-    if (!is_head && head_bypass >= max_bypass) return kAdmitStop;
     *slot = fs;
     return kAdmitTake;
 }

@@ -38,10 +38,25 @@ def start(L, beta, r_c, k_max, precision, pos, q, dt, vel=None, mass=None) -> di
 
 
 def save(state: dict, path: str) -> None:
-    """Write the state to `path` (.npz), atomically (a temporary file, then a rename)."""
+    """Write the state to `path` (.npz), atomically: a temporary file, flushed to disk, then a
+    rename, then the directory entry flushed, so that after a crash `path` holds either the
+    previous checkpoint or this one in full."""
     tmp = path + ".tmp.npz"
-    np.savez(tmp, **{k: np.asarray(state[k]) for k in _KEYS})
+    with open(tmp, "wb") as f:
+        np.savez(f, **{k: np.asarray(state[k]) for k in _KEYS})
+        f.flush()
+        os.fsync(f.fileno())
     os.replace(tmp, path)
+    try:
+        fd = os.open(os.path.dirname(os.path.abspath(path)), os.O_RDONLY)
+    except OSError:
+        return
+    try:
+        os.fsync(fd)
+    except OSError:
+        pass
+    finally:
+        os.close(fd)
 
 
 def resume(path: str) -> dict:

@@ -26,6 +26,35 @@ def rel(a, b):
     return abs(a - b) / abs(b)
 
 
+# Per-particle factor of assert_close: no single particle may be off by more than this many
+# times the tolerance, measured in units of the RMS size of the reference values.
+LOCAL_FACTOR = 20.0
+
+
+def local_max(a, b):
+    """Largest per-particle error relative to the RMS size of the reference: max_i |a_i - b_i|
+    / sqrt(mean_i |b_i|^2), where a_i is a row (a force vector) for 2-D arrays and an element
+    for 1-D ones."""
+    a = np.asarray(a, dtype=np.float64); b = np.asarray(b, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]; b = b[:, None]
+    d = np.sqrt(((a - b) ** 2).sum(axis=1))
+    scale = math.sqrt(float((b ** 2).sum(axis=1).mean()))
+    return float(d.max()) / scale
+
+
+def assert_close(a, b, tol):
+    """Global and local parity: the relative RMS error over all particles is below tol, and
+    no particle's error exceeds LOCAL_FACTOR * tol times the RMS size of the reference (a
+    wrong result on a few particles of a large system, e.g. at a tile edge or in a ragged
+    tail, barely moves the RMS but fails the local bound)."""
+    g = rel_rms(a, b)
+    loc = local_max(a, b)
+    assert g < tol, f"relative RMS error {g:.3e} >= {tol:.1e}"
+    assert loc <= LOCAL_FACTOR * tol, (
+        f"largest per-particle error {loc:.3e} of the RMS size > {LOCAL_FACTOR:g} x {tol:.1e}")
+
+
 @functools.lru_cache(maxsize=None)
 def oracle_cached(name, beta, rc, kmax, sub=None):
     import oracle

@@ -10,7 +10,7 @@ error is expected near 1e-7..1e-6.  EWALD_MIXED_BF16 keeps 8 fewer mantissa bits
 import numpy as np
 import pytest
 
-from gpu_common import dev, mode_scale, need_gpu, oracle_cached, rel, rel_rms, torch
+from gpu_common import dev, mode_scale, need_gpu, oracle_cached, rel, rel_rms, assert_close, torch
 
 import oracle
 from paper_1708_01135_gb300 import Ewald, PART_REAL, PART_RECIP, PART_SELF, tune
@@ -54,9 +54,9 @@ def test_parts_match_oracle(case):
         Fa, ea = _run(ew, pos, q, PART_REAL | PART_RECIP | PART_SELF)
     assert np.array_equal(m, ref["m"])
     assert np.all(np.abs(S - ref["S"]) < 1e-5 * mode_scale(q, m, ref["S"]))
-    assert rel_rms(Fk, ref["F_recip"]) < 1e-5
+    assert_close(Fk, ref["F_recip"], 1e-5)
     assert rel(ek[1], ref["E_recip"]) < 1e-5
-    assert rel_rms(Fa, ref["F"]) < 1e-5
+    assert_close(Fa, ref["F"], 1e-5)
     assert rel(ea[3], ref["E_total"]) < 1e-5
 
 
@@ -71,7 +71,7 @@ def test_random_systems_ragged(n, seed):
     ref = oracle.ewald(pos, q, L, beta, rc, kmax)
     with Ewald(L, beta, rc, kmax, "mixed") as ew:
         F, e = ew.compute(dev(pos), dev(q))
-    assert rel_rms(F.cpu().numpy(), ref["F"]) < 1e-5
+    assert_close(F.cpu().numpy(), ref["F"], 1e-5)
     assert rel(e[3], ref["E_total"]) < 1e-5
 
 
@@ -83,7 +83,7 @@ def test_large_kmax_two_column_passes():
     ref = oracle.ewald(pos, q, L, beta, rc, kmax)
     with Ewald(L, beta, rc, kmax, "mixed") as ew:
         F, e = ew.compute(dev(pos), dev(q))
-    assert rel_rms(F.cpu().numpy(), ref["F"]) < 1e-5
+    assert_close(F.cpu().numpy(), ref["F"], 1e-5)
     assert rel(e[3], ref["E_total"]) < 1e-5
 
 
@@ -93,7 +93,7 @@ def test_bf16_split_variant():
     ref = oracle_cached("rocksalt_512", 1.0, 4.0, 10)
     with Ewald(L, 1.0, 4.0, 10, "mixed_bf16") as ew:
         F, e = ew.compute(dev(pos), dev(q))
-    assert rel_rms(F.cpu().numpy(), ref["F"]) < 2e-4
+    assert_close(F.cpu().numpy(), ref["F"], 2e-4)
     assert rel(e[3], ref["E_total"]) < 2e-4
 
 
@@ -121,6 +121,6 @@ def test_full_size_random_32768_sampled():
         F, e = ew.compute(dev(pos), dev(q))
         Sg = ew.structure_factor()
     F = F.cpu().numpy()[sub]
-    assert rel_rms(F, Fr + Fk) < 1e-5
+    assert_close(F, Fr + Fk, 1e-5)
     assert rel(e[1], ek) < 1e-5
     assert np.all(np.abs(Sg - S) < 1e-5 * mode_scale(q, oracle.kset_half(kmax), S))

@@ -12,7 +12,7 @@ Each part (real, reciprocal, self) is compared separately as well as the total.
 import numpy as np
 import pytest
 
-from gpu_common import dev, mode_scale, need_gpu, oracle_cached, rel, rel_rms, torch
+from gpu_common import dev, mode_scale, need_gpu, oracle_cached, rel, rel_rms, assert_close, torch
 
 import oracle
 from paper_1708_01135_gb300 import Ewald, PART_REAL, PART_RECIP, PART_SELF
@@ -52,9 +52,9 @@ def test_parts_match_oracle(prec, case):
         Fr, er = _run(ew, pos, q, PART_REAL)
         Fk, ek = _run(ew, pos, q, PART_RECIP)
         Fa, ea = _run(ew, pos, q, PART_REAL | PART_RECIP | PART_SELF)
-    assert rel_rms(Fr, ref["F_real"]) < tol
-    assert rel_rms(Fk, ref["F_recip"]) < tol
-    assert rel_rms(Fa, ref["F"]) < tol
+    assert_close(Fr, ref["F_real"], tol)
+    assert_close(Fk, ref["F_recip"], tol)
+    assert_close(Fa, ref["F"], tol)
     assert rel(er[0], ref["E_real"]) < tol and er[1] == 0 and er[2] == 0
     assert rel(ek[1], ref["E_recip"]) < tol and ek[0] == 0
     assert rel(ea[2], ref["E_self"]) < 1e-14
@@ -104,7 +104,7 @@ def test_random_system_multi_tile(prec):
         F, e = ew.compute(dev(pos), dev(q))
     F = F.cpu().numpy()
     tol = TOL[prec]
-    assert rel_rms(F, ref["F"]) < tol
+    assert_close(F, ref["F"], tol)
     assert rel(e[3], ref["E_total"]) < tol
 
 
@@ -117,7 +117,7 @@ def test_fp64_is_deterministic_and_wraps_positions():
         shifted = pos + L * np.array([3.0, -1.0, 2.0])
         F3, e3 = ew.compute(dev(shifted), dev(q))
     assert torch.equal(F1, F2) and np.array_equal(e1, e2)
-    assert rel_rms(F3.cpu().numpy(), F1.cpu().numpy()) < 1e-12
+    assert_close(F3.cpu().numpy(), F1.cpu().numpy(), 1e-12)
     assert rel(e3[3], e1[3]) < 1e-12
 
 
@@ -128,7 +128,7 @@ def test_workspace_grows_and_shrinks():
             pos, q, L = W.random_neutral(n, L=10.0, hard_core=0.5, seed=seed)
             ref = oracle.ewald(pos, q, L, 1.0, 3.0, 8)
             F, e = ew.compute(dev(pos), dev(q))
-            assert rel_rms(F.cpu().numpy(), ref["F"]) < 1e-10
+            assert_close(F.cpu().numpy(), ref["F"], 1e-10)
             assert rel(e[3], ref["E_total"]) < 1e-10
 
 
@@ -138,5 +138,5 @@ def test_host_buffer_entry_point():
     ref = oracle_cached("rocksalt_512", 1.0, 4.0, 10)
     with Ewald(L, 1.0, 4.0, 10, "fp64") as ew:
         F, e = ew.compute_host(pos, q)
-    assert rel_rms(F, ref["F"]) < 1e-10
+    assert_close(F, ref["F"], 1e-10)
     assert rel(e[3], ref["E_total"]) < 1e-10
