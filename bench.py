@@ -95,13 +95,20 @@ def run_params(args, n, L):
     return rc, beta, kmax, spme
 
 
+# (r_c, beta, k_max) of every named workload at a 1e-6 relative force error: the library
+# tuner's choices (ewald_tune, r_c fixed where WORKLOADS fixes it), written out as plain
+# numbers so that the oracle's reference arm needs nothing from the library;
+# tests/test_bench_params.py checks that the tuner still returns them.
+PARAMS = {
+    "rocksalt_512": (4.0, 1.0, 10),          # r_c = L/2, k_max raised to 10 to reach 1e-6
+    "random_32768": (4.0, 0.9292305472124596, 36),
+    "rocksalt_262144": (6.8, 0.5466062042426233, 42),
+    "random_2097152": (9.6, 0.3871793946718582, 59),
+}
+
+
 def params_for(workload, n, L):
-    from paper_1708_01135_gb300 import tune
-    if workload == "rocksalt_512":
-        return 4.0, 1.0, 10          # r_c = L/2, k_max raised to 10 to reach 1e-6
-    rc_fixed = WORKLOADS[workload][1]
-    rc, beta, km = tune(n, L, TOL, r_c=rc_fixed)
-    return rc, beta, km
+    return PARAMS[workload]
 
 
 # ---- roofline bookkeeping ---------------------------------------------------------------
@@ -168,19 +175,29 @@ def tensor_flops(n, kmax):
     return fwd, back
 
 
-# DRAM bytes per launch of the back-scatter kernel from an ncu capture of the benchmark
-# workload, valid while the kernel source is unchanged (sha256 prefix of recip_tc.cu)
-BS_TRAFFIC = {("random_32768", "mixed", "b35ef610511fc771"): 4227328}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from an
+# ncu capture of the same workload, valid while that kernel's source file is unchanged (its
+# sha256 prefix is part of the key); the capture each figure comes from is named in
+# profiles/.  Kernels without a current capture report null.
+TRAFFIC = {}
 
 
-def bs_traffic(workload, precision):
+def kernel_traffic(kernel, workload, precision):
     import hashlib
-    src = os.path.join(ROOT, "paper_1708_01135_gb300", "csrc", "recip_tc.cu")
+    src = {"real": "realspace.cu", "forward": "recip_tc.cu", "back": "recip_tc.cu"}.get(kernel)
+    if not src:
+        return None
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        path = os.path.join(ROOT, "paper_1708_01135_gb300", "csrc", src)
+        h = hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return BS_TRAFFIC.get((workload, precision, h))
+    return TRAFFIC.get((kernel, workload, precision, h))
+
+
+def unique_pairs(n, L, rc):
+    """Unique pairs within r_c of a homogeneous system: N (2 pi / 3) r_c^3 rho."""
+    return n * (2.0 * math.pi / 3.0) * rc ** 3 * (n / L ** 3)
 
 
 def simt_flops(n, kmax):
@@ -358,41 +375,48 @@ def _gen_request(item):
     return np_.ascontiguousarray(pos), np_.ascontiguousarray(q), float(L)
 
 
-def run_serving(args, rank, world, local):
-    """Serving stream: independent systems of uneven N (log-uniform in [256, 65536], half
-    jittered rock-salt, half random neutral, density U[0.8, 1.2], each with its own box and
-    tuned parameters), submitted to the continuous-batching server.  First a closed-loop run
-    measures the saturation rate; then Poisson arrivals at several fractions of it give p50/p99
-    latency (submit -> result) and the aggregate particles/s."""
+def serving_systems(count, seed=1238):
+    """The serving stream's systems, generated in spawned worker processes (before any CUDA
+    call of this process)."""
     import multiprocessing as mp
-    seed = 1238
-    count = args.requests
     items = [(r, kind, n, rho, m, seed) for r, (kind, n, rho, m) in
              enumerate(W.request_sizes(count, 256, 65536, seed))]
-    ctx = mp.get_context("spawn")          # before the first CUDA call of this process
+    ctx = mp.get_context("spawn")
     with ctx.Pool(min(16, os.cpu_count() or 4)) as pool:
-        systems = pool.map(_gen_request, items)
+        return pool.map(_gen_request, items)
+
+
+def serving_summary(systems, local, precision, slots, tol, loads=(0.25, 0.5, 0.75, 0.9, 1.1),
+                    comparators=True, seed=1238):
+    """Serving stream: independent systems of uneven N (log-uniform in [256, 65536], half
+    jittered rock-salt, half random neutral, density U[0.8, 1.2], each with its own box and
+    tuned parameters), submitted to the continuous-batching server.  A closed-loop run (all
+    requests at once) gives the saturation rate; Poisson arrivals at fractions of it give
+    p50/p99 latency (submit -> result) and the aggregate particles/s.  With comparators, the
+    same requests are also evaluated one at a time through plans on one stream (mixed and
+    FP64: the sequential baseline at the same accuracy), and the server's results are
+    compared with the one-at-a-time ones."""
     import torch
     torch.cuda.set_device(local)
-    from paper_1708_01135_gb300 import Server, tune
+    from paper_1708_01135_gb300 import Ewald, Server, tune
     dev = torch.device("cuda", local)
     reqs = []
     for pos, q, L in systems:
-        rc, beta, km = tune(len(q), L, 1e-5, r_c=min(0.5 * L, 4.0 * (len(q) / L ** 3) ** (-1.0 / 3.0)))
+        rc, beta, km = tune(len(q), L, tol, r_c=min(0.5 * L, 4.0 * (len(q) / L ** 3) ** (-1.0 / 3.0)))
         reqs.append(dict(pos=torch.tensor(pos, device=dev), q=torch.tensor(q, device=dev),
                          F=torch.empty((len(q), 3), dtype=torch.float64, device=dev),
                          L=L, beta=beta, rc=rc, km=km, n=len(q)))
+    count = len(reqs)
     total_n = sum(r["n"] for r in reqs)
-    srv = Server(max_slots=args.slots)
 
-    def run(times):
+    def run(srv, times):
         t0 = time.perf_counter()
         tickets = []
         for r, ta in zip(reqs, times):
             while time.perf_counter() - t0 < ta:
                 time.sleep(0.0002)
             tickets.append(srv.submit(r["pos"], r["q"], r["F"], r["L"], r["beta"], r["rc"], r["km"],
-                                      args.precision))
+                                      precision))
         res = [srv.wait(t, 600.0) for t in tickets]
         if any(x["status"] != 0 for x in res):
             raise RuntimeError("a serving request failed")
@@ -400,27 +424,59 @@ def run_serving(args, rank, world, local):
         span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
         return lat, span
 
-    run([0.0] * min(16, count))            # warm-up: plans, pools, module load
-    lat, span = run([0.0] * count)         # closed loop: everything at once
+    srv = Server(max_slots=slots)
+    run(srv, [0.0] * min(16, count))            # warm-up: plans, pools, module load
+    lat, span = run(srv, [0.0] * count)         # closed loop: everything at once
     sat_rate = count / span
-    out = {"saturation": {"requests_per_s": sat_rate, "particles_per_s": total_n / span,
+    F_srv = [r["F"].clone() for r in reqs]
+    out = {"requests": count, "total_particles": total_n, "slots": slots, "tol": tol,
+           "precision": precision,
+           "saturation": {"requests_per_s": sat_rate, "particles_per_s": total_n / span,
                           "p50_ms": float(np.percentile(lat, 50)),
                           "p99_ms": float(np.percentile(lat, 99))}}
     rng = np.random.default_rng(seed + 7)
-    for frac in (0.25, 0.5, 0.75, 0.9, 1.1):
+    for frac in loads:
         rate = frac * sat_rate
         times = np.cumsum(rng.exponential(1.0 / rate, size=count))
-        lat, span = run(list(times - times[0]))
+        lat, span = run(srv, list(times - times[0]))
         out[f"load_{frac}"] = {"arrival_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
                                "p99_ms": float(np.percentile(lat, 99)),
                                "particles_per_s": total_n / span}
-    stats = srv.stats()
+    out["server"] = srv.stats()
     srv.close()
+    if comparators:
+        # one request at a time through a plan per request on one stream (no overlap), with
+        # the precision of the server and with the plain FP64 path, at the same parameters
+        for prec, key in ((precision, "sequential_same_precision"), ("fp64", "sequential_fp64")):
+            E = torch.empty(4, dtype=torch.float64, device=dev)
+            plans = [Ewald(r["L"], r["beta"], r["rc"], r["km"], prec) for r in reqs]
+            Fs = [torch.empty_like(r["F"]) for r in reqs]
+            for ew, r, F in zip(plans, reqs, Fs):        # warm-up (workspaces, graphs)
+                ew.compute_async(r["pos"], r["q"], F, E)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for ew, r, F in zip(plans, reqs, Fs):
+                ew.compute_async(r["pos"], r["q"], F, E)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            for ew in plans:
+                ew.close()
+            diff = max(math.sqrt(float(((a - b) ** 2).sum()) / float((b ** 2).sum()))
+                       for a, b in zip(F_srv, Fs))
+            out[key] = {"particles_per_s": total_n / dt, "seconds": dt,
+                        "server_speedup": (total_n / dt) and (out["saturation"]["particles_per_s"]
+                                                              / (total_n / dt)),
+                        "max_rel_force_rms_server_vs_this": diff}
+    return out
+
+
+def run_serving(args, rank, world, local):
+    """--workload serving: the serving summary as its own JSON line."""
+    systems = serving_systems(args.requests)
+    out = serving_summary(systems, local, args.precision, args.slots, args.serving_tol)
     if rank == 0:
         print(json.dumps({"metric": "ewald_serving", "unit": "ms / particles/s", "n_gpus": world,
-                          "requests": count, "total_particles": total_n, "slots": args.slots,
-                          "precision": args.precision, "tol": 1e-5, "data": "synthetic",
-                          "results": out, "server": stats}), flush=True)
+                          "data": "synthetic", "results": out}), flush=True)
 
 
 def run_md(args, rank, world, local):
@@ -524,7 +580,66 @@ def dist_env():
     return rank, world, local
 
 
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo or lscpu), and its core count."""
+    name = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model Name", "CPU part") and v.strip():
+                    name = v.strip()
+                    break
+    except OSError:
+        pass
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                name = v.strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": name, "cores": os.cpu_count()}
+
+
+def oracle_one_thread():
+    """The oracle on one host thread: a full evaluation of the 512-ion lattice and a sampled
+    evaluation of the 32,768-ion system (S(k) on a subset of modes, forces of 64 particles,
+    scaled as oracle_sample does)."""
+    import oracle
+    out = {}
+    prev = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        for name in ("rocksalt_512", "random_32768"):
+            pos, q, L = WORKLOADS[name][0]()
+            n = len(q)
+            rc, beta, kmax = PARAMS[name]
+            if n <= 4096:
+                t0 = time.perf_counter()
+                oracle.ewald(pos, q, L, beta, rc, kmax)
+                t = time.perf_counter() - t0
+                note = "full evaluation"
+            else:
+                t, _, nt, _, _, note = oracle_sample(pos, q, L, beta, rc, kmax, 64,
+                                                     S_given=np.zeros(len(oracle.kset_half(kmax)),
+                                                                      dtype=complex),
+                                                     max_sk_terms=2e8)
+                note = (note.replace("(reciprocal forces from the GPU's S(k))",
+                                     "(reciprocal forces against a stand-in S(k))")
+                        + f"; forces of {nt} particles, scaled to {n}")
+            out[name] = {"particles_per_s": n / t, "seconds_per_evaluation": t, "sample": note}
+    finally:
+        oracle.set_threads(prev)
+    return out
+
+
 def run_reference(args, rank, world):
+    """The oracle (plain FP64 CPU Ewald) as it stands, on the host cores, on the same workload,
+    metric and parameters (plain numbers, PARAMS): every step a bounded sample of one
+    evaluation scaled to the whole (see oracle_sample).  Nothing from the library is loaded."""
     if rank != 0:
         return
     import oracle
@@ -551,16 +666,18 @@ def run_reference(args, rank, world):
     targets = int(min(args.cpu_targets, max(16, 0.5 * budget / c_t)))
     max_terms = max(float(n), 0.5 * budget / c_s)
     times = []
-    for s in range(args.warmup + args.steps):
-        full, wall, nt, _, _, note = oracle_sample(pos, q, L, beta, rc, kmax, targets, seed=s,
+    nt = targets
+    for st in range(args.warmup + args.steps):
+        full, wall, nt, _, _, note = oracle_sample(pos, q, L, beta, rc, kmax, targets, seed=st,
                                                    S_given=S0, max_sk_terms=max_terms)
-        if s >= args.warmup:
+        if st >= args.warmup:
             times.append(full)
     t = float(np.mean(times))
     value = n / t
     note = note.replace("(reciprocal forces from the GPU's S(k))",
                         "(reciprocal forces of the targets timed against a stand-in S(k) of "
                         "the same size)")
+    one = oracle_one_thread() if not args.no_one_thread else None
     line = {
         "impl": "reference", "metric": "ewald_particles_per_s", "value": value,
         "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -569,27 +686,284 @@ def run_reference(args, rank, world):
         "config": {"workload": args.workload, "n": n, "L": L, "r_c": rc, "beta": beta,
                    "k_max": kmax, "tol": TOL},
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": oracle.num_threads(),
-                         "kind": "oracle",
-                         "sample": f"{note}; forces of {targets} random particles, scaled "
+                         "kind": "oracle", "cpu": cpu_model(),
+                         "sample": f"{note}; forces of {nt} random particles, scaled "
                                    f"to {n}"},
+        "one_thread": one,
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+def converged_params(L, p=4.3):
+    """Cutoffs at which both truncation errors are ~exp(-p^2) ~ 1e-8 of the force: r_c = L/2
+    (the largest the minimum image allows), beta = p / r_c, k_max = ceil(p beta L / pi)."""
+    rc = 0.5 * L
+    beta = p / rc
+    return rc, beta, int(math.ceil(p * beta * L / math.pi))
+
+
+def accuracy_converged(pos, q, L, F_gpu, n_targets=1024, seed=11):
+    """Total relative RMS force error of a result against the oracle at converged cutoffs
+    (converged_params), on a random subset of particles: the truncation error of the
+    benchmark's parameters and the arithmetic error of the path together."""
+    import oracle
+    n = len(q)
+    rng = np.random.default_rng(seed)
+    sub = np.sort(rng.choice(n, size=min(n_targets, n), replace=False))
+    rc, beta, kmax = converged_params(L)
+    t0 = time.perf_counter()
+    _, Fr, _ = oracle.real(pos, q, L, beta, rc, sub=sub)
+    _, Fk, _, _, _ = oracle.recip(pos, q, L, beta, kmax, sub=sub)
+    Fo = Fr + Fk
+    d = F_gpu[sub] - Fo
+    scale = math.sqrt(float((Fo ** 2).sum(axis=1).mean()))
+    return {"rel_force_rms": float(np.sqrt((d ** 2).sum() / (Fo ** 2).sum())),
+            "largest_particle_rel": float(np.sqrt((d ** 2).sum(axis=1)).max() / scale),
+            "particles": int(len(sub)),
+            "reference": {"r_c": rc, "beta": beta, "k_max": kmax,
+                          "note": "FP64 oracle, minimum-image pairs of the subset and the "
+                                  "k-space sum of all particles"},
+            "cpu_seconds": time.perf_counter() - t0}
+
+
+def structure_factor_error(pos, q, L, m, S_gpu, modes=1024, seed=12):
+    """Relative error of the path's S(k) on random modes: |S_gpu - S_oracle| over
+    sqrt(sum q^2) + |S| (the size of a random-phase sum), the largest and the RMS."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(len(m), size=min(modes, len(m)), replace=False))
+    So = oracle.structure_factor(pos, q, L, m[sel])
+    e = np.abs(S_gpu[sel] - So) / (np.sqrt((q ** 2).sum()) + np.abs(So))
+    return {"max": float(e.max()), "rms": float(np.sqrt((e ** 2).mean())), "modes": int(len(sel))}
+
+
+def kernel_rooflines(n, L, rc, kmax, precision, spme, times, pk, pk_kind, alu_peaks,
+                     workload):
+    """Roofline of the three kernels that carry the method's work, each from its own CUDA
+    event bracket (ewald_profile): achieved = algorithmic flop per launch / kernel time, where
+    the algorithmic work is 40 flop per unique pair within r_c (real space), 8 flop per
+    (particle, mode) term for the S(k) product and 10 for the back-scatter; peak = the measured
+    bf16 dense rate (sustained) for tensor-core products, the measured FP32/FP64 FMA rate for
+    CUDA-core kernels.  The list is ordered by kernel time, the first entry dominating."""
+    fp64 = precision == "fp64"
+    tc = precision in ("mixed", "mixed_bf16")
+    alu = alu_peaks["fp64" if fp64 else "fp32"]
+    alu_kind = ("measured here (ewald_fma_peak, "
+                + ("FP64" if fp64 else "FP32") + " FMA loop on every SM)")
+    tensor_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    tensor_kind = f"{pk_kind} bf16 dense sustained (the fp16 dense rate is equal)"
+    nk = len_kset_half(kmax)
+    out = []
+    pairs = unique_pairs(n, L, rc)
+    rows = [("real", "real-space pairs (a4)", times.get("real_kernel"), 40.0 * pairs,
+             "40 flop per unique pair within r_c", "alu", alu, alu_kind)]
+    if not spme:
+        fwd_f, back_f = tensor_flops(n, kmax) if tc else simt_flops(n, kmax)
+        rows.append(("forward", "structure-factor product (a5-a6)", times.get("recip_forward"),
+                     8.0 * n * nk, "8 flop per (particle, mode) term",
+                     "tensor" if tc else "alu", tensor_peak if tc else alu,
+                     tensor_kind if tc else alu_kind, fwd_f))
+        rows.append(("back", "back-scatter product (a8)", times.get("backscatter_kernel"),
+                     10.0 * n * nk, "10 flop per (particle, mode) term",
+                     "tensor" if tc else "alu", tensor_peak if tc else alu,
+                     tensor_kind if tc else alu_kind, back_f))
+    for row in rows:
+        key, name, ms, flop, work, bound, peak, kind = row[:8]
+        if not ms or ms <= 0:
+            continue
+        achieved = flop / (ms * 1e-3) / 1e12
+        r = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak,
+             "unit": "TFLOP/s", "frac": achieved / peak, "ms": ms, "work": work,
+             "flop_per_launch": flop, "peak_kind": kind,
+             "traffic": kernel_traffic(key, workload, precision)}
+        if len(row) > 8 and bound == "tensor":
+            issued = row[8]
+            r["issued_tensor_flop"] = issued
+            r["issued_tensor_frac"] = issued / (ms * 1e-3) / 1e12 / peak
+        out.append(r)
+    out.sort(key=lambda r: -r["ms"])
+    return out
+
+
+def time_steps(ew, tp, tq, F, E, flush, stream, steps):
+    """Device time (ms, mean) of `steps` evaluations, each bracketed by CUDA events on the
+    launching stream after an L2 flush."""
+    import torch
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for st in range(steps):
+        flush.fill_(float(st))
+        ev0[st].record(stream)
+        ew.compute_async(tp, tq, F, E)
+        ev1[st].record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)]))
+
+
+def profiled_times(ew, tp, tq, F, E, flush, reps):
+    """Median kernel and stage times (ms) over `reps` evaluations with the plan's profiling
+    events recorded (those evaluations run launch by launch instead of as a graph)."""
+    stage = {}
+    ew.profile(1)
+    for st in range(reps):
+        flush.fill_(float(st))
+        ew.compute_async(tp, tq, F, E)
+        t, _ = ew.profile(-1)           # synchronises on the last stage event
+        for k, v in t.items():
+            stage.setdefault(k, []).append(v)
+    ew.profile(0)
+    return {k: float(np.median(v)) for k, v in stage.items()}
+
+
+def measure_workload(args, workload, local, world, dev, flush, alu_peaks, steps, warmup,
+                     e2e=True, spme_spec="", accuracy="full"):
+    """One workload on this rank's GPU: device-timed evaluations, kernel times, the end-to-end
+    figure through the host-buffer entry point, kernel rooflines and (rank 0) accuracy
+    against the oracle.  Returns the fields of its JSON line and the inputs (for reuse)."""
+    import torch
+    from paper_1708_01135_gb300 import Ewald
+    gen, _ = WORKLOADS[workload]
+    pos, q, L = gen()
+    n = len(q)
+
+    class A:
+        pass
+    a = A()
+    a.workload, a.spme, a.spme_rc = workload, spme_spec, args.spme_rc
+    rc, beta, kmax, spme = run_params(a, n, L)
+    tp = torch.tensor(pos, device=dev)
+    tq = torch.tensor(q, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    E = torch.empty(4, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    ew = Ewald(L, beta, rc, kmax, args.precision)
+    if spme:
+        ew.set_spme(spme["K"], spme["order"])
+    # the clock sampler runs through the warm-up (at least ~0.5 s of back-to-back steps) and
+    # the timed steps, so that its samples see the GPU under this workload's load
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_warm = time.perf_counter()
+    w = 0
+    while w < warmup or time.perf_counter() - t_warm < 0.5:
+        ew.compute_async(tp, tq, F, E)
+        w += 1
+        if w % 8 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    if ew.status() != 0:
+        raise RuntimeError("warm-up evaluation reported an error")
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms = time_steps(ew, tp, tq, F, E, flush, stream, steps)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    if ew.status() != 0:
+        raise RuntimeError("timed evaluation reported an error")
+    _, per_step = ew.profile(-1)        # kernels of one evaluation (one graph launch replays them)
+    times = profiled_times(ew, tp, tq, F, E, flush, min(steps, 10))
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_rate(n, ms, world)
+    out = {"n": n, "L": L, "r_c": rc, "beta": beta, "k_max": kmax, "spme": spme,
+           "value": value, "ms_per_step": ms, "steps": steps, "warmup": w,
+           "gpu_launches": per_step * steps, "clocks": clk}
+    Fg = F.cpu().numpy()
+    if e2e:
+        # end to end through the host-buffer entry point (pinned host memory)
+        hp = torch.tensor(pos).pin_memory().numpy()
+        hq = torch.tensor(q).pin_memory().numpy()
+        hf = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+        for _ in range(2):
+            ew.compute_host(hp, hq, hf)
+        torch.cuda.synchronize()
+        e_times = []
+        for _ in range(max(3, steps // 2)):
+            t0 = time.perf_counter()
+            ew.compute_host(hp, hq, hf)
+            e_times.append(time.perf_counter() - t0)
+        out["e2e"] = {"value": whole_job_rate(n, max_over_ranks(1e3 * float(np.mean(e_times)),
+                                                                world, dev), world),
+                      "unit": "particles/s", "h2d_bytes_per_step": 32 * n,
+                      "d2h_bytes_per_step": 24 * n + 32}
+        Fg = np.array(hf)
+    pk, pk_kind = peaks()
+    roofs = kernel_rooflines(n, L, rc, kmax, args.precision, spme, times, pk, pk_kind,
+                             alu_peaks, workload)
+    out["roofline_kernels"] = roofs
+    out["kernel_ms"] = {k: times.get(k) for k in ("real_kernel", "recip_forward",
+                                                   "backscatter_kernel", "finalize_kernels",
+                                                   "binning")}
+    out["stage_spans_ms"] = {k: v for k, v in times.items() if k not in out["kernel_ms"]}
+    nk = 0 if spme else len_kset_half(kmax)
+    pairs = unique_pairs(n, L, rc)
+    out["algorithmic"] = {"unique_pairs": pairs, "recip_terms": float(n) * nk,
+                          "flop": 40.0 * pairs + 18.0 * n * nk,
+                          "tflops_over_step": (40.0 * pairs + 18.0 * n * nk) / (ms * 1e-3) / 1e12,
+                          "note": ("SPME mesh work not counted" if spme else
+                                   "40 flop per unique pair, 18 per (particle, mode) term")}
+    Sg = None if spme else ew.structure_factor()
+    m = None if spme else ew.kset()
+    ew.close()
+    rank = int(os.environ.get("RANK", "0"))
+    if rank == 0 and world == 1 and accuracy != "none":
+        import oracle
+        acc = {}
+        if spme:
+            full, wall, nt, sub, Fo, note = spme_oracle_sample(pos, q, L, beta, rc, spme["K"],
+                                                               spme["order"], args.cpu_targets)
+            acc["same_parameters"] = {
+                "rel_force_rms": float(np.sqrt(((Fg[sub] - Fo) ** 2).sum() / (Fo ** 2).sum())),
+                "particles": int(nt),
+                "reference": "FP64 SPME oracle at the same (beta, r_c, K, p)"}
+        else:
+            full, wall, nt, sub, Fo, note = oracle_sample(pos, q, L, beta, rc, kmax,
+                                                          args.cpu_targets, S_given=Sg)
+            sk_all = "all" in note.split("modes")[0]
+            acc["same_parameters"] = {
+                "rel_force_rms": float(np.sqrt(((Fg[sub] - Fo) ** 2).sum() / (Fo ** 2).sum())),
+                "particles": int(nt),
+                "reference": ("FP64 oracle at the same (beta, r_c, k_max), S(k) of the oracle"
+                              if sk_all else
+                              "FP64 oracle at the same (beta, r_c, k_max); its reciprocal "
+                              "forces use this path's S(k), whose own error is "
+                              "structure_factor_error")}
+            acc["structure_factor_error"] = structure_factor_error(pos, q, L, m, Sg)
+        out["cpu_baseline"] = {"value": n / full, "unit": "particles/s",
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "cpu": cpu_model(),
+                               "sample": f"{note}; forces of {nt} random particles, scaled "
+                                         f"to {n} ({wall:.1f} s of CPU work)"}
+        if accuracy == "full" and not spme:
+            acc["total_vs_converged"] = accuracy_converged(pos, q, L, Fg,
+                                                           n_targets=args.converged_targets)
+            acc["meets_tolerance"] = acc["total_vs_converged"]["rel_force_rms"] <= TOL
+        out["accuracy"] = acc
+    return out, (pos, q, L, tp, tq)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="random_32768", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="random_2097152", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32", "mixed_bf16"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-targets", type=int, default=2048)
+    ap.add_argument("--converged-targets", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-one-thread", action="store_true")
+    ap.add_argument("--extras", default="rocksalt_262144,serving",
+                    help="comma list of extra keys beside the line: rocksalt_262144, serving ('' for none)")
     ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--extra-requests", type=int, default=128,
+                    help="requests of the serving summary beside the line")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serving-tol", type=float, default=1e-6)
     ap.add_argument("--fp64-max-n", type=int, default=300000,
                     help="time the FP64 GPU path beside the line up to this N")
     ap.add_argument("--md", type=int, default=0, help="velocity-Verlet MD steps (0: single evaluations)")
@@ -600,6 +974,8 @@ def main():
                     "'auto' (order 8), 'auto:P' or 'K,P'")
     ap.add_argument("--spme-rc", type=float, default=0.0,
                     help="real-space cutoff of the SPME line (beta from the tuner at this r_c)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print only the measured FP32/FP64 FMA rates of the GPU")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -611,220 +987,102 @@ def main():
     if args.md:
         return run_md(args, rank, world, local)
 
+    extras = [x for x in args.extras.split(",") if x] if (rank == 0 and world == 1) else []
+    systems = serving_systems(args.extra_requests) if "serving" in extras else None
+
     import torch
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_1708_01135_gb300 import Ewald
-
-    gen, _ = WORKLOADS[args.workload]
-    pos, q, L = gen()
-    n = len(q)
-    rc, beta, kmax, spme = run_params(args, n, L)
+    from paper_1708_01135_gb300 import Ewald, fma_peak
     dev = torch.device("cuda", local)
-    tp = torch.tensor(pos, device=dev)
-    tq = torch.tensor(q, device=dev)
-    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
-    E = torch.empty(4, dtype=torch.float64, device=dev)
+    alu_peaks = {"fp32": fma_peak("fp32"), "fp64": fma_peak("fp64")}
+    if args.peaks:
+        if rank == 0:
+            print(json.dumps({"metric": "fma_peak", "unit": "TFLOP/s", **alu_peaks}), flush=True)
+        return
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
-    ew = Ewald(L, beta, rc, kmax, args.precision)
-    if spme:
-        ew.set_spme(spme["K"], spme["order"])
-
-    # the clock sampler runs through the warm-up (at least ~0.5 s of back-to-back steps) and
-    # the timed steps, so that its samples see the GPU under this workload's load
-    clocks = ClockSampler(local)
-    clocks.start()
-    t_warm = time.perf_counter()
-    w = 0
-    while w < args.warmup or time.perf_counter() - t_warm < 0.5:
-        ew.compute_async(tp, tq, F, E)
-        w += 1
-        if w % 8 == 0:
-            torch.cuda.synchronize()
-    torch.cuda.synchronize()
-    if ew.status() != 0:
-        raise RuntimeError("warm-up evaluation reported an error")
-
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage = {k: [] for k in ("binning", "real", "recip_forward", "recip_coef", "recip_back",
-                             "finalize", "total", "recip_branch")}
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    for s in range(args.steps):
-        flush.fill_(float(s))
-        ev0[s].record(stream)
-        ew.compute_async(tp, tq, F, E)
-        ev1[s].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    if ew.status() != 0:
-        raise RuntimeError("timed evaluation reported an error")
-    _, per_step = ew.profile(-1)        # kernels of one evaluation (one graph launch replays them)
-    launches = per_step * args.steps
-    # stage breakdown (not part of the timed steps): evaluations with stage events recorded,
-    # which run the pipeline launch by launch
-    ew.profile(1)
-    for s in range(min(args.steps, 10)):
-        flush.fill_(float(s))
-        ew.compute_async(tp, tq, F, E)
-        t, _ = ew.profile(-1)           # synchronises on the last stage event
-        for k, v in t.items():
-            stage[k].append(v)
-    ew.profile(0)
-    ms = max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)])), world, dev)
-    value = whole_job_rate(n, ms, world)
-
-    # end to end through the host-buffer entry point (pinned host memory)
-    hp = torch.tensor(pos).pin_memory().numpy()
-    hq = torch.tensor(q).pin_memory().numpy()
-    hf = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
-    for _ in range(2):
-        ew.compute_host(hp, hq, hf)
-    torch.cuda.synchronize()
-    e_times = []
-    for _ in range(max(3, args.steps // 2)):
-        t0 = time.perf_counter()
-        _, eh = ew.compute_host(hp, hq, hf)
-        e_times.append(time.perf_counter() - t0)
-    e2e = whole_job_rate(n, max_over_ranks(1e3 * float(np.mean(e_times)), world, dev), world)
-
-    pk, pk_kind = peaks()
-    tc = args.precision in ("mixed", "mixed_bf16")
-    back_ms = float(np.median(stage["recip_back"]))
-    fwd_ms = float(np.median(stage["recip_forward"]))
-    if spme:
-        # the dominant kernel of an SPME step is the real-space pair kernel (FP32 on the mixed
-        # path): 40 flop per pair evaluation within r_c, each pair evaluated from both sides
-        # (no atomics), N (4 pi / 3) r_c^3 rho pairs per side for density rho
-        real_ms = float(np.median(stage["real"]))
-        pairs = n * (4.0 * math.pi / 3.0) * rc ** 3 * (n / L ** 3)
-        achieved = 40.0 * pairs / (real_ms * 1e-3) / 1e12
-        fp32 = args.precision != "fp64"
-        peak = fp32_peak(pk) if fp32 else 1.25
-        roof = {"bound": "alu", "kernel": "real-space pairs (a4)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "work": "40 flop per pair evaluation within r_c (both sides of every pair)",
-                "peak_kind": ("FP32 CUDA-core rate from unit counts and the maximum SM clock "
-                              "(152 SMs x 128 lanes x 2 flop x 2.07 GHz)" if fp32 else
-                              "nominal FP64 rate")}
-    elif tc:
-        fwd_f, back_f = tensor_flops(n, kmax)
-        achieved = back_f / (back_ms * 1e-3) / 1e12
-        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-        roof = {"bound": "tensor", "kernel": "back-scatter product (a8)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": bs_traffic(args.workload, args.precision),
-                "work": "issued MMA flop (three split-FP16 products, padded tiles)",
-                "peak_kind": f"{pk_kind} bf16 dense sustained (fp16 dense rate is equal)"}
-    else:
-        fwd_f, back_f = simt_flops(n, kmax)
-        achieved = back_f / (back_ms * 1e-3) / 1e12
-        peak = 1.25 if args.precision == "fp64" else 76.0
-        roof = {"bound": "alu", "kernel": "back-scatter product (a8)", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_kind": "nominal FP64/FP32 CUDA-core rate (unit counts x clock)"}
-    stages_ms = {k: float(np.median(v)) for k, v in stage.items()}
-    # the method's own work per evaluation, whatever the kernels issue: 40 flop per pair
-    # evaluation within r_c (each pair from both sides, N (4 pi / 3) r_c^3 rho of them) and,
-    # for the classical sum, 18 flop per (particle, mode) term (one complex multiply-add for
-    # S(k), ~10 flop for the back-scatter), over the whole step time
-    pairs = n * (4.0 * math.pi / 3.0) * rc ** 3 * (n / L ** 3)
-    nk = 0 if spme else len_kset_half(kmax)
-    algo = {"real_pair_evaluations": pairs, "recip_terms": float(n) * nk,
-            "flop": 40.0 * pairs + 18.0 * n * nk,
-            "tflops_over_step": (40.0 * pairs + 18.0 * n * nk) / (ms * 1e-3) / 1e12,
-            "note": ("SPME mesh work not counted" if spme else
-                     "classical k-space sum over the half-space modes")}
+    res, (pos, q, L, tp, tq) = measure_workload(args, args.workload, local, world, dev, flush,
+                                                alu_peaks, args.steps, args.warmup,
+                                                spme_spec=args.spme,
+                                                accuracy="none" if args.no_cpu_baseline else "full")
+    n = res["n"]
+    ms = res["ms_per_step"]
 
     # the plain FP64 GPU path on the same system and parameters
     fp64 = None
     if args.precision != "fp64" and n <= args.fp64_max_n:
-        with Ewald(L, beta, rc, kmax, "fp64") as ew64:
+        F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        E = torch.empty(4, dtype=torch.float64, device=dev)
+        with Ewald(L, res["beta"], res["r_c"], res["k_max"], "fp64") as ew64:
             for _ in range(2):
                 ew64.compute_async(tp, tq, F, E)
             torch.cuda.synchronize()
-            t64 = []
-            for s in range(3):
-                flush.fill_(float(s))
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                ew64.compute_async(tp, tq, F, E)
-                b.record(stream)
-                torch.cuda.synchronize()
-                t64.append(a.elapsed_time(b))
+            ms64 = time_steps(ew64, tp, tq, F, E, flush, torch.cuda.current_stream(), 3)
             if ew64.status() != 0:
                 raise RuntimeError("FP64 evaluation reported an error")
-        ms64 = float(np.mean(t64))
         fp64 = {"value": world * n / (ms64 * 1e-3), "unit": "particles/s", "ms_per_step": ms64,
                 "steps": 3, "speedup_of_this_line": ms64 / ms}
-
-    cpu = None
-    accuracy = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        Fg = hf                 # forces of the last end-to-end evaluation (same input)
-        if spme:
-            full, wall, nt, sub, Fo, note = spme_oracle_sample(pos, q, L, beta, rc, spme["K"],
-                                                               spme["order"], args.cpu_targets)
-            ref_note = ("FP64 oracle at the same (beta, r_c, K, p): real-space pairs plus "
-                        "the SPME reciprocal part; arithmetic error of this path (the mesh "
-                        "error of (K, p) is the separate spme_vs_classical figure)")
-        else:
-            full, wall, nt, sub, Fo, note = oracle_sample(pos, q, L, beta, rc, kmax,
-                                                          args.cpu_targets,
-                                                          S_given=ew.structure_factor())
-            ref_note = ("FP64 oracle at the same (beta, r_c, k_max): arithmetic error of this "
-                        "path; the truncation error of the parameters is stated separately")
-        cpu = {"value": n / full, "unit": "particles/s", "cores": oracle.num_threads(),
-               "kind": "oracle", "sample": f"{note}; forces of {nt} random particles, scaled "
-                                           f"to {n} ({wall:.1f} s of CPU work)"}
-        accuracy = {"rel_force_rms_vs_oracle": float(np.sqrt(((Fg[sub] - Fo) ** 2).sum() /
-                                                             (Fo ** 2).sum())),
-                    "particles": int(nt), "reference": ref_note, "oracle_sample": note}
+    spme = res["spme"]
     if rank == 0 and spme and spme["classical_k_max"] <= 127:
         # the mesh error of SPME: its forces against the classical k-space sum at the same
-        # beta and r_c (the tensor-core path, itself within ~1e-6 of the oracle)
-        with Ewald(L, beta, rc, kmax, "mixed") as ewc:
-            Fc = torch.empty_like(F)
-            ewc.compute_async(tp, tq, Fc, torch.empty_like(E))
-            Fc = Fc.cpu().numpy()
-        Fs = hf
+        # beta and r_c (the tensor-core path)
+        F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        with Ewald(L, res["beta"], res["r_c"], res["k_max"], args.precision) as ew:
+            ew.set_spme(spme["K"], spme["order"])
+            ew.compute_async(tp, tq, F, torch.empty(4, dtype=torch.float64, device=dev))
+            Fs = F.cpu().numpy()
+        with Ewald(L, res["beta"], res["r_c"], res["k_max"], "mixed") as ewc:
+            ewc.compute_async(tp, tq, F, torch.empty(4, dtype=torch.float64, device=dev))
+            Fc = F.cpu().numpy()
         spme["vs_classical_rel_force_rms"] = float(np.sqrt(((Fs - Fc) ** 2).sum() / (Fc ** 2).sum()))
+    del tp, tq
+
+    extra = {}
+    for x in extras:
+        if x == "serving":
+            extra["serving"] = serving_summary(systems, local, args.precision, args.slots,
+                                               args.serving_tol, loads=(0.5, 0.9))
+        elif x in WORKLOADS and x != args.workload:
+            r, _ = measure_workload(args, x, local, world, dev, flush, alu_peaks,
+                                    min(args.steps, 10), 3, e2e=False,
+                                    accuracy="none" if args.no_cpu_baseline else "sample")
+            r.pop("clocks", None)
+            extra[x] = r
     if rank == 0:
+        roofs = res["roofline_kernels"]
         line = {
-            "metric": "ewald_particles_per_s", "value": value, "unit": "particles/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "metric": "ewald_particles_per_s", "value": res["value"], "unit": "particles/s",
+            "n_gpus": world, "steps": args.steps, "warmup": res["warmup"], "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"mixed": "fp32 pairs + fp16x2 tensor products (fp32 accum) + f64 reductions",
                       "mixed_bf16": "fp32 pairs + bf16x2 tensor products (fp32 accum) + f64 reductions",
                       "fp64": "f64", "fp32": "f32 (f64 reductions)"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "L": L, "r_c": rc, "beta": beta,
-                       "k_max": kmax, "tol": TOL, "precision": args.precision,
+            "config": {"workload": args.workload, "n": n, "L": L, "r_c": res["r_c"],
+                       "beta": res["beta"], "k_max": res["k_max"], "tol": TOL,
+                       "precision": args.precision,
                        "reciprocal": ({"method": "spme", **spme} if spme else
                                       {"method": "classical k-space sum"}),
                        "l2": "flushed before every step (512 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "e2e": {"value": e2e, "unit": "particles/s", "h2d_bytes_per_step": 32 * n,
-                    "d2h_bytes_per_step": 24 * n + 32},
-            "gpu_launches": launches,
-            "roofline": roof,
-            "stages_ms": stages_ms,
-            "algorithmic": algo,
-            "clocks": clk,
-            "cpu_baseline": cpu,
-            "accuracy": accuracy,
+            "e2e": res.get("e2e"),
+            "gpu_launches": res["gpu_launches"],
+            "roofline": roofs[0] if roofs else None,
+            "roofline_kernels": roofs,
+            "kernel_ms": res["kernel_ms"],
+            "stage_spans_ms": res["stage_spans_ms"],
+            "algorithmic": res["algorithmic"],
+            "peaks_measured": {**alu_peaks, "unit": "TFLOP/s",
+                               "how": "ewald_fma_peak: FMA loop on every SM, CUDA events"},
+            "clocks": res["clocks"],
+            "cpu_baseline": res.get("cpu_baseline"),
+            "accuracy": res.get("accuracy"),
             "fp64_gpu": fp64,
+            **extra,
         }
         print(json.dumps(line), flush=True)
-    ew.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -237,6 +237,16 @@ int ewald_set_spme(ewald_plan_t plan, int K, int order);
  */
 int ewald_probe_timeout(ewald_plan_t plan, void *stream);
 
+/*
+ * ewald_fma_peak - measured fused multiply-add rate of the CUDA cores of the current device
+ * (a diagnostic with no counterpart in the paper: the denominator of the roofline of the
+ * arithmetic-bound pair kernels and of the CUDA-core reciprocal products).
+ *   precision  EWALD_FP32 or EWALD_FP64 (anything else: EWALD_E_INVAL)
+ *   tflops     host out: TFLOP/s (two flops per FMA) of a bounded FMA loop on every SM,
+ *              timed with CUDA events (synchronous; a few tenths of a second)
+ */
+int ewald_fma_peak(int precision, double *tflops);
+
 /* ewald_status_sync - synchronise the plan's last stream and return (and clear) the
  * device-side status of the last evaluation: EWALD_OK, EWALD_E_NONNEUTRAL,
  * EWALD_E_NONFINITE, EWALD_E_TIMEOUT or EWALD_E_CUDA. */
@@ -256,15 +266,25 @@ int ewald_compute_host(ewald_plan_t plan, int64_t n, const double *pos_host,
  * ewald_profile - per-stage timing of later evaluations with CUDA events recorded on the
  * stream each stage runs on (off by default; recording adds a few event records per call).
  *   enable    1 to record from the next evaluation on, 0 to stop, -1 to leave unchanged
- *   times_ms  host float64 [8] or NULL: synchronises and returns the stage durations of the
- *             last recorded evaluation: [0] binning and packing (a1-a3), [1] real-space
- *             pairs (a4), [2] phases and structure-factor product (a5-a6), [3] S(k)
- *             reduction, energy and coefficients (a6-a7), [4] back-scatter product and
- *             forces (a8), [5] self term, totals and unsort (a9), [6] whole evaluation,
- *             [7] reciprocal branch (stages 2-4 on their stream)
+ *   times_ms  host float64 [EWALD_PROFILE_TIMES] or NULL: synchronises and returns the
+ *             durations of the last recorded evaluation.  Spans between stage boundaries
+ *             of one stream (they include waits for the other stream):
+ *             [0] binning and packing (a1-a3), [1] from the end of binning to the end of
+ *             the real-space pairs (the forward operands and the pair kernel, a4),
+ *             [2] phases and structure-factor product (a5-a6), [3] S(k) reduction, energy
+ *             and coefficients (a6-a7), [4] back-scatter product and its reduction (a8),
+ *             [5] from the end of the real-space pairs to the end of the evaluation (the
+ *             wait for the reciprocal branch, then a9), [6] whole evaluation,
+ *             [7] reciprocal branch (stages 2-4 on their stream).
+ *             Single kernels (bracketed by their own events): [8] the real-space pair
+ *             kernel, [9] the back-scatter product kernel, [10] the self term, totals and
+ *             unsort (a9) after the join.  -1 where a span was not recorded (e.g. [9] for
+ *             the mesh reciprocal part).
  *   launches  host int or NULL: kernels launched by the last evaluation
  */
-int ewald_profile(ewald_plan_t plan, int enable, double times_ms[8], int *launches);
+#define EWALD_PROFILE_TIMES 11
+int ewald_profile(ewald_plan_t plan, int enable, double times_ms[EWALD_PROFILE_TIMES],
+                  int *launches);
 
 /* ewald_plan_info - read plan parameters chosen at creation.
  *   info[0] = number of cells per side, info[1] = stencil half-width in cells

@@ -393,6 +393,7 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     // reported against this one
     (void)cudaGetLastError();
     prof_mark(p, kEvStart, st);
+    p.prof_bs = false;
     if (clear_status && (e = cudaMemsetAsync(p.d_status, 0, sizeof(int), st)) != cudaSuccess)
         return e;
     if ((e = launch_binning(p, n, pos, q, st)) != cudaSuccess) return e;
@@ -431,6 +432,7 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
         }
         if ((e = cudaEventRecord(p.ev_join, p.side_stream)) != cudaSuccess) return e;
     }
+    prof_mark(p, kEvRealStart, st);
     if (parts & EWALD_PART_REAL) {
         if ((e = launch_real(p, n, st, vir != nullptr)) != cudaSuccess) return e;
     }
@@ -438,6 +440,7 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
     if (do_recip) {
         if ((e = cudaStreamWaitEvent(st, p.ev_join, 0)) != cudaSuccess) return e;
     }
+    prof_mark(p, kEvJoined, st);
     int erc = p.e_recip_count;
     const double *erp = p.e_recip_part;
     if (spme) erp = spme_energy_parts(p, &erc);
@@ -960,7 +963,8 @@ extern "C" int ewald_compute_host(ewald_plan_t plan, int64_t n, const double *po
     return EWALD_OK;
 }
 
-extern "C" int ewald_profile(ewald_plan_t plan, int enable, double times_ms[8], int *launches)
+extern "C" int ewald_profile(ewald_plan_t plan, int enable, double times_ms[EWALD_PROFILE_TIMES],
+                             int *launches)
 {
     if (!plan) return EWALD_E_INVAL;
     Plan &p = plan->p;
@@ -976,7 +980,7 @@ extern "C" int ewald_profile(ewald_plan_t plan, int enable, double times_ms[8], 
     }
     if (launches) *launches = p.launches;
     if (times_ms) {
-        for (int i = 0; i < 8; ++i) times_ms[i] = 0.0;
+        for (int i = 0; i < EWALD_PROFILE_TIMES; ++i) times_ms[i] = 0.0;
         if (!p.prof_valid) return EWALD_OK;
         cudaError_t e = cudaEventSynchronize(p.ev[kEvFinal]);
         if (e != cudaSuccess) return cuda_status(e);
@@ -992,6 +996,9 @@ extern "C" int ewald_profile(ewald_plan_t plan, int enable, double times_ms[8], 
         times_ms[5] = span(kEvRealEnd, kEvFinal);
         times_ms[6] = span(kEvStart, kEvFinal);
         times_ms[7] = span(kEvRecipStart, kEvBackEnd);
+        times_ms[8] = span(kEvRealStart, kEvRealEnd);
+        times_ms[9] = p.prof_bs ? span(kEvBsStart, kEvBsEnd) : -1.0;
+        times_ms[10] = span(kEvJoined, kEvFinal);
     }
     return EWALD_OK;
 }

@@ -150,14 +150,16 @@ struct Plan {
     // profiling: events at stage boundaries (see ewald_profile), kernel launch counter
     bool prof = false;
     bool prof_valid = false;
-    cudaEvent_t ev[10] = {};
+    bool prof_bs = false;        // the back-scatter kernel events were recorded
+    cudaEvent_t ev[12] = {};
     int launches = 0;
 };
 
 // Stage boundary events (recorded only while profiling is on).
 enum : int {
     kEvStart = 0, kEvBinned = 1, kEvRealEnd = 2, kEvRecipStart = 3, kEvFwdEnd = 4,
-    kEvCoefEnd = 5, kEvBackEnd = 6, kEvFinal = 7,
+    kEvCoefEnd = 5, kEvBackEnd = 6, kEvFinal = 7, kEvRealStart = 8, kEvBsStart = 9,
+    kEvBsEnd = 10, kEvJoined = 11,
 };
 inline void prof_mark(Plan &p, int which, cudaStream_t st)
 {

@@ -371,8 +371,11 @@ cudaError_t launch_t(Plan &p, int64_t n, cudaStream_t st)
     dim3 gb((unsigned)((n + kBP - 1) / kBP), 3, npass);
     // the second half of the partials buffer holds the back-scatter pass sums
     double *part = reinterpret_cast<double *>(reinterpret_cast<char *>(ws.spart) + ws.spart_bytes / 2);
+    prof_mark(p, kEvBsStart, st);
     k_bscat<T><<<gb, 256, 0, st>>>(n, cap, p.R, p.kmax, ncol, npass, p.rows_d, X, Y, Z,
                                    (const T *)ws.gmat, part);
+    prof_mark(p, kEvBsEnd, st);
+    p.prof_bs = p.prof;
     k_bscat_sum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, npass, part, ws.pg, p.L,
                                                              ws.f_recip, ws.phi_recip);
     prof_mark(p, kEvBackEnd, st);

@@ -1117,9 +1117,12 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
     if ((e = cudaFuncSetAttribute(k_bs_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs)) != cudaSuccess)
         return e;
     const int ptiles = (int)((n + kBMT * 128 - 1) / (kBMT * 128));
+    prof_mark(p, kEvBsStart, st);
     k_bs_tc<BF><<<dim3(ptiles, s.npass), kBThreads, bs, st>>>(
         (int)n, p.R, p.kmax, s.ncol, s.np, s.nkb, make_int4(s.kb0[0], s.kb0[1], s.kb0[2], s.kb0[3]),
         ws.pu, s.blob, s.bpart, p.d_status);
+    prof_mark(p, kEvBsEnd, st);
+    p.prof_bs = p.prof;
     k_bs_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s.npass, s.bpart, ws.pg, s.gscale,
                                                             p.L, ws.f_recip, ws.phi_recip);
     prof_mark(p, kEvBackEnd, st);

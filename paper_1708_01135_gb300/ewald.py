@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
                                                ctypes.POINTER(_i64)]),
                 "ewald_real_noalloc": (_i, [_d, _d, _d, _i64, _p, _p, _p, _p, _p]),
                 "ewald_md": (_i, [_p, _i64, _p, _p, _p, _p, _d, _i, _p, _p, _p]),
+                "ewald_fma_peak": (_i, [_i, ctypes.POINTER(_d)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -152,6 +153,16 @@ def tune(n: int, L: float, tol: float = 1e-6, r_c: float | None = None):
 
 
 NOALLOC_MAX_N = 16384
+PROFILE_TIMES = 11          # entries of ewald_profile's times (EWALD_PROFILE_TIMES)
+
+
+def fma_peak(precision: str = "fp32") -> float:
+    """Measured CUDA-core FMA rate of the current device in TFLOP/s (ewald_fma_peak):
+    precision 'fp32' or 'fp64'."""
+    code = {"fp32": FP32, "fp64": FP64}[precision]
+    out = _d(0.0)
+    _check(lib().ewald_fma_peak(code, ctypes.byref(out)), "ewald_fma_peak")
+    return out.value
 
 
 def real_noalloc(L, beta, r_c, pos, q, forces, energy, stream=None):
@@ -303,12 +314,13 @@ class Ewald:
     def profile(self, enable: int = -1):
         """Stage times (ms) of the last recorded evaluation and its kernel launch count.
         enable: 1 start recording, 0 stop, -1 leave as is."""
-        t = np.zeros(8)
+        t = np.zeros(PROFILE_TIMES)
         nl = _i(0)
         _check(lib().ewald_profile(self._h, int(enable), t.ctypes.data, ctypes.byref(nl)),
                "ewald_profile")
-        names = ["binning", "real", "recip_forward", "recip_coef", "recip_back", "finalize",
-                 "total", "recip_branch"]
+        names = ["binning", "to_real_end", "recip_forward", "recip_coef", "recip_back",
+                 "real_end_to_end", "total", "recip_branch", "real_kernel", "backscatter_kernel",
+                 "finalize_kernels"]
         return dict(zip(names, t.tolist())), nl.value
 
     # -- introspection --

@@ -16,9 +16,11 @@ of shape [n]; every system is exactly neutral.
 """
 from __future__ import annotations
 
+import ctypes
 import hashlib
 import math
 import os
+import subprocess
 from dataclasses import dataclass
 
 import numpy as np
@@ -87,19 +89,46 @@ def _neutral_charges(n: int, mix, rng: np.random.Generator) -> np.ndarray:
     return q[rng.permutation(n)]
 
 
+_RSA_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "rsa.c")
+_RSA_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "librsa.so")
+_rsa = None
+
+
+def build_rsa(force: bool = False) -> str:
+    """Compile the sequential-insertion helper (rsa.c) with gcc into _build/librsa.so."""
+    if force or not os.path.exists(_RSA_LIB) or os.path.getmtime(_RSA_LIB) < os.path.getmtime(_RSA_SRC):
+        os.makedirs(os.path.dirname(_RSA_LIB), exist_ok=True)
+        tmp = f"{_RSA_LIB}.tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _RSA_SRC, "-lm"])
+        os.replace(tmp, _RSA_LIB)
+    return _RSA_LIB
+
+
+def _rsa_lib():
+    global _rsa
+    if _rsa is None:
+        lib = ctypes.CDLL(build_rsa())
+        p = ctypes.c_void_p
+        lib.rsa_insert.restype = ctypes.c_int64
+        lib.rsa_insert.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int64,
+                                   ctypes.c_int64, p, p, p, p, ctypes.c_int64, p]
+        _rsa = lib
+    return _rsa
+
+
 def random_neutral(n: int, L: float | None = None, density: float = 1.0, hard_core: float = 0.8,
-                   mix=((1.0, 0.5),), seed: int = 0, batch: int | None = None):
-    """Random neutral ionic system: n points uniform in a cubic box with random
-    sequential insertion (a candidate closer than ``hard_core`` to any accepted point,
-    under periodic images, is rejected).  Charges follow ``mix`` (see
-    :func:`_neutral_charges`); the default is half +1 and half -1.
+                   mix=((1.0, 0.5),), seed: int = 0):
+    """Random neutral ionic system: n points uniform in a cubic box by random sequential
+    insertion: candidates uniform in the box, in the order the seeded generator draws them,
+    each accepted unless it lies closer than ``hard_core`` to an accepted point under
+    periodic images.  Charges follow ``mix`` (see :func:`_neutral_charges`); the default is
+    half +1 and half -1.  The box side defaults to (n / density)^(1/3).
 
-    The box side defaults to (n / density)^(1/3).  Insertion is batched: candidates are
-    checked against accepted points through a grid whose cells are small enough to hold
-    at most one accepted point (side <= hard_core / sqrt(3)), and against earlier
-    candidates of the same batch the same way.
-
-    Returns (pos [n, 3], q [n], L).
+    The charges are drawn first, then the candidate stream (uniform doubles of the same
+    generator, x, y, z per candidate); the accept/reject pass over the stream is the C helper
+    rsa.c (a cell grid of side >= hard_core, so a candidate meets only the points of 27
+    cells).  Returns (pos [n, 3], q [n], L).
     """
     rng = _rng(seed)
     if L is None:
@@ -110,79 +139,24 @@ def random_neutral(n: int, L: float | None = None, density: float = 1.0, hard_co
     q = _neutral_charges(n, list(mix), rng)
     if hard_core <= 0:
         return rng.uniform(0.0, L, size=(n, 3)), q, L
-    g = max(1, int(math.floor(L / (hard_core / math.sqrt(3.0)))))
-    h = L / g
-    reach = int(math.ceil(hard_core / h))
-    if 2 * reach + 1 > g:
-        raise ValueError("box too small for the hard-core grid")
-    grid = np.full(g * g * g, -1, dtype=np.int64 if n >= 2 ** 31 else np.int32)
-    pts = np.empty((n, 3), dtype=np.float64)
-    count = 0
-    kt = np.int32 if g ** 3 < 2 ** 31 else np.int64
-    offs = np.arange(-reach, reach + 1, dtype=kt)
-    hc2 = hard_core * hard_core
-    batch = batch or max(64, min(n, 1 << 16))
-    stall = 0
+    # cells at least a little wider than the hard core, so that rounding of the cell index
+    # can never hide a point closer than the hard core two cells away
+    g = int(math.floor(L / (hard_core * (1.0 + 1e-9))))
+    lib = _rsa_lib()
+    pts = np.zeros((n, 3), dtype=np.float64)
+    head = np.full(max(1, g) ** 3 if g >= 3 else 1, -1, dtype=np.int64)
+    nxt = np.full(max(1, n), -1, dtype=np.int64)
+    count, drawn = 0, 0
+    used = ctypes.c_int64(0)
     while count < n:
-        want = min(batch, max(64, 2 * (n - count)))
-        cand = rng.uniform(0.0, L, size=(want, 3))
-        cell = np.minimum((cand / h).astype(np.int64), g - 1).astype(kt)
-        # neighbour cells of every candidate: [want, (2 reach + 1)^3], built per axis
-        cx = (cell[:, 0:1] + offs) % g
-        cy = (cell[:, 1:2] + offs) % g
-        cz = (cell[:, 2:3] + offs) % g
-        nkey_all = (((cx * g)[:, :, None] + cy[:, None, :]) * g)[:, :, :, None] + cz[:, None, None, :]
-        nkey_all = nkey_all.reshape(want, -1)
-        occ = grid[nkey_all]
-        ok = np.ones(want, dtype=bool)
-        has = occ >= 0
-        if has.any():
-            rows, cols = np.nonzero(has)
-            d = cand[rows] - pts[occ[rows, cols]]
-            d -= L * np.round(d / L)
-            bad = (d * d).sum(axis=1) < hc2
-            ok[rows[bad]] = False
-        # conflicts inside the batch: a candidate is dropped when it lies closer than the
-        # hard core to any earlier candidate of the same batch (earlier in proposal order).
-        # The batch's own cells are looked up by binary search in its sorted cell keys.
-        idx = np.nonzero(ok)[0]
-        if idx.size > 1:
-            key = (cell[idx, 0] * g + cell[idx, 1]) * g + cell[idx, 2]
-            order = np.lexsort((idx, key))                 # by cell, then proposal order
-            skey, sidx = key[order], idx[order]
-            first = np.ones(skey.size, dtype=bool)
-            first[1:] = skey[1:] != skey[:-1]
-            # two candidates in one grid cell are always too close: keep the first one
-            ukey, uidx = skey[first], sidx[first]
-            alive = np.zeros(want, dtype=bool)
-            alive[uidx] = True
-            idx = np.nonzero(alive)[0]
-            nkey = nkey_all[idx]                           # [m, (2 reach + 1)^3]
-            pos_ = np.searchsorted(ukey, nkey)
-            pos_ = np.minimum(pos_, ukey.size - 1)
-            hit = ukey[pos_] == nkey
-            other = np.where(hit, uidx[pos_], np.iinfo(np.int64).max)
-            has = other < idx[:, None]
-            keep = np.ones(idx.size, dtype=bool)
-            if has.any():
-                rows, cols = np.nonzero(has)
-                d = cand[idx[rows]] - cand[other[rows, cols]]
-                d -= L * np.round(d / L)
-                bad = (d * d).sum(axis=1) < hc2
-                keep[rows[bad]] = False
-            ok[:] = False
-            ok[idx[keep]] = True
-        acc = np.nonzero(ok)[0][: n - count]
-        if acc.size == 0:
-            stall += 1
-            if stall > 200:
-                raise RuntimeError("random sequential insertion stalled")
-            continue
-        stall = 0
-        pts[count:count + acc.size] = cand[acc]
-        c = cell[acc]
-        grid[(c[:, 0] * g + c[:, 1]) * g + c[:, 2]] = np.arange(count, count + acc.size)
-        count += acc.size
+        chunk = max(1 << 16, 2 * (n - count))
+        cand = np.ascontiguousarray(rng.uniform(0.0, L, size=(chunk, 3)))
+        drawn += chunk
+        count = lib.rsa_insert(L, float(hard_core), g, n, count, pts.ctypes.data,
+                               head.ctypes.data, nxt.ctypes.data, cand.ctypes.data, chunk,
+                               ctypes.byref(used))
+        if count < n and drawn > 1000 * n + (1 << 20):
+            raise RuntimeError("random sequential insertion stalled (hard core too large)")
     return np.ascontiguousarray(pts), q, L
 
 
@@ -205,8 +179,8 @@ def rocksalt_262144(seed: int = 1237):
 
 def random_2097152(seed: int = 1239):
     """N = 2,097,152 with charges +-1 (40 % each) and +-2 (10 % each), uniform at
-    density 1.0 (L = 128) with a 0.8 hard core.  Generation takes minutes, so the result
-    is kept in the on-disk cache (see :func:`_cached`)."""
+    density 1.0 (L = 128) with a 0.8 hard core.  The result is also kept in the on-disk
+    cache (see :func:`_cached`)."""
     return _cached(f"random_2097152_s{seed}",
                    lambda: random_neutral(2097152, density=1.0, hard_core=0.8,
                                           mix=((1.0, 0.4), (2.0, 0.1)), seed=seed))
