@@ -922,7 +922,7 @@ def measure_workload(args, workload, local, world, dev, flush, alu_peaks, steps,
         else:
             full, wall, nt, sub, Fo, note = oracle_sample(pos, q, L, beta, rc, kmax,
                                                           args.cpu_targets, S_given=Sg)
-            sk_all = "all" in note.split("modes")[0]
+            sk_all = note.startswith(f"S(k) over all {n} particles and all")
             acc["same_parameters"] = {
                 "rel_force_rms": float(np.sqrt(((Fg[sub] - Fo) ** 2).sum() / (Fo ** 2).sum())),
                 "particles": int(nt),

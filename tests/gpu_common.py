@@ -26,6 +26,14 @@ def rel(a, b):
     return abs(a - b) / abs(b)
 
 
+def rel_total(e_total, ref):
+    """Error of a total energy relative to the size of its parts, |E_real| + |E_recip| +
+    |E_self| of the oracle: at large beta the total is a small difference of the reciprocal
+    and self energies, and a path's error is set by the parts it sums."""
+    return abs(e_total - ref["E_total"]) / (abs(ref["E_real"]) + abs(ref["E_recip"]) +
+                                            abs(ref["E_self"]))
+
+
 # Per-particle factor of assert_close: no single particle may be off by more than this many
 # times the tolerance, measured in units of the RMS size of the reference values.
 LOCAL_FACTOR = 20.0
