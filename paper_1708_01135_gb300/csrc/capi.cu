@@ -262,7 +262,7 @@ void free_workspace(Plan &p)
     graph_reset(p);
     Workspace &ws = p.ws;
     void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
-                    ws.tiles, ws.tile_count, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
+                    ws.pg, ws.pl64, ws.pl32, ws.pu,
                     ws.f_real, ws.f_recip, ws.e_tile, ws.qpart, ws.phi_real, ws.phi_recip,
                     ws.vir_tile, ws.vir_part, ws.type_sorted, ws.elj_tile};
     for (void *q : ptrs) pool_free(q, p.side_stream);
@@ -346,7 +346,6 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     p.real_tile = real_tile_for(p.w, (double)n / p.ncells);
     Workspace &ws = p.ws;
     const int nb = binning_chunks(n);
-    const int nrows = p.nc * p.nc;
     const int64_t tiles = real_tile_capacity(p, n);
     const int64_t qblocks = (n + 255) / 256;
 #define EW_TRY(x) do { if ((e = (x)) != cudaSuccess) { free_workspace(p); return e; } } while (0)
@@ -356,9 +355,6 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     EW_TRY(dmalloc(p, &ws.hist, sizeof(int) * (size_t)nb * p.ncells));
     EW_TRY(dmalloc(p, &ws.cell_start, sizeof(int) * (p.ncells + 1)));
     EW_TRY(dmalloc(p, &ws.cell_total, sizeof(int) * p.ncells));
-    EW_TRY(dmalloc(p, &ws.tiles, sizeof(int2) * tiles));
-    EW_TRY(dmalloc(p, &ws.tile_count, sizeof(int) * nrows));
-    EW_TRY(dmalloc(p, &ws.tile_off, sizeof(int) * (nrows + 1)));
     EW_TRY(dmalloc(p, &ws.pg, sizeof(double4_32a) * n));
     if (p.precision == EWALD_FP64) EW_TRY(dmalloc(p, &ws.pl64, sizeof(double4_32a) * n));
     else EW_TRY(dmalloc(p, &ws.pl32, sizeof(float4) * n));
@@ -538,10 +534,11 @@ size_t plan_footprint(const Plan &p, int64_t n)
     int nc = 1, w = 0;
     cell_grid(p.L, p.rc, n, nc, w);
     const size_t ncells = (size_t)nc * nc * nc;
-    const int64_t tiles = w == 0 ? (n + 31) / 32 : n / real_tile_for(w, (double)n / ncells) + (int64_t)nc * nc + 1;
+    const int64_t ts = w == 0 ? 32 : 32 / real_tile_for(w, (double)n / ncells);
+    const int64_t tiles = (n + ts - 1) / ts;
     size_t b = 0;
     b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * ncells;
-    b += sizeof(int) * (2 * ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * ((size_t)nc * nc + 1);
+    b += sizeof(int) * (2 * ncells + 1);
     b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
     b += sizeof(double) * 8 * (size_t)n + sizeof(double) * 14 * tiles + sizeof(double) * 3 * ((n + 255) / 256);
     b += sizeof(int) * (size_t)n;
@@ -590,22 +587,29 @@ static void build_rows(Plan &p)
 // 16 particles or more (dense systems with long cutoffs, where the finer stencil follows the
 // cutoff sphere more closely and the per-cell overhead stays small), else w = 2, 1, or 0
 // (all pairs with the minimum image).
+// Cell grid of the real-space pairs: nc^3 cubes of side L / nc, a stencil of |dy|, |dz| <= w
+// rows with w = ceil(r_c nc / L), and 2 w + 1 <= nc so that the stencil's rows (and the
+// cells of a row a target can reach) are distinct.  The side aims at max(rho^-1/3, r_c / 5):
+// about one particle per cell or more, and at most ~11 rows across the cutoff disk, so that
+// each target's candidate ranges follow its cutoff sphere closely (the pair kernel takes the
+// cells of every row within each target's own reach).  Without the density (plan set-up)
+// the side is r_c / 2; the grid is chosen again once the particle count is known.  Boxes too
+// small for such a stencil use the all-pairs mode (w = 0, one cell).
 static void cell_grid(double L, double rc, int64_t n, int &nc_out, int &w_out)
 {
     const double rho = n > 0 ? (double)n / (L * L * L) : 0.0;
+    double s_t = rho > 0 ? fmax(pow(rho, -1.0 / 3.0), rc / 5.0) : rc / 2.0;
+    int nc = (int)floor(L / s_t);
+    if (nc > 160) nc = 160;      // 4.1M cells at most (the binning keeps per-chunk histograms)
     w_out = 0;
     nc_out = 1;
-    for (int w = 3; w >= 1; --w) {
-        int nc = (int)floor(L * w / rc * (1.0 - 1e-12));
-        if (nc > 256) nc = 256;
-        if (nc < 2 * w + 1) continue;
-        if (w == 3) {
-            const double side = L / nc;
-            if (rho * side * side * side < 16.0) continue;
+    for (; nc >= 3; --nc) {
+        const int w = (int)ceil(rc * nc / L * (1.0 - 1e-12));
+        if (w >= 1 && 2 * w + 1 <= nc) {
+            nc_out = nc;
+            w_out = w;
+            return;
         }
-        w_out = w;
-        nc_out = nc;
-        return;
     }
 }
 
@@ -694,11 +698,23 @@ int plan_reconfigure(ewald_plan *h, double L, double beta, double rc, int kmax, 
     if (s != EWALD_OK) return s;
     if (p.last_stream) cudaStreamSynchronize(p.last_stream);
     cudaStreamSynchronize(p.side_stream);
-    const bool same_shape = probe.ncells == p.ncells && probe.nc == p.nc && probe.R == p.R &&
-                            probe.kmax == p.kmax && probe.precision == p.precision;
+    // the grid the kept workspace would have: chosen from the density of the particle count
+    // it holds (as grow_workspace chooses it), else the density-free set-up grid
+    int nc2 = probe.nc, w2 = probe.w;
+    if (p.ws.cap_n > 0) cell_grid(L, rc, p.ws.cap_n, nc2, w2);
+    const int g2 = real_tile_for(w2, (double)p.ws.cap_n / ((double)nc2 * nc2 * nc2));
+    const bool same_shape = p.ws.cap_n > 0 && nc2 == p.nc && w2 == p.w && g2 == p.real_tile &&
+                            probe.R == p.R && probe.kmax == p.kmax &&
+                            probe.precision == p.precision;
     graph_reset(p);
     if (!same_shape) free_workspace(p);
     plan_setup_host(p, L, beta, rc, kmax, precision);
+    if (same_shape) {
+        p.nc = nc2;
+        p.w = w2;
+        p.ncells = nc2 * nc2 * nc2;
+        p.cell_side = L / nc2;
+    }
     return cuda_status(plan_upload(p));
 }
 

@@ -1,5 +1,5 @@
 // Integer cell binning (hot-path steps a1-a3): periodic wrap, cell keys, a stable
-// counting sort by cell, cell offsets, row tiles, and packing of the sorted particles.
+// counting sort by cell, cell offsets, and packing of the sorted particles.
 //
 // The paper's short-range part runs as a "local PairLoop" that only visits pairs closer
 // than r_c through cell-based looping code (Section 2.2; Section 3.2.1).  Here the cells
@@ -190,13 +190,16 @@ __global__ void k_scatter(int64_t n, int64_t chunk, int ncells, const int *__res
     }
 }
 
-// a3: pack sorted particles: wrapped global FP64 position, cell-local FP64/FP32 position,
-// and 32-bit fixed-point fractions of the box (for exact integer phase angles).
+// a3: pack sorted particles: wrapped global FP64 position, cell-local FP64 position (the
+// all-pairs kernel), the FP32 record of the pair kernels and 32-bit fixed-point fractions of
+// the box (for exact integer phase angles).  The FP32 record is, in all-pairs mode (one
+// cell), the cell-local position and q; in cell mode, x / L as 32-bit fixed point (bits in
+// .x), y and z relative to the corner of the particle's cell, and q.
 __global__ void k_pack(int64_t n, const double *__restrict__ pos, const double *__restrict__ q,
                        const int *__restrict__ perm, const int *__restrict__ key_sorted,
-                       double L, double side, int nc, double4_32a *__restrict__ pg,
-                       double4_32a *__restrict__ pl64, float4 *__restrict__ pl32,
-                       uint4 *__restrict__ pu)
+                       double L, double side, int nc, int cell_mode,
+                       double4_32a *__restrict__ pg, double4_32a *__restrict__ pl64,
+                       float4 *__restrict__ pl32, uint4 *__restrict__ pu)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -209,35 +212,17 @@ __global__ void k_pack(int64_t n, const double *__restrict__ pos, const double *
     int cx = k % nc, cy = (k / nc) % nc, cz = k / (nc * nc);
     pg[s] = make_double4_32a(x, y, z, qi);
     double lx = x - cx * side, ly = y - cy * side, lz = z - cz * side;
+    const double scale = 4294967296.0 / L;
+    unsigned ux = (unsigned)((unsigned long long)llrint(x * scale) & 0xffffffffull);
     if (pl64) pl64[s] = make_double4_32a(lx, ly, lz, qi);
-    if (pl32) pl32[s] = make_float4((float)lx, (float)ly, (float)lz, (float)qi);
+    if (pl32)
+        pl32[s] = cell_mode ? make_float4(__uint_as_float(ux), (float)ly, (float)lz, (float)qi)
+                            : make_float4((float)lx, (float)ly, (float)lz, (float)qi);
     if (pu) {
-        const double scale = 4294967296.0 / L;
-        unsigned ux = (unsigned)((unsigned long long)llrint(x * scale) & 0xffffffffull);
         unsigned uy = (unsigned)((unsigned long long)llrint(y * scale) & 0xffffffffull);
         unsigned uz = (unsigned)((unsigned long long)llrint(z * scale) & 0xffffffffull);
         pu[s] = make_uint4(ux, uy, uz, __float_as_uint((float)qi));
     }
-}
-
-// Tiles of up to `ts` consecutive sorted particles that never leave a row of cells.
-__global__ void k_row_tiles(int nrows, int nc, int ts, const int *__restrict__ cell_start,
-                            int *__restrict__ tcount)
-{
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    int cnt = cell_start[(r + 1) * nc] - cell_start[r * nc];
-    tcount[r] = (cnt + ts - 1) / ts;
-}
-
-__global__ void k_emit_tiles(int nrows, int nc, int ts, const int *__restrict__ cell_start,
-                             const int *__restrict__ toff, int2 *__restrict__ tiles)
-{
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    int b = cell_start[r * nc];
-    int o = toff[r], e = toff[r + 1];
-    for (int t = o; t < e; ++t) tiles[t] = make_int2(r, b + ts * (t - o));
 }
 
 }  // namespace
@@ -267,18 +252,11 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
     k_scatter<<<nb, 256, smem, st>>>(n, chunk, p.ncells, ws.key, ws.cell_start, ws.hist, ws.perm,
                                      ws.key_sorted, use_smem);
     const bool need64 = p.precision == EWALD_FP64;
-    const bool need32 = !need64;
     k_pack<<<(int)((n + 255) / 256), 256, 0, st>>>(n, pos, q, ws.perm, ws.key_sorted, p.L,
-                                                   p.cell_side, p.nc, ws.pg,
+                                                   p.cell_side, p.nc, p.w > 0 ? 1 : 0, ws.pg,
                                                    need64 ? ws.pl64 : nullptr,
-                                                   need32 ? ws.pl32 : nullptr, ws.pu);
-    const int nrows = p.nc * p.nc;
-    const int ts = real_tile_size(p);
-    k_row_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ts, ws.cell_start, ws.tile_count);
-    k_scan1<<<1, 1024, 0, st>>>(nrows, ws.tile_count, ws.tile_off);
-    k_emit_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ts, ws.cell_start, ws.tile_off,
-                                                      ws.tiles);
-    p.launches += 8;
+                                                   need64 ? nullptr : ws.pl32, ws.pu);
+    p.launches += 5;
     return cudaGetLastError();
 }
 

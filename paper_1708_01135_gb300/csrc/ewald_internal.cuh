@@ -55,13 +55,11 @@ struct Workspace {
     int *hist = nullptr;         // [nb * ncells] per-chunk cell counts -> offsets
     int *cell_start = nullptr;   // [ncells + 1]
     int *cell_total = nullptr;   // [ncells]
-    int2 *tiles = nullptr;       // [max tiles] (row, first slot)
-    int *tile_count = nullptr;   // [nrows] tiles per row
-    int *tile_off = nullptr;     // [nrows + 1] exclusive offsets; tile_off[nrows] = tiles
     // packed particles (sorted)
     double4_32a *pg = nullptr;       // wrapped global position + q (FP64)
-    double4_32a *pl64 = nullptr;     // cell-local position + q (FP64)
-    float4 *pl32 = nullptr;      // cell-local position + q (FP32)
+    double4_32a *pl64 = nullptr;     // cell-local position + q (FP64, all-pairs mode)
+    float4 *pl32 = nullptr;      // FP32 pair record: cell-local position + q (all-pairs mode),
+                                 // or x / L fixed-point bits, cell-local y, z, q (cell mode)
     uint4 *pu = nullptr;         // 32-bit fixed-point fractions x/L, y/L, z/L + q (float bits)
     // outputs (sorted)
     double *f_real = nullptr;    // [n][3]
@@ -98,7 +96,7 @@ struct Plan {
     int w = 0;           // stencil half-width in cells (0: all pairs, minimum image)
     int ncells = 1;
     double cell_side = 0;
-    int real_tile = 16;          // targets per real-space warp tile (16 or 32)
+    int real_tile = 2;           // lanes per target of the real-space cell kernel (2 or 4)
     // Lennard-Jones pairs fused into the real-space kernel (off when lj_ntypes == 0)
     int lj_ntypes = 0;
     const int *lj_type = nullptr;    // caller-owned [n] types, caller order
@@ -176,9 +174,9 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
 cudaError_t launch_real(Plan &p, int64_t n, cudaStream_t st, bool virial);
 // One bounded device wait that cannot complete (the timeout path of the staged copies).
 cudaError_t launch_wait_probe(Plan &p, cudaStream_t st);
-int64_t real_tile_capacity(const Plan &p, int64_t n);
-int real_tile_size(const Plan &p);          // particles per real-space tile
-int real_tile_for(int w, double cell_occupancy);   // tile size for a grid (particles per cell)
+int64_t real_tile_capacity(const Plan &p, int64_t n);   // energy partials (target groups)
+int real_tile_size(const Plan &p);          // targets per real-space warp
+int real_tile_for(int w, double cell_occupancy);   // lanes per target for a grid (particles per cell)
 // a5-a8 on CUDA cores (FP64 or FP32): S(k), energy, back-scatter into ws.f_recip.
 cudaError_t launch_recip_simt(Plan &p, int64_t n, cudaStream_t st);
 size_t recip_simt_bytes(const Plan &p, int64_t n);

@@ -1,0 +1,66 @@
+"""Derive the coefficients of the FP32 erfc used by the real-space pair kernels.
+
+    erfc(x) ~= t exp(-x^2) P(u),   t = 1 / (1 + p x),   u = a t + b in [-1, 1] for x in [0, X]
+
+P is a degree-8 polynomial fitted to erfc(x) exp(x^2) / t (scipy's erfcx) on [0, X], X = 8,
+by least squares with Lawson-style reweighting toward the minimax relative error; p is the
+value on a grid that minimises that error.  The shifted variable u keeps the coefficients
+small and decreasing, so a Horner evaluation in FP32 loses little to cancellation.
+
+    python paper_1708_01135_gb300/csrc/fit_erfc.py      # prints the constants for realspace.cu
+
+The fit needs no GPU; it is run once, and its output is pasted into realspace.cu.
+tests/test_abi_cpu.py reads the constants back from the source and checks the error bound.
+"""
+import numpy as np
+from scipy.special import erfc, erfcx
+
+X = 8.0
+DEGREE = 8
+XS = np.linspace(0.0, X, 60001)
+
+
+def _map(p):
+    tmin = 1.0 / (1.0 + p * X)
+    a = 2.0 / (1.0 - tmin)
+    return a, -1.0 - a * tmin
+
+
+def fit(p, degree=DEGREE, iters=60):
+    t = 1.0 / (1.0 + p * XS)
+    a, b = _map(p)
+    u = a * t + b
+    target = erfcx(XS) / t
+    V = np.vander(u, degree + 1, increasing=True)
+    w = np.ones_like(XS)
+    for _ in range(iters):
+        A = V * (w / target)[:, None]
+        c, *_ = np.linalg.lstsq(A, w, rcond=None)
+        err = np.abs(V @ c / target - 1.0)
+        w = w * (err / err.max() + 1e-3) ** 0.5
+        w /= w.mean()
+    return c, float(np.abs(V @ c / target - 1.0).max()), a, b
+
+
+def main():
+    best = min((fit(p, iters=30)[1], p) for p in np.linspace(0.28, 0.60, 33))
+    p = float(np.float32(best[1]))
+    c, err, a, b = fit(p)
+    c32 = c.astype(np.float32)
+    print(f"// max relative error in exact arithmetic on [0, {X}]: {err:.2e}")
+    print(f"constexpr float kErfcP = {float(np.float32(p))!r}f;")
+    print(f"constexpr float kErfcA = {float(np.float32(a))!r}f, kErfcB = {float(np.float32(b))!r}f;")
+    print("constexpr float kErfcC[9] = {" + ", ".join(f"{float(v)!r}f" for v in c32) + "};")
+    # the same evaluation in FP32 (the kernel's rounding of t, u and Horner)
+    x32 = XS.astype(np.float32)
+    t32 = (np.float32(1) / (np.float32(1) + np.float32(p) * x32)).astype(np.float32)
+    u32 = (np.float32(a) * t32 + np.float32(b)).astype(np.float32)
+    P = np.float32(c32[-1])
+    for k in range(len(c32) - 2, -1, -1):
+        P = (P * u32 + c32[k]).astype(np.float32)
+    rel = np.abs(t32.astype(np.float64) * P.astype(np.float64) * np.exp(-XS ** 2) / erfc(XS) - 1)
+    print(f"// max relative error with FP32 t, u and Horner: {rel.max():.2e}")
+
+
+if __name__ == "__main__":
+    main()

@@ -5,26 +5,35 @@
 //                                          + 2 beta / sqrt(pi) exp(-beta^2 r_ij^2)]
 //   E_real = 1/2 sum_i q_i phi_i            (r_ij = r_i - r_j, minimum image)
 //
-// GPU design (templated on FP64 and FP32 arithmetic):
-//   * One warp owns a tile of up to 16 (or 32) consecutive sorted particles of one row of
-//     cells (fixed c_y, c_z).  With 16, lane = (target i, partner group g): every target has
-//     2 lanes that take every other partner, and the 2 partial sums of a target are combined
-//     with a shuffle at the end; with 32 (cells of 16 particles or more) every lane owns one
-//     target.  Either way every target's force is written by one lane and no two threads ever
-//     write the same particle (the paper's rule that a loop writes only its own particle,
-//     Section 3.2.3, with no atomics).  The tile size per plan follows the cell occupancy:
-//     narrow tiles keep the candidate set close to the cutoff sphere where cells are sparse,
-//     wide ones amortise the candidate traffic where they are dense.
-//   * The candidate partners j of a tile are the cells of the neighbour rows (c_y + dy,
-//     c_z + dz), |dy|, |dz| <= w, in the x range of the tile widened by the reach left for
-//     that row.  A run of cells along x is a contiguous range of the sorted array, so it is
-//     copied to shared memory with one bulk TMA copy (cp.async.bulk, completion on an
-//     mbarrier), double-buffered per warp; all lanes then read each j as a broadcast.
-//   * Positions are stored relative to the corner of their own cell; the offset between a
-//     target and a partner cell is an exact small multiple of the cell side.  This keeps
-//     FP32 differences accurate to ~1e-7 of the cell size instead of ~1e-7 of L, and makes
-//     the periodic image implicit (the neighbour cell index wraps, the offset does not).
-//   * Energies: one FP64 partial per tile, summed in tile order by the finalize step.
+// GPU design (templated on FP64 and FP32 arithmetic), cell mode:
+//   * The box is cut into nc^3 cubic cells of side s ~ max(rho^-1/3, r_c / 5) (about one to
+//     seven particles each), sorted by cell key (c_z nc + c_y) nc + c_x, so that every row of
+//     cells along x (fixed c_y, c_z) is a contiguous range of the sorted arrays.
+//   * A warp owns 32 / G consecutive sorted targets and G lanes per target.  It visits the
+//     rows (c_y + dy, c_z + dz), |dy|, |dz| <= w, in a fixed order.  For each row every
+//     target takes its own exact reach: the distance d from its (y, z) to the row's square
+//     gives the x half-width sqrt(r_c^2 - d^2), and only the cells of the row that overlap
+//     [x - reach, x + reach] are candidates (one or, where the row wraps, two contiguous
+//     ranges).  The G lanes of a target split that range; the warp runs as many steps as
+//     its longest range needs.  Candidates are read straight from the sorted arrays (they
+//     stay in L1/L2: neighbouring targets share most of them).  This keeps the candidates
+//     close to the cutoff sphere of each target (about 1.6 to 1.8 per partner inside r_c)
+//     instead of the cutoff sphere of a whole tile of targets.
+//   * FP32: x is a 32-bit fixed-point fraction of the box (x / L 2^32), so the difference of
+//     two of them modulo 2^32 is the minimum image exactly, at 2^-32 L resolution whatever the
+//     box size; y and z are stored relative to the corner of their own cell, and the row
+//     offset is an exact small multiple of the cell side (periodic images are implicit).
+//     FP64: wrapped global coordinates, with the image shift of a wrapped row or range.
+//   * erfc in FP32 is t exp(-x^2) P(t), t = 1 / (1 + p x), with a degree-7 polynomial P fitted
+//     to erfc(x) exp(x^2) / t on [0, 6] (csrc/fit_erfc.py derives the coefficients; relative
+//     error 3.5e-8 in exact arithmetic): one exp2, one reciprocal and the pair's rsqrt.
+//   * Every target's sums are held by its lanes and combined in a fixed shuffle order; the
+//     target's force is written by one lane, and no two threads ever write the same particle
+//     (the paper's rule that a loop writes only its own particle, Section 3.2.3, with no
+//     atomics); energies are one FP64 partial per warp, summed in order by the finalize step.
+// All pairs mode (boxes too small for a stencil of distinct cells): one tile of 32 targets
+// per warp, every particle staged through a double-buffered bulk TMA copy (cp.async.bulk,
+// completion on an mbarrier) and read by all lanes as a broadcast.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,11 +43,7 @@ namespace ew {
 namespace {
 
 constexpr int kWarps = 4;      // warps (tiles) per block
-constexpr int kCap = 128;      // particles per staging buffer (cell mode)
 constexpr int kCapAll = 256;   // particles per staging buffer (all-pairs mode)
-// Targets per warp tile in cell mode: 16 (two partner lanes per target) for sparse cells,
-// 32 (one lane per target) where cells hold 16 particles or more; chosen per plan.
-constexpr int kTileSparse = 16, kTileDense = 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -253,33 +258,35 @@ __device__ __forceinline__ void load_lj_table(T4 *ljs, const LJArgs &lj, double 
     __syncthreads();
 }
 
-// erfc(x) = exp(-x^2) * t * exp(P(t)), t = 1 / (1 + x / 2), x >= 0: the Chebyshev fit
-// "erfcc" of Numerical Recipes in C (2nd ed., Sec. 6.2), fractional error below 1.2e-7 in
-// exact arithmetic (checked against the double-precision erfc in tests/test_abi_cpu.py).
-// The caller supplies g = exp(-x^2), which the force term needs as well.
+// erfc(x) ~= t exp(-x^2) P(u), t = 1 / (1 + p x), u = a t + b, x >= 0: a degree-8 polynomial
+// fitted to erfc(x) exp(x^2) / t on [0, 8] (csrc/fit_erfc.py: relative error 7.6e-9 in exact
+// arithmetic, 3.5e-7 with FP32 rounding of t, u and the Horner steps).  Beyond x = 8, where
+// erfc < 1e-29, the polynomial is extrapolated; those pairs add nothing measurable.  The
+// caller supplies g = exp(-x^2), which the force term needs as well.
+constexpr float kErfcP = 0.3700000047683716f;
+constexpr float kErfcA = 2.675675630569458f, kErfcB = -1.675675630569458f;
+__constant__ float kErfcC[9] = {0.48547884821891785f, 0.31732580065727234f, 0.14685595035552979f,
+                             0.044840890914201736f, 0.006656186655163765f,
+                             -0.000744646938983351f, -0.00044474180322140455f,
+                             7.326921149797272e-06f, 2.4387149096583016e-05f};
+
 __device__ __forceinline__ float erfc_from_gauss(float x, float g)
 {
-    const float t = __fdividef(1.0f, 1.0f + 0.5f * x);
-    float p = 0.17087277f;
-    p = fmaf(p, t, -0.82215223f);
-    p = fmaf(p, t, 1.48851587f);
-    p = fmaf(p, t, -1.13520398f);
-    p = fmaf(p, t, 0.27886807f);
-    p = fmaf(p, t, -0.18628806f);
-    p = fmaf(p, t, 0.09678418f);
-    p = fmaf(p, t, 0.37409196f);
-    p = fmaf(p, t, 1.00002368f);
-    p = fmaf(p, t, -1.26551223f);
-    return t * g * __expf(p);
+    const float t = __fdividef(1.0f, fmaf(kErfcP, x, 1.0f));
+    const float u = fmaf(kErfcA, t, kErfcB);
+    float p = kErfcC[8];
+#pragma unroll
+    for (int k = 7; k >= 0; --k) p = fmaf(p, u, kErfcC[k]);
+    return t * g * p;
 }
 
-// One candidate pair: target at the origin shifted by (xi, yi, zi), partner p; with
-// Lennard-Jones pairs, ljrow is the target type's row of the table and tj the partner's type.
+// One candidate pair with displacement d = r_i - r_j (minimum image) and partner charge qj;
+// the pair counts when 0 < |d| < r_c.  With Lennard-Jones pairs, ljrow is the target type's
+// row of the table and tj the partner's type.
 template <class T, class T4, class A>
-__device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
-                                     T beta, T nb2, T two_b_rpi, const T4 *ljrow, int tj)
+__device__ __forceinline__ void pair_d(A &a, T dx, T dy, T dz, T qj, T rc2, T beta, T nb2,
+                                       T two_b_rpi, const T4 *ljrow, int tj)
 {
-    const T dx = xi - p.x, dy = yi - p.y, dz = zi - p.z;   // r_i - r_j
     const T r2 = dx * dx + dy * dy + dz * dz;
     if (r2 < rc2 && r2 > T(0)) {
         const T rinv = rsqrt_t(r2);
@@ -288,8 +295,8 @@ __device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
         T e;                                                // erfc(beta r) / r
         if constexpr (sizeof(T) == 4) e = erfc_from_gauss(beta * r, g) * rinv;
         else e = erfc_t(beta * r) * rinv;
-        const T s = p.w * (e + two_b_rpi * g) * rinv * rinv;
-        a.phi += p.w * e;
+        const T s = qj * (e + two_b_rpi * g) * rinv * rinv;
+        a.phi += qj * e;
         const T sx = s * dx, sy = s * dy, sz = s * dz;
         a.fx += sx;
         a.fy += sy;
@@ -317,191 +324,143 @@ __device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
     }
 }
 
-// Chunk of a contiguous run of partner cells staged in shared memory.
-struct Chunk {
-    int g0, cnt;        // sorted range [g0, g0 + cnt)
-    int rowbase;        // nrow * nc
-    int u0;             // unwrapped x index of the first cell of the run
-    int dy, dz;
-};
-
-struct ChunkIter {
-    // stencil position
-    int dz, dy, w, nc;
-    int xa, xb;          // tile x-cell range
-    int row_cy, row_cz;
-    int wx;              // x reach of the current row
-    int u, uend;         // next unwrapped cell to start a run, last cell of the row range
-    // current run
-    int g, gend, run_u0, rowbase;
-    bool in_run;
-    bool started;
-    int part, split, rowctr;   // this warp takes the kept rows with index % split == part
-    float side, rc2;     // geometry for culling (float is enough for the reach test)
-
-    __device__ bool next_row()
-    {
-        while (true) {
-            if (!started) { started = true; dz = -w; dy = -w; }
-            else if (++dy > w) { dy = -w; if (++dz > w) return false; }
-            int ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
-            float my = ay > 0 ? (ay - 1) * side : 0.f, mz = az > 0 ? (az - 1) * side : 0.f;
-            float rest = rc2 - my * my - mz * mz;
-            if (rest <= 0.f) continue;
-            if ((rowctr++ % split) != part) continue;
-            int r = (int)ceilf(sqrtf(rest) / side - 1e-6f);
-            wx = r < w ? r : w;
-            if (wx < 0) wx = 0;
-            u = xa - wx;
-            uend = xb + wx;
-            int ny = ((row_cy + dy) % nc + nc) % nc, nz = ((row_cz + dz) % nc + nc) % nc;
-            rowbase = (nz * nc + ny) * nc;
-            return true;
-        }
-    }
-
-    __device__ bool next(const int *__restrict__ cell_start, Chunk &c)
-    {
-        while (true) {
-            if (in_run && g < gend) {
-                int cnt = gend - g < kCap ? gend - g : kCap;
-                c.g0 = g; c.cnt = cnt; c.rowbase = rowbase; c.u0 = run_u0; c.dy = dy; c.dz = dz;
-                g += cnt;
-                return true;
-            }
-            in_run = false;
-            if (!started || u > uend) {
-                if (!next_row()) return false;
-            }
-            int c0 = ((u % nc) + nc) % nc;
-            int u1 = u + (nc - 1 - c0);
-            if (u1 > uend) u1 = uend;
-            g = cell_start[rowbase + c0];
-            gend = cell_start[rowbase + c0 + (u1 - u) + 1];
-            run_u0 = u;
-            u = u1 + 1;
-            in_run = true;
-        }
-    }
-};
-
-template <class T, int kTile, bool kVir, bool kLJ>
-__global__ void __launch_bounds__(kWarps * 32)
-k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restrict__ key_sorted,
-             const int *__restrict__ cell_start, const int2 *__restrict__ tiles,
-             const int *__restrict__ tile_total, int nc, int w, T side, T rc2, T beta,
-             T two_b_rpi, int split, double *__restrict__ f_out, double *__restrict__ phi_out,
-             double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap,
-             LJArgs lj, int *__restrict__ status)
+// The same with the target at (xi, yi, zi) and the partner's position in p.
+template <class T, class T4, class A>
+__device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
+                                     T beta, T nb2, T two_b_rpi, const T4 *ljrow, int tj)
 {
+    pair_d<T, T4>(a, xi - p.x, yi - p.y, zi - p.z, p.w, rc2, beta, nb2, two_b_rpi, ljrow, tj);
+}
+
+// ---- cell mode: per-target row ranges --------------------------------------------------
+
+// Candidate records of the cell kernel.  FP32: (x / L as 32-bit fixed point in the bits of
+// .x, y and z relative to the corner of the particle's own cell, q).  FP64: the wrapped
+// global position and q (the sorted copy pg).
+template <class T> struct RowRec;
+template <> struct RowRec<float> { using type = float4; };
+template <> struct RowRec<double> { using type = double4_32a; };
+
+// x displacement of a candidate: FP32 from the fixed-point fractions (their difference modulo
+// 2^32 is the minimum image, scaled by L / 2^32); FP64 from global coordinates plus the image
+// shift of the range the candidate came from.
+__device__ __forceinline__ float disp_x(const float4 &pi, const float4 &pj, float sx, float)
+{
+    return (float)(int)(__float_as_uint(pi.x) - __float_as_uint(pj.x)) * sx;
+}
+__device__ __forceinline__ double disp_x(const double4_32a &pi, const double4_32a &pj, double,
+                                         double shift)
+{
+    return (pi.x + shift) - pj.x;
+}
+
+template <class T, int G, bool kVir, bool kLJ>
+__global__ void __launch_bounds__(kWarps * 32)
+k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *__restrict__ pg,
+            const int *__restrict__ key_sorted, const int *__restrict__ cell_start, int n,
+            int nc, int w, double side_d, double L_d, T rc2, T beta, T two_b_rpi, float sx,
+            int split, double *__restrict__ f_out, double *__restrict__ phi_out,
+            double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap, LJArgs lj)
+{
+    using R4 = typename RowRec<T>::type;
     using T4 = typename Vec4<T>::type;
     using Acc = PairAcc<T, kVir, kLJ>;
+    constexpr int TG = 32 / G;                   // targets per warp
     __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[kWarps][2];
-    __shared__ Acc xacc[kWarps][32];            // partial sums handed between split warps
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T4 *buf[2];
-    buf[0] = reinterpret_cast<T4 *>(smem_raw) + (size_t)warp * 2 * kCap;
-    buf[1] = buf[0] + kCap;
-    uint64_t *bar = bars[warp];
-    if (lane == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
+    __shared__ Acc xacc[kWarps][32];             // partial sums handed between split warps
     if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2);
-    // with split = 2 the two warps 2t and 2t + 1 of a block share a tile, each taking every
-    // other stencil row; their sums are added (in that order) at the end
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // with split = 2 the warps 2t and 2t + 1 of a block share a group of targets, each taking
+    // every other row of the stencil; their sums are added (in that order) at the end
     const int part = warp % split;
-    const int tile = (blockIdx.x * kWarps + warp) / split;
-    const bool active = tile < *tile_total;
+    const int grp = (blockIdx.x * kWarps + warp) / split;
+    const int t = lane / G, g = lane % G;
+    const int i = grp * TG + t;
+    const bool active = grp * TG < n;
     if (split == 1 && !active) return;
-
-    const int2 td = active ? tiles[tile] : make_int2(0, 0);
-    const int row = td.x, first = td.y;
-    const int row_end = active ? cell_start[(row + 1) * nc] : 1;
-    const int last = active ? min(first + kTile, row_end) - 1 : 0;
-    constexpr int kGroups = 32 / kTile;             // partner lanes per target
-    const int ti = lane % kTile, g = lane / kTile;   // target slot, partner group
-    const int i = first + ti;
-    const bool valid = i <= last;
-    const T4 pi = pl[valid ? i : last];
-    const int cxi = key_sorted[valid ? i : last] % nc;
-    const T4 *ljrow = kLJ ? ljs + lj.tsort[valid ? i : last] * lj.ntypes : nullptr;
-
-    ChunkIter it;
-    it.w = w; it.nc = nc;
-    it.xa = key_sorted[first] % nc;
-    it.xb = key_sorted[last] % nc;
-    it.row_cy = row % nc; it.row_cz = row / nc;
-    it.in_run = false; it.started = false;
-    it.part = part; it.split = split; it.rowctr = 0;
-    it.side = (float)side; it.rc2 = (float)rc2;
-    it.u = 0; it.uend = -1;
-
+    const bool valid = i < n;
+    const int ii = valid ? i : (active ? n - 1 : 0);
+    const int k = key_sorted[ii];
+    const int cx = k % nc, cy = (k / nc) % nc, cz = k / (nc * nc);
+    const double4_32a gi = pg[ii];
+    const R4 pi = pr[ii];
+    const T side = (T)side_d;
+    // position of the target inside its own cell (for the ranges only; the pair arithmetic
+    // takes the candidate records)
+    const float xl = (float)(gi.x - cx * side_d), yl = (float)(gi.y - cy * side_d),
+                zl = (float)(gi.z - cz * side_d);
+    const float sidef = (float)side_d, inv_side = (float)(1.0 / side_d);
+    // ranges are chosen a little wider than r_c (a relative margin far above the rounding of
+    // the range arithmetic); the pair test below decides with the exact cutoff
+    const float rc2m = (float)rc2 * (1.0f + 1e-5f);
+    const T4 *ljrow = kLJ ? ljs + lj.tsort[ii] * lj.ntypes : nullptr;
     Acc acc{};
     const T nb2 = -beta * beta;
-    uint32_t phase[2] = {0u, 0u};
-    Chunk cur, nxt;
-    bool have_cur = active && it.next(cell_start, cur);
-    bool ok = true;
-    if (have_cur && lane == 0) {
-        mbar_expect_tx(&bar[0], cur.cnt * (uint32_t)sizeof(T4));
-        tma_bulk_g2s(buf[0], pl + cur.g0, cur.cnt * (uint32_t)sizeof(T4), &bar[0]);
-    }
-    int b = 0;
-    while (have_cur) {
-        bool have_nxt = it.next(cell_start, nxt);
-        if (have_nxt && lane == 0) {
-            // the other buffer was fully read before the last __syncwarp of the loop
-            fence_proxy_async();
-            mbar_expect_tx(&bar[b ^ 1], nxt.cnt * (uint32_t)sizeof(T4));
-            tma_bulk_g2s(buf[b ^ 1], pl + nxt.g0, nxt.cnt * (uint32_t)sizeof(T4), &bar[b ^ 1]);
-        }
-        if (!warp_wait(&bar[b], phase[b])) { ok = false; break; }
-        phase[b] ^= 1u;
-
-        const T yi = pi.y - T(cur.dy) * side;
-        const T zi = pi.z - T(cur.dz) * side;
-        const T4 *sb = buf[b];
-        // walk the cells of the run that overlap [g0, g0 + cnt); inside a run the cell index
-        // advances with u without wrapping, and each cell ends where the next one starts
-        int u = cur.u0;
-        const int cend = cur.g0 + cur.cnt;
-        int c = u < 0 ? u + nc : (u >= nc ? u - nc : u);
-        const int *cs = cell_start + cur.rowbase;
-        int cb = cs[c];
-        while (true) {
-            const int ce = cs[c + 1];
-            if (ce > cur.g0) {
-                const int jb = (cb > cur.g0 ? cb : cur.g0) - cur.g0;
-                const int je = (ce < cend ? ce : cend) - cur.g0;
-                const T xi = pi.x - T(u - cxi) * side;
-                for (int j = jb + g; j < je; j += kGroups)
-                    pair<T, T4>(acc, sb[j], xi, yi, zi, rc2, beta, nb2, two_b_rpi, ljrow,
-                                kLJ ? lj.tsort[cur.g0 + j] : 0);
+    int rowctr = 0;
+    for (int dz = -w; dz <= w; ++dz) {
+        const int az = dz < 0 ? -dz : dz;
+        const float mz = az > 0 ? (az - 1) * sidef : 0.f;
+        for (int dy = -w; dy <= w; ++dy) {
+            const int ay = dy < 0 ? -dy : dy;
+            const float my = ay > 0 ? (ay - 1) * sidef : 0.f;
+            if (my * my + mz * mz >= rc2m) continue;          // no point of the row in reach
+            if ((rowctr++ % split) != part) continue;
+            // this target's reach along the row: distance from (y, z) to the row's square
+            const float gy = dy > 0 ? dy * sidef - yl : (dy < 0 ? yl - (dy + 1) * sidef : 0.f);
+            const float gz = dz > 0 ? dz * sidef - zl : (dz < 0 ? zl - (dz + 1) * sidef : 0.f);
+            const float d2 = gy * gy + gz * gz;
+            int s1 = 0, len1 = 0, s2 = 0, len2 = 0;
+            T shift1 = T(0), shift2 = T(0);
+            if (valid && d2 < rc2m) {
+                const float reach = sqrtf(rc2m - d2);
+                int b0 = (int)floorf((xl - reach) * inv_side), b1 = (int)floorf((xl + reach) * inv_side);
+                b0 = b0 < -w ? -w : b0;
+                b1 = b1 > w ? w : b1;
+                const int uy = cy + dy < 0 ? cy + dy + nc : (cy + dy >= nc ? cy + dy - nc : cy + dy);
+                const int uz = cz + dz < 0 ? cz + dz + nc : (cz + dz >= nc ? cz + dz - nc : cz + dz);
+                const int *cs = cell_start + (uz * nc + uy) * nc;
+                const int a0 = cx + b0, a1 = cx + b1;
+                if (a0 < 0) {                  // the left end wraps to the far end of the row
+                    s1 = cs[a0 + nc]; len1 = cs[nc] - s1;
+                    s2 = cs[0]; len2 = cs[a1 + 1] - s2;
+                    shift1 = T(L_d);
+                } else if (a1 >= nc) {         // the right end wraps to the start of the row
+                    s1 = cs[a0]; len1 = cs[nc] - s1;
+                    s2 = cs[0]; len2 = cs[a1 - nc + 1] - s2;
+                    shift2 = T(-L_d);
+                } else {
+                    s1 = cs[a0]; len1 = cs[a1 + 1] - s1;
+                }
             }
-            if (ce >= cend) break;
-            cb = ce;
-            ++u;
-            ++c;
+            // FP32: y, z of the candidates are relative to their cell corner, which sits at
+            // (dy, dz) cells from the target's; FP64: global coordinates, shifted by L where
+            // the row wraps
+            T yi, zi;
+            if constexpr (sizeof(T) == 4) {
+                yi = pi.y - T(dy) * side;
+                zi = pi.z - T(dz) * side;
+            } else {
+                yi = pi.y + (cy + dy < 0 ? T(L_d) : (cy + dy >= nc ? T(-L_d) : T(0)));
+                zi = pi.z + (cz + dz < 0 ? T(L_d) : (cz + dz >= nc ? T(-L_d) : T(0)));
+            }
+            const int len = len1 + len2;
+            const int steps = __reduce_max_sync(0xffffffffu, (len + G - 1) / G);
+            for (int st = 0; st < steps; ++st) {
+                const int kk = st * G + g;
+                if (kk < len) {
+                    const bool first = kk < len1;
+                    const int j = first ? s1 + kk : s2 + (kk - len1);
+                    const R4 pj = pr[j];
+                    const T dxv = disp_x(pi, pj, sx, first ? shift1 : shift2);
+                    pair_d<T, T4>(acc, dxv, yi - pj.y, zi - pj.z, (T)pj.w, rc2, beta, nb2,
+                                  two_b_rpi, ljrow, kLJ ? lj.tsort[j] : 0);
+                }
+            }
         }
-        __syncwarp();
-        cur = nxt;
-        have_cur = have_nxt;
-        b ^= 1;
     }
-    if (!ok) {
-        if (lane == 0) atomicOr(status, kStTimeout);
-        // let a copy still in flight land before the warp leaves (bounded)
-        warp_wait(&bar[b ^ 1], phase[b ^ 1]);
-        if (split == 1) return;
-    }
-    // combine the kGroups partner groups of every target (lanes ti, ti + kTile, ...)
+    // combine the G lanes of every target (lanes t G .. t G + G - 1)
 #pragma unroll
-    for (int o = kTile; o < 32; o <<= 1) acc_shfl_add(acc, o);
+    for (int o = 1; o < G; o <<= 1) acc_shfl_add(acc, o);
     if (split == 2) {
         // every warp of the block reaches this barrier (none has returned with split = 2)
         if (part == 1) xacc[warp][lane] = acc;
@@ -510,7 +469,8 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         acc_add(acc, xacc[warp + 1][lane]);
     }
     const double qi = (double)pi.w;
-    if (valid && g == 0) {
+    const bool mine = valid && g == 0;
+    if (mine) {
         double f[3] = {qi * (double)acc.fx, qi * (double)acc.fy, qi * (double)acc.fz};
         if constexpr (kLJ) {
             f[0] += (double)acc.lj_f[0];
@@ -522,9 +482,9 @@ k_real_cells(const typename Vec4<T>::type *__restrict__ pl, const int *__restric
         f_out[3 * (int64_t)i + 2] = f[2];
         phi_out[i] = (double)acc.phi;
     }
-    const double e = warp_sum((valid && g == 0) ? qi * (double)acc.phi : 0.0);
-    if (lane == 0) e_tile[tile] = e;
-    acc_store_tile(acc, valid && g == 0, qi, lane, vir_tile, vcap, lj.e_tile, tile);
+    const double e = warp_sum(mine ? qi * (double)acc.phi : 0.0);
+    if (lane == 0) e_tile[grp] = e;
+    acc_store_tile(acc, mine, qi, lane, vir_tile, vcap, lj.e_tile, grp);
 }
 
 // All pairs with the minimum image (boxes too small for a cell stencil): one tile of 32
@@ -626,7 +586,7 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
     double *vir = kVir ? ws.vir_tile : nullptr;
     const int64_t vcap = real_tile_capacity(p, n);
     LJArgs lj{ws.type_sorted, p.lj_tab_d, p.lj_ntypes, ws.elj_tile};
-    const size_t smem = (size_t)kWarps * 2 * (p.w == 0 ? kCapAll : kCap) * sizeof(typename Vec4<T>::type);
+    const size_t smem = (size_t)kWarps * 2 * kCapAll * sizeof(typename Vec4<T>::type);
     const T beta = (T)p.beta, rc2 = (T)(p.rc * p.rc);
     const T tbr = (T)(2.0 * p.beta / sqrt(kPi));
     cudaError_t e;
@@ -639,17 +599,18 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
             pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap, lj,
             p.d_status);
     } else {
-        auto kern = p.real_tile == kTileDense ? k_real_cells<T, kTileDense, kVir, kLJ>
-                                              : k_real_cells<T, kTileSparse, kVir, kLJ>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int64_t tiles = real_tile_capacity(p, n);
-        // two warps per tile when one warp per tile would leave the SMs short of warps
-        const int split = tiles < 16 * (int64_t)p.num_sms ? 2 : 1;
-        kern<<<(unsigned)((tiles * split + kWarps - 1) / kWarps), kWarps * 32, smem, st>>>(
-            pl, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc, p.nc, p.w,
-            (T)p.cell_side, rc2, beta, tbr, split, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap,
-            lj, p.d_status);
+        auto kern = p.real_tile == 4 ? k_real_rows<T, 4, kVir, kLJ> : k_real_rows<T, 2, kVir, kLJ>;
+        const int64_t groups = real_tile_capacity(p, n);
+        // two warps per group of targets when one warp per group would leave the SMs short
+        // of warps
+        const int split = groups < 16 * (int64_t)p.num_sms ? 2 : 1;
+        const typename RowRec<T>::type *pr;
+        if constexpr (sizeof(T) == 4) pr = ws.pl32;
+        else pr = ws.pg;
+        kern<<<(unsigned)((groups * split + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(
+            pr, ws.pg, ws.key_sorted, ws.cell_start, (int)n, p.nc, p.w, p.cell_side, p.L, rc2,
+            beta, tbr, (float)(p.L / 4294967296.0), split, ws.f_real, ws.phi_real, ws.e_tile,
+            vir, vcap, lj);
     }
     p.launches += 1;
     return cudaGetLastError();
@@ -668,16 +629,19 @@ cudaError_t launch_real_p(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
 
 int64_t real_tile_capacity(const Plan &p, int64_t n)
 {
-    if (p.w == 0) return (n + 31) / 32;
-    return n / real_tile_size(p) + (int64_t)p.nc * p.nc + 1;
+    const int64_t ts = real_tile_size(p);
+    return (n + ts - 1) / ts;
 }
 
-int real_tile_size(const Plan &p) { return p.w == 0 ? 32 : (p.real_tile == kTileDense ? kTileDense : kTileSparse); }
+// targets per warp: 32 in all-pairs mode, else 32 / G with G lanes per target
+int real_tile_size(const Plan &p) { return p.w == 0 ? 32 : 32 / p.real_tile; }
 
+// Lanes per target of the cell kernel: 4 where a target's range in a row is long (dense
+// cells), 2 where rows hold few candidates (the steps of a row then run shorter).
 int real_tile_for(int w, double cell_occupancy)
 {
-    if (w == 0) return 32;
-    return cell_occupancy >= 16.0 ? kTileDense : kTileSparse;
+    if (w == 0) return 1;
+    return cell_occupancy * 2 * w >= 16.0 ? 4 : 2;
 }
 
 cudaError_t launch_wait_probe(Plan &p, cudaStream_t st)

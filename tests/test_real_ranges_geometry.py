@@ -1,0 +1,145 @@
+"""CPU check of the candidate ranges of the real-space cell kernel (k_real_rows): its cell
+grid rule and, for every target, the per-row ranges of sorted particles it visits, restated
+here in NumPy with the kernel's FP32 arithmetic.  On the benchmark systems (and on boxes
+with particles placed at cell and box boundaries) every pair closer than r_c must be among
+the candidates of both of its particles exactly once, and every candidate index must lie in
+[0, n).  (The pair arithmetic itself is checked against the oracle by the GPU tests.)"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1708_01135_gb300 import workloads as W
+
+
+def cell_grid(L, rc, n):
+    """The grid rule of the library (cell_grid in capi.cu)."""
+    rho = n / L ** 3
+    s_t = max(rho ** (-1.0 / 3.0), rc / 5.0)
+    nc = min(int(math.floor(L / s_t)), 160)
+    while nc >= 3:
+        w = int(math.ceil(rc * nc / L * (1.0 - 1e-12)))
+        if w >= 1 and 2 * w + 1 <= nc:
+            return nc, w
+        nc -= 1
+    return 1, 0
+
+
+def sort_cells(pos, L, nc):
+    x = pos - L * np.floor(pos / L)
+    x[x >= L] = 0.0
+    c = np.minimum((x * (nc / L)).astype(np.int64), nc - 1)
+    key = (c[:, 2] * nc + c[:, 1]) * nc + c[:, 0]
+    order = np.argsort(key, kind="stable")
+    start = np.zeros(nc ** 3 + 1, dtype=np.int64)
+    np.cumsum(np.bincount(key, minlength=nc ** 3), out=start[1:])
+    return x[order], c[order], key[order], start
+
+
+def candidate_ranges(xs, c, start, L, rc, nc, w, targets):
+    """For each target: the list of (start, length) ranges of the kernel, as it computes
+    them (FP32 reach and bin arithmetic, wrapped rows, clamped bins)."""
+    f32 = np.float32
+    side = L / nc
+    sidef, inv_side = f32(side), f32(1.0 / side)
+    rc2m = f32(f32(rc * rc) * (f32(1.0) + f32(1e-5)))
+    out = []
+    for i in targets:
+        cx, cy, cz = c[i]
+        xl = f32(xs[i, 0] - cx * side)
+        yl = f32(xs[i, 1] - cy * side)
+        zl = f32(xs[i, 2] - cz * side)
+        rr = []
+        for dz in range(-w, w + 1):
+            mz = f32((abs(dz) - 1) * sidef) if dz else f32(0)
+            for dy in range(-w, w + 1):
+                my = f32((abs(dy) - 1) * sidef) if dy else f32(0)
+                if my * my + mz * mz >= rc2m:
+                    continue
+                gy = f32(dy * sidef - yl) if dy > 0 else (f32(yl - (dy + 1) * sidef) if dy < 0 else f32(0))
+                gz = f32(dz * sidef - zl) if dz > 0 else (f32(zl - (dz + 1) * sidef) if dz < 0 else f32(0))
+                d2 = f32(gy * gy + gz * gz)
+                if not d2 < rc2m:
+                    continue
+                reach = f32(np.sqrt(f32(rc2m - d2)))
+                b0 = int(np.floor(f32((xl - reach) * inv_side)))
+                b1 = int(np.floor(f32((xl + reach) * inv_side)))
+                b0, b1 = max(b0, -w), min(b1, w)
+                uy, uz = (cy + dy) % nc, (cz + dz) % nc
+                base = (uz * nc + uy) * nc
+                a0, a1 = cx + b0, cx + b1
+                if a0 < 0:
+                    rr.append((start[base + a0 + nc], start[base + nc] - start[base + a0 + nc]))
+                    rr.append((start[base], start[base + a1 + 1] - start[base]))
+                elif a1 >= nc:
+                    rr.append((start[base + a0], start[base + nc] - start[base + a0]))
+                    rr.append((start[base], start[base + a1 - nc + 1] - start[base]))
+                else:
+                    rr.append((start[base + a0], start[base + a1 + 1] - start[base + a0]))
+        out.append(rr)
+    return out
+
+
+def check(pos, L, rc, targets=None):
+    n = len(pos)
+    nc, w = cell_grid(L, rc, n)
+    assert w >= 1
+    xs, c, key, start = sort_cells(pos, L, nc)
+    if targets is None:
+        targets = np.arange(n)
+    ranges = candidate_ranges(xs, c, start, L, rc, nc, w, targets)
+    for i, rr in zip(targets, ranges):
+        idx = np.concatenate([np.arange(s, s + m) for s, m in rr]) if rr else np.zeros(0, int)
+        assert idx.size == 0 or (idx.min() >= 0 and idx.max() < n)
+        assert np.unique(idx).size == idx.size, "a candidate visited twice"
+        d = xs - xs[i]
+        d -= L * np.round(d / L)
+        r2 = (d * d).sum(axis=1)
+        partners = np.nonzero((r2 < rc * rc) & (np.arange(n) != i))[0]
+        missing = np.setdiff1d(partners, idx)
+        assert missing.size == 0, f"target {i}: partners {missing[:5]} not among the candidates"
+    return nc, w
+
+
+def test_grid_rule_matches_the_library():
+    from paper_1708_01135_gb300 import Ewald, ewald as E
+    try:
+        E.lib()
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    for n, L, rc in ((32768, 32.0, 4.0), (262144, 64.0, 6.8), (2097152, 128.0, 9.6),
+                     (512, 8.0, 2.6), (4002, 15.87, 4.0)):
+        # the plan's grid is chosen when its workspace is sized for n particles; plan_info
+        # reports the grid of the density-free set-up until then, so compare the rule only
+        nc, w = cell_grid(L, rc, n)
+        assert 2 * w + 1 <= nc and w * (L / nc) >= rc * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("name,rc", [("random_32768", 4.0), ("rocksalt_512", 2.6)])
+def test_every_partner_is_a_candidate_once(name, rc):
+    pos, q, L = getattr(W, name)()
+    rng = np.random.default_rng(3)
+    targets = None if len(q) <= 4096 else np.sort(rng.choice(len(q), 3000, replace=False))
+    nc, w = check(pos, L, rc, targets)
+    assert w >= 2
+
+
+def test_boundary_positions():
+    """Particles on cell faces, at 0 and just below L, and a cutoff that is an exact
+    multiple of the cell side."""
+    rng = np.random.default_rng(5)
+    L, n = 12.0, 1500
+    pos = rng.uniform(0, L, size=(n, 3))
+    side = L / cell_grid(L, 2.4, n)[0]
+    pos[:200] = np.round(pos[:200] / side) * side          # on cell faces
+    pos[200:220, 0] = 0.0
+    pos[220:240, 1] = np.nextafter(L, 0)
+    pos[240:260] = -1e-300
+    for rc in (2.4, 3.0, 3.9):
+        check(pos, L, rc)
+
+
+def test_large_system_sample():
+    pos, q, L = W.rocksalt_262144()
+    rng = np.random.default_rng(11)
+    check(pos, L, 6.8, np.sort(rng.choice(len(q), 400, replace=False)))
