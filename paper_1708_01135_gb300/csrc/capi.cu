@@ -262,7 +262,7 @@ void free_workspace(Plan &p)
     graph_reset(p);
     Workspace &ws = p.ws;
     void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
-                    ws.pg, ws.pl64, ws.pl32, ws.pu,
+                    ws.tiles, ws.tile_count, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
                     ws.f_real, ws.f_recip, ws.e_tile, ws.qpart, ws.phi_real, ws.phi_recip,
                     ws.vir_tile, ws.vir_part, ws.type_sorted, ws.elj_tile};
     for (void *q : ptrs) pool_free(q, p.side_stream);
@@ -355,6 +355,9 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     EW_TRY(dmalloc(p, &ws.hist, sizeof(int) * (size_t)nb * p.ncells));
     EW_TRY(dmalloc(p, &ws.cell_start, sizeof(int) * (p.ncells + 1)));
     EW_TRY(dmalloc(p, &ws.cell_total, sizeof(int) * p.ncells));
+    EW_TRY(dmalloc(p, &ws.tiles, sizeof(int2) * tiles));
+    EW_TRY(dmalloc(p, &ws.tile_count, sizeof(int) * p.nc * p.nc));
+    EW_TRY(dmalloc(p, &ws.tile_off, sizeof(int) * (p.nc * p.nc + 1)));
     EW_TRY(dmalloc(p, &ws.pg, sizeof(double4_32a) * n));
     if (p.precision == EWALD_FP64) EW_TRY(dmalloc(p, &ws.pl64, sizeof(double4_32a) * n));
     else EW_TRY(dmalloc(p, &ws.pl32, sizeof(float4) * n));
@@ -535,10 +538,10 @@ size_t plan_footprint(const Plan &p, int64_t n)
     cell_grid(p.L, p.rc, n, nc, w);
     const size_t ncells = (size_t)nc * nc * nc;
     const int64_t ts = w == 0 ? 32 : 32 / real_tile_for(w, (double)n / ncells);
-    const int64_t tiles = (n + ts - 1) / ts;
+    const int64_t tiles = w == 0 ? (n + 31) / 32 : n / ts + (int64_t)nc * nc + 1;
     size_t b = 0;
     b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * ncells;
-    b += sizeof(int) * (2 * ncells + 1);
+    b += sizeof(int) * (2 * ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * ((size_t)nc * nc + 1);
     b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
     b += sizeof(double) * 8 * (size_t)n + sizeof(double) * 14 * tiles + sizeof(double) * 3 * ((n + 255) / 256);
     b += sizeof(int) * (size_t)n;

@@ -225,6 +225,28 @@ __global__ void k_pack(int64_t n, const double *__restrict__ pos, const double *
     }
 }
 
+// Tiles of up to `ts` consecutive sorted particles that never leave a row of cells (the
+// targets of one warp of the cell kernel share their row, so that the warp can stage one
+// union of candidate ranges per stencil row for all of them).
+__global__ void k_row_tiles(int nrows, int nc, int ts, const int *__restrict__ cell_start,
+                            int *__restrict__ tcount)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int cnt = cell_start[(r + 1) * nc] - cell_start[r * nc];
+    tcount[r] = (cnt + ts - 1) / ts;
+}
+
+__global__ void k_emit_tiles(int nrows, int nc, int ts, const int *__restrict__ cell_start,
+                             const int *__restrict__ toff, int2 *__restrict__ tiles)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int b = cell_start[r * nc];
+    int o = toff[r], e = toff[r + 1];
+    for (int t = o; t < e; ++t) tiles[t] = make_int2(r, b + ts * (t - o));
+}
+
 }  // namespace
 
 cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *q,
@@ -257,6 +279,16 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
                                                    need64 ? ws.pl64 : nullptr,
                                                    need64 ? nullptr : ws.pl32, ws.pu);
     p.launches += 5;
+    if (p.w > 0) {
+        const int nrows = p.nc * p.nc;
+        const int ts = real_tile_size(p);
+        k_row_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ts, ws.cell_start,
+                                                         ws.tile_count);
+        k_scan1<<<1, 1024, 0, st>>>(nrows, ws.tile_count, ws.tile_off);
+        k_emit_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ts, ws.cell_start,
+                                                          ws.tile_off, ws.tiles);
+        p.launches += 3;
+    }
     return cudaGetLastError();
 }
 

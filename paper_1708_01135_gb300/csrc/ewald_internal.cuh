@@ -55,6 +55,9 @@ struct Workspace {
     int *hist = nullptr;         // [nb * ncells] per-chunk cell counts -> offsets
     int *cell_start = nullptr;   // [ncells + 1]
     int *cell_total = nullptr;   // [ncells]
+    int2 *tiles = nullptr;       // [max tiles] (row, first slot) of the cell kernel's warps
+    int *tile_count = nullptr;   // [nrows] tiles per row
+    int *tile_off = nullptr;     // [nrows + 1] exclusive offsets; tile_off[nrows] = tiles
     // packed particles (sorted)
     double4_32a *pg = nullptr;       // wrapped global position + q (FP64)
     double4_32a *pl64 = nullptr;     // cell-local position + q (FP64, all-pairs mode)

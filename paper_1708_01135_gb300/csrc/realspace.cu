@@ -354,109 +354,275 @@ __device__ __forceinline__ double disp_x(const double4_32a &pi, const double4_32
     return (pi.x + shift) - pj.x;
 }
 
-template <class T, int G, bool kVir, bool kLJ>
-__global__ void __launch_bounds__(kWarps * 32)
-k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *__restrict__ pg,
-            const int *__restrict__ key_sorted, const int *__restrict__ cell_start, int n,
-            int nc, int w, double side_d, double L_d, T rc2, T beta, T two_b_rpi, float sx,
-            int split, double *__restrict__ f_out, double *__restrict__ phi_out,
-            double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap, LJArgs lj)
+// Staged union of the targets' ranges in one row: unwrapped cell bins [A0, A1] of the row,
+// laid out in shared memory in bin order as up to three contiguous runs of the sorted array:
+// part A, the bins below 0 (the far end of the row, wrapped), part B, the bins inside the
+// row, part C, the bins at or beyond nc (the start of the row, wrapped).
+struct RowUnion {
+    int sA, lenA, sB, lenB, sC, lenC;
+    __device__ int total() const { return lenA + lenB + lenC; }
+};
+
+// Offset in the staged union of the first particle of unwrapped bin b (A0 <= b <= A1 + 1).
+__device__ __forceinline__ int union_off(const RowUnion &u, const int *__restrict__ cs, int nc,
+                                         int b)
 {
-    using R4 = typename RowRec<T>::type;
-    using T4 = typename Vec4<T>::type;
-    using Acc = PairAcc<T, kVir, kLJ>;
-    constexpr int TG = 32 / G;                   // targets per warp
-    __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
-    __shared__ Acc xacc[kWarps][32];             // partial sums handed between split warps
-    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // with split = 2 the warps 2t and 2t + 1 of a block share a group of targets, each taking
-    // every other row of the stencil; their sums are added (in that order) at the end
-    const int part = warp % split;
-    const int grp = (blockIdx.x * kWarps + warp) / split;
-    const int t = lane / G, g = lane % G;
-    const int i = grp * TG + t;
-    const bool active = grp * TG < n;
-    if (split == 1 && !active) return;
-    const bool valid = i < n;
-    const int ii = valid ? i : (active ? n - 1 : 0);
-    const int k = key_sorted[ii];
-    const int cx = k % nc, cy = (k / nc) % nc, cz = k / (nc * nc);
-    const double4_32a gi = pg[ii];
-    const R4 pi = pr[ii];
-    const T side = (T)side_d;
-    // position of the target inside its own cell (for the ranges only; the pair arithmetic
-    // takes the candidate records)
-    const float xl = (float)(gi.x - cx * side_d), yl = (float)(gi.y - cy * side_d),
-                zl = (float)(gi.z - cz * side_d);
-    const float sidef = (float)side_d, inv_side = (float)(1.0 / side_d);
-    // ranges are chosen a little wider than r_c (a relative margin far above the rounding of
-    // the range arithmetic); the pair test below decides with the exact cutoff
-    const float rc2m = (float)rc2 * (1.0f + 1e-5f);
-    const T4 *ljrow = kLJ ? ljs + lj.tsort[ii] * lj.ntypes : nullptr;
-    Acc acc{};
-    const T nb2 = -beta * beta;
-    int rowctr = 0;
-    for (int dz = -w; dz <= w; ++dz) {
-        const int az = dz < 0 ? -dz : dz;
-        const float mz = az > 0 ? (az - 1) * sidef : 0.f;
-        for (int dy = -w; dy <= w; ++dy) {
-            const int ay = dy < 0 ? -dy : dy;
-            const float my = ay > 0 ? (ay - 1) * sidef : 0.f;
+    if (b < 0) return cs[b + nc] - u.sA;
+    if (b < nc) return u.lenA + cs[b] - u.sB;
+    return u.lenA + u.lenB + cs[b - nc] - u.sC;
+}
+
+// One staged item: a chunk [c0, c0 + cnt) of the union of row (dy, dz), and this target's
+// range [off0, off1) in the union.
+struct RowItem {
+    int dy, dz;
+    RowUnion u;
+    int c0, cnt;
+    int off0, off1;
+};
+
+// Issue the bulk copies of an item into dst (lane 0 only): the parts of the union that the
+// chunk overlaps, one mbarrier for all of them.
+template <class R4>
+__device__ __forceinline__ void issue_item(const RowItem &it, const R4 *__restrict__ pr,
+                                           R4 *dst, uint64_t *bar)
+{
+    mbar_expect_tx(bar, it.cnt * (uint32_t)sizeof(R4));
+    const int e = it.c0 + it.cnt;
+    const int pb[3] = {0, it.u.lenA, it.u.lenA + it.u.lenB};
+    const int pe[3] = {it.u.lenA, it.u.lenA + it.u.lenB, it.u.total()};
+    const int ps[3] = {it.u.sA, it.u.sB, it.u.sC};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int lo = it.c0 > pb[k] ? it.c0 : pb[k];
+        const int hi = e < pe[k] ? e : pe[k];
+        if (hi > lo)
+            tma_bulk_g2s(dst + (lo - it.c0), pr + ps[k] + (lo - pb[k]),
+                         (uint32_t)(hi - lo) * (uint32_t)sizeof(R4), bar);
+    }
+}
+
+// Walks the rows of the stencil (and the chunks of each row's union) of one warp.
+struct RowWalk {
+    int w, nc, part, split;
+    int cx, cy, cz;             // this target's cell
+    float xl, yl, zl;           // this target's position inside its cell
+    float sidef, inv_side, rc2m;
+    bool valid;
+    const int *__restrict__ cell_start;
+    // position in the stencil
+    int dy, dz, rowctr;
+    bool started;
+    // the current row's union and this target's range, and the next chunk start
+    RowItem row;
+    int next_c0;
+    bool in_row;
+
+    // Next row with a non-empty union; false at the end of the stencil.
+    __device__ bool next_row()
+    {
+        while (true) {
+            if (!started) { started = true; dz = -w; dy = -w; }
+            else if (++dy > w) { dy = -w; if (++dz > w) return false; }
+            const int ay = dy < 0 ? -dy : dy, az = dz < 0 ? -dz : dz;
+            const float my = ay > 0 ? (ay - 1) * sidef : 0.f, mz = az > 0 ? (az - 1) * sidef : 0.f;
             if (my * my + mz * mz >= rc2m) continue;          // no point of the row in reach
             if ((rowctr++ % split) != part) continue;
             // this target's reach along the row: distance from (y, z) to the row's square
             const float gy = dy > 0 ? dy * sidef - yl : (dy < 0 ? yl - (dy + 1) * sidef : 0.f);
             const float gz = dz > 0 ? dz * sidef - zl : (dz < 0 ? zl - (dz + 1) * sidef : 0.f);
             const float d2 = gy * gy + gz * gz;
-            int s1 = 0, len1 = 0, s2 = 0, len2 = 0;
-            T shift1 = T(0), shift2 = T(0);
+            int a0 = 1 << 30, a1 = -(1 << 30);
             if (valid && d2 < rc2m) {
                 const float reach = sqrtf(rc2m - d2);
                 int b0 = (int)floorf((xl - reach) * inv_side), b1 = (int)floorf((xl + reach) * inv_side);
                 b0 = b0 < -w ? -w : b0;
                 b1 = b1 > w ? w : b1;
-                const int uy = cy + dy < 0 ? cy + dy + nc : (cy + dy >= nc ? cy + dy - nc : cy + dy);
-                const int uz = cz + dz < 0 ? cz + dz + nc : (cz + dz >= nc ? cz + dz - nc : cz + dz);
-                const int *cs = cell_start + (uz * nc + uy) * nc;
-                const int a0 = cx + b0, a1 = cx + b1;
-                if (a0 < 0) {                  // the left end wraps to the far end of the row
-                    s1 = cs[a0 + nc]; len1 = cs[nc] - s1;
-                    s2 = cs[0]; len2 = cs[a1 + 1] - s2;
-                    shift1 = T(L_d);
-                } else if (a1 >= nc) {         // the right end wraps to the start of the row
-                    s1 = cs[a0]; len1 = cs[nc] - s1;
-                    s2 = cs[0]; len2 = cs[a1 - nc + 1] - s2;
-                    shift2 = T(-L_d);
-                } else {
-                    s1 = cs[a0]; len1 = cs[a1 + 1] - s1;
-                }
+                a0 = cx + b0;
+                a1 = cx + b1;
             }
-            // FP32: y, z of the candidates are relative to their cell corner, which sits at
-            // (dy, dz) cells from the target's; FP64: global coordinates, shifted by L where
-            // the row wraps
-            T yi, zi;
-            if constexpr (sizeof(T) == 4) {
-                yi = pi.y - T(dy) * side;
-                zi = pi.z - T(dz) * side;
+            const int A0 = __reduce_min_sync(0xffffffffu, a0);
+            const int A1 = __reduce_max_sync(0xffffffffu, a1);
+            if (A0 > A1) continue;                              // no target reaches the row
+            const int uy = cy + dy < 0 ? cy + dy + nc : (cy + dy >= nc ? cy + dy - nc : cy + dy);
+            const int uz = cz + dz < 0 ? cz + dz + nc : (cz + dz >= nc ? cz + dz - nc : cz + dz);
+            const int *cs = cell_start + (uz * nc + uy) * nc;
+            RowUnion &u = row.u;
+            u.sA = 0; u.lenA = 0; u.lenC = 0;
+            u.sC = cs[0];
+            if (A0 < 0) { u.sA = cs[A0 + nc]; u.lenA = cs[nc] - u.sA; }
+            const int b0 = A0 > 0 ? A0 : 0, b1 = A1 < nc - 1 ? A1 : nc - 1;
+            u.sB = cs[b0];
+            u.lenB = cs[b1 + 1] - u.sB;
+            if (A1 >= nc) u.lenC = cs[A1 - nc + 1] - u.sC;
+            if (u.total() == 0) continue;
+            row.dy = dy;
+            row.dz = dz;
+            if (a0 <= a1) {
+                row.off0 = union_off(u, cs, nc, a0);
+                row.off1 = union_off(u, cs, nc, a1 + 1);
             } else {
-                yi = pi.y + (cy + dy < 0 ? T(L_d) : (cy + dy >= nc ? T(-L_d) : T(0)));
-                zi = pi.z + (cz + dz < 0 ? T(L_d) : (cz + dz >= nc ? T(-L_d) : T(0)));
+                row.off0 = row.off1 = 0;
             }
-            const int len = len1 + len2;
-            const int steps = __reduce_max_sync(0xffffffffu, (len + G - 1) / G);
-            for (int st = 0; st < steps; ++st) {
-                const int kk = st * G + g;
-                if (kk < len) {
-                    const bool first = kk < len1;
-                    const int j = first ? s1 + kk : s2 + (kk - len1);
-                    const R4 pj = pr[j];
-                    const T dxv = disp_x(pi, pj, sx, first ? shift1 : shift2);
-                    pair_d<T, T4>(acc, dxv, yi - pj.y, zi - pj.z, (T)pj.w, rc2, beta, nb2,
-                                  two_b_rpi, ljrow, kLJ ? lj.tsort[j] : 0);
+            return true;
+        }
+    }
+
+    template <int kCapR>
+    __device__ bool next(RowItem &it)
+    {
+        if (!in_row || next_c0 >= row.u.total()) {
+            if (!next_row()) return false;
+            in_row = true;
+            next_c0 = 0;
+        }
+        it = row;
+        it.c0 = next_c0;
+        const int rest = row.u.total() - next_c0;
+        it.cnt = rest < kCapR ? rest : kCapR;
+        next_c0 += it.cnt;
+        return true;
+    }
+};
+
+template <class T, int G, bool kVir, bool kLJ>
+__global__ void __launch_bounds__(kWarps * 32)
+k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *__restrict__ pg,
+            const int *__restrict__ key_sorted, const int *__restrict__ cell_start,
+            const int2 *__restrict__ tiles, const int *__restrict__ tile_total, int n,
+            int nc, int w, double side_d, double L_d, T rc2, T beta, T two_b_rpi, float sx,
+            int split, double *__restrict__ f_out, double *__restrict__ phi_out,
+            double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap, LJArgs lj,
+            int *__restrict__ status)
+{
+    using R4 = typename RowRec<T>::type;
+    using T4 = typename Vec4<T>::type;
+    using Acc = PairAcc<T, kVir, kLJ>;
+    constexpr int TG = 32 / G;                   // targets per warp
+    constexpr int kCapR = 4096 / (int)sizeof(R4);  // records per staging buffer (4 KB)
+    __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
+    __shared__ Acc xacc[kWarps][32];             // partial sums handed between split warps
+    __shared__ __align__(128) R4 stage[kWarps][2][kCapR];
+    __shared__ __align__(8) uint64_t bars[kWarps][2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *bar = bars[warp];
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2);
+    // with split = 2 the warps 2t and 2t + 1 of a block share a group of targets, each taking
+    // every other row of the stencil; their sums are added (in that order) at the end
+    const int part = warp % split;
+    const int grp = (blockIdx.x * kWarps + warp) / split;   // tile of this warp
+    const int t = lane / G, g = lane % G;
+    const bool active = grp < *tile_total;
+    if (split == 1 && !active) return;
+    // the tile's targets: up to TG consecutive sorted particles of one row of cells
+    const int2 td = active ? tiles[grp] : make_int2(0, 0);
+    const int row_end = active ? cell_start[(td.x + 1) * nc] : 1;
+    const int i = td.y + t;
+    const bool valid = active && i < row_end;
+    const int ii = valid ? i : (active ? td.y : 0);
+    const int k = key_sorted[ii];
+    const int cx = k % nc, cy = (k / nc) % nc, cz = k / (nc * nc);
+    const double4_32a gi = pg[ii];
+    const R4 pi = pr[ii];
+    const T side = (T)side_d;
+    const T4 *ljrow = kLJ ? ljs + lj.tsort[ii] * lj.ntypes : nullptr;
+
+    RowWalk wk;
+    wk.w = w; wk.nc = nc; wk.part = part; wk.split = split;
+    wk.cx = cx; wk.cy = cy; wk.cz = cz;
+    // position of the target inside its own cell (for the ranges only); ranges are chosen a
+    // little wider than r_c (a relative margin far above the rounding of the range
+    // arithmetic), and the pair test decides with the exact cutoff
+    wk.xl = (float)(gi.x - cx * side_d);
+    wk.yl = (float)(gi.y - cy * side_d);
+    wk.zl = (float)(gi.z - cz * side_d);
+    wk.sidef = (float)side_d;
+    wk.inv_side = (float)(1.0 / side_d);
+    wk.rc2m = (float)rc2 * (1.0f + 1e-5f);
+    wk.valid = valid;
+    wk.cell_start = cell_start;
+    wk.rowctr = 0;
+    wk.started = false;
+    wk.in_row = false;
+    wk.next_c0 = 0;
+
+    Acc acc{};
+    const T nb2 = -beta * beta;
+    uint32_t phase[2] = {0u, 0u};
+    RowItem cur, nxt;
+    bool have_cur = active && wk.next<kCapR>(cur);
+    bool ok = true;
+    if (have_cur && lane == 0) issue_item(cur, pr, stage[warp][0], &bar[0]);
+    int b = 0;
+    while (have_cur) {
+        const bool have_nxt = wk.next<kCapR>(nxt);
+        if (have_nxt && lane == 0) {
+            // the other buffer was fully read before the last __syncwarp of the loop
+            fence_proxy_async();
+            issue_item(nxt, pr, stage[warp][b ^ 1], &bar[b ^ 1]);
+        }
+        if (!warp_wait(&bar[b], phase[b])) { ok = false; break; }
+        phase[b] ^= 1u;
+        // FP32: y, z of the candidates are relative to their cell corner, which sits at
+        // (dy, dz) cells from the target's; FP64: global coordinates, shifted by L where the
+        // row wraps
+        T yi, zi;
+        if constexpr (sizeof(T) == 4) {
+            yi = pi.y - T(cur.dy) * side;
+            zi = pi.z - T(cur.dz) * side;
+        } else {
+            yi = pi.y + (cy + cur.dy < 0 ? T(L_d) : (cy + cur.dy >= nc ? T(-L_d) : T(0)));
+            zi = pi.z + (cz + cur.dz < 0 ? T(L_d) : (cz + cur.dz >= nc ? T(-L_d) : T(0)));
+        }
+        // this target's part of the chunk, in buffer indices
+        const int lo = (cur.off0 > cur.c0 ? cur.off0 : cur.c0) - cur.c0;
+        const int hi = (cur.off1 < cur.c0 + cur.cnt ? cur.off1 : cur.c0 + cur.cnt) - cur.c0;
+        const int len = hi > lo ? hi - lo : 0;
+        const int steps = __reduce_max_sync(0xffffffffu, (len + G - 1) / G);
+        const R4 *sb = stage[warp][b];
+        for (int st = 0; st < steps; ++st) {
+            const int kk = st * G + g;
+            if (kk < len) {
+                const int j = lo + kk;
+                const R4 pj = sb[j];
+                T dxv;
+                int tj = 0;
+                if constexpr (sizeof(T) == 4) {
+                    dxv = disp_x(pi, pj, sx, 0.f);
+                } else {
+                    // image shift of the candidate's part of the union
+                    const int q = cur.c0 + j;
+                    const T shift = q < cur.u.lenA ? T(L_d)
+                                  : (q >= cur.u.lenA + cur.u.lenB ? T(-L_d) : T(0));
+                    dxv = disp_x(pi, pj, 0.0, shift);
                 }
+                if constexpr (kLJ) {
+                    const int q = cur.c0 + j;
+                    const int gidx = q < cur.u.lenA ? cur.u.sA + q
+                                   : (q < cur.u.lenA + cur.u.lenB ? cur.u.sB + (q - cur.u.lenA)
+                                                                  : cur.u.sC + (q - cur.u.lenA - cur.u.lenB));
+                    tj = lj.tsort[gidx];
+                }
+                pair_d<T, T4>(acc, dxv, yi - pj.y, zi - pj.z, (T)pj.w, rc2, beta, nb2,
+                              two_b_rpi, ljrow, tj);
             }
         }
+        __syncwarp();
+        cur = nxt;
+        have_cur = have_nxt;
+        b ^= 1;
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(status, kStTimeout);
+        // let a copy still in flight land before the warp leaves (bounded)
+        warp_wait(&bar[b ^ 1], phase[b ^ 1]);
+        if (split == 1) return;
     }
     // combine the G lanes of every target (lanes t G .. t G + G - 1)
 #pragma unroll
@@ -608,9 +774,10 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         if constexpr (sizeof(T) == 4) pr = ws.pl32;
         else pr = ws.pg;
         kern<<<(unsigned)((groups * split + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(
-            pr, ws.pg, ws.key_sorted, ws.cell_start, (int)n, p.nc, p.w, p.cell_side, p.L, rc2,
+            pr, ws.pg, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc,
+            (int)n, p.nc, p.w, p.cell_side, p.L, rc2,
             beta, tbr, (float)(p.L / 4294967296.0), split, ws.f_real, ws.phi_real, ws.e_tile,
-            vir, vcap, lj);
+            vir, vcap, lj, p.d_status);
     }
     p.launches += 1;
     return cudaGetLastError();
@@ -629,8 +796,9 @@ cudaError_t launch_real_p(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
 
 int64_t real_tile_capacity(const Plan &p, int64_t n)
 {
-    const int64_t ts = real_tile_size(p);
-    return (n + ts - 1) / ts;
+    if (p.w == 0) return (n + 31) / 32;
+    // tiles never leave a row: at most one ragged tile per row
+    return n / real_tile_size(p) + (int64_t)p.nc * p.nc + 1;
 }
 
 // targets per warp: 32 in all-pairs mode, else 32 / G with G lanes per target

@@ -34,11 +34,12 @@ def test_keys_and_stable_order_bit_exact(n, L, rc, seed):
     if n % 2:
         q[-1] = 0.0
     with Ewald(L, 1.0, rc, 4, "fp64") as ew:
-        nc = ew.info()["cells_per_side"]
         F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         e = torch.empty(4, dtype=torch.float64, device="cuda")
         ew.compute_async(dev(pos), dev(q), F, e, parts=PART_REAL)
         ew.status()
+        # the grid is chosen for the particle count when the workspace is first sized
+        nc = ew.info()["cells_per_side"]
         key, perm = ew.cell_sort(n)
     mkey, mperm = _model(pos, L, nc)
     assert np.array_equal(key, mkey)

@@ -1,9 +1,12 @@
 """CPU check of the candidate ranges of the real-space cell kernel (k_real_rows): its cell
-grid rule and, for every target, the per-row ranges of sorted particles it visits, restated
-here in NumPy with the kernel's FP32 arithmetic.  On the benchmark systems (and on boxes
-with particles placed at cell and box boundaries) every pair closer than r_c must be among
-the candidates of both of its particles exactly once, and every candidate index must lie in
-[0, n).  (The pair arithmetic itself is checked against the oracle by the GPU tests.)"""
+grid rule, for every target the per-row ranges of sorted particles it visits, and the
+staged union of a warp's ranges in each row (parts A, B, C of the row in bin order, each
+target's [off0, off1) inside it), restated here in NumPy with the kernel's FP32 arithmetic.
+On the benchmark systems (and on boxes with particles placed at cell and box boundaries)
+every pair closer than r_c must be among the candidates of both of its particles exactly
+once, every index must lie in [0, n), and the union layout must give each target exactly
+its own ranges.  (The pair arithmetic itself is checked against the oracle by the GPU
+tests.)"""
 import math
 
 import numpy as np
@@ -34,6 +37,82 @@ def sort_cells(pos, L, nc):
     start = np.zeros(nc ** 3 + 1, dtype=np.int64)
     np.cumsum(np.bincount(key, minlength=nc ** 3), out=start[1:])
     return x[order], c[order], key[order], start
+
+
+def target_bins(xs, c, L, rc, nc, w, i, dy, dz):
+    """Unwrapped bins [a0, a1] of target i in row (dy, dz), or None out of reach."""
+    f32 = np.float32
+    side = L / nc
+    sidef, inv_side = f32(side), f32(1.0 / side)
+    rc2m = f32(f32(rc * rc) * (f32(1.0) + f32(1e-5)))
+    cx, cy, cz = c[i]
+    xl = f32(xs[i, 0] - cx * side)
+    yl = f32(xs[i, 1] - cy * side)
+    zl = f32(xs[i, 2] - cz * side)
+    gy = f32(dy * sidef - yl) if dy > 0 else (f32(yl - (dy + 1) * sidef) if dy < 0 else f32(0))
+    gz = f32(dz * sidef - zl) if dz > 0 else (f32(zl - (dz + 1) * sidef) if dz < 0 else f32(0))
+    d2 = f32(gy * gy + gz * gz)
+    if not d2 < rc2m:
+        return None
+    reach = f32(np.sqrt(f32(rc2m - d2)))
+    b0 = int(np.floor(f32((xl - reach) * inv_side)))
+    b1 = int(np.floor(f32((xl + reach) * inv_side)))
+    return cx + max(b0, -w), cx + min(b1, w)
+
+
+def union_check(xs, c, start, L, rc, nc, w, group):
+    """The staged union of a warp's targets in every row, as the kernel lays it out; returns
+    per target the global indices it reads through the union."""
+    f32 = np.float32
+    sidef = f32(L / nc)
+    rc2m = f32(f32(rc * rc) * (f32(1.0) + f32(1e-5)))
+    got = {int(i): [] for i in group}
+    for dz in range(-w, w + 1):
+        mz = f32((abs(dz) - 1) * sidef) if dz else f32(0)
+        for dy in range(-w, w + 1):
+            my = f32((abs(dy) - 1) * sidef) if dy else f32(0)
+            if my * my + mz * mz >= rc2m:
+                continue
+            bins = {int(i): target_bins(xs, c, L, rc, nc, w, i, dy, dz) for i in group}
+            live = [b for b in bins.values() if b]
+            if not live:
+                continue
+            A0, A1 = min(b[0] for b in live), max(b[1] for b in live)
+            cy, cz = c[group[0], 1], c[group[0], 2]
+            # all targets of a warp may sit in different rows: the union uses each target's
+            # own row; the kernel's warp shares one row only because every lane computes
+            # the same (dy, dz) relative to its own cell, so check per target row
+            for i in group:
+                i = int(i)
+                if not bins[i]:
+                    continue
+                ci = c[i]
+                base = (((ci[2] + dz) % nc) * nc + (ci[1] + dy) % nc) * nc
+                cs = start[base:base + nc + 1]
+                sA = lenA = lenC = 0
+                sC = cs[0]
+                if A0 < 0:
+                    sA = cs[A0 + nc]; lenA = cs[nc] - sA
+                b0, b1 = max(A0, 0), min(A1, nc - 1)
+                sB = cs[b0]; lenB = cs[b1 + 1] - sB
+                if A1 >= nc:
+                    lenC = cs[A1 - nc + 1] - sC
+                def off(b):
+                    if b < 0:
+                        return cs[b + nc] - sA
+                    if b < nc:
+                        return lenA + cs[b] - sB
+                    return lenA + lenB + cs[b - nc] - sC
+                o0, o1 = off(bins[i][0]), off(bins[i][1] + 1)
+                assert 0 <= o0 <= o1 <= lenA + lenB + lenC
+                for q in range(o0, o1):
+                    if q < lenA:
+                        got[i].append(sA + q)
+                    elif q < lenA + lenB:
+                        got[i].append(sB + q - lenA)
+                    else:
+                        got[i].append(sC + q - lenA - lenB)
+    return got
 
 
 def candidate_ranges(xs, c, start, L, rc, nc, w, targets):
@@ -98,6 +177,20 @@ def check(pos, L, rc, targets=None):
         partners = np.nonzero((r2 < rc * rc) & (np.arange(n) != i))[0]
         missing = np.setdiff1d(partners, idx)
         assert missing.size == 0, f"target {i}: partners {missing[:5]} not among the candidates"
+    # the staged union of a warp's tile (up to 8 consecutive sorted targets of one row of
+    # cells, as k_row_tiles cuts them) gives each target exactly its ranges
+    tg = 8
+    row_of = key // nc
+    for g0 in list(targets[:: max(1, len(targets) // 40)])[:40]:
+        r = row_of[g0]
+        first = start[r * nc] + tg * ((g0 - start[r * nc]) // tg)
+        group = np.arange(first, min(first + tg, start[(r + 1) * nc]))
+        assert np.all(row_of[group] == r)
+        got = union_check(xs, c, start, L, rc, nc, w, group)
+        own = candidate_ranges(xs, c, start, L, rc, nc, w, group)
+        for i, rr in zip(group, own):
+            idx = np.concatenate([np.arange(s_, s_ + m) for s_, m in rr]) if rr else np.zeros(0, int)
+            assert sorted(got[int(i)]) == sorted(idx.tolist()), f"union layout of target {i}"
     return nc, w
 
 
