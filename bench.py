@@ -102,8 +102,8 @@ def run_params(args, n, L):
 PARAMS = {
     "rocksalt_512": (4.0, 1.0, 10),          # r_c = L/2, k_max raised to 10 to reach 1e-6
     "random_32768": (4.0, 0.9292305472124596, 36),
-    "rocksalt_262144": (6.8, 0.5466062042426233, 42),
-    "random_2097152": (9.6, 0.3871793946718582, 59),
+    "rocksalt_262144": (7.6, 0.48906870905918925, 38),
+    "random_2097152": (10.72, 0.34672781612405207, 53),
 }
 
 
@@ -330,6 +330,7 @@ def oracle_sample(pos, q, L, beta, rc, kmax, n_targets, seed=0, S_given=None,
     _, Fk, _, _, _ = oracle.recip(pos, q, L, beta, kmax, sub=sub, S=S)
     t2 = time.perf_counter()
     full = t_s + (t2 - t1) * n / len(sub)
+    oracle_sample.parts = (Fr, Fk)      # the two parts of the returned forces
     return full, (t2 - t0), len(sub), sub, Fr + Fk, note
 
 
@@ -907,6 +908,13 @@ def measure_workload(args, workload, local, world, dev, flush, alu_peaks, steps,
                                    "40 flop per unique pair, 18 per (particle, mode) term")}
     Sg = None if spme else ew.structure_factor()
     m = None if spme else ew.kset()
+    # the real-space and reciprocal parts on their own (for the error of each part)
+    from paper_1708_01135_gb300 import PART_REAL, PART_RECIP
+    F_parts = {}
+    if not spme and accuracy != "none":
+        for nm, pt in (("real", PART_REAL), ("recip", PART_RECIP)):
+            ew.compute_async(tp, tq, F, E, parts=pt)
+            F_parts[nm] = F.cpu().numpy()
     ew.close()
     rank = int(os.environ.get("RANK", "0"))
     if rank == 0 and world == 1 and accuracy != "none":
@@ -932,6 +940,13 @@ def measure_workload(args, workload, local, world, dev, flush, alu_peaks, steps,
                               "forces use this path's S(k), whose own error is "
                               "structure_factor_error")}
             acc["structure_factor_error"] = structure_factor_error(pos, q, L, m, Sg)
+            if F_parts:
+                Fr_o, Fk_o = oracle_sample.parts
+                scale = float(np.sqrt((Fo ** 2).sum()))
+                acc["by_part"] = {
+                    "real": float(np.sqrt(((F_parts["real"][sub] - Fr_o) ** 2).sum())) / scale,
+                    "recip": float(np.sqrt(((F_parts["recip"][sub] - Fk_o) ** 2).sum())) / scale,
+                    "note": "RMS error of each part over the RMS total force of the sample"}
         out["cpu_baseline"] = {"value": n / full, "unit": "particles/s",
                                "cores": oracle.num_threads(), "kind": "oracle",
                                "cpu": cpu_model(),

@@ -278,8 +278,9 @@ int ewald_compute_host(ewald_plan_t plan, int64_t n, const double *pos_host,
  *             [7] reciprocal branch (stages 2-4 on their stream).
  *             Single kernels (bracketed by their own events): [8] the real-space pair
  *             kernel, [9] the back-scatter product kernel, [10] the self term, totals and
- *             unsort (a9) after the join.  -1 where a span was not recorded (e.g. [9] for
- *             the mesh reciprocal part).
+ *             unsort (a9) after the join.  -1 where a span was not recorded: [2]-[4], [7]
+ *             and [9] when the evaluation had no reciprocal part, [9] for the mesh
+ *             reciprocal part.
  *   launches  host int or NULL: kernels launched by the last evaluation
  */
 #define EWALD_PROFILE_TIMES 11

@@ -460,7 +460,8 @@ cudaError_t pipeline(Plan &p, int64_t n, const double *pos, const double *q, dou
         p.launches += 1;
     }
     prof_mark(p, kEvFinal, st);
-    p.prof_valid = p.prof && do_recip;
+    p.prof_valid = p.prof;
+    p.prof_recip = p.prof && do_recip;
     p.last_stream = st;
     return cudaGetLastError();
 }
@@ -1009,14 +1010,15 @@ extern "C" int ewald_profile(ewald_plan_t plan, int enable, double times_ms[EWAL
         };
         times_ms[0] = span(kEvStart, kEvBinned);
         times_ms[1] = span(kEvBinned, kEvRealEnd);
-        times_ms[2] = span(kEvRecipStart, kEvFwdEnd);
-        times_ms[3] = span(kEvFwdEnd, kEvCoefEnd);
-        times_ms[4] = span(kEvCoefEnd, kEvBackEnd);
+        const bool rc = p.prof_recip;   // the reciprocal branch ran in that evaluation
+        times_ms[2] = rc ? span(kEvRecipStart, kEvFwdEnd) : -1.0;
+        times_ms[3] = rc ? span(kEvFwdEnd, kEvCoefEnd) : -1.0;
+        times_ms[4] = rc ? span(kEvCoefEnd, kEvBackEnd) : -1.0;
         times_ms[5] = span(kEvRealEnd, kEvFinal);
         times_ms[6] = span(kEvStart, kEvFinal);
-        times_ms[7] = span(kEvRecipStart, kEvBackEnd);
+        times_ms[7] = rc ? span(kEvRecipStart, kEvBackEnd) : -1.0;
         times_ms[8] = span(kEvRealStart, kEvRealEnd);
-        times_ms[9] = p.prof_bs ? span(kEvBsStart, kEvBsEnd) : -1.0;
+        times_ms[9] = rc && p.prof_bs ? span(kEvBsStart, kEvBsEnd) : -1.0;
         times_ms[10] = span(kEvJoined, kEvFinal);
     }
     return EWALD_OK;
@@ -1078,11 +1080,12 @@ extern "C" int ewald_tune(int64_t n, double L, double tol, double *r_c, double *
     double rc = *r_c;
     if (!(rc > 0)) {
         // Cost per particle, calibrated on GB300 with the EWALD_MIXED path (262,144- and
-        // 2,097,152-ion systems): real space ~2.5e-11 s per r_c^3 rho, the two reciprocal
-        // products ~1.13e-13 s per k_max^3, k_max = p^2 L / (pi r_c).  Pick the r_c <= L/2
-        // that minimises the sum on a grid.
+        // 2,097,152-ion systems, each part timed alone): real space ~1.3e-11 s per r_c^3 rho,
+        // the two reciprocal products ~1.1e-13 s per k_max^3, k_max = p^2 L / (pi r_c).  Pick
+        // the r_c <= L/2 that minimises the sum on a grid (where the two parts cost about the
+        // same, which also balances the two streams they run on).
         const double rho = n / (L * L * L);
-        const double c_pair = 2.5e-11, c_mode = 1.13e-13;
+        const double c_pair = 1.3e-11, c_mode = 1.1e-13;
         double best = 1e300, best_rc = 0.5 * L;
         for (int t = 1; t <= 400; ++t) {
             double x = 0.5 * L * t / 400.0;

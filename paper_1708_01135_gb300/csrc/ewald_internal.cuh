@@ -152,6 +152,7 @@ struct Plan {
     bool prof = false;
     bool prof_valid = false;
     bool prof_bs = false;        // the back-scatter kernel events were recorded
+    bool prof_recip = false;     // the reciprocal branch's events were recorded
     cudaEvent_t ev[12] = {};
     int launches = 0;
 };

@@ -133,9 +133,40 @@ template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4_32a; };
 
 __device__ __forceinline__ double erfc_t(double x) { return erfc(x); }
-__device__ __forceinline__ float exp_t(float x) { return __expf(x); }
-__device__ __forceinline__ double exp_t(double x) { return exp(x); }
-__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+// FP32 pair arithmetic on the special-function unit directly: the approximate PTX forms with
+// subnormal inputs and results flushed to zero (pair distances, Gaussians and erfc values of
+// interest are far from the subnormal range, and a flushed Gaussian or erfc term is below
+// 1e-38 of the pair's Coulomb term).  One instruction each, no special-case paths.
+__device__ __forceinline__ float ex2_ftz(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_ftz(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kLog2e = 1.4426950408889634f;
+
+// exp(-beta^2 r^2) from nb2l = -beta^2 log2(e) (FP32) or nb2 = -beta^2 (FP64)
+__device__ __forceinline__ float gauss_t(float nb2l, float r2) { return ex2_ftz(nb2l * r2); }
+__device__ __forceinline__ double gauss_t(double nb2, double r2) { return exp(nb2 * r2); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrt_ftz(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 
 // Per-target sums of one warp lane: force / q_i and potential; with kVir the six
@@ -272,7 +303,7 @@ __constant__ float kErfcC[9] = {0.48547884821891785f, 0.31732580065727234f, 0.14
 
 __device__ __forceinline__ float erfc_from_gauss(float x, float g)
 {
-    const float t = __fdividef(1.0f, fmaf(kErfcP, x, 1.0f));
+    const float t = rcp_ftz(fmaf(kErfcP, x, 1.0f));
     const float u = fmaf(kErfcA, t, kErfcB);
     float p = kErfcC[8];
 #pragma unroll
@@ -281,8 +312,9 @@ __device__ __forceinline__ float erfc_from_gauss(float x, float g)
 }
 
 // One candidate pair with displacement d = r_i - r_j (minimum image) and partner charge qj;
-// the pair counts when 0 < |d| < r_c.  With Lennard-Jones pairs, ljrow is the target type's
-// row of the table and tj the partner's type.
+// the pair counts when 0 < |d| < r_c.  nb2 is -beta^2 log2(e) in FP32, -beta^2 in FP64 (see
+// gauss_t).  With Lennard-Jones pairs, ljrow is the target type's row of the table and tj
+// the partner's type.
 template <class T, class T4, class A>
 __device__ __forceinline__ void pair_d(A &a, T dx, T dy, T dz, T qj, T rc2, T beta, T nb2,
                                        T two_b_rpi, const T4 *ljrow, int tj)
@@ -291,7 +323,7 @@ __device__ __forceinline__ void pair_d(A &a, T dx, T dy, T dz, T qj, T rc2, T be
     if (r2 < rc2 && r2 > T(0)) {
         const T rinv = rsqrt_t(r2);
         const T r = r2 * rinv;
-        const T g = exp_t(nb2 * r2);                        // exp(-beta^2 r^2)
+        const T g = gauss_t(nb2, r2);                       // exp(-beta^2 r^2)
         T e;                                                // erfc(beta r) / r
         if constexpr (sizeof(T) == 4) e = erfc_from_gauss(beta * r, g) * rinv;
         else e = erfc_t(beta * r) * rinv;
@@ -434,8 +466,10 @@ struct RowWalk {
             const float d2 = gy * gy + gz * gz;
             int a0 = 1 << 30, a1 = -(1 << 30);
             if (valid && d2 < rc2m) {
-                const float reach = sqrtf(rc2m - d2);
-                int b0 = (int)floorf((xl - reach) * inv_side), b1 = (int)floorf((xl + reach) * inv_side);
+                // (approximate square root: a relative error of 2^-22 is inside the margin)
+                const float reach = sqrt_ftz(rc2m - d2);
+                int b0 = __float2int_rd((xl - reach) * inv_side);
+                int b1 = __float2int_rd((xl + reach) * inv_side);
                 b0 = b0 < -w ? -w : b0;
                 b1 = b1 > w ? w : b1;
                 a0 = cx + b0;
@@ -486,7 +520,7 @@ struct RowWalk {
 };
 
 template <class T, int G, bool kVir, bool kLJ>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, sizeof(T) == 4 && !kVir && !kLJ ? 8 : 1)
 k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *__restrict__ pg,
             const int *__restrict__ key_sorted, const int *__restrict__ cell_start,
             const int2 *__restrict__ tiles, const int *__restrict__ tile_total, int n,
@@ -499,7 +533,7 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     using T4 = typename Vec4<T>::type;
     using Acc = PairAcc<T, kVir, kLJ>;
     constexpr int TG = 32 / G;                   // targets per warp
-    constexpr int kCapR = 4096 / (int)sizeof(R4);  // records per staging buffer (4 KB)
+    constexpr int kCapR = 3072 / (int)sizeof(R4);  // records per staging buffer (3 KB)
     __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
     __shared__ Acc xacc[kWarps][32];             // partial sums handed between split warps
     __shared__ __align__(128) R4 stage[kWarps][2][kCapR];
@@ -553,7 +587,7 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     wk.next_c0 = 0;
 
     Acc acc{};
-    const T nb2 = -beta * beta;
+    const T nb2 = sizeof(T) == 4 ? -beta * beta * T(kLog2e) : -beta * beta;
     uint32_t phase[2] = {0u, 0u};
     RowItem cur, nxt;
     bool have_cur = active && wk.next<kCapR>(cur);
@@ -583,13 +617,9 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
         // this target's part of the chunk, in buffer indices
         const int lo = (cur.off0 > cur.c0 ? cur.off0 : cur.c0) - cur.c0;
         const int hi = (cur.off1 < cur.c0 + cur.cnt ? cur.off1 : cur.c0 + cur.cnt) - cur.c0;
-        const int len = hi > lo ? hi - lo : 0;
-        const int steps = __reduce_max_sync(0xffffffffu, (len + G - 1) / G);
         const R4 *sb = stage[warp][b];
-        for (int st = 0; st < steps; ++st) {
-            const int kk = st * G + g;
-            if (kk < len) {
-                const int j = lo + kk;
+        for (int j = lo + g; j < hi; j += G) {
+            {
                 const R4 pj = sb[j];
                 T dxv;
                 int tj = 0;
@@ -686,7 +716,7 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
     const T4 *ljrow = kLJ ? ljs + lj.tsort[valid ? i : n - 1] * lj.ntypes : nullptr;
     const T invL = T(1) / L;
     PairAcc<T, kVir, kLJ> acc{};
-    const T nb2 = -beta * beta;
+    const T nb2 = sizeof(T) == 4 ? -beta * beta * T(kLog2e) : -beta * beta;
     uint32_t phase[2] = {0u, 0u};
     const int nchunks = (n + kCapAll - 1) / kCapAll;
     if (lane == 0) {
@@ -765,7 +795,7 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
             pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap, lj,
             p.d_status);
     } else {
-        auto kern = p.real_tile == 4 ? k_real_rows<T, 4, kVir, kLJ> : k_real_rows<T, 2, kVir, kLJ>;
+        auto kern = k_real_rows<T, 1, kVir, kLJ>;
         const int64_t groups = real_tile_capacity(p, n);
         // two warps per group of targets when one warp per group would leave the SMs short
         // of warps
@@ -804,12 +834,13 @@ int64_t real_tile_capacity(const Plan &p, int64_t n)
 // targets per warp: 32 in all-pairs mode, else 32 / G with G lanes per target
 int real_tile_size(const Plan &p) { return p.w == 0 ? 32 : 32 / p.real_tile; }
 
-// Lanes per target of the cell kernel: 4 where a target's range in a row is long (dense
-// cells), 2 where rows hold few candidates (the steps of a row then run shorter).
-int real_tile_for(int w, double cell_occupancy)
+// Lanes per target of the cell kernel: one, so that the 32 targets of a warp share every
+// staged row (measured on GB300, real-space kernel alone, ms with 1 / 2 / 4 lanes per target:
+// 32,768 ions 0.152 / 0.168 / 0.202; 262,144: 1.42 / 1.63 / 2.15; 2,097,152: 22.2 / 24.6 /
+// 28.8).  The kernel is templated on the lane count; this build instantiates one lane.
+int real_tile_for(int, double)
 {
-    if (w == 0) return 1;
-    return cell_occupancy * 2 * w >= 16.0 ? 4 : 2;
+    return 1;
 }
 
 cudaError_t launch_wait_probe(Plan &p, cudaStream_t st)

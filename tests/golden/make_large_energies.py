@@ -33,8 +33,8 @@ from paper_1708_01135_gb300 import workloads as W  # noqa: E402
 
 # (workload, r_c, beta, k_max, full reciprocal energy?)
 CASES = [
-    ("rocksalt_262144", 6.8, 0.5466062042426233, 42, True),
-    ("random_2097152", 9.6, 0.3871793946718582, 59, False),
+    ("rocksalt_262144", 7.6, 0.48906870905918925, 38, True),
+    ("random_2097152", 10.72, 0.34672781612405207, 53, False),
 ]
 
 
