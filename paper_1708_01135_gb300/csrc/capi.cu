@@ -640,6 +640,28 @@ int plan_setup_host(Plan &p, double L, double beta, double rc, int kmax, int pre
     return EWALD_OK;
 }
 
+// The modes of every row in K_half order (m_x ascending; m_x > 0 only on the row (0, 0)) and
+// g(k) = 4 pi exp(-k^2 / (4 beta^2)) / (V k^2) (C_k of Eq. 3), k = 2 pi m / L.  One block per
+// row.
+__global__ void k_plan_tables(const RowInfo *__restrict__ rows, double tpl, double V,
+                              double beta, int *__restrict__ kset, double *__restrict__ g)
+{
+    const RowInfo r = rows[blockIdx.x];
+    const int lo = (r.my == 0 && r.mz == 0) ? 1 : -r.nxmax;
+    const int cnt = r.nxmax - lo + 1;
+    const double inv4b2 = 1.0 / (4.0 * beta * beta);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int mx = lo + t;
+        const int64_t idx = (int64_t)r.koff + t;
+        kset[3 * idx + 0] = mx;
+        kset[3 * idx + 1] = r.my;
+        kset[3 * idx + 2] = r.mz;
+        const double m2 = (double)mx * mx + (double)r.my * r.my + (double)r.mz * r.mz;
+        const double k2 = tpl * tpl * m2;
+        g[idx] = 4.0 * kPi * exp(-k2 * inv4b2) / (V * k2);
+    }
+}
+
 // Upload the row table and k list of the current parameters, (re)allocating the plan-level
 // arrays when they grow.  Runs on the side stream and waits for it.
 static cudaError_t plan_upload(Plan &p)
@@ -663,32 +685,16 @@ static cudaError_t plan_upload(Plan &p)
         if ((e = pool_alloc((void **)&p.g_d, sizeof(double) * p.nk, st)) != cudaSuccess) return e;
         p.cap_nk = p.nk;
     }
-    std::vector<int> kset(3 * (size_t)p.nk);
-    for (const RowInfo &r : p.rows_h) {
-        int lo = (r.my == 0 && r.mz == 0) ? 1 : -r.nxmax;
-        int64_t t = r.koff;
-        for (int mx = lo; mx <= r.nxmax; ++mx) {
-            kset[3 * t + 0] = mx; kset[3 * t + 1] = r.my; kset[3 * t + 2] = r.mz;
-            ++t;
-        }
-    }
     if ((e = cudaMemcpyAsync(p.rows_d, p.rows_h.data(), sizeof(RowInfo) * p.R, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
     // forward order of the rows: decreasing n_x,max (the reverse of the row order), so that
     // each 64-row tile of the forward product needs only the m_x columns of its first row
     std::vector<int> fperm(p.R);
     for (int i = 0; i < p.R; ++i) fperm[i] = p.R - 1 - i;
     if ((e = cudaMemcpyAsync(p.fperm_d, fperm.data(), sizeof(int) * p.R, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(p.kset_d, kset.data(), sizeof(int) * 3 * p.nk, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-    // g(k) = 4 pi exp(-k^2 / (4 beta^2)) / (V k^2) (C_k of Eq. 3), once per plan, K_half order
-    std::vector<double> g(p.nk);
-    const double tpl = 2.0 * kPi / p.L, V = p.L * p.L * p.L;
-    for (int64_t t = 0; t < p.nk; ++t) {
-        const double m2 = (double)kset[3 * t] * kset[3 * t] + (double)kset[3 * t + 1] * kset[3 * t + 1] +
-                          (double)kset[3 * t + 2] * kset[3 * t + 2];
-        const double k2 = tpl * tpl * m2;
-        g[t] = 4.0 * kPi * exp(-k2 / (4.0 * p.beta * p.beta)) / (V * k2);
-    }
-    if ((e = cudaMemcpyAsync(p.g_d, g.data(), sizeof(double) * p.nk, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    // the k list and g(k) of every mode, generated on the device from the row table
+    k_plan_tables<<<p.R, 128, 0, st>>>(p.rows_d, 2.0 * kPi / p.L, p.L * p.L * p.L, p.beta,
+                                       p.kset_d, p.g_d);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(p.S_d, 0, sizeof(double) * 2 * p.nk, st)) != cudaSuccess) return e;
     return cudaStreamSynchronize(st);
 }

@@ -106,6 +106,7 @@ __device__ __forceinline__ uint64_t globaltimer()
 // Whole-warp bounded wait on an mbarrier phase: true when it completed, false after ~1 s.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity)
 {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;   // usually landed
     const uint64_t t0 = globaltimer();
     while (true) {
         uint32_t ok = mbar_try_wait(bar, parity);
@@ -482,13 +483,12 @@ struct RowWalk {
             const int uz = cz + dz < 0 ? cz + dz + nc : (cz + dz >= nc ? cz + dz - nc : cz + dz);
             const int *cs = cell_start + (uz * nc + uy) * nc;
             RowUnion &u = row.u;
-            u.sA = 0; u.lenA = 0; u.lenC = 0;
-            u.sC = cs[0];
+            u.sA = 0; u.lenA = 0; u.sC = 0; u.lenC = 0;
             if (A0 < 0) { u.sA = cs[A0 + nc]; u.lenA = cs[nc] - u.sA; }
             const int b0 = A0 > 0 ? A0 : 0, b1 = A1 < nc - 1 ? A1 : nc - 1;
             u.sB = cs[b0];
             u.lenB = cs[b1 + 1] - u.sB;
-            if (A1 >= nc) u.lenC = cs[A1 - nc + 1] - u.sC;
+            if (A1 >= nc) { u.sC = cs[0]; u.lenC = cs[A1 - nc + 1] - u.sC; }
             if (u.total() == 0) continue;
             row.dy = dy;
             row.dz = dz;
