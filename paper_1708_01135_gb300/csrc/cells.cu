@@ -190,14 +190,13 @@ __global__ void k_scatter(int64_t n, int64_t chunk, int ncells, const int *__res
     }
 }
 
-// a3: pack sorted particles: wrapped global FP64 position, cell-local FP64 position (the
-// all-pairs kernel), the FP32 record of the pair kernels and 32-bit fixed-point fractions of
-// the box (for exact integer phase angles).  The FP32 record is, in all-pairs mode (one
-// cell), the cell-local position and q; in cell mode, x / L as 32-bit fixed point (bits in
-// .x), y and z relative to the corner of the particle's cell, and q.
+// a3: pack sorted particles: wrapped global FP64 position, cell-local FP64 / FP32 positions
+// (the all-pairs kernel, written only in that mode) and 32-bit fixed-point fractions of the
+// box (the FP32 cell kernel's exact minimum-image displacements and the exact integer phase
+// angles of the tensor-core reciprocal part).
 __global__ void k_pack(int64_t n, const double *__restrict__ pos, const double *__restrict__ q,
                        const int *__restrict__ perm, const int *__restrict__ key_sorted,
-                       double L, double side, int nc, int cell_mode,
+                       double L, double side, int nc,
                        double4_32a *__restrict__ pg, double4_32a *__restrict__ pl64,
                        float4 *__restrict__ pl32, uint4 *__restrict__ pu)
 {
@@ -215,9 +214,7 @@ __global__ void k_pack(int64_t n, const double *__restrict__ pos, const double *
     const double scale = 4294967296.0 / L;
     unsigned ux = (unsigned)((unsigned long long)llrint(x * scale) & 0xffffffffull);
     if (pl64) pl64[s] = make_double4_32a(lx, ly, lz, qi);
-    if (pl32)
-        pl32[s] = cell_mode ? make_float4(__uint_as_float(ux), (float)ly, (float)lz, (float)qi)
-                            : make_float4((float)lx, (float)ly, (float)lz, (float)qi);
+    if (pl32) pl32[s] = make_float4((float)lx, (float)ly, (float)lz, (float)qi);
     if (pu) {
         unsigned uy = (unsigned)((unsigned long long)llrint(y * scale) & 0xffffffffull);
         unsigned uz = (unsigned)((unsigned long long)llrint(z * scale) & 0xffffffffull);
@@ -275,9 +272,9 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
                                      ws.key_sorted, use_smem);
     const bool need64 = p.precision == EWALD_FP64;
     k_pack<<<(int)((n + 255) / 256), 256, 0, st>>>(n, pos, q, ws.perm, ws.key_sorted, p.L,
-                                                   p.cell_side, p.nc, p.w > 0 ? 1 : 0, ws.pg,
-                                                   need64 ? ws.pl64 : nullptr,
-                                                   need64 ? nullptr : ws.pl32, ws.pu);
+                                                   p.cell_side, p.nc, ws.pg,
+                                                   (need64 && p.w == 0) ? ws.pl64 : nullptr,
+                                                   (!need64 && p.w == 0) ? ws.pl32 : nullptr, ws.pu);
     p.launches += 5;
     if (p.w > 0) {
         const int nrows = p.nc * p.nc;

@@ -60,10 +60,10 @@ struct Workspace {
     int *tile_off = nullptr;     // [nrows + 1] exclusive offsets; tile_off[nrows] = tiles
     // packed particles (sorted)
     double4_32a *pg = nullptr;       // wrapped global position + q (FP64)
-    double4_32a *pl64 = nullptr;     // cell-local position + q (FP64, all-pairs mode)
-    float4 *pl32 = nullptr;      // FP32 pair record: cell-local position + q (all-pairs mode),
-                                 // or x / L fixed-point bits, cell-local y, z, q (cell mode)
-    uint4 *pu = nullptr;         // 32-bit fixed-point fractions x/L, y/L, z/L + q (float bits)
+    double4_32a *pl64 = nullptr;     // cell-local position + q (FP64, all-pairs mode only)
+    float4 *pl32 = nullptr;      // cell-local position + q (FP32, all-pairs mode only)
+    uint4 *pu = nullptr;         // 32-bit fixed-point fractions x/L, y/L, z/L + q (float bits):
+                                 // the FP32 cell kernel's records and the tensor-core phases
     // outputs (sorted)
     double *f_real = nullptr;    // [n][3]
     double *phi_real = nullptr;  // [n] real-space potential of every sorted particle

@@ -19,11 +19,11 @@
 //     stay in L1/L2: neighbouring targets share most of them).  This keeps the candidates
 //     close to the cutoff sphere of each target (about 1.6 to 1.8 per partner inside r_c)
 //     instead of the cutoff sphere of a whole tile of targets.
-//   * FP32: x is a 32-bit fixed-point fraction of the box (x / L 2^32), so the difference of
-//     two of them modulo 2^32 is the minimum image exactly, at 2^-32 L resolution whatever the
-//     box size; y and z are stored relative to the corner of their own cell, and the row
-//     offset is an exact small multiple of the cell side (periodic images are implicit).
-//     FP64: wrapped global coordinates, with the image shift of a wrapped row or range.
+//   * FP32: positions are 32-bit fixed-point fractions of the box (x / L 2^32), so the
+//     difference of two of them modulo 2^32 is the minimum-image displacement exactly, at
+//     2^-32 L resolution whatever the box size (periodic images are implicit); each component
+//     is rounded once, to FP32.  FP64: wrapped global coordinates, with the image shift of a
+//     wrapped row or range.
 //   * erfc in FP32 is t exp(-x^2) P(t), t = 1 / (1 + p x), with a degree-7 polynomial P fitted
 //     to erfc(x) exp(x^2) / t on [0, 6] (csrc/fit_erfc.py derives the coefficients; relative
 //     error 3.5e-8 in exact arithmetic): one exp2, one reciprocal and the pair's rsqrt.
@@ -241,12 +241,13 @@ __device__ __forceinline__ double warp_sum(double v)
 template <class A>
 __device__ __forceinline__ void acc_store_tile(const A &a, bool mine, double qi, int lane,
                                                double *__restrict__ vir_tile, int64_t vcap,
-                                               double *__restrict__ e_lj, int64_t tile)
+                                               double *__restrict__ e_lj, int64_t tile,
+                                               double vscale = 1.0)
 {
     if constexpr (A::vir) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const double v = warp_sum(mine ? 0.5 * qi * (double)a.w[c] : 0.0);
+            const double v = warp_sum(mine ? 0.5 * qi * vscale * (double)a.w[c] : 0.0);
             if (lane == 0) vir_tile[c * vcap + tile] = v;
         }
     }
@@ -274,14 +275,16 @@ struct LJArgs {
 
 // Shared-memory copy of the pair table with the shift u(r_c) of every pair type in the
 // fourth entry; every thread of the block takes part (call before any thread returns).
+// (s2scale multiplies sigma^2, for kernels that take distances in other units than L.)
 template <class T, class T4>
-__device__ __forceinline__ void load_lj_table(T4 *ljs, const LJArgs &lj, double rc2)
+__device__ __forceinline__ void load_lj_table(T4 *ljs, const LJArgs &lj, double rc2,
+                                              double s2scale = 1.0)
 {
     for (int u = threadIdx.x; u < lj.ntypes * lj.ntypes; u += blockDim.x) {
         const double s2 = lj.tab[4 * u], e4 = lj.tab[4 * u + 1];
         const double x2 = s2 / rc2, x6 = x2 * x2 * x2;
         T4 c;
-        c.x = (T)s2;
+        c.x = (T)(s2 * s2scale);
         c.y = (T)e4;
         c.z = (T)lj.tab[4 * u + 2];
         c.w = (T)(e4 * (x6 * x6 - x6));
@@ -365,27 +368,151 @@ __device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
     pair_d<T, T4>(a, xi - p.x, yi - p.y, zi - p.z, p.w, rc2, beta, nb2, two_b_rpi, ljrow, tj);
 }
 
+// ---- FP32 pairs in fixed-point units ----------------------------------------------------
+//
+// The FP32 cell kernel works in units of the fixed-point step S = L / 2^32: a displacement
+// component is the integer difference D of two fractions, h = float(D) (rounded once), and
+// r^2, beta, the cutoff and the constants are all expressed in these units, so that no
+// product with S rounds the geometry.  The accumulated sums are rescaled once per target, in
+// FP64 (forces by 1 / S^2, potentials, the Coulomb virial and the Lennard-Jones force by
+// 1 / S).
+//
+// Near pairs (r below r_near, where the pair forces are large and the relative error of the
+// total force is set): the FP32 r^2 of the rounded components is off by ~2^-24, and for
+// ionic systems, whose net force is a small sum of large pair forces, that alone gives about
+// 1e-6 of the RMS force.  There the exact r^2 = sum D^2 is formed as an FP32 pair (hi + lo):
+// D = h + l with l = D - int(h) exact, h^2 = P + e with e = fma(h, h, -P), and TwoSum errors
+// of the sums; the force factor A = (erfc(beta r)/r + c g)/r^2 and the potential
+// e = erfc(beta r)/r are then corrected to first order in delta = r^2_exact - r^2:
+//   dA/d(r^2) = -(1.5 A + c beta^2 g) / r^2,   de/d(r^2) = -(e + c g) / (2 r^2),
+// c = 2 beta / sqrt(pi), g = exp(-beta^2 r^2) (delta / r^2 is ~2^-24, so the second order
+// is ~2^-48).
+struct ScaledK {
+    float rc2s, rn2s;       // r_c^2 and r_near^2 in units of S^2
+    float beta_s;           // beta S
+    float nb2l_s;           // -beta^2 S^2 log2(e)
+    float c_s;              // 2 beta / sqrt(pi) S
+    float cb2_s;            // c_s beta_s^2
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &err)
+{
+    s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+
+// Residual delta = (exact sum of D_a^2) - r2 for the rounded components h_a = float(D_a),
+// r2 being the FP32 value the pair was evaluated at.
+__device__ __forceinline__ float r2_residual(int Dx, int Dy, int Dz, float hx, float hy,
+                                             float hz, float r2)
+{
+    const float lx = (float)(Dx - __float2int_rn(hx));
+    const float ly = (float)(Dy - __float2int_rn(hy));
+    const float lz = (float)(Dz - __float2int_rn(hz));
+    const float px = hx * hx, py = hy * hy, pz = hz * hz;
+    const float ex = fmaf(hx, hx, -px), ey = fmaf(hy, hy, -py), ez = fmaf(hz, hz, -pz);
+    float s1, t1, s2, t2;
+    two_sum(px, py, s1, t1);
+    two_sum(s1, pz, s2, t2);
+    const float cross = fmaf(2.0f * hx, lx, lx * lx) + fmaf(2.0f * hy, ly, ly * ly) +
+                        fmaf(2.0f * hz, lz, lz * lz);
+    return (s2 - r2) + ((t1 + t2) + ((ex + ey + ez) + cross));
+}
+
+template <class T4, class A>
+__device__ __forceinline__ void pair_s(A &a, int Dx, int Dy, int Dz, float qj, const ScaledK &K,
+                                       const T4 *ljrow, int tj)
+{
+    const float hx = (float)Dx, hy = (float)Dy, hz = (float)Dz;
+    const float r2 = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+    if (r2 < K.rc2s && r2 > 0.0f) {
+        const float rinv = rsqrt_ftz(r2);
+        const float rinv2 = rinv * rinv;
+        const float r = r2 * rinv;
+        const float g = ex2_ftz(K.nb2l_s * r2);
+        float e = erfc_from_gauss(K.beta_s * r, g) * rinv;
+        float fA = fmaf(K.c_s, g, e) * rinv2;
+        if (r2 < K.rn2s) {
+            const float rho = r2_residual(Dx, Dy, Dz, hx, hy, hz, r2) * rinv2;
+            fA = fmaf(-fmaf(1.5f, fA, K.cb2_s * g), rho, fA);
+            e = fmaf(-0.5f * fmaf(K.c_s, g, e), rho, e);
+        }
+        const float s = qj * fA;
+        a.phi += qj * e;
+        const float sx = s * hx, sy = s * hy, sz = s * hz;
+        a.fx += sx;
+        a.fy += sy;
+        a.fz += sz;
+        if constexpr (A::vir) {
+            a.w[0] += sx * hx; a.w[1] += sy * hy; a.w[2] += sz * hz;
+            a.w[3] += sx * hy; a.w[4] += sx * hz; a.w[5] += sy * hz;
+        }
+        if constexpr (A::lj) {
+            // the pair table holds sigma^2 in units of S^2 (load_lj_table's scale)
+            const T4 c = ljrow[tj];
+            const float x2 = c.x * rinv2, x6 = x2 * x2 * x2;
+            const float fl = c.z * (2.0f * x6 * x6 - x6) * rinv2;
+            const float lx = fl * hx, ly = fl * hy, lz = fl * hz;
+            a.lj_f[0] += lx;
+            a.lj_f[1] += ly;
+            a.lj_f[2] += lz;
+            a.lj_f[3] += c.y * (x6 * x6 - x6) - c.w;
+            if constexpr (A::vir) {
+                a.lj_w[0] += lx * hx; a.lj_w[1] += ly * hy; a.lj_w[2] += lz * hz;
+                a.lj_w[3] += lx * hy; a.lj_w[4] += lx * hz; a.lj_w[5] += ly * hz;
+            }
+        }
+    }
+}
+
+// Compensated (Kahan) addition of the row sums of the forces and potential into the totals;
+// the other sums are added plainly.
+__device__ __forceinline__ void kahan1(float &sum, float &comp, float v)
+{
+    const float y = v - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+__device__ __forceinline__ void kahan1(double &sum, double &, double v) { sum += v; }
+template <class A>
+__device__ __forceinline__ void acc_add_rows(A &tot, A &comp, const A &row)
+{
+    kahan1(tot.fx, comp.fx, row.fx);
+    kahan1(tot.fy, comp.fy, row.fy);
+    kahan1(tot.fz, comp.fz, row.fz);
+    kahan1(tot.phi, comp.phi, row.phi);
+    if constexpr (A::vir) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tot.w[c] += row.w[c];
+    }
+    if constexpr (A::lj) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tot.lj_f[c] += row.lj_f[c];
+    }
+    if constexpr (A::vir && A::lj) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tot.lj_w[c] += row.lj_w[c];
+    }
+}
+
 // ---- cell mode: per-target row ranges --------------------------------------------------
 
-// Candidate records of the cell kernel.  FP32: (x / L as 32-bit fixed point in the bits of
-// .x, y and z relative to the corner of the particle's own cell, q).  FP64: the wrapped
-// global position and q (the sorted copy pg).
+// Candidate records of the cell kernel.  FP32: the 32-bit fixed-point fractions x / L, y / L,
+// z / L and the bits of q (the sorted copy pu): the difference of two fractions modulo 2^32 is
+// the minimum-image displacement exactly, at 2^-32 L resolution, so the only rounding of a
+// displacement component is its conversion to FP32 (2^-24 relative).  (Cell-local FP32
+// coordinates would carry an absolute error of 2^-24 of the cell side in every stored
+// position and in every row offset; for ionic crystals, where the net force is a small sum
+// of large pair forces, that doubles the relative force error.)  FP64: the wrapped global
+// position and q (the sorted copy pg).
 template <class T> struct RowRec;
-template <> struct RowRec<float> { using type = float4; };
+template <> struct RowRec<float> { using type = uint4; };
 template <> struct RowRec<double> { using type = double4_32a; };
 
-// x displacement of a candidate: FP32 from the fixed-point fractions (their difference modulo
-// 2^32 is the minimum image, scaled by L / 2^32); FP64 from global coordinates plus the image
-// shift of the range the candidate came from.
-__device__ __forceinline__ float disp_x(const float4 &pi, const float4 &pj, float sx, float)
-{
-    return (float)(int)(__float_as_uint(pi.x) - __float_as_uint(pj.x)) * sx;
-}
-__device__ __forceinline__ double disp_x(const double4_32a &pi, const double4_32a &pj, double,
-                                         double shift)
-{
-    return (pi.x + shift) - pj.x;
-}
+__device__ __forceinline__ float rec_q(const uint4 &p) { return __uint_as_float(p.w); }
+__device__ __forceinline__ double rec_q(const double4_32a &p) { return p.w; }
 
 // Staged union of the targets' ranges in one row: unwrapped cell bins [A0, A1] of the row,
 // laid out in shared memory in bin order as up to three contiguous runs of the sorted array:
@@ -520,19 +647,18 @@ struct RowWalk {
 };
 
 template <class T, int G, bool kVir, bool kLJ>
-__global__ void __launch_bounds__(kWarps * 32, sizeof(T) == 4 && !kVir && !kLJ ? 8 : 1)
+__global__ void __launch_bounds__(kWarps * 32, sizeof(T) == 4 && !kVir && !kLJ ? 7 : 1)
 k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *__restrict__ pg,
             const int *__restrict__ key_sorted, const int *__restrict__ cell_start,
             const int2 *__restrict__ tiles, const int *__restrict__ tile_total, int n,
-            int nc, int w, double side_d, double L_d, T rc2, T beta, T two_b_rpi, float sx,
-            int split, double *__restrict__ f_out, double *__restrict__ phi_out,
+            int nc, int w, double side_d, double L_d, T rc2, T beta, T two_b_rpi, ScaledK K,
+            double inv_s, int split, double *__restrict__ f_out, double *__restrict__ phi_out,
             double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap, LJArgs lj,
             int *__restrict__ status)
 {
     using R4 = typename RowRec<T>::type;
     using T4 = typename Vec4<T>::type;
     using Acc = PairAcc<T, kVir, kLJ>;
-    constexpr int TG = 32 / G;                   // targets per warp
     constexpr int kCapR = 3072 / (int)sizeof(R4);  // records per staging buffer (3 KB)
     __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
     __shared__ Acc xacc[kWarps][32];             // partial sums handed between split warps
@@ -546,7 +672,8 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
         fence_mbar_init();
     }
     __syncwarp();
-    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2);
+    // (FP32: sigma^2 in units of S^2, S = inv_s^-1 the fixed-point step)
+    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2, sizeof(T) == 4 ? inv_s * inv_s : 1.0);
     // with split = 2 the warps 2t and 2t + 1 of a block share a group of targets, each taking
     // every other row of the stencil; their sums are added (in that order) at the end
     const int part = warp % split;
@@ -564,7 +691,6 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     const int cx = k % nc, cy = (k / nc) % nc, cz = k / (nc * nc);
     const double4_32a gi = pg[ii];
     const R4 pi = pr[ii];
-    const T side = (T)side_d;
     const T4 *ljrow = kLJ ? ljs + lj.tsort[ii] * lj.ntypes : nullptr;
 
     RowWalk wk;
@@ -586,7 +712,7 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     wk.in_row = false;
     wk.next_c0 = 0;
 
-    Acc acc{};
+    Acc acc{}, tot{}, comp{};     // sums of the current row, totals, Kahan compensation
     const T nb2 = sizeof(T) == 4 ? -beta * beta * T(kLog2e) : -beta * beta;
     uint32_t phase[2] = {0u, 0u};
     RowItem cur, nxt;
@@ -603,14 +729,10 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
         }
         if (!warp_wait(&bar[b], phase[b])) { ok = false; break; }
         phase[b] ^= 1u;
-        // FP32: y, z of the candidates are relative to their cell corner, which sits at
-        // (dy, dz) cells from the target's; FP64: global coordinates, shifted by L where the
-        // row wraps
-        T yi, zi;
-        if constexpr (sizeof(T) == 4) {
-            yi = pi.y - T(cur.dy) * side;
-            zi = pi.z - T(cur.dz) * side;
-        } else {
+        // FP64: global coordinates, shifted by L where the row wraps (FP32: fixed point,
+        // where the wrap is implicit)
+        T yi = T(0), zi = T(0);
+        if constexpr (sizeof(T) == 8) {
             yi = pi.y + (cy + cur.dy < 0 ? T(L_d) : (cy + cur.dy >= nc ? T(-L_d) : T(0)));
             zi = pi.z + (cz + cur.dz < 0 ? T(L_d) : (cz + cur.dz >= nc ? T(-L_d) : T(0)));
         }
@@ -621,16 +743,16 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
         for (int j = lo + g; j < hi; j += G) {
             {
                 const R4 pj = sb[j];
-                T dxv;
+                T dxv = T(0), dyv = T(0), dzv = T(0);
                 int tj = 0;
-                if constexpr (sizeof(T) == 4) {
-                    dxv = disp_x(pi, pj, sx, 0.f);
-                } else {
+                if constexpr (sizeof(T) == 8) {
                     // image shift of the candidate's part of the union
                     const int q = cur.c0 + j;
                     const T shift = q < cur.u.lenA ? T(L_d)
                                   : (q >= cur.u.lenA + cur.u.lenB ? T(-L_d) : T(0));
-                    dxv = disp_x(pi, pj, 0.0, shift);
+                    dxv = (pi.x + shift) - pj.x;
+                    dyv = yi - pj.y;
+                    dzv = zi - pj.z;
                 }
                 if constexpr (kLJ) {
                     const int q = cur.c0 + j;
@@ -639,10 +761,16 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
                                                                   : cur.u.sC + (q - cur.u.lenA - cur.u.lenB));
                     tj = lj.tsort[gidx];
                 }
-                pair_d<T, T4>(acc, dxv, yi - pj.y, zi - pj.z, (T)pj.w, rc2, beta, nb2,
-                              two_b_rpi, ljrow, tj);
+                if constexpr (sizeof(T) == 4)
+                    pair_s<T4>(acc, (int)(pi.x - pj.x), (int)(pi.y - pj.y), (int)(pi.z - pj.z),
+                               rec_q(pj), K, ljrow, tj);
+                else
+                    pair_d<T, T4>(acc, dxv, dyv, dzv, (T)rec_q(pj), rc2, beta, nb2, two_b_rpi,
+                                  ljrow, tj);
             }
         }
+        acc_add_rows(tot, comp, acc);
+        acc = Acc{};
         __syncwarp();
         cur = nxt;
         have_cur = have_nxt;
@@ -654,6 +782,11 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
         warp_wait(&bar[b ^ 1], phase[b ^ 1]);
         if (split == 1) return;
     }
+    acc = tot;
+    // FP32: back from fixed-point units (forces 1 / S^2, potential, Coulomb virial and
+    // Lennard-Jones force 1 / S), see pair_s
+    const double fsc = sizeof(T) == 4 ? inv_s * inv_s : 1.0;
+    const double psc = sizeof(T) == 4 ? inv_s : 1.0;
     // combine the G lanes of every target (lanes t G .. t G + G - 1)
 #pragma unroll
     for (int o = 1; o < G; o <<= 1) acc_shfl_add(acc, o);
@@ -664,23 +797,25 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
         if (part == 1 || !active) return;
         acc_add(acc, xacc[warp + 1][lane]);
     }
-    const double qi = (double)pi.w;
+    const double qi = (double)rec_q(pi);
     const bool mine = valid && g == 0;
+    const double phi_i = psc * (double)acc.phi;
     if (mine) {
-        double f[3] = {qi * (double)acc.fx, qi * (double)acc.fy, qi * (double)acc.fz};
+        double f[3] = {qi * fsc * (double)acc.fx, qi * fsc * (double)acc.fy,
+                       qi * fsc * (double)acc.fz};
         if constexpr (kLJ) {
-            f[0] += (double)acc.lj_f[0];
-            f[1] += (double)acc.lj_f[1];
-            f[2] += (double)acc.lj_f[2];
+            f[0] += psc * (double)acc.lj_f[0];
+            f[1] += psc * (double)acc.lj_f[1];
+            f[2] += psc * (double)acc.lj_f[2];
         }
         f_out[3 * (int64_t)i + 0] = f[0];
         f_out[3 * (int64_t)i + 1] = f[1];
         f_out[3 * (int64_t)i + 2] = f[2];
-        phi_out[i] = (double)acc.phi;
+        phi_out[i] = phi_i;
     }
-    const double e = warp_sum(mine ? qi * (double)acc.phi : 0.0);
+    const double e = warp_sum(mine ? qi * phi_i : 0.0);
     if (lane == 0) e_tile[grp] = e;
-    acc_store_tile(acc, mine, qi, lane, vir_tile, vcap, lj.e_tile, grp);
+    acc_store_tile(acc, mine, qi, lane, vir_tile, vcap, lj.e_tile, grp, psc);
 }
 
 // All pairs with the minimum image (boxes too small for a cell stencil): one tile of 32
@@ -801,13 +936,24 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         // of warps
         const int split = groups < 16 * (int64_t)p.num_sms ? 2 : 1;
         const typename RowRec<T>::type *pr;
-        if constexpr (sizeof(T) == 4) pr = ws.pl32;
+        if constexpr (sizeof(T) == 4) pr = ws.pu;
         else pr = ws.pg;
+        // FP32: constants in units of the fixed-point step S = L / 2^32 (see pair_s); near
+        // pairs are those within 2.5 mean particle spacings (at most r_c)
+        const double S = p.L / 4294967296.0;
+        const double spacing = cbrt(p.L * p.L * p.L / (double)(n > 0 ? n : 1));
+        const double rnear = fmin(2.5 * spacing, p.rc);
+        ScaledK K;
+        K.rc2s = (float)(p.rc * p.rc / (S * S));
+        K.rn2s = (float)(rnear * rnear / (S * S));
+        K.beta_s = (float)(p.beta * S);
+        K.nb2l_s = (float)(-p.beta * p.beta * S * S * 1.4426950408889634);
+        K.c_s = (float)(2.0 * p.beta / sqrt(kPi) * S);
+        K.cb2_s = (float)(2.0 * p.beta / sqrt(kPi) * S * (p.beta * S) * (p.beta * S));
         kern<<<(unsigned)((groups * split + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(
             pr, ws.pg, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc,
-            (int)n, p.nc, p.w, p.cell_side, p.L, rc2,
-            beta, tbr, (float)(p.L / 4294967296.0), split, ws.f_real, ws.phi_real, ws.e_tile,
-            vir, vcap, lj, p.d_status);
+            (int)n, p.nc, p.w, p.cell_side, p.L, rc2, beta, tbr, K, 1.0 / S, split, ws.f_real,
+            ws.phi_real, ws.e_tile, vir, vcap, lj, p.d_status);
     }
     p.launches += 1;
     return cudaGetLastError();
