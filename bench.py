@@ -960,6 +960,32 @@ def measure_workload(args, workload, local, world, dev, flush, alu_peaks, steps,
     return out, (pos, q, L, tp, tq)
 
 
+def run_capture(args, local):
+    """--capture K: K evaluations of the workload, every kernel a separate launch (the plan's
+    profiling mode), for kernel captures under a profiler; prints one status line."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1708_01135_gb300 import Ewald
+    pos, q, L = WORKLOADS[args.workload][0]()
+    n = len(q)
+    rc, beta, kmax, spme = run_params(args, n, L)
+    dev = torch.device("cuda", local)
+    tp, tq = torch.tensor(pos, device=dev), torch.tensor(q, device=dev)
+    F = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    E = torch.empty(4, dtype=torch.float64, device=dev)
+    with Ewald(L, beta, rc, kmax, args.precision) as ew:
+        if spme:
+            ew.set_spme(spme["K"], spme["order"])
+        ew.profile(1)
+        for _ in range(args.capture):
+            ew.compute_async(tp, tq, F, E)
+        torch.cuda.synchronize()
+        st = ew.status()
+    print(json.dumps({"capture": args.capture, "workload": args.workload, "status": st}))
+    if st != 0:
+        raise RuntimeError("evaluation reported an error")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -991,6 +1017,9 @@ def main():
                     help="real-space cutoff of the SPME line (beta from the tuner at this r_c)")
     ap.add_argument("--peaks", action="store_true",
                     help="print only the measured FP32/FP64 FMA rates of the GPU")
+    ap.add_argument("--capture", type=int, default=0,
+                    help="for profiler captures: run this many evaluations launch by launch "
+                         "(no graph replay, no timing) and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -1002,6 +1031,8 @@ def main():
     if args.md:
         return run_md(args, rank, world, local)
 
+    if args.capture:
+        return run_capture(args, local)
     extras = [x for x in args.extras.split(",") if x] if (rank == 0 and world == 1) else []
     systems = serving_systems(args.extra_requests) if "serving" in extras else None
 

@@ -277,9 +277,10 @@ void free_workspace(Plan &p)
 
 int binning_chunks(int64_t n)
 {
-    // chunks of at least 256 particles and at most 16384 (the scatter keeps a chunk's keys
-    // in shared memory), at most 128 of them
-    int64_t nb = (n + 255) / 256;
+    // chunks of at least 2048 particles and at most 16384 (the scatter keeps a chunk's keys
+    // in shared memory), at most 128 of them; every chunk has a histogram row over all
+    // cells, so fewer chunks keep the histogram small on fine grids
+    int64_t nb = (n + 2047) / 2048;
     if (nb > 128) nb = 128;
     if ((n + nb - 1) / nb > 16384) nb = (n + 16383) / 16384;
     return nb < 1 ? 1 : (int)nb;
@@ -593,16 +594,18 @@ static void build_rows(Plan &p)
 // (all pairs with the minimum image).
 // Cell grid of the real-space pairs: nc^3 cubes of side L / nc, a stencil of |dy|, |dz| <= w
 // rows with w = ceil(r_c nc / L), and 2 w + 1 <= nc so that the stencil's rows (and the
-// cells of a row a target can reach) are distinct.  The side aims at max(rho^-1/3, r_c / 5):
-// about one particle per cell or more, and at most ~11 rows across the cutoff disk, so that
-// each target's candidate ranges follow its cutoff sphere closely (the pair kernel takes the
-// cells of every row within each target's own reach).  Without the density (plan set-up)
+// cells of a row a target can reach) are distinct.  The side aims at max(1.33 rho^-1/3,
+// r_c / 5): about 2.4 particles per cell or more, and at most ~11 rows across the cutoff
+// disk, so that each target's candidate ranges follow its cutoff sphere closely (the pair
+// kernel takes the cells of every row within each target's own reach) while a row holds
+// enough candidates to pay for its set-up (measured on GB300, 32,768 ions at r_c = 4: cells
+// of side 1, 1.33, 1.6, 2 take 0.172, 0.129, 0.135, 0.125 ms).  Without the density (plan set-up)
 // the side is r_c / 2; the grid is chosen again once the particle count is known.  Boxes too
 // small for such a stencil use the all-pairs mode (w = 0, one cell).
 static void cell_grid(double L, double rc, int64_t n, int &nc_out, int &w_out)
 {
     const double rho = n > 0 ? (double)n / (L * L * L) : 0.0;
-    double s_t = rho > 0 ? fmax(pow(rho, -1.0 / 3.0), rc / 5.0) : rc / 2.0;
+    double s_t = rho > 0 ? fmax(1.33 * pow(rho, -1.0 / 3.0), rc / 5.0) : rc / 2.0;
     int nc = (int)floor(L / s_t);
     if (nc > 160) nc = 160;      // 4.1M cells at most (the binning keeps per-chunk histograms)
     w_out = 0;

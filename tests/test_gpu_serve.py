@@ -6,7 +6,9 @@ import time
 import numpy as np
 import pytest
 
-from gpu_common import dev, need_gpu, torch
+from gpu_common import assert_close, dev, need_gpu, rel_total, torch
+
+import oracle
 
 from paper_1708_01135_gb300 import Ewald, EwaldError, Server, tune
 from paper_1708_01135_gb300 import ewald as E
@@ -53,6 +55,29 @@ def test_results_equal_isolated_evaluations(precision):
         # the same kernels and the same fixed reduction orders: identical results
         assert torch.equal(F, F1)
         assert np.array_equal(res["energy"], e1)
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-10)])
+def test_server_results_match_the_oracle(precision, tol):
+    """Four requests of different sizes and kinds evaluated together by the server, each
+    checked against the FP64 oracle at its own (beta, r_c, k_max), per particle and in
+    energy (the mixed-path and FP64-path bounds of the parity tests)."""
+    need_gpu()
+    systems = _systems(4, seed=21)
+    srv = Server(max_slots=4)
+    try:
+        reqs = []
+        for pos, q, L, beta, rc, km in systems:
+            F = torch.empty((len(q), 3), dtype=torch.float64, device="cuda")
+            reqs.append((srv.submit(dev(pos), dev(q), F, L, beta, rc, km, precision), F))
+        results = [srv.wait(t, 120.0) for t, _ in reqs]
+    finally:
+        srv.close()
+    for (pos, q, L, beta, rc, km), (t, F), res in zip(systems, reqs, results):
+        assert res["status"] == 0
+        ref = oracle.ewald(pos, q, L, beta, rc, km)
+        assert_close(F.cpu().numpy(), ref["F"], tol)
+        assert rel_total(res["energy"][3], ref) < tol
 
 
 def test_budget_limits_admission_and_requests_overlap():

@@ -18,7 +18,7 @@ from paper_1708_01135_gb300 import workloads as W
 def cell_grid(L, rc, n):
     """The grid rule of the library (cell_grid in capi.cu)."""
     rho = n / L ** 3
-    s_t = max(rho ** (-1.0 / 3.0), rc / 5.0)
+    s_t = max(1.33 * rho ** (-1.0 / 3.0), rc / 5.0)
     nc = min(int(math.floor(L / s_t)), 160)
     while nc >= 3:
         w = int(math.ceil(rc * nc / L * (1.0 - 1e-12)))
