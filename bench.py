@@ -179,7 +179,10 @@ def tensor_flops(n, kmax):
 # ncu capture of the same workload, valid while that kernel's source file is unchanged (its
 # sha256 prefix is part of the key); the capture each figure comes from is named in
 # profiles/.  Kernels without a current capture report null.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/k_real_rows_random_2097152.md: 118.678784 MB read + 39.697408 MB written
+    ("real", "random_2097152", "mixed", "1a7f67fa7662124a"): 158376192,
+}
 
 
 def kernel_traffic(kernel, workload, precision):
@@ -741,13 +744,15 @@ def structure_factor_error(pos, q, L, m, S_gpu, modes=1024, seed=12):
 
 
 def kernel_rooflines(n, L, rc, kmax, precision, spme, times, pk, pk_kind, alu_peaks,
-                     workload):
+                     workload, alone=None):
     """Roofline of the three kernels that carry the method's work, each from its own CUDA
     event bracket (ewald_profile): achieved = algorithmic flop per launch / kernel time, where
     the algorithmic work is 40 flop per unique pair within r_c (real space), 8 flop per
     (particle, mode) term for the S(k) product and 10 for the back-scatter; peak = the measured
     bf16 dense rate (sustained) for tensor-core products, the measured FP32/FP64 FMA rate for
-    CUDA-core kernels.  The list is ordered by kernel time, the first entry dominating."""
+    CUDA-core kernels.  The list is ordered by kernel time, the first entry dominating.  With
+    `alone` (the kernel times of evaluations of one part only), every entry also gives the
+    kernel's rate when it does not share the SMs with the other branch."""
     fp64 = precision == "fp64"
     tc = precision in ("mixed", "mixed_bf16")
     alu = alu_peaks["fp64" if fp64 else "fp32"]
@@ -779,6 +784,11 @@ def kernel_rooflines(n, L, rc, kmax, precision, spme, times, pk, pk_kind, alu_pe
              "unit": "TFLOP/s", "frac": achieved / peak, "ms": ms, "work": work,
              "flop_per_launch": flop, "peak_kind": kind,
              "traffic": kernel_traffic(key, workload, precision)}
+        akey = {"real": "real_kernel", "forward": "recip_forward", "back": "backscatter_kernel"}[key]
+        ms_a = (alone or {}).get(akey)
+        if ms_a and ms_a > 0:
+            r["ms_alone"] = ms_a
+            r["frac_alone"] = flop / (ms_a * 1e-3) / 1e12 / peak
         if len(row) > 8 and bound == "tensor":
             issued = row[8]
             r["issued_tensor_flop"] = issued
@@ -803,14 +813,16 @@ def time_steps(ew, tp, tq, F, E, flush, stream, steps):
     return float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)]))
 
 
-def profiled_times(ew, tp, tq, F, E, flush, reps):
+def profiled_times(ew, tp, tq, F, E, flush, reps, parts=None):
     """Median kernel and stage times (ms) over `reps` evaluations with the plan's profiling
-    events recorded (those evaluations run launch by launch instead of as a graph)."""
+    events recorded (those evaluations run launch by launch instead of as a graph); parts
+    selects the real-space or reciprocal part alone (default: the whole evaluation)."""
+    from paper_1708_01135_gb300 import PART_ALL
     stage = {}
     ew.profile(1)
     for st in range(reps):
         flush.fill_(float(st))
-        ew.compute_async(tp, tq, F, E)
+        ew.compute_async(tp, tq, F, E, parts=PART_ALL if parts is None else parts)
         t, _ = ew.profile(-1)           # synchronises on the last stage event
         for k, v in t.items():
             stage.setdefault(k, []).append(v)
@@ -867,6 +879,12 @@ def measure_workload(args, workload, local, world, dev, flush, alu_peaks, steps,
         raise RuntimeError("timed evaluation reported an error")
     _, per_step = ew.profile(-1)        # kernels of one evaluation (one graph launch replays them)
     times = profiled_times(ew, tp, tq, F, E, flush, min(steps, 10))
+    # each branch alone (the other part not evaluated), for the kernels' own rates
+    from paper_1708_01135_gb300 import PART_REAL, PART_RECIP
+    alone = {"real_kernel": profiled_times(ew, tp, tq, F, E, flush, 3, PART_REAL).get("real_kernel")}
+    rt = profiled_times(ew, tp, tq, F, E, flush, 3, PART_RECIP)
+    alone["recip_forward"] = rt.get("recip_forward")
+    alone["backscatter_kernel"] = rt.get("backscatter_kernel")
     ms = max_over_ranks(ms, world, dev)
     value = whole_job_rate(n, ms, world)
     out = {"n": n, "L": L, "r_c": rc, "beta": beta, "k_max": kmax, "spme": spme,
@@ -893,7 +911,7 @@ def measure_workload(args, workload, local, world, dev, flush, alu_peaks, steps,
         Fg = np.array(hf)
     pk, pk_kind = peaks()
     roofs = kernel_rooflines(n, L, rc, kmax, args.precision, spme, times, pk, pk_kind,
-                             alu_peaks, workload)
+                             alu_peaks, workload, alone)
     out["roofline_kernels"] = roofs
     out["kernel_ms"] = {k: times.get(k) for k in ("real_kernel", "recip_forward",
                                                    "backscatter_kernel", "finalize_kernels",
