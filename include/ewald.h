@@ -179,6 +179,26 @@ int ewald_compute_virial_async(ewald_plan_t plan, int64_t n, const double *pos,
                                double *energy_dev, int parts, void *stream);
 
 /*
+ * ewald_set_near_pairs - arithmetic of the near real-space Coulomb pairs of every later
+ * evaluation of this plan (EWALD_MIXED, EWALD_MIXED_BF16 and EWALD_FP32 plans; FP64 plans
+ * accept the call and are unchanged).  Near pairs are those with 0 < d < r_near,
+ * r_near = min(2.5 (L^3 / n)^(1/3), r_c): the pairs that carry most of the force on a
+ * particle (the real-space sum of Eq. 4, Section 2).
+ *   double_float  0 (the default): FP32 with the exact r^2 (a first-order correction of the
+ *                 pair terms for the rounding of r^2), about 1e-7 of every pair term;
+ *                 1: double-float arithmetic (pairs of FP32 numbers), about 1e-8.
+ * Where the net force on a particle is a small sum of large pair forces (ionic crystals)
+ * the FP32 rounding of the near pairs is amplified: on a rock-salt crystal it gives about
+ * 1e-6 of the RMS force with 0 and 2e-7 with 1; on disordered systems both are below
+ * 2e-7.  Mode 1 costs a second scan of the staged candidates within r_near (measured on
+ * GB300, real-space kernel alone: +15 % at 2,097,152 ions, r_c = 10.7; +30 % at 262,144,
+ * r_c = 7.6; +80 % at 32,768, r_c = 4).  Returns EWALD_OK or EWALD_E_INVAL (NULL plan, a
+ * mode other than 0 or 1).  Synchronises the plan's streams; not thread-safe against a
+ * running evaluation of the same plan.
+ */
+int ewald_set_near_pairs(ewald_plan_t plan, int double_float);
+
+/*
  * ewald_set_lj - fuse short-range Lennard-Jones pairs into the real-space kernel of every
  * later evaluation of this plan (the paper's NaCl benchmark adds such a repulsion to the
  * Coulomb sum, Section 4; its parameters are not printed, so they are the caller's).

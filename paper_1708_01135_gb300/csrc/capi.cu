@@ -907,6 +907,18 @@ extern "C" int ewald_set_lj(ewald_plan_t plan, int ntypes, const double *epsilon
     return EWALD_OK;
 }
 
+extern "C" int ewald_set_near_pairs(ewald_plan_t plan, int double_float)
+{
+    if (!plan || (double_float != 0 && double_float != 1)) return EWALD_E_INVAL;
+    Plan &p = plan->p;
+    if (p.last_stream) cudaStreamSynchronize(p.last_stream);
+    if (p.side_stream) cudaStreamSynchronize(p.side_stream);
+    // the captured graph holds the kernel of the old mode
+    graph_reset(p);
+    p.near_df = double_float == 1;
+    return EWALD_OK;
+}
+
 extern "C" int ewald_set_spme(ewald_plan_t plan, int K, int order)
 {
     if (!plan || K < 0) return EWALD_E_INVAL;

@@ -100,6 +100,7 @@ struct Plan {
     int ncells = 1;
     double cell_side = 0;
     int real_tile = 2;           // lanes per target of the real-space cell kernel (2 or 4)
+    bool near_df = false;        // FP32 kernel: near Coulomb pairs in double-float arithmetic
     // Lennard-Jones pairs fused into the real-space kernel (off when lj_ntypes == 0)
     int lj_ntypes = 0;
     const int *lj_type = nullptr;    // caller-owned [n] types, caller order

@@ -9,6 +9,9 @@ small and decreasing, so a Horner evaluation in FP32 loses little to cancellatio
 
     python paper_1708_01135_gb300/csrc/fit_erfc.py      # prints the constants for realspace.cu
 
+The coefficients are printed as FP32 values (kErfcC) and their FP32 remainders (kErfcCL): the
+FP32 pair path uses the former, the double-float near-pair path the sum of both.
+
 The fit needs no GPU; it is run once, and its output is pasted into realspace.cu.
 tests/test_abi_cpu.py reads the constants back from the source and checks the error bound.
 """
@@ -21,9 +24,10 @@ XS = np.linspace(0.0, X, 60001)
 
 
 def _map(p):
+    # a and b rounded to FP32 first: the kernels form u from exactly these values
     tmin = 1.0 / (1.0 + p * X)
-    a = 2.0 / (1.0 - tmin)
-    return a, -1.0 - a * tmin
+    a = float(np.float32(2.0 / (1.0 - tmin)))
+    return a, float(np.float32(-1.0 - a * tmin))
 
 
 def fit(p, degree=DEGREE, iters=60):
@@ -51,6 +55,17 @@ def main():
     print(f"constexpr float kErfcP = {float(np.float32(p))!r}f;")
     print(f"constexpr float kErfcA = {float(np.float32(a))!r}f, kErfcB = {float(np.float32(b))!r}f;")
     print("constexpr float kErfcC[9] = {" + ", ".join(f"{float(v)!r}f" for v in c32) + "};")
+    # the remainders c - fp32(c): the near-pair path evaluates P in double-float arithmetic
+    lo = (c - c32.astype(np.float64)).astype(np.float32)
+    print("constexpr float kErfcCL[9] = {" + ", ".join(f"{float(v)!r}f" for v in lo) + "};")
+    hl = c32.astype(np.float64) + lo.astype(np.float64)
+    t = 1.0 / (1.0 + p * XS)
+    P = np.zeros_like(XS)
+    for v in hl[::-1]:
+        P = P * (a * t + b) + v
+    rel = np.abs(t * P * np.exp(-XS ** 2) / erfc(XS) - 1)
+    print(f"// max relative error with the double-float coefficients: {rel.max():.2e} on [0, {X}],"
+          f" {rel[XS <= 3.0].max():.2e} on [0, 3]")
     # the same evaluation in FP32 (the kernel's rounding of t, u and Horner)
     x32 = XS.astype(np.float32)
     t32 = (np.float32(1) / (np.float32(1) + np.float32(p) * x32)).astype(np.float32)

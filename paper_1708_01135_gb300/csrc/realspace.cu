@@ -295,15 +295,22 @@ __device__ __forceinline__ void load_lj_table(T4 *ljs, const LJArgs &lj, double 
 
 // erfc(x) ~= t exp(-x^2) P(u), t = 1 / (1 + p x), u = a t + b, x >= 0: a degree-8 polynomial
 // fitted to erfc(x) exp(x^2) / t on [0, 8] (csrc/fit_erfc.py: relative error 7.6e-9 in exact
-// arithmetic, 3.5e-7 with FP32 rounding of t, u and the Horner steps).  Beyond x = 8, where
+// arithmetic with the coefficients kErfcC + kErfcCL, 3.5e-7 with kErfcC and FP32 rounding of
+// t, u and the Horner steps).  Beyond x = 8, where
 // erfc < 1e-29, the polynomial is extrapolated; those pairs add nothing measurable.  The
 // caller supplies g = exp(-x^2), which the force term needs as well.
 constexpr float kErfcP = 0.3700000047683716f;
 constexpr float kErfcA = 2.675675630569458f, kErfcB = -1.675675630569458f;
 __constant__ float kErfcC[9] = {0.48547884821891785f, 0.31732580065727234f, 0.14685595035552979f,
-                             0.044840890914201736f, 0.006656186655163765f,
-                             -0.000744646938983351f, -0.00044474180322140455f,
-                             7.326921149797272e-06f, 2.4387149096583016e-05f};
+                             0.044840894639492035f, 0.006656187120825052f,
+                             -0.0007446469971910119f, -0.000444741832325235f,
+                             7.326919330807868e-06f, 2.438715091557242e-05f};
+// FP32 remainders of the fitted coefficients (the double-float near-pair path)
+__constant__ float kErfcCL[9] = {-3.958085414978996e-09f, -4.999006097961001e-09f,
+                              7.110552147082672e-10f, -1.6942547365061955e-09f,
+                              1.4456411068231034e-10f, 1.9717394383889086e-11f,
+                              4.030599205090413e-12f, -2.7720381396670497e-14f,
+                              8.240692741905142e-13f};
 
 __device__ __forceinline__ float erfc_from_gauss(float x, float g)
 {
@@ -377,16 +384,24 @@ __device__ __forceinline__ void pair(A &a, const T4 &p, T xi, T yi, T zi, T rc2,
 // FP64 (forces by 1 / S^2, potentials, the Coulomb virial and the Lennard-Jones force by
 // 1 / S).
 //
-// Near pairs (r below r_near, where the pair forces are large and the relative error of the
-// total force is set): the FP32 r^2 of the rounded components is off by ~2^-24, and for
-// ionic systems, whose net force is a small sum of large pair forces, that alone gives about
-// 1e-6 of the RMS force.  There the exact r^2 = sum D^2 is formed as an FP32 pair (hi + lo):
-// D = h + l with l = D - int(h) exact, h^2 = P + e with e = fma(h, h, -P), and TwoSum errors
-// of the sums; the force factor A = (erfc(beta r)/r + c g)/r^2 and the potential
-// e = erfc(beta r)/r are then corrected to first order in delta = r^2_exact - r^2:
-//   dA/d(r^2) = -(1.5 A + c beta^2 g) / r^2,   de/d(r^2) = -(e + c g) / (2 r^2),
-// c = 2 beta / sqrt(pi), g = exp(-beta^2 r^2) (delta / r^2 is ~2^-24, so the second order
-// is ~2^-48).
+// Near pairs (r below r_near, a few mean particle spacings) carry most of the pair forces
+// on an ion, and in ionic systems the net force is a small sum of large pair forces.  Two
+// treatments (the plan's near-pair mode):
+//   * FP32 (default): the pair in FP32 with the exact r^2.  The FP32 r^2 of the rounded
+//     components is off by ~2^-24, which alone gives about 1e-6 of the RMS force in a
+//     rock-salt crystal; so the exact r^2 = sum D^2 is formed as an FP32 pair (hi + lo):
+//     D = h + l with l = D - int(h) exact, h^2 = P + e with e = fma(h, h, -P), and TwoSum
+//     errors of the sums; the force factor A = (erfc(beta r)/r + c g)/r^2 and the potential
+//     e = erfc(beta r)/r are then corrected to first order in delta = r^2_exact - r^2:
+//       dA/d(r^2) = -(1.5 A + c beta^2 g) / r^2,   de/d(r^2) = -(e + c g) / (2 r^2),
+//     c = 2 beta / sqrt(pi), g = exp(-beta^2 r^2) (delta / r^2 is ~2^-24, so the second
+//     order is ~2^-48).  What remains is the FP32 rounding of the special functions and of
+//     the products, ~1e-7 of every pair.
+//   * double-float (kDF): the near pairs leave pair_s and are evaluated in double-float
+//     arithmetic (near_term), ~1e-8 of every pair, at the cost of a second scan of the
+//     staged candidates within r_near.
+// The split is taken on the FP32 r^2 of the rounded components in both passes, so every pair
+// is counted once.
 struct ScaledK {
     float rc2s, rn2s;       // r_c^2 and r_near^2 in units of S^2
     float beta_s;           // beta S
@@ -394,6 +409,18 @@ struct ScaledK {
     float c_s;              // 2 beta / sqrt(pi) S
     float cb2_s;            // c_s beta_s^2
 };
+
+// Double-float constants of the near pairs (value = h + l).
+struct NearK {
+    float beta_h, beta_l;   // beta S
+    float c_h, c_l;         // 2 beta / sqrt(pi) S
+    float rn2m;             // r_near^2 (physical units) with the range margin
+};
+
+__device__ __forceinline__ float r2_f32(float hx, float hy, float hz)
+{
+    return fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &err)
 {
@@ -420,33 +447,40 @@ __device__ __forceinline__ float r2_residual(int Dx, int Dy, int Dz, float hx, f
     return (s2 - r2) + ((t1 + t2) + ((ex + ey + ez) + cross));
 }
 
-template <class T4, class A>
+// One candidate of the FP32 pass.  Coulomb: 0 < r < r_c, with the first-order r^2 correction
+// below r_near; with kDF, r_near <= r < r_c only.  Lennard-Jones: 0 < r < r_c.
+template <bool kDF, class T4, class A>
 __device__ __forceinline__ void pair_s(A &a, int Dx, int Dy, int Dz, float qj, const ScaledK &K,
                                        const T4 *ljrow, int tj)
 {
     const float hx = (float)Dx, hy = (float)Dy, hz = (float)Dz;
-    const float r2 = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
-    if (r2 < K.rc2s && r2 > 0.0f) {
+    const float r2 = r2_f32(hx, hy, hz);
+    const bool coul = kDF ? (r2 < K.rc2s && r2 >= K.rn2s) : (r2 < K.rc2s && r2 > 0.0f);
+    if ((kDF && A::lj) ? (r2 < K.rc2s && r2 > 0.0f) : coul) {
         const float rinv = rsqrt_ftz(r2);
         const float rinv2 = rinv * rinv;
-        const float r = r2 * rinv;
-        const float g = ex2_ftz(K.nb2l_s * r2);
-        float e = erfc_from_gauss(K.beta_s * r, g) * rinv;
-        float fA = fmaf(K.c_s, g, e) * rinv2;
-        if (r2 < K.rn2s) {
-            const float rho = r2_residual(Dx, Dy, Dz, hx, hy, hz, r2) * rinv2;
-            fA = fmaf(-fmaf(1.5f, fA, K.cb2_s * g), rho, fA);
-            e = fmaf(-0.5f * fmaf(K.c_s, g, e), rho, e);
-        }
-        const float s = qj * fA;
-        a.phi += qj * e;
-        const float sx = s * hx, sy = s * hy, sz = s * hz;
-        a.fx += sx;
-        a.fy += sy;
-        a.fz += sz;
-        if constexpr (A::vir) {
-            a.w[0] += sx * hx; a.w[1] += sy * hy; a.w[2] += sz * hz;
-            a.w[3] += sx * hy; a.w[4] += sx * hz; a.w[5] += sy * hz;
+        if (!(kDF && A::lj) || coul) {
+            const float r = r2 * rinv;
+            const float g = ex2_ftz(K.nb2l_s * r2);
+            float e = erfc_from_gauss(K.beta_s * r, g) * rinv;
+            float fA = fmaf(K.c_s, g, e) * rinv2;
+            if constexpr (!kDF) {
+                if (r2 < K.rn2s) {
+                    const float rho = r2_residual(Dx, Dy, Dz, hx, hy, hz, r2) * rinv2;
+                    fA = fmaf(-fmaf(1.5f, fA, K.cb2_s * g), rho, fA);
+                    e = fmaf(-0.5f * fmaf(K.c_s, g, e), rho, e);
+                }
+            }
+            const float s = qj * fA;
+            a.phi += qj * e;
+            const float sx = s * hx, sy = s * hy, sz = s * hz;
+            a.fx += sx;
+            a.fy += sy;
+            a.fz += sz;
+            if constexpr (A::vir) {
+                a.w[0] += sx * hx; a.w[1] += sy * hy; a.w[2] += sz * hz;
+                a.w[3] += sx * hy; a.w[4] += sx * hz; a.w[5] += sy * hz;
+            }
         }
         if constexpr (A::lj) {
             // the pair table holds sigma^2 in units of S^2 (load_lj_table's scale)
@@ -464,6 +498,206 @@ __device__ __forceinline__ void pair_s(A &a, int Dx, int Dy, int Dz, float qj, c
             }
         }
     }
+}
+
+// ---- double-float arithmetic: a value is the unevaluated sum h + l of two FP32 numbers -----
+// (Dekker's and Knuth's error-free transformations: TwoSum, and TwoProduct with an FMA.)
+struct df { float h, l; };
+
+__device__ __forceinline__ df df_fast(float a, float b)     // |a| >= |b|
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ df df_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df df_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    const df s = df_sum(a.h, b.h);
+    return df_fast(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    const df p = df_prod(a.h, b.h);
+    return df_fast(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
+}
+__device__ __forceinline__ df df_mulf(df a, float b)
+{
+    const df p = df_prod(a.h, b);
+    return df_fast(p.h, fmaf(a.l, b, p.l));
+}
+__device__ __forceinline__ df df_from_int(int v)
+{
+    const float h = (float)v;
+    return {h, (float)(v - __float2int_rn(h))};
+}
+
+// 2^(j/64), j = 0..63, as double-float pairs (filled once per block from FP64 exp2)
+__device__ __forceinline__ void load_exp2_table(float2 *tab)
+{
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+        const double v = exp2((double)j / 64.0);
+        const float h = (float)v;
+        tab[j] = make_float2(h, (float)(v - (double)h));
+    }
+}
+
+// exp(-x^2) for a double-float x, 0 <= x < 9: 2^y with y = -x^2 log2(e) in double-float,
+// y = (64 m + j + f) / 64 with |f| <= 1/2, 2^(j/64) from the table and
+// 2^(f/64) - 1 = w (1 + w/2 + w^2/6 + w^3/24), w = f ln2 / 64 (|w| < 0.0055, the series'
+// remainder < 4e-14).
+__device__ __forceinline__ df gauss_df(df x, const float2 *tab)
+{
+    const df x2 = df_mul(x, x);
+    // -log2(e) = -(1.4426950 + 1.9259630e-8) in double-float
+    const df y = df_mul(x2, df{-1.44269502162933349609375f, -1.925963033500011079e-8f});
+    const float zh = y.h * 64.0f, zl = y.l * 64.0f;          // exact scalings
+    const float nz = rintf(zh);
+    const float f = (zh - nz) + zl;                          // zh - nz is exact
+    const int n = (int)nz;
+    const int j = n & 63, m = (n - j) >> 6;                  // n = 64 m + j, 0 <= j < 64
+    const float w = f * 0.010830424696249145f;               // ln(2) / 64
+    const float d = w * fmaf(w, fmaf(w, fmaf(w, 0.041666666666666664f, 0.16666666666666666f), 0.5f), 1.0f);
+    const float2 t = tab[j];
+    df g = df_fast(t.x, fmaf(t.x, d, t.y));
+    const float sc = __int_as_float((127 + m) << 23);        // 2^m, m >= -117 for x < 9
+    g.h *= sc;
+    g.l *= sc;
+    return g;
+}
+
+// Terms of one near pair: force components and potential (double-float), virial (FP32).
+template <bool kVir> struct NearTerm {
+    df fx{0.f, 0.f}, fy{0.f, 0.f}, fz{0.f, 0.f}, phi{0.f, 0.f};
+    float w[kVir ? 6 : 1] = {};
+};
+
+// The Coulomb terms of a near pair (0 < r < r_near) in double-float arithmetic, from the
+// integer displacement D (units of S) and the partner charge qj.
+template <bool kVir>
+__device__ __forceinline__ NearTerm<kVir> near_term(int Dx, int Dy, int Dz, float qj,
+                                                    const NearK &N, const float2 *tab)
+{
+    // D = h + l exactly; r^2 = sum h^2 + sum (2 h l + l^2), the first sum with its rounding
+    // errors (|l| <= 128, so the second sum is ~2^-23 of r^2 and its own rounding negligible)
+    const df dx = df_from_int(Dx), dy = df_from_int(Dy), dz = df_from_int(Dz);
+    const df px = df_prod(dx.h, dx.h), py = df_prod(dy.h, dy.h), pz = df_prod(dz.h, dz.h);
+    const df s1 = df_sum(px.h, py.h), s2 = df_sum(s1.h, pz.h);
+    const float cross = fmaf(2.0f * dx.h, dx.l, dx.l * dx.l) + fmaf(2.0f * dy.h, dy.l, dy.l * dy.l) +
+                        fmaf(2.0f * dz.h, dz.l, dz.l * dz.l);
+    const df r2 = df_fast(s2.h, (s1.l + s2.l) + ((px.l + py.l + pz.l) + cross));
+    // 1 / r: the FP32 estimate y and one Newton step on the double-float residual
+    // e = 1 - r^2 y^2 (1 / r = y (1 + e / 2), the neglected term is 3 e^2 / 8 ~ 2^-44)
+    const float y = rsqrt_ftz(r2.h);
+    const df y2 = df_prod(y, y);
+    const df p = df_prod(r2.h, y2.h);
+    const float res = ((1.0f - p.h) - p.l) - fmaf(r2.h, y2.l, r2.l * y2.h);
+    const df rinv = df_fast(y, 0.5f * y * res);
+    const df rinv2 = df_mul(rinv, rinv);
+    const df x = df_mul(df{N.beta_h, N.beta_l}, df_mul(r2, rinv));   // beta r
+    const df g = gauss_df(x, tab);                                   // exp(-beta^2 r^2)
+    // erfc(x) = t g P(a t + b), t = 1 / (1 + p x)
+    const df pxp = df_prod(kErfcP, x.h);
+    df dd = df_sum(1.0f, pxp.h);
+    dd = df_fast(dd.h, dd.l + (pxp.l + kErfcP * x.l));
+    const float th = rcp_ftz(dd.h);
+    const float et = fmaf(-th, dd.l, fmaf(-th, dd.h, 1.0f));  // 1 - d th
+    const df t = df_fast(th, th * et);
+    const df u = df_add(df_mulf(t, kErfcA), df{kErfcB, 0.0f});
+    // Horner: the small high-order terms (k >= 4) in FP32, the rest in double-float
+    float q = kErfcC[8];
+#pragma unroll
+    for (int k = 7; k >= 4; --k) q = fmaf(q, u.h, kErfcC[k]);
+    df P = df_fast(q, 0.0f);
+#pragma unroll
+    for (int k = 3; k >= 0; --k) P = df_add(df_mul(P, u), df{kErfcC[k], kErfcCL[k]});
+    const df e = df_mul(df_mul(df_mul(t, P), g), rinv);     // erfc(beta r) / r
+    const df A = df_mul(df_add(e, df_mul(df{N.c_h, N.c_l}, g)), rinv2);
+    const df sq = df_mulf(A, qj);
+    NearTerm<kVir> o;
+    o.fx = df_mul(sq, dx);
+    o.fy = df_mul(sq, dy);
+    o.fz = df_mul(sq, dz);
+    o.phi = df_mulf(e, qj);
+    if constexpr (kVir) {
+        o.w[0] = o.fx.h * dx.h; o.w[1] = o.fy.h * dy.h; o.w[2] = o.fz.h * dz.h;
+        o.w[3] = o.fx.h * dy.h; o.w[4] = o.fx.h * dz.h; o.w[5] = o.fy.h * dz.h;
+    }
+    return o;
+}
+
+template <bool kVir>
+__device__ __forceinline__ void near_add(NearTerm<kVir> &a, const NearTerm<kVir> &o)
+{
+    a.fx = df_add(a.fx, o.fx);
+    a.fy = df_add(a.fy, o.fy);
+    a.fz = df_add(a.fz, o.fz);
+    a.phi = df_add(a.phi, o.phi);
+    if constexpr (kVir) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) a.w[c] += o.w[c];
+    }
+}
+
+template <bool kVir>
+__device__ __forceinline__ NearTerm<kVir> near_shfl(const NearTerm<kVir> &v, int src)
+{
+    NearTerm<kVir> o;
+    o.fx = {__shfl_sync(0xffffffffu, v.fx.h, src), __shfl_sync(0xffffffffu, v.fx.l, src)};
+    o.fy = {__shfl_sync(0xffffffffu, v.fy.h, src), __shfl_sync(0xffffffffu, v.fy.l, src)};
+    o.fz = {__shfl_sync(0xffffffffu, v.fz.h, src), __shfl_sync(0xffffffffu, v.fz.l, src)};
+    o.phi = {__shfl_sync(0xffffffffu, v.phi.h, src), __shfl_sync(0xffffffffu, v.phi.l, src)};
+    if constexpr (kVir) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) o.w[c] = __shfl_sync(0xffffffffu, v.w[c], src);
+    }
+    return o;
+}
+
+// Evaluate the first cnt (<= 32) queued near pairs of a warp, one per lane, and add every
+// target's terms into its lane's sums: the entries of one target are added in queue order
+// by the first lane that holds one of them, and that sum is passed to the target's lane.
+// (ldr: 32 ints of shared memory per warp.)  Whole warp.
+template <bool kVir>
+__device__ __noinline__ void near_flush(NearTerm<kVir> &acc, const int4 *qd, const int *qt,
+                                           int *ldr, int cnt, int lane, const NearK &N,
+                                           const float2 *tab)
+{
+    const bool has = lane < cnt;
+    const int tgt = has ? qt[lane] : -1 - lane;      // lanes without an entry: own groups
+    NearTerm<kVir> v;
+    if (has) {
+        const int4 e = qd[lane];
+        v = near_term<kVir>(e.x, e.y, e.z, __int_as_float(e.w), N, tab);
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, tgt);
+    const bool leader = (grp & ((1u << lane) - 1u)) == 0u;
+    const int rounds = __reduce_max_sync(0xffffffffu, __popc(grp));
+    // the leader adds its group's later entries into its own terms (a leader's terms are
+    // never read by another group, a member's only by its leader, before any change)
+    unsigned rest = grp & (grp - 1u);
+    for (int k = 1; k < rounds; ++k) {
+        const int src = rest ? __ffs(rest) - 1 : lane;
+        const NearTerm<kVir> o = near_shfl<kVir>(v, src);
+        if (leader && rest) near_add<kVir>(v, o);
+        rest &= rest - 1u;
+    }
+    ldr[lane] = -1;
+    __syncwarp();
+    if (has && leader) ldr[tgt] = lane;
+    __syncwarp();
+    const int from = ldr[lane];
+    const NearTerm<kVir> o = near_shfl<kVir>(v, from >= 0 ? from : lane);
+    if (from >= 0) near_add<kVir>(acc, o);
+    __syncwarp();
 }
 
 // Compensated (Kahan) addition of the row sums of the forces and potential into the totals;
@@ -539,6 +773,7 @@ struct RowItem {
     RowUnion u;
     int c0, cnt;
     int off0, off1;
+    int noff0, noff1;           // this target's near range (reach r_near) in the union
 };
 
 // Issue the bulk copies of an item into dst (lane 0 only): the parts of the union that the
@@ -568,6 +803,7 @@ struct RowWalk {
     int cx, cy, cz;             // this target's cell
     float xl, yl, zl;           // this target's position inside its cell
     float sidef, inv_side, rc2m;
+    float rn2m;                 // r_near^2 with the margin (0: no near ranges)
     bool valid;
     const int *__restrict__ cell_start;
     // position in the stencil
@@ -592,7 +828,7 @@ struct RowWalk {
             const float gy = dy > 0 ? dy * sidef - yl : (dy < 0 ? yl - (dy + 1) * sidef : 0.f);
             const float gz = dz > 0 ? dz * sidef - zl : (dz < 0 ? zl - (dz + 1) * sidef : 0.f);
             const float d2 = gy * gy + gz * gz;
-            int a0 = 1 << 30, a1 = -(1 << 30);
+            int a0 = 1 << 30, a1 = -(1 << 30), n0 = 1 << 30, n1 = -(1 << 30);
             if (valid && d2 < rc2m) {
                 // (approximate square root: a relative error of 2^-22 is inside the margin)
                 const float reach = sqrt_ftz(rc2m - d2);
@@ -602,6 +838,13 @@ struct RowWalk {
                 b1 = b1 > w ? w : b1;
                 a0 = cx + b0;
                 a1 = cx + b1;
+                if (d2 < rn2m) {
+                    const float rn = sqrt_ftz(rn2m - d2);
+                    int e0 = __float2int_rd((xl - rn) * inv_side);
+                    int e1 = __float2int_rd((xl + rn) * inv_side);
+                    n0 = cx + (e0 < b0 ? b0 : e0);
+                    n1 = cx + (e1 > b1 ? b1 : e1);
+                }
             }
             const int A0 = __reduce_min_sync(0xffffffffu, a0);
             const int A1 = __reduce_max_sync(0xffffffffu, a1);
@@ -625,6 +868,12 @@ struct RowWalk {
             } else {
                 row.off0 = row.off1 = 0;
             }
+            if (n0 <= n1) {
+                row.noff0 = union_off(u, cs, nc, n0);
+                row.noff1 = union_off(u, cs, nc, n1 + 1);
+            } else {
+                row.noff0 = row.noff1 = 0;
+            }
             return true;
         }
     }
@@ -646,22 +895,31 @@ struct RowWalk {
     }
 };
 
-template <class T, int G, bool kVir, bool kLJ>
-__global__ void __launch_bounds__(kWarps * 32, sizeof(T) == 4 && !kVir && !kLJ ? 7 : 1)
+template <class T, int G, bool kVir, bool kLJ, bool kDF>
+__global__ void __launch_bounds__(kWarps * 32, sizeof(T) == 4 && !kVir && !kLJ ? (kDF ? 6 : 7) : 1)
 k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *__restrict__ pg,
             const int *__restrict__ key_sorted, const int *__restrict__ cell_start,
             const int2 *__restrict__ tiles, const int *__restrict__ tile_total, int n,
             int nc, int w, double side_d, double L_d, T rc2, T beta, T two_b_rpi, ScaledK K,
-            double inv_s, int split, double *__restrict__ f_out, double *__restrict__ phi_out,
-            double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap, LJArgs lj,
-            int *__restrict__ status)
+            NearK NK, double inv_s, int split, double *__restrict__ f_out,
+            double *__restrict__ phi_out, double *__restrict__ e_tile,
+            double *__restrict__ vir_tile, int64_t vcap, LJArgs lj, int *__restrict__ status)
 {
     using R4 = typename RowRec<T>::type;
     using T4 = typename Vec4<T>::type;
     using Acc = PairAcc<T, kVir, kLJ>;
+    constexpr bool kFP32 = sizeof(T) == 4;
+    constexpr bool kNear = kFP32 && kDF;          // near pairs in double-float
     constexpr int kCapR = 3072 / (int)sizeof(R4);  // records per staging buffer (3 KB)
     __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
     __shared__ Acc xacc[kWarps][32];             // partial sums handed between split warps
+    __shared__ double4_32a xsum[kFP32 ? kWarps : 1][32];   // (the Coulomb sums, FP32 kernel)
+    __shared__ float2 ex2tab[kNear ? 64 : 1];
+    // near-pair queue of every warp: (D, q bits) and target lane, up to 63 entries; group
+    // leaders of a flush
+    __shared__ int4 nq_d[kNear ? kWarps : 1][kNear ? 64 : 1];
+    __shared__ int nq_t[kNear ? kWarps : 1][kNear ? 64 : 1];
+    __shared__ int nq_l[kNear ? kWarps : 1][kNear ? 32 : 1];
     __shared__ __align__(128) R4 stage[kWarps][2][kCapR];
     __shared__ __align__(8) uint64_t bars[kWarps][2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -671,9 +929,10 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    __syncwarp();
+    if constexpr (kNear) load_exp2_table(ex2tab);
+    __syncthreads();
     // (FP32: sigma^2 in units of S^2, S = inv_s^-1 the fixed-point step)
-    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2, sizeof(T) == 4 ? inv_s * inv_s : 1.0);
+    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2, kFP32 ? inv_s * inv_s : 1.0);
     // with split = 2 the warps 2t and 2t + 1 of a block share a group of targets, each taking
     // every other row of the stencil; their sums are added (in that order) at the end
     const int part = warp % split;
@@ -705,6 +964,7 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     wk.sidef = (float)side_d;
     wk.inv_side = (float)(1.0 / side_d);
     wk.rc2m = (float)rc2 * (1.0f + 1e-5f);
+    wk.rn2m = kNear ? NK.rn2m : 0.0f;
     wk.valid = valid;
     wk.cell_start = cell_start;
     wk.rowctr = 0;
@@ -712,97 +972,179 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     wk.in_row = false;
     wk.next_c0 = 0;
 
-    Acc acc{}, tot{}, comp{};     // sums of the current row, totals, Kahan compensation
-    const T nb2 = sizeof(T) == 4 ? -beta * beta * T(kLog2e) : -beta * beta;
+    // Staged walk over the rows of a RowWalk: item(sb, lo, hi, cur) for every staged item,
+    // with [lo, hi) this target's part of the chunk in the buffer sb.  The two buffers and
+    // their barrier phases carry over from one walk to the next.  False when a bounded wait
+    // gave up.
     uint32_t phase[2] = {0u, 0u};
-    RowItem cur, nxt;
-    bool have_cur = active && wk.next<kCapR>(cur);
-    bool ok = true;
-    if (have_cur && lane == 0) issue_item(cur, pr, stage[warp][0], &bar[0]);
     int b = 0;
-    while (have_cur) {
-        const bool have_nxt = wk.next<kCapR>(nxt);
-        if (have_nxt && lane == 0) {
-            // the other buffer was fully read before the last __syncwarp of the loop
+    auto walk = [&](RowWalk &rw, auto &&item) -> bool {
+        RowItem cur, nxt;
+        bool have_cur = active && rw.template next<kCapR>(cur);
+        if (have_cur && lane == 0) {
+            // (the buffer may have been read by the last walk, before its last __syncwarp)
             fence_proxy_async();
-            issue_item(nxt, pr, stage[warp][b ^ 1], &bar[b ^ 1]);
+            issue_item(cur, pr, stage[warp][b], &bar[b]);
         }
-        if (!warp_wait(&bar[b], phase[b])) { ok = false; break; }
-        phase[b] ^= 1u;
-        // FP64: global coordinates, shifted by L where the row wraps (FP32: fixed point,
-        // where the wrap is implicit)
-        T yi = T(0), zi = T(0);
-        if constexpr (sizeof(T) == 8) {
-            yi = pi.y + (cy + cur.dy < 0 ? T(L_d) : (cy + cur.dy >= nc ? T(-L_d) : T(0)));
-            zi = pi.z + (cz + cur.dz < 0 ? T(L_d) : (cz + cur.dz >= nc ? T(-L_d) : T(0)));
+        while (have_cur) {
+            const bool have_nxt = rw.template next<kCapR>(nxt);
+            if (have_nxt && lane == 0) {
+                // the other buffer was fully read before the last __syncwarp of the loop
+                fence_proxy_async();
+                issue_item(nxt, pr, stage[warp][b ^ 1], &bar[b ^ 1]);
+            }
+            if (!warp_wait(&bar[b], phase[b])) {
+                // let a copy still in flight land before the warp leaves (bounded)
+                if (have_nxt) warp_wait(&bar[b ^ 1], phase[b ^ 1]);
+                return false;
+            }
+            phase[b] ^= 1u;
+            const int lo = (cur.off0 > cur.c0 ? cur.off0 : cur.c0) - cur.c0;
+            const int hi = (cur.off1 < cur.c0 + cur.cnt ? cur.off1 : cur.c0 + cur.cnt) - cur.c0;
+            item(stage[warp][b], lo, hi, cur);
+            __syncwarp();
+            cur = nxt;
+            have_cur = have_nxt;
+            b ^= 1;
         }
-        // this target's part of the chunk, in buffer indices
-        const int lo = (cur.off0 > cur.c0 ? cur.off0 : cur.c0) - cur.c0;
-        const int hi = (cur.off1 < cur.c0 + cur.cnt ? cur.off1 : cur.c0 + cur.cnt) - cur.c0;
-        const R4 *sb = stage[warp][b];
+        return true;
+    };
+
+    Acc acc{}, tot{}, comp{};     // sums of the current row, totals, Kahan compensation
+    // Double-float near pairs (kNear): the near pairs (r < r_near) of every staged item are
+    // queued in shared memory in the order they are found (candidate step, then lane) and
+    // evaluated 32 at a time, one per lane; each target's results are added in queue order.
+    NearTerm<kVir> nr;            // the Coulomb sums of this target (double-float), its virial
+    int4 *qd = kNear ? nq_d[warp] : nullptr;
+    int *qt = kNear ? nq_t[warp] : nullptr;
+    int qn = 0;
+    bool ok = walk(wk, [&](const R4 *sb, int lo, int hi, const RowItem &cur) {
         for (int j = lo + g; j < hi; j += G) {
-            {
-                const R4 pj = sb[j];
-                T dxv = T(0), dyv = T(0), dzv = T(0);
-                int tj = 0;
-                if constexpr (sizeof(T) == 8) {
-                    // image shift of the candidate's part of the union
-                    const int q = cur.c0 + j;
-                    const T shift = q < cur.u.lenA ? T(L_d)
-                                  : (q >= cur.u.lenA + cur.u.lenB ? T(-L_d) : T(0));
-                    dxv = (pi.x + shift) - pj.x;
-                    dyv = yi - pj.y;
-                    dzv = zi - pj.z;
-                }
-                if constexpr (kLJ) {
-                    const int q = cur.c0 + j;
-                    const int gidx = q < cur.u.lenA ? cur.u.sA + q
-                                   : (q < cur.u.lenA + cur.u.lenB ? cur.u.sB + (q - cur.u.lenA)
-                                                                  : cur.u.sC + (q - cur.u.lenA - cur.u.lenB));
-                    tj = lj.tsort[gidx];
-                }
-                if constexpr (sizeof(T) == 4)
-                    pair_s<T4>(acc, (int)(pi.x - pj.x), (int)(pi.y - pj.y), (int)(pi.z - pj.z),
-                               rec_q(pj), K, ljrow, tj);
-                else
-                    pair_d<T, T4>(acc, dxv, dyv, dzv, (T)rec_q(pj), rc2, beta, nb2, two_b_rpi,
-                                  ljrow, tj);
+            const R4 pj = sb[j];
+            int tj = 0;
+            if constexpr (kLJ) {
+                const int q = cur.c0 + j;
+                const int gidx = q < cur.u.lenA ? cur.u.sA + q
+                               : (q < cur.u.lenA + cur.u.lenB ? cur.u.sB + (q - cur.u.lenA)
+                                                              : cur.u.sC + (q - cur.u.lenA - cur.u.lenB));
+                tj = lj.tsort[gidx];
+            }
+            if constexpr (kFP32) {
+                pair_s<kDF, T4>(acc, (int)(pi.x - pj.x), (int)(pi.y - pj.y), (int)(pi.z - pj.z),
+                                rec_q(pj), K, ljrow, tj);
+            } else {
+                // global coordinates, shifted by L where the row wraps
+                const T yi = pi.y + (cy + cur.dy < 0 ? T(L_d) : (cy + cur.dy >= nc ? T(-L_d) : T(0)));
+                const T zi = pi.z + (cz + cur.dz < 0 ? T(L_d) : (cz + cur.dz >= nc ? T(-L_d) : T(0)));
+                const int q = cur.c0 + j;
+                const T shift = q < cur.u.lenA ? T(L_d)
+                              : (q >= cur.u.lenA + cur.u.lenB ? T(-L_d) : T(0));
+                pair_d<T, T4>(acc, (pi.x + shift) - pj.x, yi - pj.y, zi - pj.z, (T)rec_q(pj), rc2,
+                              beta, -beta * beta, two_b_rpi, ljrow, tj);
             }
         }
         acc_add_rows(tot, comp, acc);
         acc = Acc{};
-        __syncwarp();
-        cur = nxt;
-        have_cur = have_nxt;
-        b ^= 1;
+        if constexpr (kNear) {
+            const int nlo = (cur.noff0 > cur.c0 ? cur.noff0 : cur.c0) - cur.c0;
+            const int nhi = (cur.noff1 < cur.c0 + cur.cnt ? cur.noff1 : cur.c0 + cur.cnt) - cur.c0;
+            const int len = nhi > nlo ? nhi - nlo : 0;
+            const int steps = __reduce_max_sync(0xffffffffu, len);
+            for (int it = 0; it < steps; ++it) {
+                bool hit = false;
+                int4 e = make_int4(0, 0, 0, 0);
+                if (it < len) {
+                    const R4 pj = sb[nlo + it];
+                    e = make_int4((int)(pi.x - pj.x), (int)(pi.y - pj.y), (int)(pi.z - pj.z),
+                                  (int)pj.w);
+                    const float r2f = r2_f32((float)e.x, (float)e.y, (float)e.z);
+                    hit = r2f < K.rn2s && r2f > 0.0f;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) {
+                    const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                    qd[pos] = e;
+                    qt[pos] = lane;
+                }
+                qn += __popc(m);
+                if (qn >= 32) {
+                    __syncwarp();
+                    near_flush<kVir>(nr, qd, qt, nq_l[warp], 32, lane, NK, ex2tab);
+                    qn -= 32;
+                    if (lane < qn) { qd[lane] = qd[32 + lane]; qt[lane] = qt[32 + lane]; }
+                    __syncwarp();
+                }
+            }
+        }
+    });
+    if constexpr (kFP32) {
+        if (kNear && ok && qn > 0) {
+            __syncwarp();
+            near_flush<kVir>(nr, qd, qt, nq_l[warp], qn, lane, NK, ex2tab);
+        }
+        // the FP32 totals (less their Kahan compensation) join the near sums
+        nr.fx = df_add(nr.fx, df_sum(tot.fx, -comp.fx));
+        nr.fy = df_add(nr.fy, df_sum(tot.fy, -comp.fy));
+        nr.fz = df_add(nr.fz, df_sum(tot.fz, -comp.fz));
+        nr.phi = df_add(nr.phi, df_sum(tot.phi, -comp.phi));
+        if constexpr (kVir) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) nr.w[c] += tot.w[c];
+        }
     }
     if (!ok) {
         if (lane == 0) atomicOr(status, kStTimeout);
-        // let a copy still in flight land before the warp leaves (bounded)
-        warp_wait(&bar[b ^ 1], phase[b ^ 1]);
         if (split == 1) return;
     }
     acc = tot;
     // FP32: back from fixed-point units (forces 1 / S^2, potential, Coulomb virial and
     // Lennard-Jones force 1 / S), see pair_s
-    const double fsc = sizeof(T) == 4 ? inv_s * inv_s : 1.0;
-    const double psc = sizeof(T) == 4 ? inv_s : 1.0;
+    const double fsc = kFP32 ? inv_s * inv_s : 1.0;
+    const double psc = kFP32 ? inv_s : 1.0;
+    // the Coulomb sums in FP64 (FP32: the FP32 totals and the near pairs, in double-float)
+    double sx, sy, sz, sp;
+    if constexpr (kFP32) {
+        sx = (double)nr.fx.h + (double)nr.fx.l;
+        sy = (double)nr.fy.h + (double)nr.fy.l;
+        sz = (double)nr.fz.h + (double)nr.fz.l;
+        sp = (double)nr.phi.h + (double)nr.phi.l;
+        if constexpr (kVir) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) acc.w[c] = nr.w[c];
+        }
+    } else {
+        sx = acc.fx; sy = acc.fy; sz = acc.fz; sp = acc.phi;
+    }
     // combine the G lanes of every target (lanes t G .. t G + G - 1)
 #pragma unroll
-    for (int o = 1; o < G; o <<= 1) acc_shfl_add(acc, o);
+    for (int o = 1; o < G; o <<= 1) {
+        acc_shfl_add(acc, o);
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    }
     if (split == 2) {
         // every warp of the block reaches this barrier (none has returned with split = 2)
-        if (part == 1) xacc[warp][lane] = acc;
+        if (part == 1) {
+            xacc[warp][lane] = acc;
+            if constexpr (kFP32) xsum[warp][lane] = double4_32a{sx, sy, sz, sp};
+        }
         __syncthreads();
         if (part == 1 || !active) return;
         acc_add(acc, xacc[warp + 1][lane]);
+        if constexpr (kFP32) {
+            const double4_32a o = xsum[warp + 1][lane];
+            sx += o.x; sy += o.y; sz += o.z; sp += o.w;
+        } else {
+            sx = acc.fx; sy = acc.fy; sz = acc.fz; sp = acc.phi;
+        }
     }
     const double qi = (double)rec_q(pi);
     const bool mine = valid && g == 0;
-    const double phi_i = psc * (double)acc.phi;
+    const double phi_i = psc * sp;
     if (mine) {
-        double f[3] = {qi * fsc * (double)acc.fx, qi * fsc * (double)acc.fy,
-                       qi * fsc * (double)acc.fz};
+        double f[3] = {qi * fsc * sx, qi * fsc * sy, qi * fsc * sz};
         if constexpr (kLJ) {
             f[0] += psc * (double)acc.lj_f[0];
             f[1] += psc * (double)acc.lj_f[1];
@@ -930,7 +1272,9 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
             pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap, lj,
             p.d_status);
     } else {
-        auto kern = k_real_rows<T, 1, kVir, kLJ>;
+        // (the FP64 kernel has no near-pair modes: one instantiation)
+        auto kern = (sizeof(T) == 4 && p.near_df) ? k_real_rows<T, 1, kVir, kLJ, sizeof(T) == 4>
+                                                  : k_real_rows<T, 1, kVir, kLJ, false>;
         const int64_t groups = real_tile_capacity(p, n);
         // two warps per group of targets when one warp per group would leave the SMs short
         // of warps
@@ -950,9 +1294,17 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         K.nb2l_s = (float)(-p.beta * p.beta * S * S * 1.4426950408889634);
         K.c_s = (float)(2.0 * p.beta / sqrt(kPi) * S);
         K.cb2_s = (float)(2.0 * p.beta / sqrt(kPi) * S * (p.beta * S) * (p.beta * S));
+        // double-float constants of the near pairs, and their reach (with the range margin)
+        NearK NK;
+        const double bs = p.beta * S, cs = 2.0 * p.beta / sqrt(kPi) * S;
+        NK.beta_h = (float)bs;
+        NK.beta_l = (float)(bs - (double)NK.beta_h);
+        NK.c_h = (float)cs;
+        NK.c_l = (float)(cs - (double)NK.c_h);
+        NK.rn2m = (float)(rnear * rnear) * (1.0f + 1e-5f);
         kern<<<(unsigned)((groups * split + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(
             pr, ws.pg, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc,
-            (int)n, p.nc, p.w, p.cell_side, p.L, rc2, beta, tbr, K, 1.0 / S, split, ws.f_real,
+            (int)n, p.nc, p.w, p.cell_side, p.L, rc2, beta, tbr, K, NK, 1.0 / S, split, ws.f_real,
             ws.phi_real, ws.e_tile, vir, vcap, lj, p.d_status);
     }
     p.launches += 1;

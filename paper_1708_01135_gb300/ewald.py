@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
                 "ewald_compute_virial_async": (_i, [_p, _i64, _p, _p, _p, _p, _p, _i, _p]),
                 "ewald_set_lj": (_i, [_p, _i, _p, _p, _p]),
                 "ewald_set_spme": (_i, [_p, _i, _i]),
+                "ewald_set_near_pairs": (_i, [_p, _i]),
                 "ewald_probe_timeout": (_i, [_p, _p]),
                 "ewald_status_sync": (_i, [_p]),
                 "ewald_compute_host": (_i, [_p, _i64, _p, _p, _p, _p, _p]),
@@ -286,6 +287,13 @@ class Ewald:
         """Reciprocal part by smooth particle-mesh Ewald on a K^3 mesh with B-splines of the
         given even order (ewald_set_spme); K = 0 returns to the classical k-space sum."""
         _check(lib().ewald_set_spme(self._h, int(K), int(order)), "ewald_set_spme")
+
+    def set_near_pairs(self, double_float: bool):
+        """Near real-space Coulomb pairs (within a few mean spacings) in double-float
+        arithmetic (True) or FP32 with the exact r^2 (False, the default)
+        (ewald_set_near_pairs)."""
+        _check(lib().ewald_set_near_pairs(self._h, 1 if double_float else 0),
+               "ewald_set_near_pairs")
 
     def probe_timeout(self, stream=None):
         """One device wait that cannot complete (ewald_probe_timeout): the next status() is

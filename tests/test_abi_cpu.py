@@ -85,6 +85,7 @@ def test_null_handles_are_rejected():
     assert lib.ewald_poll(None, 1, ctypes.byref(r)) == E.E_INVAL
     assert lib.ewald_md(None, 4, None, None, None, None, 1e-3, 10, None, None, None) == E.E_INVAL
     assert lib.ewald_set_spme(None, 32, 8) == E.E_INVAL
+    assert lib.ewald_set_near_pairs(None, 1) == E.E_INVAL
     assert lib.ewald_set_lj(None, 1, None, None, None) == E.E_INVAL
     out = ctypes.c_double(0.0)
     assert lib.ewald_fma_peak(E.MIXED, ctypes.byref(out)) == E.E_INVAL   # FP32 or FP64 only

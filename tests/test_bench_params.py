@@ -1,6 +1,7 @@
 """The benchmark's parameter table (bench.PARAMS, plain numbers the oracle's reference arm
-uses without loading the library) agrees with the library's tuner (ewald_tune at a 1e-6
-relative force error, r_c fixed where bench.WORKLOADS fixes it), so that both arms of the
+uses without loading the library) agrees with the library's tuner (ewald_tune at the
+workload's tuning tolerance, bench.TUNE_TOL, else 1e-6; r_c fixed where bench.WORKLOADS fixes
+it), so that both arms of the
 benchmark evaluate the same (beta, r_c, k_max).  Host-only: the tuner launches nothing."""
 import math
 
@@ -19,7 +20,7 @@ def test_parameter_table_matches_the_tuner():
              "random_2097152": (2097152, 128.0)}
     for name, (n, L) in sizes.items():
         rc_fixed = bench.WORKLOADS[name][1]
-        rc, beta, km = E.tune(n, L, bench.TOL, r_c=rc_fixed)
+        rc, beta, km = E.tune(n, L, bench.TUNE_TOL.get(name, bench.TOL), r_c=rc_fixed)
         prc, pbeta, pkm = bench.PARAMS[name]
         assert rc == prc and km == pkm and math.isclose(beta, pbeta, rel_tol=1e-14), name
 
