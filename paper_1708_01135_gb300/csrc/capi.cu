@@ -262,7 +262,8 @@ void free_workspace(Plan &p)
     graph_reset(p);
     Workspace &ws = p.ws;
     void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
-                    ws.tiles, ws.tile_count, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
+                    ws.row_start, ws.perm1, ws.key1,
+                    ws.tiles, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
                     ws.f_real, ws.f_recip, ws.e_tile, ws.qpart, ws.phi_real, ws.phi_recip,
                     ws.vir_tile, ws.vir_part, ws.type_sorted, ws.elj_tile};
     for (void *q : ptrs) pool_free(q, p.side_stream);
@@ -278,8 +279,8 @@ void free_workspace(Plan &p)
 int binning_chunks(int64_t n)
 {
     // chunks of at least 2048 particles and at most 16384 (the scatter keeps a chunk's keys
-    // in shared memory), at most 128 of them; every chunk has a histogram row over all
-    // cells, so fewer chunks keep the histogram small on fine grids
+    // in shared memory), at most 128 of them; every chunk has a histogram over all rows of
+    // cells
     int64_t nb = (n + 2047) / 2048;
     if (nb > 128) nb = 128;
     if ((n + nb - 1) / nb > 16384) nb = (n + 16383) / 16384;
@@ -353,11 +354,13 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     EW_TRY(dmalloc(p, &ws.key, sizeof(int) * n));
     EW_TRY(dmalloc(p, &ws.perm, sizeof(int) * n));
     EW_TRY(dmalloc(p, &ws.key_sorted, sizeof(int) * n));
-    EW_TRY(dmalloc(p, &ws.hist, sizeof(int) * (size_t)nb * p.ncells));
+    EW_TRY(dmalloc(p, &ws.hist, sizeof(int) * (size_t)nb * p.nc * p.nc));
     EW_TRY(dmalloc(p, &ws.cell_start, sizeof(int) * (p.ncells + 1)));
-    EW_TRY(dmalloc(p, &ws.cell_total, sizeof(int) * p.ncells));
+    EW_TRY(dmalloc(p, &ws.cell_total, sizeof(int) * p.nc * p.nc));
+    EW_TRY(dmalloc(p, &ws.row_start, sizeof(int) * (p.nc * p.nc + 1)));
+    EW_TRY(dmalloc(p, &ws.perm1, sizeof(int) * n));
+    EW_TRY(dmalloc(p, &ws.key1, sizeof(int) * n));
     EW_TRY(dmalloc(p, &ws.tiles, sizeof(int2) * tiles));
-    EW_TRY(dmalloc(p, &ws.tile_count, sizeof(int) * p.nc * p.nc));
     EW_TRY(dmalloc(p, &ws.tile_off, sizeof(int) * (p.nc * p.nc + 1)));
     EW_TRY(dmalloc(p, &ws.pg, sizeof(double4_32a) * n));
     if (p.precision == EWALD_FP64) EW_TRY(dmalloc(p, &ws.pl64, sizeof(double4_32a) * n));
@@ -542,8 +545,9 @@ size_t plan_footprint(const Plan &p, int64_t n)
     const int64_t ts = w == 0 ? 32 : 32 / real_tile_for(w, (double)n / ncells);
     const int64_t tiles = w == 0 ? (n + 31) / 32 : n / ts + (int64_t)nc * nc + 1;
     size_t b = 0;
-    b += sizeof(int) * 3 * (size_t)n + sizeof(int) * (size_t)nb * ncells;
-    b += sizeof(int) * (2 * ncells + 1) + sizeof(int2) * tiles + sizeof(int) * 2 * ((size_t)nc * nc + 1);
+    const size_t nrows = (size_t)nc * nc;
+    b += sizeof(int) * 5 * (size_t)n + sizeof(int) * (size_t)nb * nrows;
+    b += sizeof(int) * (ncells + 1 + 2 * nrows + 1) + sizeof(int2) * tiles + sizeof(int) * (nrows + 1);
     b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
     b += sizeof(double) * 8 * (size_t)n + sizeof(double) * 14 * tiles + sizeof(double) * 3 * ((n + 255) / 256);
     b += sizeof(int) * (size_t)n;
@@ -607,7 +611,7 @@ static void cell_grid(double L, double rc, int64_t n, int &nc_out, int &w_out)
     const double rho = n > 0 ? (double)n / (L * L * L) : 0.0;
     double s_t = rho > 0 ? fmax(1.33 * pow(rho, -1.0 / 3.0), rc / 5.0) : rc / 2.0;
     int nc = (int)floor(L / s_t);
-    if (nc > 160) nc = 160;      // 4.1M cells at most (the binning keeps per-chunk histograms)
+    if (nc > kMaxCellsPerSide) nc = kMaxCellsPerSide;   // a row's counts in shared memory
     w_out = 0;
     nc_out = 1;
     for (; nc >= 3; --nc) {

@@ -5,10 +5,15 @@
 // than r_c through cell-based looping code (Section 2.2; Section 3.2.1).  Here the cells
 // are a regular grid of nc^3 cubes of side L / nc >= r_c / w; particles are sorted by cell
 // key (c_z nc + c_y) nc + c_x so that every cell, and every row of cells along x, is a
-// contiguous range of the sorted arrays.  The sort is a two-pass counting sort over
-// `nb` contiguous chunks of the input: per-chunk histograms, a column scan over chunks, a
-// scan over cells, and an in-order scatter per chunk; equal keys keep their input order, so
-// the result is exactly determined by the input (bit-exact integer work).
+// contiguous range of the sorted arrays.  The sort runs in two levels, each a stable
+// counting sort, so that no histogram spans all cells:
+//   1. by row of cells (c_z nc + c_y) over `nb` contiguous chunks of the input: per-chunk
+//      row histograms, a column scan over chunks, a scan over rows, and an in-order scatter
+//      per chunk;
+//   2. inside every row, by c_x: one block per row counts its cells, scans them (the cell
+//      offsets) and places the row's particles in the order level 1 left them.
+// Equal keys keep their input order, so the result is exactly determined by the input
+// (bit-exact integer work).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -34,9 +39,9 @@ __device__ __forceinline__ int cell_of(double w, double inv_side, int nc)
     return c < nc - 1 ? c : nc - 1;
 }
 
-// a1: wrap + key + per-chunk histogram; finiteness flag; per-block charge sums.
+// a1: wrap + key + per-chunk histogram of rows; finiteness flag; per-block charge sums.
 __global__ void k_keys(int64_t n, const double *__restrict__ pos, const double *__restrict__ q,
-                       double L, double inv_side, int nc, int ncells, int64_t chunk,
+                       double L, double inv_side, int nc, int nrows, int64_t chunk,
                        int *__restrict__ key, int *__restrict__ hist, double *__restrict__ qpart,
                        int *__restrict__ status)
 {
@@ -56,7 +61,7 @@ __global__ void k_keys(int64_t n, const double *__restrict__ pos, const double *
         int cz = cell_of(wrap_box(z, L), inv_side, nc);
         int k = (cz * nc + cy) * nc + cx;
         key[i] = k;
-        atomicAdd(&hist[(i / chunk) * (int64_t)ncells + k], 1);
+        atomicAdd(&hist[(i / chunk) * (int64_t)nrows + (cz * nc + cy)], 1);
         qs = qi;
         qa = fabs(qi);
         q2 = qi * qi;
@@ -108,41 +113,16 @@ __global__ void k_colscan(int nb, int ncells, int *__restrict__ hist, int *__res
     total[c] = run;
 }
 
-// Exclusive scan of cnt[0..m) into out[0..m] (out[m] = total), one block of 1024 threads.
-// Every thread scans a contiguous slice serially; slice sums are scanned in shared memory.
-__global__ void k_scan1(int m, const int *__restrict__ cnt, int *__restrict__ out)
+// a2 (level 1): in-order scatter of chunk b by row.  The whole block loads the chunk's
+// running offsets per row and the chunk's keys into shared memory; then warp 0 walks the
+// chunk in input order, 32 particles at a time.  (When the offsets do not fit, the chunk's
+// histogram row in global memory holds them.)
+__global__ void k_scatter(int64_t n, int64_t chunk, int nrows, int nc, const int *__restrict__ key,
+                          const int *__restrict__ row_start, int *__restrict__ hist,
+                          int *__restrict__ perm1, int *__restrict__ key1, int use_smem)
 {
-    __shared__ int part[1024];
-    int t = threadIdx.x;
-    int per = (m + blockDim.x - 1) / blockDim.x;
-    int b = t * per, e = min(m, b + per);
-    int s = 0;
-    for (int c = b; c < e; ++c) s += cnt[c];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        int v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int run = part[t] - s;  // exclusive prefix of this slice
-    for (int c = b; c < e; ++c) {
-        int v = cnt[c];
-        out[c] = run;
-        run += v;
-    }
-    if (t == blockDim.x - 1) out[m] = part[t];
-}
-
-// a2 (part): in-order scatter of chunk b.  The whole block loads the chunk's running
-// offsets per cell and the chunk's keys into shared memory; then warp 0 walks the chunk in
-// input order, 32 particles at a time.  (When the offsets do not fit, the chunk's histogram
-// row in global memory holds them.)
-__global__ void k_scatter(int64_t n, int64_t chunk, int ncells, const int *__restrict__ key,
-                          const int *__restrict__ cell_start, int *__restrict__ hist,
-                          int *__restrict__ perm, int *__restrict__ key_sorted, int use_smem)
-{
+    const int ncells = nrows;
+    const int *__restrict__ cell_start = row_start;
     extern __shared__ int sh[];
     const int b = blockIdx.x;
     const int64_t beg = (int64_t)b * chunk;
@@ -174,7 +154,8 @@ __global__ void k_scatter(int64_t n, int64_t chunk, int ncells, const int *__res
     for (int base = 0; base < cnt; base += 32) {
         const int i = base + lane;
         const bool valid = i < cnt;
-        const int k = valid ? keys[i] : -1 - lane;   // invalid lanes match nobody
+        const int key_i = valid ? keys[i] : 0;
+        const int k = valid ? key_i / nc : -1 - lane;   // the row; invalid lanes match nobody
         const unsigned peers = __match_any_sync(0xffffffffu, k);
         const int rank = __popc(peers & lt);
         const int leader = __ffs(peers) - 1;
@@ -182,32 +163,28 @@ __global__ void k_scatter(int64_t n, int64_t chunk, int ncells, const int *__res
         __syncwarp();
         if (valid) {
             const int slot = start + rank;
-            perm[slot] = (int)(beg + i);
-            key_sorted[slot] = k;
+            perm1[slot] = (int)(beg + i);
+            key1[slot] = key_i;
             if (lane == leader) off[k] = start + __popc(peers);
         }
         __syncwarp();
     }
 }
 
-// a3: pack sorted particles: wrapped global FP64 position, cell-local FP64 / FP32 positions
-// (the all-pairs kernel, written only in that mode) and 32-bit fixed-point fractions of the
-// box (the FP32 cell kernel's exact minimum-image displacements and the exact integer phase
-// angles of the tensor-core reciprocal part).
-__global__ void k_pack(int64_t n, const double *__restrict__ pos, const double *__restrict__ q,
-                       const int *__restrict__ perm, const int *__restrict__ key_sorted,
-                       double L, double side, int nc,
-                       double4_32a *__restrict__ pg, double4_32a *__restrict__ pl64,
-                       float4 *__restrict__ pl32, uint4 *__restrict__ pu)
+// a3: pack sorted particle s (caller index i, cell key k): wrapped global FP64 position,
+// cell-local FP64 / FP32 positions (the all-pairs kernel, written only in that mode) and
+// 32-bit fixed-point fractions of the box (the FP32 cell kernel's exact minimum-image
+// displacements and the exact integer phase angles of the tensor-core reciprocal part).
+__device__ __forceinline__ void pack_one(int64_t s, int i, int k, const double *__restrict__ pos,
+                                         const double *__restrict__ q, double L, double side,
+                                         int nc, double4_32a *__restrict__ pg,
+                                         double4_32a *__restrict__ pl64,
+                                         float4 *__restrict__ pl32, uint4 *__restrict__ pu)
 {
-    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    int i = perm[s];
     double x = pos[3 * (int64_t)i + 0], y = pos[3 * (int64_t)i + 1], z = pos[3 * (int64_t)i + 2];
     double qi = q[i];
     if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(qi))) { x = y = z = 0.0; qi = 0.0; }
     x = wrap_box(x, L); y = wrap_box(y, L); z = wrap_box(z, L);
-    int k = key_sorted[s];
     int cx = k % nc, cy = (k / nc) % nc, cz = k / (nc * nc);
     pg[s] = make_double4_32a(x, y, z, qi);
     double lx = x - cx * side, ly = y - cy * side, lz = z - cz * side;
@@ -222,26 +199,111 @@ __global__ void k_pack(int64_t n, const double *__restrict__ pos, const double *
     }
 }
 
-// Tiles of up to `ts` consecutive sorted particles that never leave a row of cells (the
-// targets of one warp of the cell kernel share their row, so that the warp can stage one
-// union of candidate ranges per stencil row for all of them).
-__global__ void k_row_tiles(int nrows, int nc, int ts, const int *__restrict__ cell_start,
-                            int *__restrict__ tcount)
+// Exclusive scans of the particles per row of cells (row_start[0..nrows]) and, with ts > 0,
+// of the warp tiles per row, ceil(count / ts) (tile_off[0..nrows]): the targets of one warp
+// of the cell kernel never leave a row, so that the warp can stage one union of candidate
+// ranges per stencil row for all of them.  One block of 1024 threads: every thread scans a
+// contiguous slice serially; slice sums are scanned in shared memory.
+__global__ void k_scan_rows(int nrows, int ts, const int *__restrict__ cnt,
+                            int *__restrict__ row_start, int *__restrict__ tile_off)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    int cnt = cell_start[(r + 1) * nc] - cell_start[r * nc];
-    tcount[r] = (cnt + ts - 1) / ts;
+    __shared__ int part[2][1024];
+    const int t = threadIdx.x;
+    const int per = (nrows + blockDim.x - 1) / blockDim.x;
+    const int b = t * per, e = min(nrows, b + per);
+    int s0 = 0, s1 = 0;
+    for (int r = b; r < e; ++r) {
+        const int v = cnt[r];
+        s0 += v;
+        s1 += ts > 0 ? (v + ts - 1) / ts : 0;
+    }
+    part[0][t] = s0;
+    part[1][t] = s1;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int v0 = t >= o ? part[0][t - o] : 0, v1 = t >= o ? part[1][t - o] : 0;
+        __syncthreads();
+        part[0][t] += v0;
+        part[1][t] += v1;
+        __syncthreads();
+    }
+    int run0 = part[0][t] - s0, run1 = part[1][t] - s1;   // exclusive prefixes of the slice
+    for (int r = b; r < e; ++r) {
+        const int v = cnt[r];
+        row_start[r] = run0;
+        run0 += v;
+        if (ts > 0) {
+            tile_off[r] = run1;
+            run1 += (v + ts - 1) / ts;
+        }
+    }
+    if (t == blockDim.x - 1) {
+        row_start[nrows] = part[0][t];
+        if (ts > 0) tile_off[nrows] = part[1][t];
+    }
 }
 
-__global__ void k_emit_tiles(int nrows, int nc, int ts, const int *__restrict__ cell_start,
-                             const int *__restrict__ toff, int2 *__restrict__ tiles)
+// a2 (level 2) and a3: row r of cells (particles [row_start[r], row_start[r+1]) in level-1
+// order): counts per cell, the cell offsets cell_start[r nc .. r nc + nc - 1], the in-order
+// placement of the row's particles by cell (warp 0), then the packing of the row's sorted
+// particles and, with tiles, the row's warp tiles (all threads).  One block per row.
+__global__ void k_rowsort(int nrows, int nc, int64_t n, const int *__restrict__ row_start,
+                          const int *__restrict__ perm1, const int *__restrict__ key1,
+                          int *__restrict__ perm, int *__restrict__ key_sorted,
+                          int *__restrict__ cell_start, const double *__restrict__ pos,
+                          const double *__restrict__ q, double L, double side,
+                          double4_32a *__restrict__ pg, double4_32a *__restrict__ pl64,
+                          float4 *__restrict__ pl32, uint4 *__restrict__ pu, int ts,
+                          const int *__restrict__ tile_off, int2 *__restrict__ tiles)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    int b = cell_start[r * nc];
-    int o = toff[r], e = toff[r + 1];
-    for (int t = o; t < e; ++t) tiles[t] = make_int2(r, b + ts * (t - o));
+    __shared__ int off[kMaxCellsPerSide];
+    const int r = blockIdx.x;
+    const int b = row_start[r], e = row_start[r + 1];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) off[c] = 0;
+    __syncthreads();
+    for (int j = b + threadIdx.x; j < e; j += blockDim.x) atomicAdd(&off[key1[j] % nc], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = b;
+        for (int c = 0; c < nc; ++c) {
+            const int v = off[c];
+            off[c] = run;
+            cell_start[r * nc + c] = run;
+            run += v;
+        }
+        if (r == nrows - 1) cell_start[nrows * nc] = (int)n;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned lt = (1u << lane) - 1u;
+        for (int base = b; base < e; base += 32) {
+            const int j = base + lane;
+            const bool valid = j < e;
+            const int key_j = valid ? key1[j] : 0;
+            const int cx = valid ? key_j % nc : -1 - lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, cx);
+            const int rank = __popc(peers & lt);
+            const int leader = __ffs(peers) - 1;
+            const int start = valid ? off[cx] : 0;
+            __syncwarp();
+            if (valid) {
+                const int slot = start + rank;
+                perm[slot] = perm1[j];
+                key_sorted[slot] = key_j;
+                if (lane == leader) off[cx] = start + __popc(peers);
+            }
+            __syncwarp();
+        }
+    }
+    // (the block's own global writes are visible to the block after the barrier)
+    __syncthreads();
+    for (int s = b + threadIdx.x; s < e; s += blockDim.x)
+        pack_one(s, perm[s], key_sorted[s], pos, q, L, side, nc, pg, pl64, pl32, pu);
+    if (tiles) {
+        const int o = tile_off[r], oe = tile_off[r + 1];
+        for (int t = o + threadIdx.x; t < oe; t += blockDim.x) tiles[t] = make_int2(r, b + ts * (t - o));
+    }
 }
 
 }  // namespace
@@ -253,39 +315,32 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
     const int nb = ws.nb;
     const int64_t chunk = (n + nb - 1) / nb;
     cudaError_t e;
-    e = cudaMemsetAsync(ws.hist, 0, sizeof(int) * (size_t)nb * p.ncells, st);
+    const int nrows = p.nc * p.nc;
+    e = cudaMemsetAsync(ws.hist, 0, sizeof(int) * (size_t)nb * nrows, st);
     if (e != cudaSuccess) return e;
     const int tb = 256;
     const int qblocks = (int)((n + tb - 1) / tb);
-    k_keys<<<qblocks, tb, 0, st>>>(n, pos, q, p.L, (double)p.nc / p.L, p.nc, p.ncells, chunk,
+    k_keys<<<qblocks, tb, 0, st>>>(n, pos, q, p.L, (double)p.nc / p.L, p.nc, nrows, chunk,
                                    ws.key, ws.hist, ws.qpart, p.d_status);
-    k_colscan<<<(p.ncells + 255) / 256, 256, 0, st>>>(nb, p.ncells, ws.hist, ws.cell_total);
-    k_scan1<<<1, 1024, 0, st>>>(p.ncells, ws.cell_total, ws.cell_start);
+    k_colscan<<<(nrows + 255) / 256, 256, 0, st>>>(nb, nrows, ws.hist, ws.cell_total);
+    const int ts = p.w > 0 ? real_tile_size(p) : 0;
+    k_scan_rows<<<1, 1024, 0, st>>>(nrows, ts, ws.cell_total, ws.row_start, ws.tile_off);
     const size_t key_bytes = sizeof(int) * (size_t)chunk;
-    const int use_smem = key_bytes + sizeof(int) * (size_t)p.ncells <= 200 * 1024;
-    size_t smem = key_bytes + (use_smem ? sizeof(int) * (size_t)p.ncells : 0);
+    const int use_smem = key_bytes + sizeof(int) * (size_t)nrows <= 200 * 1024;
+    size_t smem = key_bytes + (use_smem ? sizeof(int) * (size_t)nrows : 0);
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_scatter<<<nb, 256, smem, st>>>(n, chunk, p.ncells, ws.key, ws.cell_start, ws.hist, ws.perm,
-                                     ws.key_sorted, use_smem);
+    k_scatter<<<nb, 256, smem, st>>>(n, chunk, nrows, p.nc, ws.key, ws.row_start, ws.hist,
+                                     ws.perm1, ws.key1, use_smem);
     const bool need64 = p.precision == EWALD_FP64;
-    k_pack<<<(int)((n + 255) / 256), 256, 0, st>>>(n, pos, q, ws.perm, ws.key_sorted, p.L,
-                                                   p.cell_side, p.nc, ws.pg,
-                                                   (need64 && p.w == 0) ? ws.pl64 : nullptr,
-                                                   (!need64 && p.w == 0) ? ws.pl32 : nullptr, ws.pu);
+    k_rowsort<<<nrows, 128, 0, st>>>(nrows, p.nc, n, ws.row_start, ws.perm1, ws.key1, ws.perm,
+                                     ws.key_sorted, ws.cell_start, pos, q, p.L, p.cell_side,
+                                     ws.pg, (need64 && p.w == 0) ? ws.pl64 : nullptr,
+                                     (!need64 && p.w == 0) ? ws.pl32 : nullptr, ws.pu, ts,
+                                     ws.tile_off, p.w > 0 ? ws.tiles : nullptr);
     p.launches += 5;
-    if (p.w > 0) {
-        const int nrows = p.nc * p.nc;
-        const int ts = real_tile_size(p);
-        k_row_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ts, ws.cell_start,
-                                                         ws.tile_count);
-        k_scan1<<<1, 1024, 0, st>>>(nrows, ws.tile_count, ws.tile_off);
-        k_emit_tiles<<<(nrows + 255) / 256, 256, 0, st>>>(nrows, p.nc, ts, ws.cell_start,
-                                                          ws.tile_off, ws.tiles);
-        p.launches += 3;
-    }
     return cudaGetLastError();
 }
 

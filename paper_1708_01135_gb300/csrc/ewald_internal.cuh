@@ -45,6 +45,8 @@ struct RowInfo {
     int my, mz, nxmax, koff;
 };
 
+constexpr int kMaxCellsPerSide = 160;   // cells per side of the real-space grid, at most
+
 struct Workspace {
     int64_t cap_n = 0;       // particles the buffers hold
     int nb = 0;              // binning chunks (histogram rows)
@@ -52,11 +54,13 @@ struct Workspace {
     int *key = nullptr;          // [n] cell index, caller order
     int *perm = nullptr;         // [n] sorted slot -> caller index
     int *key_sorted = nullptr;   // [n]
-    int *hist = nullptr;         // [nb * ncells] per-chunk cell counts -> offsets
+    int *hist = nullptr;         // [nb * nrows] per-chunk counts of the rows of cells -> offsets
     int *cell_start = nullptr;   // [ncells + 1]
-    int *cell_total = nullptr;   // [ncells]
+    int *cell_total = nullptr;   // [nrows] particles per row of cells
+    int *row_start = nullptr;    // [nrows + 1]
+    int *perm1 = nullptr;        // [n] caller index, sorted by row (binning level 1)
+    int *key1 = nullptr;         // [n] cell key, sorted by row (binning level 1)
     int2 *tiles = nullptr;       // [max tiles] (row, first slot) of the cell kernel's warps
-    int *tile_count = nullptr;   // [nrows] tiles per row
     int *tile_off = nullptr;     // [nrows + 1] exclusive offsets; tile_off[nrows] = tiles
     // packed particles (sorted)
     double4_32a *pg = nullptr;       // wrapped global position + q (FP64)
