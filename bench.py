@@ -435,8 +435,9 @@ def serving_summary(systems, local, precision, slots, tol, loads=(0.25, 0.5, 0.7
             tickets.append(srv.submit(r["pos"], r["q"], r["F"], r["L"], r["beta"], r["rc"], r["km"],
                                       precision))
         res = [srv.wait(t, 600.0) for t in tickets]
-        if any(x["status"] != 0 for x in res):
-            raise RuntimeError("a serving request failed")
+        bad = [(i, x["status"]) for i, x in enumerate(res) if x["status"] != 0]
+        if bad:
+            raise RuntimeError(f"serving requests failed (index, status): {bad[:8]}")
         lat = np.array([x["t_done"] - x["t_submit"] for x in res]) * 1e3
         span = max(x["t_done"] for x in res) - min(x["t_submit"] for x in res)
         return lat, span

@@ -276,13 +276,14 @@ void free_workspace(Plan &p)
     ws.h_pos = hp; ws.h_q = hq; ws.h_f = hf; ws.h_e = he;
 }
 
-int binning_chunks(int64_t n)
+int binning_chunks(int64_t n, int64_t nrows)
 {
-    // chunks of at least 2048 particles and at most 16384 (the scatter keeps a chunk's keys
-    // in shared memory), at most 128 of them; every chunk has a histogram over all rows of
-    // cells
+    // chunks of 2048 particles (one warp places a chunk in input order), as many as keep the
+    // per-chunk histograms over the rows of cells within 2^24 counters, and at most 16384
+    // particles a chunk (the scatter keeps a chunk's keys in shared memory)
     int64_t nb = (n + 2047) / 2048;
-    if (nb > 128) nb = 128;
+    const int64_t cap = (int64_t)(1 << 24) / (nrows > 0 ? nrows : 1);
+    if (nb > cap) nb = cap > 0 ? cap : 1;
     if ((n + nb - 1) / nb > 16384) nb = (n + 16383) / 16384;
     return nb < 1 ? 1 : (int)nb;
 }
@@ -314,6 +315,38 @@ cudaMemPool_t lib_pool()
     return pools[dev];
 }
 
+// Opt a kernel into the largest dynamic shared memory a block may have on the current
+// device, once per (kernel, device).  The attribute belongs to the kernel, not to a plan or a
+// thread, so it is never set to a launch's own size: the server launches several plans from
+// several threads, and a smaller value set by one of them between another's setting and its
+// launch would fail that launch.
+cudaError_t smem_optin(const void *func, size_t *max_dynamic)
+{
+    struct Done { const void *f; int dev; int bytes; };
+    static std::mutex mu;
+    static std::vector<Done> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(mu);
+    for (const Done &d : done)
+        if (d.f == func && d.dev == dev) {
+            if (max_dynamic) *max_dynamic = (size_t)d.bytes;
+            return cudaSuccess;
+        }
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess) return e;
+    const int bytes = optin - (int)fa.sharedSizeBytes;
+    if ((e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+        return e;
+    done.push_back(Done{func, dev, bytes});
+    if (max_dynamic) *max_dynamic = (size_t)bytes;
+    return cudaSuccess;
+}
+
 cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st)
 {
     cudaMemPool_t pl = lib_pool();
@@ -336,50 +369,84 @@ cudaError_t dmalloc(Plan &pl, P **p, size_t bytes)
 
 cudaError_t grow_workspace(Plan &p, int64_t n)
 {
-    if (n <= p.ws.cap_n) return cudaSuccess;
+    // The cell grid follows the density of this evaluation's particle count (not the
+    // capacity of the workspace), so that a system's results do not depend on what the plan
+    // evaluated before; buffers sized by the particle count keep the larger capacity.
+    int nc = 1, w = 0;
+    cell_grid(p.L, p.rc, n, nc, w);
+    if (n <= p.ws.cap_n && nc == p.nc && w == p.w) return cudaSuccess;
+    if (n <= p.ws.cap_n) {
+        // another grid in the same buffers where they are large enough
+        const int64_t cells = (int64_t)nc * nc * nc, rows = (int64_t)nc * nc;
+        const int nb = binning_chunks(p.ws.cap_n, rows);
+        const int nc0 = p.nc, w0 = p.w;
+        p.nc = nc;
+        p.w = w;
+        const int64_t tiles = real_tile_capacity(p, p.ws.cap_n);
+        p.nc = nc0;
+        p.w = w0;
+        if (cells <= p.ws.cap_cells && rows <= p.ws.cap_rows && tiles <= p.ws.cap_tiles &&
+            (int64_t)nb * rows <= p.ws.cap_hist) {
+            cudaError_t e = cudaStreamSynchronize(p.last_stream ? p.last_stream : 0);
+            if (e != cudaSuccess) return e;
+            if ((e = cudaStreamSynchronize(p.side_stream)) != cudaSuccess) return e;
+            graph_reset(p);
+            p.nc = nc;
+            p.w = w;
+            p.ncells = (int)cells;
+            p.cell_side = p.L / nc;
+            p.ws.nb = nb;
+            return cudaSuccess;
+        }
+    }
+    const int64_t cap = n > p.ws.cap_n ? n : p.ws.cap_n;
     cudaError_t e = cudaStreamSynchronize(p.last_stream ? p.last_stream : 0);
     if (e != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(p.side_stream)) != cudaSuccess) return e;
     free_workspace(p);
-    // the cell grid can depend on the density, known from here on
-    cell_grid(p.L, p.rc, n, p.nc, p.w);
+    p.nc = nc;
+    p.w = w;
     p.ncells = p.nc * p.nc * p.nc;
     p.cell_side = p.L / p.nc;
     p.real_tile = real_tile_for(p.w, (double)n / p.ncells);
     Workspace &ws = p.ws;
-    const int nb = binning_chunks(n);
-    const int64_t tiles = real_tile_capacity(p, n);
-    const int64_t qblocks = (n + 255) / 256;
+    const int nb = binning_chunks(cap, (int64_t)p.nc * p.nc);
+    const int64_t tiles = real_tile_capacity(p, cap);
+    const int64_t qblocks = (cap + 255) / 256;
 #define EW_TRY(x) do { if ((e = (x)) != cudaSuccess) { free_workspace(p); return e; } } while (0)
-    EW_TRY(dmalloc(p, &ws.key, sizeof(int) * n));
-    EW_TRY(dmalloc(p, &ws.perm, sizeof(int) * n));
-    EW_TRY(dmalloc(p, &ws.key_sorted, sizeof(int) * n));
+    EW_TRY(dmalloc(p, &ws.key, sizeof(int) * cap));
+    EW_TRY(dmalloc(p, &ws.perm, sizeof(int) * cap));
+    EW_TRY(dmalloc(p, &ws.key_sorted, sizeof(int) * cap));
     EW_TRY(dmalloc(p, &ws.hist, sizeof(int) * (size_t)nb * p.nc * p.nc));
     EW_TRY(dmalloc(p, &ws.cell_start, sizeof(int) * (p.ncells + 1)));
     EW_TRY(dmalloc(p, &ws.cell_total, sizeof(int) * p.nc * p.nc));
     EW_TRY(dmalloc(p, &ws.row_start, sizeof(int) * (p.nc * p.nc + 1)));
-    EW_TRY(dmalloc(p, &ws.perm1, sizeof(int) * n));
-    EW_TRY(dmalloc(p, &ws.key1, sizeof(int) * n));
+    EW_TRY(dmalloc(p, &ws.perm1, sizeof(int) * cap));
+    EW_TRY(dmalloc(p, &ws.key1, sizeof(int) * cap));
     EW_TRY(dmalloc(p, &ws.tiles, sizeof(int2) * tiles));
     EW_TRY(dmalloc(p, &ws.tile_off, sizeof(int) * (p.nc * p.nc + 1)));
-    EW_TRY(dmalloc(p, &ws.pg, sizeof(double4_32a) * n));
-    if (p.precision == EWALD_FP64) EW_TRY(dmalloc(p, &ws.pl64, sizeof(double4_32a) * n));
-    else EW_TRY(dmalloc(p, &ws.pl32, sizeof(float4) * n));
-    EW_TRY(dmalloc(p, &ws.pu, sizeof(uint4) * n));
-    EW_TRY(dmalloc(p, &ws.f_real, sizeof(double) * 3 * n));
-    EW_TRY(dmalloc(p, &ws.phi_real, sizeof(double) * n));
-    EW_TRY(dmalloc(p, &ws.phi_recip, sizeof(double) * n));
-    EW_TRY(dmalloc(p, &ws.f_recip, sizeof(double) * 3 * n));
+    EW_TRY(dmalloc(p, &ws.pg, sizeof(double4_32a) * cap));
+    if (p.precision == EWALD_FP64) EW_TRY(dmalloc(p, &ws.pl64, sizeof(double4_32a) * cap));
+    else EW_TRY(dmalloc(p, &ws.pl32, sizeof(float4) * cap));
+    EW_TRY(dmalloc(p, &ws.pu, sizeof(uint4) * cap));
+    EW_TRY(dmalloc(p, &ws.f_real, sizeof(double) * 3 * cap));
+    EW_TRY(dmalloc(p, &ws.phi_real, sizeof(double) * cap));
+    EW_TRY(dmalloc(p, &ws.phi_recip, sizeof(double) * cap));
+    EW_TRY(dmalloc(p, &ws.f_recip, sizeof(double) * 3 * cap));
     EW_TRY(dmalloc(p, &ws.e_tile, sizeof(double) * tiles));
     EW_TRY(dmalloc(p, &ws.vir_tile, sizeof(double) * 12 * tiles));
     EW_TRY(dmalloc(p, &ws.elj_tile, sizeof(double) * tiles));
-    EW_TRY(dmalloc(p, &ws.type_sorted, sizeof(int) * n));
+    EW_TRY(dmalloc(p, &ws.type_sorted, sizeof(int) * cap));
     EW_TRY(dmalloc(p, &ws.vir_part, sizeof(double) * 6 * kVirBlocks));
     EW_TRY(dmalloc(p, &ws.qpart, sizeof(double) * 3 * qblocks));
-    ws.cap_n = n;
+    ws.cap_n = cap;
     ws.nb = nb;
-    if (uses_tc(p.precision)) EW_TRY(alloc_recip_tc(p, n));
-    else EW_TRY(alloc_recip_simt(p, n));
+    ws.cap_cells = p.ncells;
+    ws.cap_rows = (int64_t)p.nc * p.nc;
+    ws.cap_tiles = tiles;
+    ws.cap_hist = (int64_t)nb * p.nc * p.nc;
+    if (uses_tc(p.precision)) EW_TRY(alloc_recip_tc(p, cap));
+    else EW_TRY(alloc_recip_simt(p, cap));
 #undef EW_TRY
     // allocations are ordered on the side stream; make them visible to every stream
     return cudaStreamSynchronize(p.side_stream);
@@ -538,9 +605,9 @@ cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, dou
 
 size_t plan_footprint(const Plan &p, int64_t n)
 {
-    const int nb = binning_chunks(n);
     int nc = 1, w = 0;
     cell_grid(p.L, p.rc, n, nc, w);
+    const int nb = binning_chunks(n, (int64_t)nc * nc);
     const size_t ncells = (size_t)nc * nc * nc;
     const int64_t ts = w == 0 ? 32 : 32 / real_tile_for(w, (double)n / ncells);
     const int64_t tiles = w == 0 ? (n + 31) / 32 : n / ts + (int64_t)nc * nc + 1;
@@ -715,22 +782,19 @@ int plan_reconfigure(ewald_plan *h, double L, double beta, double rc, int kmax, 
     if (s != EWALD_OK) return s;
     if (p.last_stream) cudaStreamSynchronize(p.last_stream);
     cudaStreamSynchronize(p.side_stream);
-    // the grid the kept workspace would have: chosen from the density of the particle count
-    // it holds (as grow_workspace chooses it), else the density-free set-up grid
-    int nc2 = probe.nc, w2 = probe.w;
-    if (p.ws.cap_n > 0) cell_grid(L, rc, p.ws.cap_n, nc2, w2);
-    const int g2 = real_tile_for(w2, (double)p.ws.cap_n / ((double)nc2 * nc2 * nc2));
-    const bool same_shape = p.ws.cap_n > 0 && nc2 == p.nc && w2 == p.w && g2 == p.real_tile &&
-                            probe.R == p.R && probe.kmax == p.kmax &&
+    // the workspace is kept where the k tables keep their shape; its cell grid is checked
+    // against the particle count of the next evaluation (grow_workspace)
+    const bool same_shape = p.ws.cap_n > 0 && probe.R == p.R && probe.kmax == p.kmax &&
                             probe.precision == p.precision;
+    const int nc0 = p.nc, w0 = p.w;
     graph_reset(p);
     if (!same_shape) free_workspace(p);
     plan_setup_host(p, L, beta, rc, kmax, precision);
     if (same_shape) {
-        p.nc = nc2;
-        p.w = w2;
-        p.ncells = nc2 * nc2 * nc2;
-        p.cell_side = L / nc2;
+        p.nc = nc0;
+        p.w = w0;
+        p.ncells = nc0 * nc0 * nc0;
+        p.cell_side = L / nc0;
     }
     return cuda_status(plan_upload(p));
 }

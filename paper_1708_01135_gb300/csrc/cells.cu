@@ -329,7 +329,7 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
     const int use_smem = key_bytes + sizeof(int) * (size_t)nrows <= 200 * 1024;
     size_t smem = key_bytes + (use_smem ? sizeof(int) * (size_t)nrows : 0);
     if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = smem_optin((const void *)k_scatter);
         if (e != cudaSuccess) return e;
     }
     k_scatter<<<nb, 256, smem, st>>>(n, chunk, nrows, p.nc, ws.key, ws.row_start, ws.hist,

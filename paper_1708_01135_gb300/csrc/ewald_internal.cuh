@@ -49,6 +49,9 @@ constexpr int kMaxCellsPerSide = 160;   // cells per side of the real-space grid
 
 struct Workspace {
     int64_t cap_n = 0;       // particles the buffers hold
+    // capacities of the buffers sized by the cell grid (cells, rows of cells, warp tiles,
+    // histogram counters), so that another grid that fits reuses them
+    int64_t cap_cells = 0, cap_rows = 0, cap_tiles = 0, cap_hist = 0;
     int nb = 0;              // binning chunks (histogram rows)
     // binning
     int *key = nullptr;          // [n] cell index, caller order
@@ -219,6 +222,9 @@ cudaError_t evaluate(Plan &p, int64_t n, const double *pos, const double *q, dou
 
 // Library memory pool (stream-ordered, retains freed memory for reuse).
 cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st);
+// The kernel may use up to the device's opt-in dynamic shared memory (set once, never lowered);
+// max_dynamic (optional) receives that size.
+cudaError_t smem_optin(const void *func, size_t *max_dynamic = nullptr);
 void pool_free(void *ptr, cudaStream_t st);
 
 // Host-side plan set-up shared by ewald_create and the server: validates the parameters,

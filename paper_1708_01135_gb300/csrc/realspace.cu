@@ -1265,7 +1265,7 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
     cudaError_t e;
     if (p.w == 0) {
         auto kern = k_real_allpairs<T, kVir, kLJ>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = smem_optin((const void *)kern);
         if (e != cudaSuccess) return e;
         int tiles = (int)((n + 31) / 32);
         kern<<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(

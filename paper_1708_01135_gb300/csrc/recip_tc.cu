@@ -1077,14 +1077,24 @@ size_t bs_smem(int np)
     return kBStages * stage + 128 + 4 * (size_t)np;
 }
 
+// CTAs of the forward product: one per SM, but at least kFMinItems (virtual group, stage)
+// items each, so that a small system (a serving request of a few thousand particles) leaves
+// most SMs to the products of other requests instead of spreading a few items over all of
+// them (every CTA holds 210 KB of shared memory for its whole life).
+constexpr int64_t kFMinItems = 16;
+int fwd_ctas(const Plan &p, int64_t W)
+{
+    const int64_t g = (W + kFMinItems - 1) / kFMinItems;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(p.num_sms, g));
+}
+
 template <bool BF>
 cudaError_t launch_fwd(Plan &p, int nst_all, TcState &s, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)s.fsmem);
+    cudaError_t e = smem_optin((const void *)k_fwd_tc<BF>);
     if (e != cudaSuccess) return e;
     const int64_t W = (int64_t)s.nvg * nst_all;
-    const int G = (int)std::min<int64_t>(p.num_sms, W);
+    const int G = fwd_ctas(p, W);
     k_fwd_tc<BF><<<G, kFThreads, s.fsmem, st>>>(
         p.R, s.nf, nst_all, W, s.maxp, s.sa, s.sx, s.sp, s.kch, s.vgs, p.rows_d, p.fperm_d, s.yz,
         s.bblob, s.dpart, p.d_status);
@@ -1105,7 +1115,7 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
     if ((e = cudaMemsetAsync(s.gmax, 0, sizeof(int), st)) != cudaSuccess) return e;
     {
         const int64_t W = (int64_t)s.nvg * nst_all;
-        const int G = (int)std::min<int64_t>(p.num_sms, W);
+        const int G = fwd_ctas(p, W);
         k_sreduce_tc<<<dim3(s.ntiles, p.kmax + 1), 64, 0, st>>>(
             nst_all, W, G, s.maxp, s.gvg, s.ntiles, p.R, p.kmax, s.nf, p.rows_d, p.fperm_d,
             s.dpart, p.g_d, p.S_d, p.e_recip_part, s.gmat, s.gmax);
@@ -1114,8 +1124,7 @@ cudaError_t launch_bf(Plan &p, int64_t n, cudaStream_t st)
                                                       s.gmax, s.gscale, s.blob);
     prof_mark(p, kEvCoefEnd, st);
     const size_t bs = bs_smem(s.np);
-    if ((e = cudaFuncSetAttribute(k_bs_tc<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bs)) != cudaSuccess)
-        return e;
+    if ((e = smem_optin((const void *)k_bs_tc<BF>)) != cudaSuccess) return e;
     const int ptiles = (int)((n + kBMT * 128 - 1) / (kBMT * 128));
     prof_mark(p, kEvBsStart, st);
     k_bs_tc<BF><<<dim3(ptiles, s.npass), kBThreads, bs, st>>>(

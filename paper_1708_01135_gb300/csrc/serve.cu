@@ -8,8 +8,11 @@
 //     needs more), a CUDA stream and a completion event,
 //   * a scheduler thread that, whenever a slot is free, admits queued requests first-fit in
 //     arrival order while the device memory held by all slots (estimated per request from its
-//     parameters and N) stays within the HBM budget, launches the request's whole pipeline
-//     on the slot's stream, and retires requests whose completion event has fired.
+//     parameters and N) stays within the HBM budget, hands each admitted request to its
+//     slot, and retires requests whose completion event has fired;
+//   * one launcher thread per slot, which re-parameterises the slot's plan and launches the
+//     request's whole pipeline on the slot's stream (the host work of a launch, ~0.1-0.3 ms
+//     for a request of a few thousand particles, runs for several slots at once).
 // Requests admitted while others are running execute concurrently on separate streams.
 // Every wait on the host is bounded (ewald_wait takes a time limit); no kernel waits on
 // another request.
@@ -53,6 +56,10 @@ struct Slot {
     double t_submit = 0;
     size_t footprint = 0;
     int launch_status = EWALD_OK;
+    // hand-over to the slot's launcher thread (under the server's mutex)
+    bool has_work = false;        // a request waits for its launch
+    bool launched = true;         // the request's pipeline (or its failure) has been issued
+    Pending work{};
 };
 
 constexpr int kMaxBypass = 64;   // requests admitted past a waiting head before it blocks them
@@ -115,9 +122,12 @@ struct ewald_server {
     std::unordered_map<uint64_t, ewald_result> results;   // finished, not yet polled
     std::unordered_map<uint64_t, int> state;              // 0 queued, 1 running, 2 done
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv;      // wakes the scheduler
+    std::condition_variable wcv;     // wakes the launcher threads
     std::thread th;
+    std::vector<std::thread> launchers;
     bool stop = false;
+    bool quit_launchers = false;
     uint64_t next_ticket = 1;
     int64_t submitted = 0, completed = 0;
     int64_t held_total = 0, peak_held = 0, peak_running = 0;
@@ -191,6 +201,27 @@ void finish(ewald_server *s, Slot &sl, int status)
     s->completed++;
 }
 
+// Launcher thread of slot idx: launches every request the scheduler hands to the slot.
+void launcher(ewald_server *s, int idx)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        Slot &sl = s->slots[idx];
+        s->wcv.wait(lk, [&] { return sl.has_work || s->quit_launchers; });
+        if (!sl.has_work) break;
+        const Pending pd = sl.work;
+        sl.has_work = false;
+        lk.unlock();
+        const int st = launch(s, sl, pd);
+        if (pd.ready) cudaEventDestroy(pd.ready);
+        lk.lock();
+        sl.launch_status = st;
+        sl.launched = true;
+        s->cv.notify_one();
+    }
+}
+
 void scheduler(ewald_server *s)
 {
     cudaSetDevice(s->device);
@@ -201,6 +232,7 @@ void scheduler(ewald_server *s)
         // retire finished requests
         for (Slot &sl : s->slots) {
             if (!sl.busy) continue;
+            if (!sl.launched) { ++running; continue; }
             if (sl.launch_status != EWALD_OK) {
                 finish(s, sl, sl.launch_status);
                 progress = true;
@@ -255,12 +287,12 @@ void scheduler(ewald_server *s)
                 ++running;
                 if (running > s->peak_running) s->peak_running = running;
                 sl.t_admit = now_s(s->t0);
-                lk.unlock();
-                sl.launch_status = launch(s, sl, pd);
-                if (pd.ready) cudaEventDestroy(pd.ready);
-                lk.lock();
+                sl.work = pd;
+                sl.has_work = true;
+                sl.launched = false;
+                s->wcv.notify_all();
                 progress = true;
-                // the queue may have changed while unlocked: restart from its head
+                // (the reclaims above unlock the mutex: restart from the queue's head)
                 it = s->queue.begin();
             }
         }
@@ -303,6 +335,7 @@ extern "C" int ewald_server_create(int max_slots, size_t hbm_budget_bytes, ewald
             return cuda_st(e);
         }
     }
+    for (int i = 0; i < max_slots; ++i) s->launchers.emplace_back(launcher, s, i);
     s->th = std::thread(scheduler, s);
     *out = s;
     return EWALD_OK;
@@ -386,6 +419,14 @@ extern "C" int ewald_server_destroy(ewald_server_t s)
         s->cv.notify_one();
     }
     if (s->th.joinable()) s->th.join();
+    {
+        // (the scheduler has exited with no request running or waiting for its launch)
+        std::lock_guard<std::mutex> g(s->mu);
+        s->quit_launchers = true;
+        s->wcv.notify_all();
+    }
+    for (std::thread &t : s->launchers)
+        if (t.joinable()) t.join();
     for (Slot &sl : s->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.plan) ewald_destroy(sl.plan);

@@ -665,12 +665,11 @@ void choose_tiling(Plan &p, SpmeState &s, int64_t n)
     s.W_g = s.bc_g ? tile_side(nc, K, P, s.bc_g) : 0;
     s.smem_g = (size_t)s.W_g * s.W_g * s.W_g * sizeof(T);
     if (!bc) return;
-    cudaError_t e = s.S == 24
-        ? cudaFuncSetAttribute(k_spme_spread_tile<T, P, 24>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem)
-        : cudaFuncSetAttribute(k_spme_spread_tile<T, P, 40>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spme_gather_tile<T, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)s.smem_g);
+    size_t cap = 0, cap_g = 0;
+    cudaError_t e = s.S == 24 ? smem_optin((const void *)k_spme_spread_tile<T, P, 24>, &cap)
+                              : smem_optin((const void *)k_spme_spread_tile<T, P, 40>, &cap);
+    if (e == cudaSuccess) e = smem_optin((const void *)k_spme_gather_tile<T, P>, &cap_g);
+    if (e == cudaSuccess && (s.smem > cap || s.smem_g > cap_g)) e = cudaErrorInvalidValue;
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         s.bc = s.bc_g = 0;
