@@ -1026,6 +1026,34 @@ def run_capture(args, local):
         raise RuntimeError("evaluation reported an error")
 
 
+def run_capture_serving(args, local):
+    """--workload serving --capture K: the first K requests of the serving stream submitted at
+    once to a server of --slots slots (tol --serving-tol), for launch lists under a profiler;
+    prints one status line."""
+    systems = serving_systems(args.capture)
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1708_01135_gb300 import Server, tune
+    dev = torch.device("cuda", local)
+    reqs = []
+    for pos, q, L in systems:
+        rc, beta, km = tune(len(q), L, args.serving_tol,
+                            r_c=min(0.5 * L, 4.0 * (len(q) / L ** 3) ** (-1.0 / 3.0)))
+        reqs.append((torch.tensor(pos, device=dev), torch.tensor(q, device=dev),
+                     torch.empty((len(q), 3), dtype=torch.float64, device=dev), L, beta, rc, km))
+    srv = Server(max_slots=args.slots)
+    try:
+        tickets = [srv.submit(p, q, F, L, b, rc, km, args.precision) for p, q, F, L, b, rc, km in reqs]
+        res = [srv.wait(t, 600.0) for t in tickets]
+    finally:
+        srv.close()
+    st = [r["status"] for r in res]
+    print(json.dumps({"capture": args.capture, "workload": "serving", "n": [len(r[1]) for r in reqs],
+                      "status": st}))
+    if any(st):
+        raise RuntimeError("a serving request failed")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1066,6 +1094,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "serving" and args.capture:
+        return run_capture_serving(args, local)
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
     if args.md:
