@@ -1161,15 +1161,21 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
 }
 
 // All pairs with the minimum image (boxes too small for a cell stencil): one tile of 32
-// targets per warp, every particle staged through the same double-buffered TMA path.
+// targets per warp, every particle staged through the same double-buffered TMA path.  FP32:
+// the fixed-point records (the difference of two fractions modulo 2^32 is the minimum-image
+// displacement) and the pair arithmetic of the cell kernel (pair_s, FP32 near pairs with the
+// exact r^2); FP64: the wrapped positions with an explicit minimum image.
 template <class T, bool kVir, bool kLJ>
 __global__ void __launch_bounds__(kWarps * 32)
-k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2, T beta,
-                T two_b_rpi, double *__restrict__ f_out, double *__restrict__ phi_out,
+k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, const uint4 *__restrict__ pu,
+                int n, T L, T rc2, T beta, T two_b_rpi, ScaledK K, double inv_s,
+                double *__restrict__ f_out, double *__restrict__ phi_out,
                 double *__restrict__ e_tile, double *__restrict__ vir_tile, int64_t vcap,
                 LJArgs lj, int *__restrict__ status)
 {
     using T4 = typename Vec4<T>::type;
+    constexpr bool kFP32 = sizeof(T) == 4;
+    static_assert(sizeof(T4) == sizeof(uint4) || !kFP32, "FP32 records and float4 share a size");
     __shared__ T4 ljs[kLJ ? EWALD_LJ_MAX_TYPES * EWALD_LJ_MAX_TYPES : 1];
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[kWarps][2];
@@ -1184,22 +1190,28 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
         fence_mbar_init();
     }
     __syncwarp();
-    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2);
+    // (FP32: sigma^2 in units of S^2, S = inv_s^-1 the fixed-point step)
+    if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2, kFP32 ? inv_s * inv_s : 1.0);
     const int tile = blockIdx.x * kWarps + warp;
     if (tile * 32 >= n) return;
     const int i = tile * 32 + lane;
     const bool valid = i < n;
-    const T4 pi = pl[valid ? i : n - 1];
-    const T4 *ljrow = kLJ ? ljs + lj.tsort[valid ? i : n - 1] * lj.ntypes : nullptr;
+    const int ii = valid ? i : n - 1;
+    // the staged records: FP32 the fixed-point fractions, FP64 the wrapped positions
+    const T4 *src = kFP32 ? reinterpret_cast<const T4 *>(pu) : pl;
+    const T4 pi = src[ii];
+    const uint4 pi_u = kFP32 ? pu[ii] : make_uint4(0, 0, 0, 0);
+    const T4 *ljrow = kLJ ? ljs + lj.tsort[ii] * lj.ntypes : nullptr;
     const T invL = T(1) / L;
-    PairAcc<T, kVir, kLJ> acc{};
-    const T nb2 = sizeof(T) == 4 ? -beta * beta * T(kLog2e) : -beta * beta;
+    using Acc = PairAcc<T, kVir, kLJ>;
+    Acc acc{}, tot{}, comp{};     // sums of the current chunk, totals, Kahan compensation
+    const T nb2 = kFP32 ? -beta * beta * T(kLog2e) : -beta * beta;
     uint32_t phase[2] = {0u, 0u};
     const int nchunks = (n + kCapAll - 1) / kCapAll;
     if (lane == 0) {
         int cnt = min(kCapAll, n);
         mbar_expect_tx(&bar[0], cnt * (uint32_t)sizeof(T4));
-        tma_bulk_g2s(buf[0], pl, cnt * (uint32_t)sizeof(T4), &bar[0]);
+        tma_bulk_g2s(buf[0], src, cnt * (uint32_t)sizeof(T4), &bar[0]);
     }
     bool ok = true;
     int b = 0;
@@ -1208,24 +1220,32 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
             int g = (c + 1) * kCapAll, cnt = min(kCapAll, n - g);
             fence_proxy_async();
             mbar_expect_tx(&bar[b ^ 1], cnt * (uint32_t)sizeof(T4));
-            tma_bulk_g2s(buf[b ^ 1], pl + g, cnt * (uint32_t)sizeof(T4), &bar[b ^ 1]);
+            tma_bulk_g2s(buf[b ^ 1], src + g, cnt * (uint32_t)sizeof(T4), &bar[b ^ 1]);
         }
         if (!warp_wait(&bar[b], phase[b])) { ok = false; break; }
         phase[b] ^= 1u;
         const int cnt = min(kCapAll, n - c * kCapAll);
         const T4 *sb = buf[b];
         for (int j = 0; j < cnt; ++j) {
-            T4 p = sb[j];
-            T dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
-            dx -= L * rint(dx * invL);
-            dy -= L * rint(dy * invL);
-            dz -= L * rint(dz * invL);
-            // evaluate the pair at the minimum image: shift the partner, keep the target
-            T4 pj = p;
-            pj.x = pi.x - dx; pj.y = pi.y - dy; pj.z = pi.z - dz;
-            pair<T, T4>(acc, pj, pi.x, pi.y, pi.z, rc2, beta, nb2, two_b_rpi, ljrow,
-                        kLJ ? lj.tsort[c * kCapAll + j] : 0);
+            const int tj = kLJ ? lj.tsort[c * kCapAll + j] : 0;
+            if constexpr (kFP32) {
+                const uint4 pj = reinterpret_cast<const uint4 *>(sb)[j];
+                pair_s<false, T4>(acc, (int)(pi_u.x - pj.x), (int)(pi_u.y - pj.y),
+                                  (int)(pi_u.z - pj.z), __uint_as_float(pj.w), K, ljrow, tj);
+            } else {
+                T4 p = sb[j];
+                T dx = pi.x - p.x, dy = pi.y - p.y, dz = pi.z - p.z;
+                dx -= L * rint(dx * invL);
+                dy -= L * rint(dy * invL);
+                dz -= L * rint(dz * invL);
+                // evaluate the pair at the minimum image: shift the partner, keep the target
+                T4 pj = p;
+                pj.x = pi.x - dx; pj.y = pi.y - dy; pj.z = pi.z - dz;
+                pair<T, T4>(acc, pj, pi.x, pi.y, pi.z, rc2, beta, nb2, two_b_rpi, ljrow, tj);
+            }
         }
+        acc_add_rows(tot, comp, acc);
+        acc = Acc{};
         __syncwarp();
         b ^= 1;
     }
@@ -1234,22 +1254,29 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, int n, T L, T rc2
         warp_wait(&bar[b ^ 1], phase[b ^ 1]);
         return;
     }
-    const double qi = (double)pi.w;
+    // FP32: back from fixed-point units (forces 1 / S^2, potential, Coulomb virial and
+    // Lennard-Jones force 1 / S), see pair_s
+    const double fsc = kFP32 ? inv_s * inv_s : 1.0;
+    const double psc = kFP32 ? inv_s : 1.0;
+    const double qi = kFP32 ? (double)__uint_as_float(pi_u.w) : (double)pi.w;
+    const double sx = (double)tot.fx - (double)comp.fx, sy = (double)tot.fy - (double)comp.fy,
+                 sz = (double)tot.fz - (double)comp.fz, sp = (double)tot.phi - (double)comp.phi;
+    const double phi_i = psc * sp;
     if (valid) {
-        double f[3] = {qi * (double)acc.fx, qi * (double)acc.fy, qi * (double)acc.fz};
+        double f[3] = {qi * fsc * sx, qi * fsc * sy, qi * fsc * sz};
         if constexpr (kLJ) {
-            f[0] += (double)acc.lj_f[0];
-            f[1] += (double)acc.lj_f[1];
-            f[2] += (double)acc.lj_f[2];
+            f[0] += psc * (double)tot.lj_f[0];
+            f[1] += psc * (double)tot.lj_f[1];
+            f[2] += psc * (double)tot.lj_f[2];
         }
         f_out[3 * (int64_t)i + 0] = f[0];
         f_out[3 * (int64_t)i + 1] = f[1];
         f_out[3 * (int64_t)i + 2] = f[2];
-        phi_out[i] = (double)acc.phi;
+        phi_out[i] = phi_i;
     }
-    const double e = warp_sum(valid ? qi * (double)acc.phi : 0.0);
+    const double e = warp_sum(valid ? qi * phi_i : 0.0);
     if (lane == 0) e_tile[tile] = e;
-    acc_store_tile(acc, valid, qi, lane, vir_tile, vcap, lj.e_tile, tile);
+    acc_store_tile(tot, valid, qi, lane, vir_tile, vcap, lj.e_tile, tile, psc);
 }
 
 template <class T, bool kVir, bool kLJ>
@@ -1262,6 +1289,18 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
     const size_t smem = (size_t)kWarps * 2 * kCapAll * sizeof(typename Vec4<T>::type);
     const T beta = (T)p.beta, rc2 = (T)(p.rc * p.rc);
     const T tbr = (T)(2.0 * p.beta / sqrt(kPi));
+    // FP32: constants in units of the fixed-point step S = L / 2^32 (see pair_s); near pairs
+    // are those within 2.5 mean particle spacings (at most r_c)
+    const double S = p.L / 4294967296.0;
+    const double spacing = cbrt(p.L * p.L * p.L / (double)(n > 0 ? n : 1));
+    const double rnear = fmin(2.5 * spacing, p.rc);
+    ScaledK K;
+    K.rc2s = (float)(p.rc * p.rc / (S * S));
+    K.rn2s = (float)(rnear * rnear / (S * S));
+    K.beta_s = (float)(p.beta * S);
+    K.nb2l_s = (float)(-p.beta * p.beta * S * S * 1.4426950408889634);
+    K.c_s = (float)(2.0 * p.beta / sqrt(kPi) * S);
+    K.cb2_s = (float)(2.0 * p.beta / sqrt(kPi) * S * (p.beta * S) * (p.beta * S));
     cudaError_t e;
     if (p.w == 0) {
         auto kern = k_real_allpairs<T, kVir, kLJ>;
@@ -1269,8 +1308,8 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         if (e != cudaSuccess) return e;
         int tiles = (int)((n + 31) / 32);
         kern<<<(tiles + kWarps - 1) / kWarps, kWarps * 32, smem, st>>>(
-            pl, (int)n, (T)p.L, rc2, beta, tbr, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap, lj,
-            p.d_status);
+            pl, ws.pu, (int)n, (T)p.L, rc2, beta, tbr, K, 1.0 / S, ws.f_real, ws.phi_real,
+            ws.e_tile, vir, vcap, lj, p.d_status);
     } else {
         // (the FP64 kernel has no near-pair modes: one instantiation)
         auto kern = (sizeof(T) == 4 && p.near_df) ? k_real_rows<T, 1, kVir, kLJ, sizeof(T) == 4>
@@ -1282,18 +1321,6 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         const typename RowRec<T>::type *pr;
         if constexpr (sizeof(T) == 4) pr = ws.pu;
         else pr = ws.pg;
-        // FP32: constants in units of the fixed-point step S = L / 2^32 (see pair_s); near
-        // pairs are those within 2.5 mean particle spacings (at most r_c)
-        const double S = p.L / 4294967296.0;
-        const double spacing = cbrt(p.L * p.L * p.L / (double)(n > 0 ? n : 1));
-        const double rnear = fmin(2.5 * spacing, p.rc);
-        ScaledK K;
-        K.rc2s = (float)(p.rc * p.rc / (S * S));
-        K.rn2s = (float)(rnear * rnear / (S * S));
-        K.beta_s = (float)(p.beta * S);
-        K.nb2l_s = (float)(-p.beta * p.beta * S * S * 1.4426950408889634);
-        K.c_s = (float)(2.0 * p.beta / sqrt(kPi) * S);
-        K.cb2_s = (float)(2.0 * p.beta / sqrt(kPi) * S * (p.beta * S) * (p.beta * S));
         // double-float constants of the near pairs, and their reach (with the range margin)
         NearK NK;
         const double bs = p.beta * S, cs = 2.0 * p.beta / sqrt(kPi) * S;
