@@ -70,3 +70,25 @@ def test_synchronous_and_host_entry_points_repeat():
         for _ in range(3):
             Fh, eh = ew.compute_host(pos, q)
             assert np.array_equal(Fh, F0) and np.array_equal(eh, E0)
+
+
+def test_results_do_not_depend_on_the_plans_history():
+    """The cell grid follows each evaluation's particle count, so a plan that evaluated a
+    larger system first (buffers kept, grid switched) gives the smaller system the same bits
+    as a fresh plan, and switching back gives the larger one its own bits again."""
+    need_gpu()
+    L, beta, rc, km = 16.0, 0.9, 4.0, 14
+    big_pos, big_q, _ = W.random_neutral(4096, L=L, hard_core=0.8, seed=51)
+    small_pos, small_q, _ = W.random_neutral(1500, L=L, hard_core=0.8, seed=52)
+    Fb0, Eb0 = _fresh(big_pos, big_q, L, beta, rc, km)
+    Fs0, Es0 = _fresh(small_pos, small_q, L, beta, rc, km)
+    with Ewald(L, beta, rc, km, "mixed") as ew:
+        for pos, q, F0, E0 in ((big_pos, big_q, Fb0, Eb0), (small_pos, small_q, Fs0, Es0),
+                               (big_pos, big_q, Fb0, Eb0), (small_pos, small_q, Fs0, Es0)):
+            n = len(q)
+            F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+            E = torch.empty(4, dtype=torch.float64, device="cuda")
+            for _ in range(3):                    # direct, capture, replay
+                ew.compute_async(dev(pos), dev(q), F, E)
+                assert ew.status() == 0
+                assert np.array_equal(F.cpu().numpy(), F0) and np.array_equal(E.cpu().numpy(), E0)
