@@ -933,8 +933,9 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     __syncthreads();
     // (FP32: sigma^2 in units of S^2, S = inv_s^-1 the fixed-point step)
     if constexpr (kLJ) load_lj_table<T, T4>(ljs, lj, (double)rc2, kFP32 ? inv_s * inv_s : 1.0);
-    // with split = 2 the warps 2t and 2t + 1 of a block share a group of targets, each taking
-    // every other row of the stencil; their sums are added (in that order) at the end
+    // with split = 2 or 4 the warps of a block share groups of targets (warps 2t, 2t + 1 or
+    // all four), each taking every split-th row of the stencil; their sums are added in that
+    // order at the end
     const int part = warp % split;
     const int grp = (blockIdx.x * kWarps + warp) / split;   // tile of this warp
     const int t = lane / G, g = lane % G;
@@ -1124,21 +1125,23 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
         sz += __shfl_xor_sync(0xffffffffu, sz, o);
         sp += __shfl_xor_sync(0xffffffffu, sp, o);
     }
-    if (split == 2) {
-        // every warp of the block reaches this barrier (none has returned with split = 2)
-        if (part == 1) {
+    if (split > 1) {
+        // every warp of the block reaches this barrier (none has returned with split > 1);
+        // part 0 adds the other parts' sums in part order
+        if (part > 0) {
             xacc[warp][lane] = acc;
             if constexpr (kFP32) xsum[warp][lane] = double4_32a{sx, sy, sz, sp};
         }
         __syncthreads();
-        if (part == 1 || !active) return;
-        acc_add(acc, xacc[warp + 1][lane]);
-        if constexpr (kFP32) {
-            const double4_32a o = xsum[warp + 1][lane];
-            sx += o.x; sy += o.y; sz += o.z; sp += o.w;
-        } else {
-            sx = acc.fx; sy = acc.fy; sz = acc.fz; sp = acc.phi;
+        if (part > 0 || !active) return;
+        for (int k = 1; k < split; ++k) {
+            acc_add(acc, xacc[warp + k][lane]);
+            if constexpr (kFP32) {
+                const double4_32a o = xsum[warp + k][lane];
+                sx += o.x; sy += o.y; sz += o.z; sp += o.w;
+            }
         }
+        if constexpr (!kFP32) { sx = acc.fx; sy = acc.fy; sz = acc.fz; sp = acc.phi; }
     }
     const double qi = (double)rec_q(pi);
     const bool mine = valid && g == 0;
@@ -1279,6 +1282,15 @@ k_real_allpairs(const typename Vec4<T>::type *__restrict__ pl, const uint4 *__re
     acc_store_tile(tot, valid, qi, lane, vir_tile, vcap, lj.e_tile, tile, psc);
 }
 
+// Warps per group of targets of the cell kernel: 4 below 24 groups per SM, 2 below 32, else
+// 1 (measured on GB300, steps in ms with 1 / 2 / 4 warps per group: 32,768 ions 0.52 / 0.47 /
+// 0.43; 65,536: 1.10 / 1.05 / 1.03; 131,072: 2.87 / 2.92 / 2.96; 262,144: 4.34 / 4.33 / 4.40).
+int real_split(int64_t groups, int num_sms)
+{
+    if (groups < 24 * (int64_t)num_sms) return 4;
+    return groups < 32 * (int64_t)num_sms ? 2 : 1;
+}
+
 template <class T, bool kVir, bool kLJ>
 cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, cudaStream_t st)
 {
@@ -1315,9 +1327,9 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         auto kern = (sizeof(T) == 4 && p.near_df) ? k_real_rows<T, 1, kVir, kLJ, sizeof(T) == 4>
                                                   : k_real_rows<T, 1, kVir, kLJ, false>;
         const int64_t groups = real_tile_capacity(p, n);
-        // two warps per group of targets when one warp per group would leave the SMs short
-        // of warps
-        const int split = groups < 16 * (int64_t)p.num_sms ? 2 : 1;
+        // two or four warps per group of targets when one warp per group would leave the SMs
+        // short of warps
+        const int split = real_split(groups, p.num_sms);
         const typename RowRec<T>::type *pr;
         if constexpr (sizeof(T) == 4) pr = ws.pu;
         else pr = ws.pg;
