@@ -13,8 +13,9 @@ from paper_1708_01135_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# 16^3 ions, r_c = 4: cell mode (12 cells per side, stencil half-width 3) with two warps per
-# group of targets; 44^3 ions: one warp per group (at least 16 groups per SM)
+# 16^3 ions, r_c = 4: cell mode (12 cells per side, stencil half-width 3) with four warps per
+# group of targets; 44^3 ions: two warps per group (one warp per group: the 262,144-ion crystal
+# of test_gpu_large.py)
 CASES = [(16, 0.93, 4.0, 11), (44, 0.80, 4.8, 13)]
 
 
