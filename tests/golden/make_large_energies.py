@@ -6,11 +6,11 @@ every particle; for these systems the oracle needs minutes for them, so this scr
 them once and stores the results.  It calls only the oracle (oracle/) and the seeded input
 generators (paper_1708_01135_gb300/workloads.py, which hold none of the method's arithmetic).
 
-  python tests/golden/make_large_energies.py
+  python tests/golden/make_large_energies.py [workload ...]
 
 Stored per workload: the parameters (r_c, beta, k_max: the ones the parameter tuner of the
-library picks for the benchmark's tuning tolerance of the workload, 4e-7 for the crystal and
-1e-6 otherwise, written out here as plain numbers), E_real (cell-list
+library picks for the benchmark's tuning tolerance of the workload, 4e-7 for the crystal
+(at the benchmark's fixed r_c = 12) and 1e-6 otherwise, written out here as plain numbers), E_real (cell-list
 real-space sum), E_recip (only where the full structure factor is affordable), E_self,
 E_real_scale = 1/2 sum_i |q_i phi_i| (the magnitude against which the rounding error of
 E_real is judged: for a random system E_real is a small difference of large sums), and
@@ -34,7 +34,7 @@ from paper_1708_01135_gb300 import workloads as W  # noqa: E402
 
 # (workload, r_c, beta, k_max, full reciprocal energy?)
 CASES = [
-    ("rocksalt_262144", 7.84, 0.4895666929104699, 39, True),
+    ("rocksalt_262144", 12.0, 0.31985023936817364, 26, True),
     ("random_2097152", 10.72, 0.34672781612405207, 53, False),
 ]
 
@@ -44,8 +44,17 @@ def digest(a):
 
 
 def main():
+    # python tests/golden/make_large_energies.py [workload ...]: only the named workloads are
+    # evaluated again, the other stored entries are kept
+    only = set(sys.argv[1:])
+    path = os.path.join(HERE, "large_energies.json")
     out = {}
+    if only and os.path.exists(path):
+        with open(path) as f:
+            out = json.load(f)
     for name, rc, beta, kmax, full_recip in CASES:
+        if only and name not in only:
+            continue
         t0 = time.time()
         pos, q, L = getattr(W, name)()
         rec = {"n": int(len(q)), "L": float(L), "r_c": rc, "beta": beta, "k_max": kmax,
@@ -61,7 +70,7 @@ def main():
             rec["E_recip"] = e_recip
         out[name] = rec
         print(name, rec, f"{time.time() - t0:.0f} s", flush=True)
-    with open(os.path.join(HERE, "large_energies.json"), "w") as f:
+    with open(path, "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
 

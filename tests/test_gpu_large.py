@@ -1,6 +1,7 @@
 """Full-size parity at the two large workloads (262,144-ion rock-salt, 2,097,152-ion random
 +-1/+-2 system), in the configuration the benchmark times: parameters from the tuner at the benchmark's tuning
-tolerance (bench.TUNE_TOL), r_c free, and the crystal's near pairs in double-float.
+tolerance (bench.TUNE_TOL) and r_c where bench.WORKLOADS fixes it, and the crystal's near pairs
+in double-float.
 
 The oracle cannot evaluate these systems in seconds, so the checks are on samples and on
 stored oracle sums:
@@ -52,7 +53,7 @@ def _load(name):
     g = _gold()[name]
     assert _digest(pos) == g["pos_sha256"] and _digest(q) == g["q_sha256"], \
         "generated inputs differ from the ones the stored energies belong to"
-    rc, beta, km = tune(len(q), L, bench.TUNE_TOL.get(name, bench.TOL))
+    rc, beta, km = tune(len(q), L, bench.TUNE_TOL.get(name, bench.TOL), r_c=bench.WORKLOADS[name][1])
     assert rc == g["r_c"] and km == g["k_max"] and abs(beta - g["beta"]) <= 1e-12 * beta
     return pos, q, L, g
 
