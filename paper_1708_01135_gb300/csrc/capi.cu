@@ -658,11 +658,6 @@ static void build_rows(Plan &p)
     p.nk = koff;
 }
 
-// Cell grid for n particles (n = 0 while the count is not known): cells of side >= r_c / w
-// with a (2w + 1)^3 stencil that does not wrap onto itself.  w = 3 where such cells still hold
-// 16 particles or more (dense systems with long cutoffs, where the finer stencil follows the
-// cutoff sphere more closely and the per-cell overhead stays small), else w = 2, 1, or 0
-// (all pairs with the minimum image).
 // Cell grid of the real-space pairs: nc^3 cubes of side L / nc, a stencil of |dy|, |dz| <= w
 // rows with w = ceil(r_c nc / L), and 2 w + 1 <= nc so that the stencil's rows (and the
 // cells of a row a target can reach) are distinct.  The side aims at max(1.33 rho^-1/3,
@@ -670,7 +665,9 @@ static void build_rows(Plan &p)
 // disk, so that each target's candidate ranges follow its cutoff sphere closely (the pair
 // kernel takes the cells of every row within each target's own reach) while a row holds
 // enough candidates to pay for its set-up (measured on GB300, 32,768 ions at r_c = 4: cells
-// of side 1, 1.33, 1.6, 2 take 0.172, 0.129, 0.135, 0.125 ms).  Without the density (plan set-up)
+// of side 1, 1.33, 1.6, 2 take 0.172, 0.129, 0.135, 0.125 ms; at long cutoffs, sides r_c / 6,
+// r_c / 7, r_c / 8 test fewer candidates per partner but walk up to twice the rows, and were no
+// faster at 262,144 and 2,097,152 ions).  Without the density (plan set-up)
 // the side is r_c / 2; the grid is chosen again once the particle count is known.  Boxes too
 // small for such a stencil use the all-pairs mode (w = 0, one cell).
 static void cell_grid(double L, double rc, int64_t n, int &nc_out, int &w_out)
