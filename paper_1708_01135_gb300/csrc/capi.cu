@@ -262,7 +262,7 @@ void free_workspace(Plan &p)
     graph_reset(p);
     Workspace &ws = p.ws;
     void *ptrs[] = {ws.key, ws.perm, ws.key_sorted, ws.hist, ws.cell_start, ws.cell_total,
-                    ws.row_start, ws.perm1, ws.key1,
+                    ws.row_start, ws.perm1, ws.key1, ws.unordered,
                     ws.tiles, ws.tile_off, ws.pg, ws.pl64, ws.pl32, ws.pu,
                     ws.f_real, ws.f_recip, ws.e_tile, ws.qpart, ws.phi_real, ws.phi_recip,
                     ws.vir_tile, ws.vir_part, ws.type_sorted, ws.elj_tile};
@@ -425,6 +425,7 @@ cudaError_t grow_workspace(Plan &p, int64_t n)
     EW_TRY(dmalloc(p, &ws.key1, sizeof(int) * cap));
     EW_TRY(dmalloc(p, &ws.tiles, sizeof(int2) * tiles));
     EW_TRY(dmalloc(p, &ws.tile_off, sizeof(int) * (p.nc * p.nc + 1)));
+    EW_TRY(dmalloc(p, &ws.unordered, sizeof(int)));
     EW_TRY(dmalloc(p, &ws.pg, sizeof(double4_32a) * cap));
     if (p.precision == EWALD_FP64) EW_TRY(dmalloc(p, &ws.pl64, sizeof(double4_32a) * cap));
     else EW_TRY(dmalloc(p, &ws.pl32, sizeof(float4) * cap));
@@ -617,7 +618,7 @@ size_t plan_footprint(const Plan &p, int64_t n)
     b += sizeof(int) * (ncells + 1 + 2 * nrows + 1) + sizeof(int2) * tiles + sizeof(int) * (nrows + 1);
     b += (sizeof(double4_32a) + (p.precision == EWALD_FP64 ? sizeof(double4_32a) : sizeof(float4)) + sizeof(uint4)) * (size_t)n;
     b += sizeof(double) * 8 * (size_t)n + sizeof(double) * 14 * tiles + sizeof(double) * 3 * ((n + 255) / 256);
-    b += sizeof(int) * (size_t)n;
+    b += sizeof(int) * (size_t)n + sizeof(int);
     b += sizeof(double) * 6 * kVirBlocks;
     b += uses_tc(p.precision) ? recip_tc_bytes(p, n) : recip_simt_bytes(p, n);
     b += sizeof(double) * 3 * (size_t)p.nk + sizeof(int) * 3 * (size_t)p.nk + sizeof(RowInfo) * p.R;

@@ -11,7 +11,8 @@
 //      row histograms, a column scan over chunks, a scan over rows, and an in-order scatter
 //      per chunk;
 //   2. inside every row, by c_x: one block per row counts its cells, scans them (the cell
-//      offsets) and places the row's particles in the order level 1 left them.
+//      offsets) and places the row's particles in the order level 1 left them; for the
+//      cell kernel, every cell is then ordered by x (fixed-point fraction, k_rowsort).
 // Equal keys keep their input order, so the result is exactly determined by the input
 // (bit-exact integer work).
 #include <cuda_runtime.h>
@@ -205,10 +206,12 @@ __device__ __forceinline__ void pack_one(int64_t s, int i, int k, const double *
 // ranges per stencil row for all of them.  One block of 1024 threads: every thread scans a
 // contiguous slice serially; slice sums are scanned in shared memory.
 __global__ void k_scan_rows(int nrows, int ts, const int *__restrict__ cnt,
-                            int *__restrict__ row_start, int *__restrict__ tile_off)
+                            int *__restrict__ row_start, int *__restrict__ tile_off,
+                            int *__restrict__ unordered)
 {
     __shared__ int part[2][1024];
     const int t = threadIdx.x;
+    if (t == 0) *unordered = 0;      // (k_rowsort sets it for a cell it cannot order)
     const int per = (nrows + blockDim.x - 1) / blockDim.x;
     const int b = t * per, e = min(nrows, b + per);
     int s0 = 0, s1 = 0;
@@ -243,18 +246,29 @@ __global__ void k_scan_rows(int nrows, int ts, const int *__restrict__ cnt,
     }
 }
 
+// Cells of more particles than this keep the order of level 2 (the x order below costs a
+// pass over the cell per particle).
+constexpr int kXOrderMax = 256;
+
 // a2 (level 2) and a3: row r of cells (particles [row_start[r], row_start[r+1]) in level-1
 // order): counts per cell, the cell offsets cell_start[r nc .. r nc + nc - 1], the in-order
 // placement of the row's particles by cell (warp 0), then the packing of the row's sorted
 // particles and, with tiles, the row's warp tiles (all threads).  One block per row.
+// With tiles (the cell kernel's layout) the particles of every cell are ordered by x before
+// they are packed: by the 32-bit fixed-point fraction that the packed record holds, taken
+// relative to the cell's centre (so a fraction that rounds to 2^32 next to x = L stays at
+// the end of the last cell), equal fractions in level-2 order.  The real-space kernel cuts
+// each target's range at its own x window with this order.  A cell of more than kXOrderMax
+// particles keeps its level-2 order and sets *unordered, which turns the cut off.
 __global__ void k_rowsort(int nrows, int nc, int64_t n, const int *__restrict__ row_start,
-                          const int *__restrict__ perm1, const int *__restrict__ key1,
+                          int *__restrict__ perm1, int *__restrict__ key1,
                           int *__restrict__ perm, int *__restrict__ key_sorted,
                           int *__restrict__ cell_start, const double *__restrict__ pos,
                           const double *__restrict__ q, double L, double side,
                           double4_32a *__restrict__ pg, double4_32a *__restrict__ pl64,
                           float4 *__restrict__ pl32, uint4 *__restrict__ pu, int ts,
-                          const int *__restrict__ tile_off, int2 *__restrict__ tiles)
+                          const int *__restrict__ tile_off, int2 *__restrict__ tiles,
+                          int *__restrict__ unordered)
 {
     __shared__ int off[kMaxCellsPerSide];
     const int r = blockIdx.x;
@@ -298,6 +312,42 @@ __global__ void k_rowsort(int nrows, int nc, int64_t n, const int *__restrict__ 
     }
     // (the block's own global writes are visible to the block after the barrier)
     __syncthreads();
+    if (tiles) {
+        // x order inside every cell; perm1 and key1 of the row (read only by this block, and
+        // no longer needed) hold the level-2 order and the sort keys
+        const double scale = 4294967296.0 / L;
+        for (int s = b + threadIdx.x; s < e; s += blockDim.x) {
+            const int i = perm[s];
+            double x = pos[3 * (int64_t)i + 0];
+            const double y = pos[3 * (int64_t)i + 1], z = pos[3 * (int64_t)i + 2];
+            if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(q[i]))) x = 0.0;
+            x = wrap_box(x, L);
+            const unsigned ux = (unsigned)((unsigned long long)llrint(x * scale) & 0xffffffffull);
+            const int c = key_sorted[s] % nc;
+            const unsigned uc =
+                (unsigned)((unsigned long long)llrint(((double)c + 0.5) * side * scale) & 0xffffffffull);
+            key1[s] = (int)(ux - uc);
+            perm1[s] = i;
+        }
+        __syncthreads();
+        for (int s = b + threadIdx.x; s < e; s += blockDim.x) {
+            const int c = key_sorted[s] % nc;
+            const int cb = cell_start[r * nc + c];
+            const int ce = c + 1 < nc ? cell_start[r * nc + c + 1] : e;
+            if (ce - cb > kXOrderMax) {
+                *unordered = 1;                  // (perm[s] is still perm1[s])
+                continue;
+            }
+            const int v = key1[s];
+            int rank = 0;
+            for (int t = cb; t < ce; ++t) {
+                const int u = key1[t];
+                rank += (u < v) || (u == v && t < s);
+            }
+            perm[cb + rank] = perm1[s];
+        }
+        __syncthreads();
+    }
     for (int s = b + threadIdx.x; s < e; s += blockDim.x)
         pack_one(s, perm[s], key_sorted[s], pos, q, L, side, nc, pg, pl64, pl32, pu);
     if (tiles) {
@@ -324,7 +374,8 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
                                    ws.key, ws.hist, ws.qpart, p.d_status);
     k_colscan<<<(nrows + 255) / 256, 256, 0, st>>>(nb, nrows, ws.hist, ws.cell_total);
     const int ts = p.w > 0 ? real_tile_size(p) : 0;
-    k_scan_rows<<<1, 1024, 0, st>>>(nrows, ts, ws.cell_total, ws.row_start, ws.tile_off);
+    k_scan_rows<<<1, 1024, 0, st>>>(nrows, ts, ws.cell_total, ws.row_start, ws.tile_off,
+                                    ws.unordered);
     const size_t key_bytes = sizeof(int) * (size_t)chunk;
     const int use_smem = key_bytes + sizeof(int) * (size_t)nrows <= 200 * 1024;
     size_t smem = key_bytes + (use_smem ? sizeof(int) * (size_t)nrows : 0);
@@ -339,7 +390,7 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
                                      ws.key_sorted, ws.cell_start, pos, q, p.L, p.cell_side,
                                      ws.pg, (need64 && p.w == 0) ? ws.pl64 : nullptr,
                                      (!need64 && p.w == 0) ? ws.pl32 : nullptr, ws.pu, ts,
-                                     ws.tile_off, p.w > 0 ? ws.tiles : nullptr);
+                                     ws.tile_off, p.w > 0 ? ws.tiles : nullptr, ws.unordered);
     p.launches += 5;
     return cudaGetLastError();
 }

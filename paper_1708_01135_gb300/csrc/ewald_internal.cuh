@@ -65,6 +65,7 @@ struct Workspace {
     int *key1 = nullptr;         // [n] cell key, sorted by row (binning level 1)
     int2 *tiles = nullptr;       // [max tiles] (row, first slot) of the cell kernel's warps
     int *tile_off = nullptr;     // [nrows + 1] exclusive offsets; tile_off[nrows] = tiles
+    int *unordered = nullptr;    // [1] nonzero when a cell was too full to order by x
     // packed particles (sorted)
     double4_32a *pg = nullptr;       // wrapped global position + q (FP64)
     double4_32a *pl64 = nullptr;     // cell-local position + q (FP64, all-pairs mode only)

@@ -6,31 +6,36 @@
 //   E_real = 1/2 sum_i q_i phi_i            (r_ij = r_i - r_j, minimum image)
 //
 // GPU design (templated on FP64 and FP32 arithmetic), cell mode:
-//   * The box is cut into nc^3 cubic cells of side s ~ max(rho^-1/3, r_c / 5) (about one to
-//     seven particles each), sorted by cell key (c_z nc + c_y) nc + c_x, so that every row of
-//     cells along x (fixed c_y, c_z) is a contiguous range of the sorted arrays.
-//   * A warp owns 32 / G consecutive sorted targets and G lanes per target.  It visits the
-//     rows (c_y + dy, c_z + dz), |dy|, |dz| <= w, in a fixed order.  For each row every
-//     target takes its own exact reach: the distance d from its (y, z) to the row's square
-//     gives the x half-width sqrt(r_c^2 - d^2), and only the cells of the row that overlap
-//     [x - reach, x + reach] are candidates (one or, where the row wraps, two contiguous
-//     ranges).  The G lanes of a target split that range; the warp runs as many steps as
-//     its longest range needs.  Candidates are read straight from the sorted arrays (they
-//     stay in L1/L2: neighbouring targets share most of them).  This keeps the candidates
-//     close to the cutoff sphere of each target (about 1.6 to 1.8 per partner inside r_c)
-//     instead of the cutoff sphere of a whole tile of targets.
+//   * The box is cut into nc^3 cubic cells of side s ~ max(1.33 rho^-1/3, r_c / 5), sorted
+//     by cell key (c_z nc + c_y) nc + c_x, so that every row of cells along x (fixed c_y,
+//     c_z) is a contiguous range of the sorted arrays; inside a cell the particles are in x
+//     order (binning, k_rowsort).
+//   * A warp owns up to 32 consecutive sorted targets of one row of cells, one lane each.
+//     It visits the rows (c_y + dy, c_z + dz), |dy|, |dz| <= w, in a fixed order.  For each
+//     row every target takes its own reach: the distance d from its (y, z) to the row's
+//     square gives the x half-width sqrt(r_c^2 - d^2), and its candidates are the particles
+//     of the row with x in [x - reach, x + reach]: the cells overlapping that window (one
+//     or, where the row wraps, two contiguous ranges), cut to the window by two binary
+//     searches on the x order.  The warp stages the union of its targets' ranges in shared
+//     memory (bulk copies on an mbarrier, double-buffered) and every lane searches and
+//     walks its own range; the warp runs as many steps as its longest range needs.  This
+//     keeps the candidates close to the cutoff sphere of each target (about 1.3 to 1.6 per
+//     partner inside r_c) instead of the cutoff sphere of a whole tile of targets.  With
+//     few groups of targets per SM, two or four warps share a group, each taking every
+//     second or fourth row.
 //   * FP32: positions are 32-bit fixed-point fractions of the box (x / L 2^32), so the
 //     difference of two of them modulo 2^32 is the minimum-image displacement exactly, at
 //     2^-32 L resolution whatever the box size (periodic images are implicit); each component
 //     is rounded once, to FP32.  FP64: wrapped global coordinates, with the image shift of a
 //     wrapped row or range.
-//   * erfc in FP32 is t exp(-x^2) P(t), t = 1 / (1 + p x), with a degree-7 polynomial P fitted
-//     to erfc(x) exp(x^2) / t on [0, 6] (csrc/fit_erfc.py derives the coefficients; relative
-//     error 3.5e-8 in exact arithmetic): one exp2, one reciprocal and the pair's rsqrt.
-//   * Every target's sums are held by its lanes and combined in a fixed shuffle order; the
-//     target's force is written by one lane, and no two threads ever write the same particle
-//     (the paper's rule that a loop writes only its own particle, Section 3.2.3, with no
-//     atomics); energies are one FP64 partial per warp, summed in order by the finalize step.
+//   * erfc in FP32 is t exp(-x^2) P(u), t = 1 / (1 + p x), u = a t + b, with a degree-8
+//     polynomial P fitted to erfc(x) exp(x^2) / t (csrc/fit_erfc.py derives the
+//     coefficients): one exp2, one reciprocal and the pair's rsqrt.
+//   * Every target's sums are held by its lane (and, with shared groups, combined across the
+//     warps in part order); the target's force is written by one lane, and no two threads
+//     ever write the same particle (the paper's rule that a loop writes only its own
+//     particle, Section 3.2.3, with no atomics); energies are one FP64 partial per warp,
+//     summed in order by the finalize step.
 // All pairs mode (boxes too small for a stencil of distinct cells): one tile of 32 targets
 // per warp, every particle staged through a double-buffered bulk TMA copy (cp.async.bulk,
 // completion on an mbarrier) and read by all lanes as a broadcast.
@@ -774,6 +779,9 @@ struct RowItem {
     int c0, cnt;
     int off0, off1;
     int noff0, noff1;           // this target's near range (reach r_near) in the union
+    // x window (x-ordered cells): the candidates of [off0, off1) whose x displacement lies
+    // outside [-xr, xr] are cut off; xr = 0: no cut
+    int xr;
 };
 
 // Issue the bulk copies of an item into dst (lane 0 only): the parts of the union that the
@@ -797,6 +805,18 @@ __device__ __forceinline__ void issue_item(const RowItem &it, const R4 *__restri
     }
 }
 
+// First g in [lo, hi) whose x displacement (int)(ux - sb[g].x) is at most R, or hi; the
+// displacements do not increase along [lo, hi) (staged records in x order).
+__device__ __forceinline__ int first_within(const uint4 *sb, int lo, int hi, unsigned ux, int R)
+{
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)(ux - sb[mid].x) <= R) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
 // Walks the rows of the stencil (and the chunks of each row's union) of one warp.
 struct RowWalk {
     int w, nc, part, split;
@@ -814,8 +834,9 @@ struct RowWalk {
     int next_c0;
     bool in_row;
 
-    // Next row with a non-empty union; false at the end of the stencil.
-    __device__ bool next_row()
+    // Next row with a non-empty union; false at the end of the stencil.  x windows (every
+    // cell ordered by x): xw on, to_s the scale from length to fixed-point units.
+    __device__ bool next_row(bool xw, float to_s)
     {
         while (true) {
             if (!started) { started = true; dz = -w; dy = -w; }
@@ -829,9 +850,10 @@ struct RowWalk {
             const float gz = dz > 0 ? dz * sidef - zl : (dz < 0 ? zl - (dz + 1) * sidef : 0.f);
             const float d2 = gy * gy + gz * gz;
             int a0 = 1 << 30, a1 = -(1 << 30), n0 = 1 << 30, n1 = -(1 << 30);
+            float reach = 0.f;
             if (valid && d2 < rc2m) {
                 // (approximate square root: a relative error of 2^-22 is inside the margin)
-                const float reach = sqrt_ftz(rc2m - d2);
+                reach = sqrt_ftz(rc2m - d2);
                 int b0 = __float2int_rd((xl - reach) * inv_side);
                 int b1 = __float2int_rd((xl + reach) * inv_side);
                 b0 = b0 < -w ? -w : b0;
@@ -862,9 +884,14 @@ struct RowWalk {
             if (u.total() == 0) continue;
             row.dy = dy;
             row.dz = dz;
+            row.xr = 0;
             if (a0 <= a1) {
                 row.off0 = union_off(u, cs, nc, a0);
                 row.off1 = union_off(u, cs, nc, a1 + 1);
+                // the target's own x window [x - reach, x + reach] (in fixed-point units,
+                // rounded up): candidates beyond it (r above the reach radius, which the
+                // pair test would reject too) are cut off when the staged chunk is walked
+                if (xw) row.xr = __float2int_ru(reach * to_s) + 1;
             } else {
                 row.off0 = row.off1 = 0;
             }
@@ -879,10 +906,10 @@ struct RowWalk {
     }
 
     template <int kCapR>
-    __device__ bool next(RowItem &it)
+    __device__ bool next(RowItem &it, bool xw, float to_s)
     {
         if (!in_row || next_c0 >= row.u.total()) {
-            if (!next_row()) return false;
+            if (!next_row(xw, to_s)) return false;
             in_row = true;
             next_c0 = 0;
         }
@@ -901,8 +928,8 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
             const int *__restrict__ key_sorted, const int *__restrict__ cell_start,
             const int2 *__restrict__ tiles, const int *__restrict__ tile_total, int n,
             int nc, int w, double side_d, double L_d, T rc2, T beta, T two_b_rpi, ScaledK K,
-            NearK NK, double inv_s, int split, double *__restrict__ f_out,
-            double *__restrict__ phi_out, double *__restrict__ e_tile,
+            NearK NK, double inv_s, int split, int xwin, const int *__restrict__ unordered,
+            double *__restrict__ f_out, double *__restrict__ phi_out, double *__restrict__ e_tile,
             double *__restrict__ vir_tile, int64_t vcap, LJArgs lj, int *__restrict__ status)
 {
     using R4 = typename RowRec<T>::type;
@@ -968,6 +995,9 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     wk.rn2m = kNear ? NK.rn2m : 0.0f;
     wk.valid = valid;
     wk.cell_start = cell_start;
+    // x windows when the host allows them (reach + side < L/2) and binning ordered every
+    // cell by x (FP32 records only)
+    const bool xw = kFP32 && xwin && *unordered == 0;
     wk.rowctr = 0;
     wk.started = false;
     wk.in_row = false;
@@ -979,16 +1009,19 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     // gave up.
     uint32_t phase[2] = {0u, 0u};
     int b = 0;
+    auto next = [&](RowWalk &rw, RowItem &it) -> bool {
+        return rw.template next<kCapR>(it, xw, (float)inv_s);
+    };
     auto walk = [&](RowWalk &rw, auto &&item) -> bool {
         RowItem cur, nxt;
-        bool have_cur = active && rw.template next<kCapR>(cur);
+        bool have_cur = active && next(rw, cur);
         if (have_cur && lane == 0) {
             // (the buffer may have been read by the last walk, before its last __syncwarp)
             fence_proxy_async();
             issue_item(cur, pr, stage[warp][b], &bar[b]);
         }
         while (have_cur) {
-            const bool have_nxt = rw.template next<kCapR>(nxt);
+            const bool have_nxt = next(rw, nxt);
             if (have_nxt && lane == 0) {
                 // the other buffer was fully read before the last __syncwarp of the loop
                 fence_proxy_async();
@@ -1020,6 +1053,16 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     int *qt = kNear ? nq_t[warp] : nullptr;
     int qn = 0;
     bool ok = walk(wk, [&](const R4 *sb, int lo, int hi, const RowItem &cur) {
+        if constexpr (kFP32) {
+            // the x window: along a target's range the candidates are in x order (cells in
+            // order, each ordered by x), so their x displacements (int)(x_i - x_j) do not
+            // increase, and with reach + side < L/2 the int32 differences are exact; two
+            // binary searches of the staged records give the part inside [-xr, xr]
+            if (cur.xr && lo < hi) {
+                lo = first_within(sb, lo, hi, pi.x, cur.xr);
+                hi = first_within(sb, lo, hi, pi.x, -cur.xr - 1);
+            }
+        }
         for (int j = lo + g; j < hi; j += G) {
             const R4 pj = sb[j];
             int tj = 0;
@@ -1341,10 +1384,13 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         NK.c_h = (float)cs;
         NK.c_l = (float)(cs - (double)NK.c_h);
         NK.rn2m = (float)(rnear * rnear) * (1.0f + 1e-5f);
+        // x windows (FP32 records): every displacement a window test takes must stay below
+        // L/2 in magnitude, i.e. reach (r_c with the range margin) + one cell side < L/2
+        const int xwin = sizeof(T) == 4 && p.rc * 1.00001 + p.cell_side < 0.5 * p.L * (1.0 - 1e-6);
         kern<<<(unsigned)((groups * split + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(
             pr, ws.pg, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc,
-            (int)n, p.nc, p.w, p.cell_side, p.L, rc2, beta, tbr, K, NK, 1.0 / S, split, ws.f_real,
-            ws.phi_real, ws.e_tile, vir, vcap, lj, p.d_status);
+            (int)n, p.nc, p.w, p.cell_side, p.L, rc2, beta, tbr, K, NK, 1.0 / S, split, xwin,
+            ws.unordered, ws.f_real, ws.phi_real, ws.e_tile, vir, vcap, lj, p.d_status);
     }
     p.launches += 1;
     return cudaGetLastError();

@@ -1,7 +1,9 @@
 """Bit-exact check of the integer binning (steps a1-a2) against a CPU model of its
 definition: wrap x - L floor(x / L) (a result equal to L maps to 0), cell index
 min(floor(x nc / L), nc - 1), key (c_z nc + c_y) nc + c_x, and a stable sort by key (ties in
-input order)."""
+input order); in cell mode every cell of at most 256 particles is then ordered by the
+fixed-point x fraction round(x 2^32 / L) mod 2^32 taken relative to the cell centre's
+fraction (as a signed 32-bit difference), ties in input order."""
 import numpy as np
 import pytest
 
@@ -13,12 +15,21 @@ from paper_1708_01135_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _model(pos, L, nc):
+def _model(pos, L, nc, cell_mode):
     w = pos - L * np.floor(pos / L)
     w[w >= L] = 0.0
     c = np.minimum((w * (nc / L)).astype(np.int64), nc - 1)
     key = (c[:, 2] * nc + c[:, 1]) * nc + c[:, 0]
     perm = np.argsort(key, kind="stable")
+    if cell_mode:
+        scale = 4294967296.0 / L
+        side = L / nc
+        ux = np.rint(w[:, 0] * scale).astype(np.int64) & 0xFFFFFFFF
+        uc = np.rint((c[:, 0] + 0.5) * side * scale).astype(np.int64) & 0xFFFFFFFF
+        xkey = ((ux - uc) & 0xFFFFFFFF).astype(np.uint32).view(np.int32).astype(np.int64)
+        counts = np.bincount(key, minlength=nc ** 3)
+        xkey = np.where(counts[key] <= 256, xkey, 0)          # fuller cells keep their order
+        perm = np.lexsort((np.arange(len(key)), xkey, key))
     return key, perm
 
 
@@ -39,8 +50,10 @@ def test_keys_and_stable_order_bit_exact(n, L, rc, seed):
         ew.compute_async(dev(pos), dev(q), F, e, parts=PART_REAL)
         ew.status()
         # the grid is chosen for the particle count when the workspace is first sized
-        nc = ew.info()["cells_per_side"]
+        info = ew.info()
         key, perm = ew.cell_sort(n)
-    mkey, mperm = _model(pos, L, nc)
+    nc = info["cells_per_side"]
+    assert info["stencil"] > 0
+    mkey, mperm = _model(pos, L, nc, True)
     assert np.array_equal(key, mkey)
     assert np.array_equal(perm, mperm)

@@ -29,18 +29,60 @@ def cell_grid(L, rc, n):
 
 
 def sort_cells(pos, L, nc):
+    """Binning as the library does it in cell mode: stable sort by cell key, then every cell
+    of at most 256 particles ordered by the fixed-point x fraction relative to the cell
+    centre (k_rowsort).  Returns the sorted positions, cells, keys, x fractions and the
+    cell starts."""
     x = pos - L * np.floor(pos / L)
     x[x >= L] = 0.0
     c = np.minimum((x * (nc / L)).astype(np.int64), nc - 1)
     key = (c[:, 2] * nc + c[:, 1]) * nc + c[:, 0]
-    order = np.argsort(key, kind="stable")
+    scale = 4294967296.0 / L
+    ux = np.rint(x[:, 0] * scale).astype(np.int64) & 0xFFFFFFFF
+    uc = np.rint((c[:, 0] + 0.5) * (L / nc) * scale).astype(np.int64) & 0xFFFFFFFF
+    xkey = ((ux - uc) & 0xFFFFFFFF).astype(np.uint32).view(np.int32).astype(np.int64)
+    counts = np.bincount(key, minlength=nc ** 3)
+    xkey = np.where(counts[key] <= 256, xkey, 0)
+    order = np.lexsort((np.arange(len(key)), xkey, key))
     start = np.zeros(nc ** 3 + 1, dtype=np.int64)
     np.cumsum(np.bincount(key, minlength=nc ** 3), out=start[1:])
-    return x[order], c[order], key[order], start
+    return x[order], c[order], key[order], ux[order], start
 
 
-def target_bins(xs, c, L, rc, nc, w, i, dy, dz):
-    """Unwrapped bins [a0, a1] of target i in row (dy, dz), or None out of reach."""
+def xwin_allowed(L, rc, nc):
+    """The host's condition for the x windows (launch_real_t)."""
+    return rc * 1.00001 + L / nc < 0.5 * L * (1.0 - 1e-6)
+
+
+def first_within(d, lo, hi, R):
+    """First g in [lo, hi) with d[g] <= R (binary search, as the kernel)."""
+    while lo < hi:
+        mid = (lo + hi) >> 1
+        if d[mid] <= R:
+            hi = mid
+        else:
+            lo = mid + 1
+    return lo
+
+
+def window(idx, ux, u, R):
+    """The kernel's x-window cut of a target's candidates idx (global indices in union
+    order): two binary searches on the int32 x displacements u - ux[j]."""
+    if R is None or idx.size == 0:
+        return idx
+    d = ((u - ux[idx]) & 0xFFFFFFFF).astype(np.uint32).view(np.int32).astype(np.int64)
+    lo = first_within(d, 0, idx.size, R)
+    hi = first_within(d, lo, idx.size, -R - 1)
+    # the searches rely on the x order: they must keep exactly the candidates inside
+    keep = (d >= -R) & (d <= R)
+    assert np.array_equal(idx[lo:hi], idx[keep]), "candidates not in x order"
+    return idx[lo:hi]
+
+
+def target_row(xs, c, L, rc, nc, w, i, dy, dz, xwin):
+    """Unwrapped bins [a0, a1] of target i in row (dy, dz) and its x-window half-width R in
+    fixed-point units (None without windows), or None out of reach (the kernel's FP32
+    arithmetic)."""
     f32 = np.float32
     side = L / nc
     sidef, inv_side = f32(side), f32(1.0 / side)
@@ -57,10 +99,12 @@ def target_bins(xs, c, L, rc, nc, w, i, dy, dz):
     reach = f32(np.sqrt(f32(rc2m - d2)))
     b0 = int(np.floor(f32((xl - reach) * inv_side)))
     b1 = int(np.floor(f32((xl + reach) * inv_side)))
-    return cx + max(b0, -w), cx + min(b1, w)
+    a0, a1 = cx + max(b0, -w), cx + min(b1, w)
+    R = int(math.ceil(f32(reach * f32(4294967296.0 / L)))) + 1 if xwin else None
+    return a0, a1, R
 
 
-def union_check(xs, c, start, L, rc, nc, w, group):
+def union_check(xs, c, ux, start, L, rc, nc, w, group, xwin):
     """The staged union of a warp's targets in every row, as the kernel lays it out; returns
     per target the global indices it reads through the union."""
     f32 = np.float32
@@ -73,19 +117,19 @@ def union_check(xs, c, start, L, rc, nc, w, group):
             my = f32((abs(dy) - 1) * sidef) if dy else f32(0)
             if my * my + mz * mz >= rc2m:
                 continue
-            bins = {int(i): target_bins(xs, c, L, rc, nc, w, i, dy, dz) for i in group}
-            live = [b for b in bins.values() if b]
+            rows = {int(i): target_row(xs, c, L, rc, nc, w, i, dy, dz, xwin) for i in group}
+            live = [b for b in rows.values() if b]
             if not live:
                 continue
             A0, A1 = min(b[0] for b in live), max(b[1] for b in live)
-            cy, cz = c[group[0], 1], c[group[0], 2]
             # all targets of a warp may sit in different rows: the union uses each target's
             # own row; the kernel's warp shares one row only because every lane computes
             # the same (dy, dz) relative to its own cell, so check per target row
             for i in group:
                 i = int(i)
-                if not bins[i]:
+                if not rows[i]:
                     continue
+                a0, a1, R = rows[i]
                 ci = c[i]
                 base = (((ci[2] + dz) % nc) * nc + (ci[1] + dy) % nc) * nc
                 cs = start[base:base + nc + 1]
@@ -103,31 +147,29 @@ def union_check(xs, c, start, L, rc, nc, w, group):
                     if b < nc:
                         return lenA + cs[b] - sB
                     return lenA + lenB + cs[b - nc] - sC
-                o0, o1 = off(bins[i][0]), off(bins[i][1] + 1)
+                o0, o1 = off(a0), off(a1 + 1)
                 assert 0 <= o0 <= o1 <= lenA + lenB + lenC
+                idx = []
                 for q in range(o0, o1):
                     if q < lenA:
-                        got[i].append(sA + q)
+                        idx.append(sA + q)
                     elif q < lenA + lenB:
-                        got[i].append(sB + q - lenA)
+                        idx.append(sB + q - lenA)
                     else:
-                        got[i].append(sC + q - lenA - lenB)
+                        idx.append(sC + q - lenA - lenB)
+                got[i].extend(window(np.array(idx, dtype=np.int64), ux, int(ux[i]), R).tolist())
     return got
 
 
-def candidate_ranges(xs, c, start, L, rc, nc, w, targets):
-    """For each target: the list of (start, length) ranges of the kernel, as it computes
-    them (FP32 reach and bin arithmetic, wrapped rows, clamped bins)."""
+def candidate_ranges(xs, c, ux, start, L, rc, nc, w, targets, xwin):
+    """For each target: the candidate indices of every row, as the kernel computes them
+    (FP32 reach and bin arithmetic, wrapped rows, clamped bins, x windows)."""
     f32 = np.float32
-    side = L / nc
-    sidef, inv_side = f32(side), f32(1.0 / side)
+    sidef = f32(L / nc)
     rc2m = f32(f32(rc * rc) * (f32(1.0) + f32(1e-5)))
     out = []
     for i in targets:
         cx, cy, cz = c[i]
-        xl = f32(xs[i, 0] - cx * side)
-        yl = f32(xs[i, 1] - cy * side)
-        zl = f32(xs[i, 2] - cz * side)
         rr = []
         for dz in range(-w, w + 1):
             mz = f32((abs(dz) - 1) * sidef) if dz else f32(0)
@@ -135,40 +177,36 @@ def candidate_ranges(xs, c, start, L, rc, nc, w, targets):
                 my = f32((abs(dy) - 1) * sidef) if dy else f32(0)
                 if my * my + mz * mz >= rc2m:
                     continue
-                gy = f32(dy * sidef - yl) if dy > 0 else (f32(yl - (dy + 1) * sidef) if dy < 0 else f32(0))
-                gz = f32(dz * sidef - zl) if dz > 0 else (f32(zl - (dz + 1) * sidef) if dz < 0 else f32(0))
-                d2 = f32(gy * gy + gz * gz)
-                if not d2 < rc2m:
+                t = target_row(xs, c, L, rc, nc, w, i, dy, dz, xwin)
+                if t is None:
                     continue
-                reach = f32(np.sqrt(f32(rc2m - d2)))
-                b0 = int(np.floor(f32((xl - reach) * inv_side)))
-                b1 = int(np.floor(f32((xl + reach) * inv_side)))
-                b0, b1 = max(b0, -w), min(b1, w)
-                uy, uz = (cy + dy) % nc, (cz + dz) % nc
-                base = (uz * nc + uy) * nc
-                a0, a1 = cx + b0, cx + b1
+                a0, a1, R = t
+                base = (((cz + dz) % nc) * nc + (cy + dy) % nc) * nc
                 if a0 < 0:
-                    rr.append((start[base + a0 + nc], start[base + nc] - start[base + a0 + nc]))
-                    rr.append((start[base], start[base + a1 + 1] - start[base]))
+                    parts = [(start[base + a0 + nc], start[base + nc]), (start[base], start[base + a1 + 1])]
                 elif a1 >= nc:
-                    rr.append((start[base + a0], start[base + nc] - start[base + a0]))
-                    rr.append((start[base], start[base + a1 - nc + 1] - start[base]))
+                    parts = [(start[base + a0], start[base + nc]), (start[base], start[base + a1 - nc + 1])]
                 else:
-                    rr.append((start[base + a0], start[base + a1 + 1] - start[base + a0]))
+                    parts = [(start[base + a0], start[base + a1 + 1])]
+                idx = np.concatenate([np.arange(a, b) for a, b in parts])
+                rr.append(window(idx, ux, int(ux[i]), R))
         out.append(rr)
     return out
 
 
-def check(pos, L, rc, targets=None):
+def check(pos, L, rc, targets=None, xwin=None):
     n = len(pos)
     nc, w = cell_grid(L, rc, n)
     assert w >= 1
-    xs, c, key, start = sort_cells(pos, L, nc)
+    if xwin is None:
+        xwin = xwin_allowed(L, rc, nc)
+    xs, c, key, ux, start = sort_cells(pos, L, nc)
     if targets is None:
         targets = np.arange(n)
-    ranges = candidate_ranges(xs, c, start, L, rc, nc, w, targets)
+    ranges = candidate_ranges(xs, c, ux, start, L, rc, nc, w, targets, xwin)
+    ncand = 0
     for i, rr in zip(targets, ranges):
-        idx = np.concatenate([np.arange(s, s + m) for s, m in rr]) if rr else np.zeros(0, int)
+        idx = np.concatenate(rr) if rr else np.zeros(0, int)
         assert idx.size == 0 or (idx.min() >= 0 and idx.max() < n)
         assert np.unique(idx).size == idx.size, "a candidate visited twice"
         d = xs - xs[i]
@@ -177,6 +215,7 @@ def check(pos, L, rc, targets=None):
         partners = np.nonzero((r2 < rc * rc) & (np.arange(n) != i))[0]
         missing = np.setdiff1d(partners, idx)
         assert missing.size == 0, f"target {i}: partners {missing[:5]} not among the candidates"
+        ncand += idx.size
     # the staged union of a warp's tile (up to 8 consecutive sorted targets of one row of
     # cells, as k_row_tiles cuts them) gives each target exactly its ranges
     tg = 8
@@ -186,12 +225,12 @@ def check(pos, L, rc, targets=None):
         first = start[r * nc] + tg * ((g0 - start[r * nc]) // tg)
         group = np.arange(first, min(first + tg, start[(r + 1) * nc]))
         assert np.all(row_of[group] == r)
-        got = union_check(xs, c, start, L, rc, nc, w, group)
-        own = candidate_ranges(xs, c, start, L, rc, nc, w, group)
+        got = union_check(xs, c, ux, start, L, rc, nc, w, group, xwin)
+        own = candidate_ranges(xs, c, ux, start, L, rc, nc, w, group, xwin)
         for i, rr in zip(group, own):
-            idx = np.concatenate([np.arange(s_, s_ + m) for s_, m in rr]) if rr else np.zeros(0, int)
+            idx = np.concatenate(rr) if rr else np.zeros(0, int)
             assert sorted(got[int(i)]) == sorted(idx.tolist()), f"union layout of target {i}"
-    return nc, w
+    return nc, w, ncand / len(targets)
 
 
 def test_grid_rule_matches_the_library():
@@ -213,8 +252,12 @@ def test_every_partner_is_a_candidate_once(name, rc):
     pos, q, L = getattr(W, name)()
     rng = np.random.default_rng(3)
     targets = None if len(q) <= 4096 else np.sort(rng.choice(len(q), 3000, replace=False))
-    nc, w = check(pos, L, rc, targets)
+    nc, w, per_target = check(pos, L, rc, targets)
     assert w >= 2
+    # the x windows drop candidates: fewer per target than with whole cells
+    _, _, whole = check(pos, L, rc, targets[:300] if targets is not None else None, xwin=False)
+    _, _, cut = check(pos, L, rc, targets[:300] if targets is not None else None)
+    assert cut < whole
 
 
 def test_boundary_positions():
