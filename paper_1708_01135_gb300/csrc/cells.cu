@@ -11,8 +11,9 @@
 //      row histograms, a column scan over chunks, a scan over rows, and an in-order scatter
 //      per chunk;
 //   2. inside every row, by c_x: one block per row counts its cells, scans them (the cell
-//      offsets) and places the row's particles in the order level 1 left them; for the
-//      cell kernel, every cell is then ordered by x (fixed-point fraction, k_rowsort).
+//      offsets) and places the row's particles in the order level 1 left them; where the
+//      cell kernel cuts its ranges to x windows, every cell is then ordered by x
+//      (fixed-point fraction, k_rowsort).
 // Equal keys keep their input order, so the result is exactly determined by the input
 // (bit-exact integer work).
 #include <cuda_runtime.h>
@@ -254,8 +255,8 @@ constexpr int kXOrderMax = 256;
 // order): counts per cell, the cell offsets cell_start[r nc .. r nc + nc - 1], the in-order
 // placement of the row's particles by cell (warp 0), then the packing of the row's sorted
 // particles and, with tiles, the row's warp tiles (all threads).  One block per row.
-// With tiles (the cell kernel's layout) the particles of every cell are ordered by x before
-// they are packed: by the 32-bit fixed-point fraction that the packed record holds, taken
+// With xorder (the cell kernel's x windows, use_xwin) the particles of every cell are ordered
+// by x before they are packed: by the 32-bit fixed-point fraction that the packed record holds, taken
 // relative to the cell's centre (so a fraction that rounds to 2^32 next to x = L stays at
 // the end of the last cell), equal fractions in level-2 order.  The real-space kernel cuts
 // each target's range at its own x window with this order.  A cell of more than kXOrderMax
@@ -268,7 +269,7 @@ __global__ void k_rowsort(int nrows, int nc, int64_t n, const int *__restrict__ 
                           double4_32a *__restrict__ pg, double4_32a *__restrict__ pl64,
                           float4 *__restrict__ pl32, uint4 *__restrict__ pu, int ts,
                           const int *__restrict__ tile_off, int2 *__restrict__ tiles,
-                          int *__restrict__ unordered)
+                          int xorder, int *__restrict__ unordered)
 {
     __shared__ int off[kMaxCellsPerSide];
     const int r = blockIdx.x;
@@ -312,7 +313,7 @@ __global__ void k_rowsort(int nrows, int nc, int64_t n, const int *__restrict__ 
     }
     // (the block's own global writes are visible to the block after the barrier)
     __syncthreads();
-    if (tiles) {
+    if (xorder) {
         // x order inside every cell; perm1 and key1 of the row (read only by this block, and
         // no longer needed) hold the level-2 order and the sort keys
         const double scale = 4294967296.0 / L;
@@ -390,7 +391,8 @@ cudaError_t launch_binning(Plan &p, int64_t n, const double *pos, const double *
                                      ws.key_sorted, ws.cell_start, pos, q, p.L, p.cell_side,
                                      ws.pg, (need64 && p.w == 0) ? ws.pl64 : nullptr,
                                      (!need64 && p.w == 0) ? ws.pl32 : nullptr, ws.pu, ts,
-                                     ws.tile_off, p.w > 0 ? ws.tiles : nullptr, ws.unordered);
+                                     ws.tile_off, p.w > 0 ? ws.tiles : nullptr, use_xwin(p),
+                                     ws.unordered);
     p.launches += 5;
     return cudaGetLastError();
 }

@@ -8,15 +8,15 @@
 // GPU design (templated on FP64 and FP32 arithmetic), cell mode:
 //   * The box is cut into nc^3 cubic cells of side s ~ max(1.33 rho^-1/3, r_c / 5), sorted
 //     by cell key (c_z nc + c_y) nc + c_x, so that every row of cells along x (fixed c_y,
-//     c_z) is a contiguous range of the sorted arrays; inside a cell the particles are in x
-//     order (binning, k_rowsort).
+//     c_z) is a contiguous range of the sorted arrays; where the rows are long (w >= 4) the
+//     particles of a cell are in x order as well (binning, k_rowsort).
 //   * A warp owns up to 32 consecutive sorted targets of one row of cells, one lane each.
 //     It visits the rows (c_y + dy, c_z + dz), |dy|, |dz| <= w, in a fixed order.  For each
 //     row every target takes its own reach: the distance d from its (y, z) to the row's
 //     square gives the x half-width sqrt(r_c^2 - d^2), and its candidates are the particles
 //     of the row with x in [x - reach, x + reach]: the cells overlapping that window (one
-//     or, where the row wraps, two contiguous ranges), cut to the window by two binary
-//     searches on the x order.  The warp stages the union of its targets' ranges in shared
+//     or, where the row wraps, two contiguous ranges), with x-ordered cells cut to the
+//     window by two binary searches.  The warp stages the union of its targets' ranges in shared
 //     memory (bulk copies on an mbarrier, double-buffered) and every lane searches and
 //     walks its own range; the warp runs as many steps as its longest range needs.  This
 //     keeps the candidates close to the cutoff sphere of each target (about 1.3 to 1.6 per
@@ -995,8 +995,7 @@ k_real_rows(const typename RowRec<T>::type *__restrict__ pr, const double4_32a *
     wk.rn2m = kNear ? NK.rn2m : 0.0f;
     wk.valid = valid;
     wk.cell_start = cell_start;
-    // x windows when the host allows them (reach + side < L/2) and binning ordered every
-    // cell by x (FP32 records only)
+    // x windows when the host chose them (use_xwin) and binning ordered every cell by x
     const bool xw = kFP32 && xwin && *unordered == 0;
     wk.rowctr = 0;
     wk.started = false;
@@ -1384,9 +1383,7 @@ cudaError_t launch_real_t(Plan &p, int64_t n, const typename Vec4<T>::type *pl, 
         NK.c_h = (float)cs;
         NK.c_l = (float)(cs - (double)NK.c_h);
         NK.rn2m = (float)(rnear * rnear) * (1.0f + 1e-5f);
-        // x windows (FP32 records): every displacement a window test takes must stay below
-        // L/2 in magnitude, i.e. reach (r_c with the range margin) + one cell side < L/2
-        const int xwin = sizeof(T) == 4 && p.rc * 1.00001 + p.cell_side < 0.5 * p.L * (1.0 - 1e-6);
+        const int xwin = sizeof(T) == 4 && use_xwin(p);
         kern<<<(unsigned)((groups * split + kWarps - 1) / kWarps), kWarps * 32, 0, st>>>(
             pr, ws.pg, ws.key_sorted, ws.cell_start, ws.tiles, ws.tile_off + p.nc * p.nc,
             (int)n, p.nc, p.w, p.cell_side, p.L, rc2, beta, tbr, K, NK, 1.0 / S, split, xwin,

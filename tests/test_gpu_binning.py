@@ -1,8 +1,9 @@
 """Bit-exact check of the integer binning (steps a1-a2) against a CPU model of its
 definition: wrap x - L floor(x / L) (a result equal to L maps to 0), cell index
 min(floor(x nc / L), nc - 1), key (c_z nc + c_y) nc + c_x, and a stable sort by key (ties in
-input order); in cell mode every cell of at most 256 particles is then ordered by the
-fixed-point x fraction round(x 2^32 / L) mod 2^32 taken relative to the cell centre's
+input order); where the real-space kernel uses x windows (FP32 records, stencil half-width
+w >= 4, r_c + one cell side < L/2) every cell of at most 256 particles is then ordered by
+the fixed-point x fraction round(x 2^32 / L) mod 2^32 taken relative to the cell centre's
 fraction (as a signed 32-bit difference), ties in input order."""
 import numpy as np
 import pytest
@@ -15,13 +16,13 @@ from paper_1708_01135_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _model(pos, L, nc, cell_mode):
+def _model(pos, L, nc, xorder):
     w = pos - L * np.floor(pos / L)
     w[w >= L] = 0.0
     c = np.minimum((w * (nc / L)).astype(np.int64), nc - 1)
     key = (c[:, 2] * nc + c[:, 1]) * nc + c[:, 0]
     perm = np.argsort(key, kind="stable")
-    if cell_mode:
+    if xorder:
         scale = 4294967296.0 / L
         side = L / nc
         ux = np.rint(w[:, 0] * scale).astype(np.int64) & 0xFFFFFFFF
@@ -33,8 +34,11 @@ def _model(pos, L, nc, cell_mode):
     return key, perm
 
 
-@pytest.mark.parametrize("n,L,rc,seed", [(5000, 17.1, 4.0, 3), (777, 9.5, 3.1, 4), (40000, 34.2, 4.0, 9)])
-def test_keys_and_stable_order_bit_exact(n, L, rc, seed):
+@pytest.mark.parametrize("n,L,rc,seed,precision", [
+    (5000, 17.1, 4.0, 3, "fp64"), (777, 9.5, 3.1, 4, "fp64"), (40000, 34.2, 4.0, 9, "fp64"),
+    (40000, 34.2, 4.0, 10, "mixed"),                         # w = 3: no x order
+    (5000, 17.1, 6.0, 5, "mixed"), (40000, 34.2, 6.5, 11, "mixed")])   # w = 5: x order
+def test_keys_and_stable_order_bit_exact(n, L, rc, seed, precision):
     need_gpu()
     import torch
     rng = np.random.default_rng(seed)
@@ -44,7 +48,7 @@ def test_keys_and_stable_order_bit_exact(n, L, rc, seed):
     q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
     if n % 2:
         q[-1] = 0.0
-    with Ewald(L, 1.0, rc, 4, "fp64") as ew:
+    with Ewald(L, 1.0, rc, 4, precision) as ew:
         F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         e = torch.empty(4, dtype=torch.float64, device="cuda")
         ew.compute_async(dev(pos), dev(q), F, e, parts=PART_REAL)
@@ -52,8 +56,10 @@ def test_keys_and_stable_order_bit_exact(n, L, rc, seed):
         # the grid is chosen for the particle count when the workspace is first sized
         info = ew.info()
         key, perm = ew.cell_sort(n)
-    nc = info["cells_per_side"]
-    assert info["stencil"] > 0
-    mkey, mperm = _model(pos, L, nc, True)
+    nc, w = info["cells_per_side"], info["stencil"]
+    assert w > 0
+    xorder = precision != "fp64" and w >= 4 and rc * 1.00001 + L / nc < 0.5 * L * (1.0 - 1e-6)
+    assert xorder == (rc > 5.0)
+    mkey, mperm = _model(pos, L, nc, xorder)
     assert np.array_equal(key, mkey)
     assert np.array_equal(perm, mperm)

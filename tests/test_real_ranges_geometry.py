@@ -49,9 +49,9 @@ def sort_cells(pos, L, nc):
     return x[order], c[order], key[order], ux[order], start
 
 
-def xwin_allowed(L, rc, nc):
-    """The host's condition for the x windows (launch_real_t)."""
-    return rc * 1.00001 + L / nc < 0.5 * L * (1.0 - 1e-6)
+def xwin_allowed(L, rc, nc, w):
+    """The host's condition for the x windows (use_xwin, FP32 records)."""
+    return w >= 4 and rc * 1.00001 + L / nc < 0.5 * L * (1.0 - 1e-6)
 
 
 def first_within(d, lo, hi, R):
@@ -199,7 +199,7 @@ def check(pos, L, rc, targets=None, xwin=None):
     nc, w = cell_grid(L, rc, n)
     assert w >= 1
     if xwin is None:
-        xwin = xwin_allowed(L, rc, nc)
+        xwin = xwin_allowed(L, rc, nc, w)
     xs, c, key, ux, start = sort_cells(pos, L, nc)
     if targets is None:
         targets = np.arange(n)
@@ -254,9 +254,11 @@ def test_every_partner_is_a_candidate_once(name, rc):
     targets = None if len(q) <= 4096 else np.sort(rng.choice(len(q), 3000, replace=False))
     nc, w, per_target = check(pos, L, rc, targets)
     assert w >= 2
-    # the x windows drop candidates: fewer per target than with whole cells
-    _, _, whole = check(pos, L, rc, targets[:300] if targets is not None else None, xwin=False)
-    _, _, cut = check(pos, L, rc, targets[:300] if targets is not None else None)
+    # the x windows (valid wherever reach + side < L/2; the library takes them from w >= 4)
+    # drop candidates: fewer per target than with whole cells
+    sub = targets[:300] if targets is not None else None
+    _, _, whole = check(pos, L, rc, sub, xwin=False)
+    _, _, cut = check(pos, L, rc, sub, xwin=True)
     assert cut < whole
 
 
@@ -273,9 +275,11 @@ def test_boundary_positions():
     pos[240:260] = -1e-300
     for rc in (2.4, 3.0, 3.9):
         check(pos, L, rc)
+        check(pos, L, rc, xwin=True)
 
 
 def test_large_system_sample():
     pos, q, L = W.rocksalt_262144()
     rng = np.random.default_rng(11)
-    check(pos, L, 6.8, np.sort(rng.choice(len(q), 400, replace=False)))
+    nc, w, _ = check(pos, L, 6.8, np.sort(rng.choice(len(q), 400, replace=False)))
+    assert xwin_allowed(L, 6.8, nc, w)          # the library's windows are on here
