@@ -1,0 +1,69 @@
+"""The x windows of the real-space cell kernel against the FP64 oracle, element by element.
+
+Where the stencil half-width is 4 or more (FP32 records), binning orders every cell by x and
+the kernel cuts each target's candidates in a row to [x - reach, x + reach] by binary
+searches of the staged records.  A wrong window drops pairs near the cutoff, so these cases
+use weak screening (beta r_c ~ 1.5): a unit-charge pair at r_c then carries a force above
+twice the per-particle bound of the comparison.  The lattice case puts whole planes of ions just
+below cell faces and one plane just below x = L, where the fixed-point fraction rounds to
+2^32 and wraps to 0 while the ion stays in the last cell; every plane holds many equal x
+values (ties of the x order).  The real-space sum is Eq. 4 (Section 3.1.1).
+"""
+import numpy as np
+import pytest
+
+from gpu_common import LOCAL_FACTOR, dev, need_gpu, assert_close
+
+import oracle
+from paper_1708_01135_gb300 import Ewald, PART_REAL
+from paper_1708_01135_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5       # the mixed path's force tolerance; FP32 pair arithmetic gives ~1e-7 here
+
+
+def _random():
+    pos, q, L = W.random_neutral(20000, density=1.0, hard_core=0.8, seed=41,
+                                 mix=((1.0, 0.4), (2.0, 0.1)))
+    return pos, q, L, 0.23, 6.5
+
+
+def _lattice():
+    # 32^3 ions on the integer lattice of a box of side 32: cells of side 4/3, so x = 0, 4,
+    # 8, ... are cell faces; shifted down by 4e-15, every plane sits just below its face and
+    # the plane x = 0 lands at 32 - 4e-15 (last cell, fixed-point fraction 2^32 -> 0).  y and
+    # z are jittered so that the forces do not vanish by symmetry.
+    pos, q, L = W.rocksalt(32, a=1.0, jitter=0.0)
+    rng = np.random.default_rng(43)
+    pos = pos.copy()
+    pos[:, 0] -= 4e-15
+    pos[:, 1:] += rng.normal(0.0, 0.05, size=(len(q), 2))
+    return pos, q, L, 0.25, 6.5
+
+
+@pytest.mark.parametrize("make", [_random, _lattice], ids=["random", "lattice"])
+def test_x_windows_match_the_oracle(make):
+    need_gpu()
+    import torch
+    pos, q, L, beta, rc = make()
+    n = len(q)
+    e_ref, F_ref, phi_ref = oracle.real_cells(pos, q, L, beta, rc)
+    F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    e = torch.empty(4, dtype=torch.float64, device="cuda")
+    phi = torch.empty(n, dtype=torch.float64, device="cuda")
+    with Ewald(L, beta, rc, 8, "mixed") as ew:
+        ew.compute_phi_async(dev(pos), dev(q), F, phi, e, parts=PART_REAL)
+        assert ew.status() == 0
+        info = ew.info()
+    nc, w = info["cells_per_side"], info["stencil"]
+    # the windows are on: w >= 4 and r_c + one cell side < L/2
+    assert w >= 4 and rc * 1.00001 + L / nc < 0.5 * L
+    F, phi, e = F.cpu().numpy(), phi.cpu().numpy(), e.cpu().numpy()
+    assert_close(F, F_ref, TOL)
+    assert_close(phi, phi_ref, TOL)
+    assert abs(e[0] - e_ref) <= TOL * 0.5 * np.abs(q * phi_ref).sum()
+    # a unit-charge pair at the cutoff is above twice the per-particle bound, so a dropped
+    # one would show
+    fc = (1.0 / rc ** 2) * (np.exp(-(beta * rc) ** 2) * 2 * beta * rc / np.sqrt(np.pi))
+    assert fc > 2 * LOCAL_FACTOR * TOL * np.sqrt((F_ref ** 2).sum() / n)
