@@ -12,7 +12,7 @@ values (ties of the x order).  The real-space sum is Eq. 4 (Section 3.1.1).
 import numpy as np
 import pytest
 
-from gpu_common import LOCAL_FACTOR, dev, need_gpu, assert_close
+from gpu_common import LOCAL_FACTOR, dev, need_gpu
 
 import oracle
 from paper_1708_01135_gb300 import Ewald, PART_REAL
@@ -21,6 +21,22 @@ from paper_1708_01135_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5       # the mixed path's force tolerance; FP32 pair arithmetic gives ~1e-7 here
+# The kernel tests r^2 < r_c^2 on FP32 values (relative error below 2e-7 in r^2), the oracle
+# in FP64, so a pair within a relative 3e-7 of r_c may be counted by one and not the other;
+# with weak screening such a pair is as large as the bound.  Each particle may therefore
+# differ by the oracle's sum over its pairs in that band, and by nothing more.
+BAND = 3e-7
+
+
+def _check(a, ref, band, tol):
+    """assert_close with a per-particle allowance |band_i| (the oracle's pairs in the cutoff
+    band): the excess error max(0, |a_i - ref_i| - |band_i|) must meet the RMS and the
+    per-particle bounds."""
+    a, ref, band = (np.asarray(x, dtype=np.float64).reshape(len(x), -1) for x in (a, ref, band))
+    ex = np.maximum(np.sqrt(((a - ref) ** 2).sum(axis=1)) - np.sqrt((band ** 2).sum(axis=1)), 0.0)
+    scale = np.sqrt((ref ** 2).sum(axis=1).mean())
+    assert np.sqrt((ex ** 2).mean()) < tol * scale, np.sqrt((ex ** 2).mean()) / scale
+    assert ex.max() <= LOCAL_FACTOR * tol * scale, ex.max() / scale
 
 
 def _random():
@@ -49,6 +65,8 @@ def test_x_windows_match_the_oracle(make):
     pos, q, L, beta, rc = make()
     n = len(q)
     e_ref, F_ref, phi_ref = oracle.real_cells(pos, q, L, beta, rc)
+    e_lo, F_lo, phi_lo = oracle.real_cells(pos, q, L, beta, rc * (1.0 - BAND))
+    e_hi, F_hi, phi_hi = oracle.real_cells(pos, q, L, beta, rc * (1.0 + BAND))
     F = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     e = torch.empty(4, dtype=torch.float64, device="cuda")
     phi = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -60,9 +78,11 @@ def test_x_windows_match_the_oracle(make):
     # the windows are on: w >= 4 and r_c + one cell side < L/2
     assert w >= 4 and rc * 1.00001 + L / nc < 0.5 * L
     F, phi, e = F.cpu().numpy(), phi.cpu().numpy(), e.cpu().numpy()
-    assert_close(F, F_ref, TOL)
-    assert_close(phi, phi_ref, TOL)
-    assert abs(e[0] - e_ref) <= TOL * 0.5 * np.abs(q * phi_ref).sum()
+    _check(F, F_ref, F_hi - F_lo, TOL)
+    _check(phi, phi_ref, phi_hi - phi_lo, TOL)
+    assert abs(e[0] - e_ref) <= TOL * 0.5 * np.abs(q * phi_ref).sum() + abs(e_hi - e_lo)
+    # the allowance covers few particles
+    assert (np.abs(F_hi - F_lo).sum(axis=1) > 0).sum() < 0.01 * n
     # a unit-charge pair at the cutoff is above twice the per-particle bound, so a dropped
     # one would show
     fc = (1.0 / rc ** 2) * (np.exp(-(beta * rc) ** 2) * 2 * beta * rc / np.sqrt(np.pi))
