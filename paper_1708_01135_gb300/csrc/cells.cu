@@ -256,11 +256,12 @@ constexpr int kXOrderMax = 256;
 // placement of the row's particles by cell (warp 0), then the packing of the row's sorted
 // particles and, with tiles, the row's warp tiles (all threads).  One block per row.
 // With xorder (the cell kernel's x windows, use_xwin) the particles of every cell are ordered
-// by x before they are packed: by the 32-bit fixed-point fraction that the packed record holds, taken
-// relative to the cell's centre (so a fraction that rounds to 2^32 next to x = L stays at
-// the end of the last cell), equal fractions in level-2 order.  The real-space kernel cuts
-// each target's range at its own x window with this order.  A cell of more than kXOrderMax
-// particles keeps its level-2 order and sets *unordered, which turns the cut off.
+// by x before they are packed: by the 32-bit fixed-point fraction that the packed record
+// holds, taken relative to the cell's centre (so a fraction that rounds to 2^32 next to
+// x = L stays at the end of the last cell), equal fractions in level-2 order.  The
+// real-space kernel cuts each target's range at its own x window with this order.  A cell
+// of more than kXOrderMax particles keeps its level-2 order and sets *unordered, which
+// turns the cut off.
 __global__ void k_rowsort(int nrows, int nc, int64_t n, const int *__restrict__ row_start,
                           int *__restrict__ perm1, int *__restrict__ key1,
                           int *__restrict__ perm, int *__restrict__ key_sorted,
