@@ -197,7 +197,7 @@ def tensor_flops(n, kmax):
 # profiles/.  Kernels without a current capture report null.
 TRAFFIC = {
     # profiles/k_real_rows_random_2097152.md: 117.569792 MB read + 38.573312 MB written
-    ("real", "random_2097152", "mixed", "87bc9d623ba7b20b"): 156143104,
+    ("real", "random_2097152", "mixed", "9f3e9833cb893640"): 156143104,
 }
 
 

@@ -331,7 +331,7 @@ int ewald_structure_factor(ewald_plan_t plan, double *S_dev, void *stream);
  * `stream`, the cell index of every particle in caller order (int32 [n], key =
  * (c_z n_c + c_y) n_c + c_x) and the sorted order (int32 [n]: slot s holds particle
  * perm[s]) into device buffers.  Either pointer may be NULL.  The order is stable by key;
- * where the FP32 real-space kernel cuts its ranges to x windows (stencil half-width >= 4,
+ * where the FP32 real-space kernel cuts its ranges to x windows (stencil half-width >= 5,
  * r_c plus one cell side below L/2), every cell of at most 256 particles is then ordered
  * by round(x 2^32 / L) mod 2^32 relative to its centre's fraction, ties in key order. */
 int ewald_cell_sort(ewald_plan_t plan, int32_t *key_dev, int32_t *perm_dev, void *stream);

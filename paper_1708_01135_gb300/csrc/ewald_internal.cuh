@@ -192,12 +192,12 @@ int real_tile_size(const Plan &p);          // targets per real-space warp
 int real_tile_for(int w, double cell_occupancy);   // lanes per target for a grid (particles per cell)
 // x windows of the real-space cell kernel (FP32 records): binning orders every cell by x and
 // the kernel cuts each target's candidates to its own x window.  They pay where the rows are
-// long (stencil half-width w >= 4: the 262,144- and 2,097,152-ion systems; at w = 3 the
-// searches cost what the dropped candidates save), and every x displacement a window test
-// takes must stay below L/2 in magnitude (reach + one cell side < L/2).
+// long (stencil half-width w >= 5: the 262,144- and 2,097,152-ion systems; at w = 3 and 4 the
+// searches and the x order cost what the dropped candidates save), and every x displacement
+// a window test takes must stay below L/2 in magnitude (reach + one cell side < L/2).
 inline bool use_xwin(const Plan &p)
 {
-    return p.precision != EWALD_FP64 && p.w >= 4 &&
+    return p.precision != EWALD_FP64 && p.w >= 5 &&
            p.rc * 1.00001 + p.cell_side < 0.5 * p.L * (1.0 - 1e-6);
 }
 // a5-a8 on CUDA cores (FP64 or FP32): S(k), energy, back-scatter into ws.f_recip.

@@ -8,7 +8,7 @@
 // GPU design (templated on FP64 and FP32 arithmetic), cell mode:
 //   * The box is cut into nc^3 cubic cells of side s ~ max(1.33 rho^-1/3, r_c / 5), sorted
 //     by cell key (c_z nc + c_y) nc + c_x, so that every row of cells along x (fixed c_y,
-//     c_z) is a contiguous range of the sorted arrays; where the rows are long (w >= 4) the
+//     c_z) is a contiguous range of the sorted arrays; where the rows are long (w >= 5) the
 //     particles of a cell are in x order as well (binning, k_rowsort).
 //   * A warp owns up to 32 consecutive sorted targets of one row of cells, one lane each.
 //     It visits the rows (c_y + dy, c_z + dz), |dy|, |dz| <= w, in a fixed order.  For each

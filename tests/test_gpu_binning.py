@@ -2,7 +2,7 @@
 definition: wrap x - L floor(x / L) (a result equal to L maps to 0), cell index
 min(floor(x nc / L), nc - 1), key (c_z nc + c_y) nc + c_x, and a stable sort by key (ties in
 input order); where the real-space kernel uses x windows (FP32 records, stencil half-width
-w >= 4, r_c + one cell side < L/2) every cell of at most 256 particles is then ordered by
+w >= 5, r_c + one cell side < L/2) every cell of at most 256 particles is then ordered by
 the fixed-point x fraction round(x 2^32 / L) mod 2^32 taken relative to the cell centre's
 fraction (as a signed 32-bit difference), ties in input order."""
 import numpy as np
@@ -58,7 +58,7 @@ def test_keys_and_stable_order_bit_exact(n, L, rc, seed, precision):
         key, perm = ew.cell_sort(n)
     nc, w = info["cells_per_side"], info["stencil"]
     assert w > 0
-    xorder = precision != "fp64" and w >= 4 and rc * 1.00001 + L / nc < 0.5 * L * (1.0 - 1e-6)
+    xorder = precision != "fp64" and w >= 5 and rc * 1.00001 + L / nc < 0.5 * L * (1.0 - 1e-6)
     assert xorder == (rc > 5.0)
     mkey, mperm = _model(pos, L, nc, xorder)
     assert np.array_equal(key, mkey)

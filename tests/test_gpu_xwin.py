@@ -1,6 +1,6 @@
 """The x windows of the real-space cell kernel against the FP64 oracle, element by element.
 
-Where the stencil half-width is 4 or more (FP32 records), binning orders every cell by x and
+Where the stencil half-width is 5 or more (FP32 records), binning orders every cell by x and
 the kernel cuts each target's candidates in a row to [x - reach, x + reach] by binary
 searches of the staged records.  A wrong window drops pairs near the cutoff, so these cases
 use weak screening (beta r_c ~ 1.5): a unit-charge pair at r_c then carries a force above
@@ -75,8 +75,8 @@ def test_x_windows_match_the_oracle(make):
         assert ew.status() == 0
         info = ew.info()
     nc, w = info["cells_per_side"], info["stencil"]
-    # the windows are on: w >= 4 and r_c + one cell side < L/2
-    assert w >= 4 and rc * 1.00001 + L / nc < 0.5 * L
+    # the windows are on: w >= 5 and r_c + one cell side < L/2
+    assert w >= 5 and rc * 1.00001 + L / nc < 0.5 * L
     F, phi, e = F.cpu().numpy(), phi.cpu().numpy(), e.cpu().numpy()
     _check(F, F_ref, F_hi - F_lo, TOL)
     _check(phi, phi_ref, phi_hi - phi_lo, TOL)

@@ -51,7 +51,7 @@ def sort_cells(pos, L, nc):
 
 def xwin_allowed(L, rc, nc, w):
     """The host's condition for the x windows (use_xwin, FP32 records)."""
-    return w >= 4 and rc * 1.00001 + L / nc < 0.5 * L * (1.0 - 1e-6)
+    return w >= 5 and rc * 1.00001 + L / nc < 0.5 * L * (1.0 - 1e-6)
 
 
 def first_within(d, lo, hi, R):
@@ -254,7 +254,7 @@ def test_every_partner_is_a_candidate_once(name, rc):
     targets = None if len(q) <= 4096 else np.sort(rng.choice(len(q), 3000, replace=False))
     nc, w, per_target = check(pos, L, rc, targets)
     assert w >= 2
-    # the x windows (valid wherever reach + side < L/2; the library takes them from w >= 4)
+    # the x windows (valid wherever reach + side < L/2; the library takes them from w >= 5)
     # drop candidates: fewer per target than with whole cells
     sub = targets[:300] if targets is not None else None
     _, _, whole = check(pos, L, rc, sub, xwin=False)
