@@ -194,10 +194,14 @@ def tensor_flops(n, kmax):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel from an
 # ncu capture of the same workload, valid while that kernel's source file is unchanged (its
 # sha256 prefix is part of the key); the capture each figure comes from is named in
-# profiles/.  Kernels without a current capture report null.
+# profiles/.  Kernels without a current capture, and SPME runs (whose real-space kernel runs
+# at another cutoff), report null.
 TRAFFIC = {
     # profiles/k_real_rows_random_2097152.md: 117.569792 MB read + 38.573312 MB written
     ("real", "random_2097152", "mixed", "9f3e9833cb893640"): 156143104,
+    # profiles/k_real_rows_rocksalt_262144_near_df.md (double-float near pairs, the crystal
+    # line's kernel): 14.301696 MB read + 0.612864 MB written
+    ("real", "rocksalt_262144", "mixed", "9f3e9833cb893640"): 14914560,
 }
 
 
@@ -802,7 +806,7 @@ def kernel_rooflines(n, L, rc, kmax, precision, spme, times, pk, pk_kind, alu_pe
         r = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak,
              "unit": "TFLOP/s", "frac": achieved / peak, "ms": ms, "work": work,
              "flop_per_launch": flop, "peak_kind": kind,
-             "traffic": kernel_traffic(key, workload, precision)}
+             "traffic": None if spme else kernel_traffic(key, workload, precision)}
         akey = {"real": "real_kernel", "forward": "recip_forward", "back": "backscatter_kernel"}[key]
         ms_a = (alone or {}).get(akey)
         if ms_a and ms_a > 0:
